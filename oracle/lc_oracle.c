@@ -1,0 +1,204 @@
+/*
+ * lc_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, direct O(n^2) CPU implementation of the Legendre<->Chebyshev
+ * connection maps of Mortensen, "A faster multipole Legendre-Chebyshev
+ * transform" (arXiv:2411.00033).  It is the oracle that the GPU library is
+ * checked against.  It shares no code with the GPU library and may only be
+ * used by the tests, by the smoke check and by the CPU-baseline leg of the
+ * benchmark; nothing on the product path calls it.
+ *
+ * What it computes (the plain definitions, no blocking or approximation):
+ *   L2C:          z = C^{-1} A f             (Sec. 1, eq:directmv)
+ *   C2L:          z = (A^{-1} C) f           (Sec. 1, eq:directmv), with the
+ *                 entries of A^{-1} C taken from the closed form L(x,y) of
+ *                 Sec. 3.3 (eq:Lxymod) and entry (0,0) = 1.
+ *   L2C adjoint:  g = A^T C^{-1} r
+ *   C2L adjoint:  g = (A^{-1} C)^T r
+ * where a_ij = Lambda((j-i)/2) Lambda((j+i)/2) for j >= i, j-i even
+ * (eq:aij / eq:hik), Lambda(x) = Gamma(x+1/2)/Gamma(x+1) (eq:Lambda), and
+ * C = diag(c_i pi/2), c_0 = 2, c_i = 1 (Sec. 1).
+ *
+ * Precision: every entry and every sum is carried in double-double
+ * (error-free TwoSum / TwoProd with fma) and rounded once to double at the
+ * end, so each output is within about one ulp of the exact value.  The
+ * lambda table is built by the integer recursion Lambda(0) = sqrt(pi),
+ * Lambda(k) = Lambda(k-1) (k - 1/2)/k (eq:Lambdaint) in double-double; this
+ * is deliberately a different route from the tau series that the GPU plan
+ * uses (eq:tau).
+ *
+ * Rows are independent; with OpenMP available they are spread over threads.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct { double hi, lo; } dd;
+
+static inline dd two_sum(double a, double b) {
+  double s = a + b;
+  double bb = s - a;
+  double e = (a - (s - bb)) + (b - bb);
+  dd r = {s, e};
+  return r;
+}
+static inline dd quick_two_sum(double a, double b) {
+  double s = a + b;
+  dd r = {s, b - (s - a)};
+  return r;
+}
+static inline dd two_prod(double a, double b) {
+  double p = a * b;
+  dd r = {p, fma(a, b, -p)};
+  return r;
+}
+static inline dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  dd t = two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return quick_two_sum(s.hi, s.lo);
+}
+static inline dd dd_mul(dd a, dd b) {
+  dd p = two_prod(a.hi, b.hi);
+  p.lo += a.hi * b.lo + a.lo * b.hi;
+  return quick_two_sum(p.hi, p.lo);
+}
+static inline dd dd_mul_d(dd a, double b) {
+  dd p = two_prod(a.hi, b);
+  p.lo += a.lo * b;
+  return quick_two_sum(p.hi, p.lo);
+}
+static inline dd dd_div(dd a, dd b) {
+  /* long division: q1 = a/b, r = a - q1 b, q2 = r/b, ... */
+  double q1 = a.hi / b.hi;
+  dd r = dd_add(a, dd_mul_d(b, -q1));
+  double q2 = r.hi / b.hi;
+  r = dd_add(r, dd_mul_d(b, -q2));
+  double q3 = r.hi / b.hi;
+  dd q = quick_two_sum(q1, q2);
+  return dd_add(q, (dd){q3, 0.0});
+}
+static inline dd dd_from(double a) { dd r = {a, 0.0}; return r; }
+static inline double dd_to(dd a) { return a.hi + a.lo; }
+
+/* sqrt(pi) = Gamma(1/2) = Lambda(0) (eq:Lambdaint) and pi, as double-doubles:
+ * hi = RN(x), lo = RN(x - hi), from a 50-digit evaluation. */
+static const dd SQRT_PI_DD = {1.772453850905516, -7.666586499825799e-17};
+static const dd PI_DD = {3.141592653589793, 1.2246467991473532e-16};
+
+/* Lambda(k) for k < n as double-double (eq:Lambdaint recursion). */
+static void lambda_table(int64_t n, dd* lam) {
+  if (n <= 0) return;
+  lam[0] = SQRT_PI_DD;
+  for (int64_t k = 1; k < n; ++k) {
+    /* (k - 1/2)/k = (2k - 1)/(2k): both exact doubles for k < 2^51. */
+    dd num = dd_mul_d(lam[k - 1], (double)(2 * k - 1));
+    lam[k] = dd_div(num, dd_from((double)(2 * k)));
+  }
+}
+
+/* Entry (i, j) of C^{-1} A in double-double, 0 <= i, j < n (no bounds check
+ * beyond j >= i and j - i even). */
+static dd l2c_entry(const dd* lam, int64_t i, int64_t j) {
+  if (j < i || ((j - i) & 1)) return dd_from(0.0);
+  int64_t k = (j - i) / 2;
+  dd a = dd_mul(lam[k], lam[i + k]);            /* a_ij, eq:hik */
+  /* C^{-1}: 1/pi for row 0, 2/pi otherwise */
+  dd cinv = dd_div(dd_from(i == 0 ? 1.0 : 2.0), PI_DD);
+  return dd_mul(a, cinv);
+}
+
+/* Entry (i, j) of A^{-1} C from L(x, y) (eq:Lxymod):
+ *   L(x,y) = 2(x+1/2) y / ((x+y)(x+y+1)(x-y+1)) * Lambda((y-x)/2)/Lambda((x+y)/2)
+ * with x = i, y = j = i + 2k, and the (0,0) entry equal to 1. */
+static dd c2l_entry(const dd* lam, int64_t i, int64_t j) {
+  if (j < i || ((j - i) & 1)) return dd_from(0.0);
+  if (i == 0 && j == 0) return dd_from(1.0);
+  int64_t k = (j - i) / 2;
+  dd num = dd_mul(dd_from((double)(2 * i + 1)), dd_from((double)j));   /* 2(x+1/2) y */
+  dd den = dd_mul(dd_from((double)(i + j)), dd_from((double)(i + j + 1)));
+  den = dd_mul(den, dd_from((double)(i - j + 1)));                      /* (x+y)(x+y+1)(x-y+1) */
+  dd ratio = dd_div(lam[k], lam[i + k]);                                 /* Lambda((y-x)/2)/Lambda((x+y)/2) */
+  return dd_mul(dd_div(num, den), ratio);
+}
+
+static dd entry(int direction, const dd* lam, int64_t i, int64_t j) {
+  return direction == 0 ? l2c_entry(lam, i, j) : c2l_entry(lam, i, j);
+}
+
+/* ---------------------------------------------------------------- API -- */
+
+/* Lambda(k), k < n, rounded to double (hi) plus the double-double tail. */
+int lco_lambda(int64_t n, double* hi, double* lo) {
+  if (n < 0 || !hi) return 1;
+  dd* lam = (dd*)malloc(sizeof(dd) * (size_t)(n > 0 ? n : 1));
+  if (!lam) return 2;
+  lambda_table(n, lam);
+  for (int64_t k = 0; k < n; ++k) {
+    dd v = quick_two_sum(lam[k].hi, lam[k].lo);
+    hi[k] = v.hi;
+    if (lo) lo[k] = v.lo;
+  }
+  free(lam);
+  return 0;
+}
+
+/* One matrix entry of the map (direction 0 = L2C matrix C^{-1}A,
+ * 1 = C2L matrix A^{-1}C), rounded to double. */
+int lco_entry(int direction, int64_t n, int64_t i, int64_t j, double* out) {
+  if (n <= 0 || i < 0 || j < 0 || i >= n || j >= n || !out) return 1;
+  dd* lam = (dd*)malloc(sizeof(dd) * (size_t)n);
+  if (!lam) return 2;
+  lambda_table(n, lam);
+  *out = dd_to(entry(direction, lam, i, j));
+  free(lam);
+  return 0;
+}
+
+/* Apply the map (or its transpose when adjoint != 0) to x[0:n].
+ * rows == NULL: compute all n outputs into out[0:n].
+ * rows != NULL: compute outputs rows[0:nrows] into out[0:nrows].
+ * Returns 0 on success. */
+int lco_apply(int direction, int adjoint, int64_t n, const double* x,
+              int64_t nrows, const int64_t* rows, double* out) {
+  if (n <= 0 || !x || !out || (direction != 0 && direction != 1)) return 1;
+  int64_t count = rows ? nrows : n;
+  for (int64_t r = 0; rows && r < count; ++r)
+    if (rows[r] < 0 || rows[r] >= n) return 1;
+  dd* lam = (dd*)malloc(sizeof(dd) * (size_t)n);
+  if (!lam) return 2;
+  lambda_table(n, lam);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t r = 0; r < count; ++r) {
+    int64_t i = rows ? rows[r] : r;
+    dd acc = dd_from(0.0);
+    if (!adjoint) {
+      /* z_i = sum_{j >= i, j - i even} M_ij x_j */
+      for (int64_t j = i; j < n; j += 2)
+        acc = dd_add(acc, dd_mul_d(entry(direction, lam, i, j), x[j]));
+    } else {
+      /* g_j = sum_{i <= j, j - i even} M_ij r_i, with j the output index */
+      int64_t j = i;
+      for (int64_t ii = (j & 1); ii <= j; ii += 2)
+        acc = dd_add(acc, dd_mul_d(entry(direction, lam, ii, j), x[ii]));
+    }
+    out[r] = dd_to(acc);
+  }
+  free(lam);
+  return 0;
+}
+
+/* Number of threads the OpenMP runtime would use (1 without OpenMP). */
+int lco_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
