@@ -1,0 +1,184 @@
+/*
+ * legcheb.h -- C ABI of the GB300 fast multipole Legendre<->Chebyshev transform.
+ *
+ * The library computes the connection maps of Mortensen, "A faster multipole
+ * Legendre-Chebyshev transform" (arXiv:2411.00033), Sec. 1, eq:directmv:
+ *
+ *   LC_L2C:  f_cheb = C^{-1} A f_leg        (Legendre -> Chebyshev coefficients)
+ *   LC_C2L:  f_leg  = A^{-1} C f_cheb       (Chebyshev -> Legendre coefficients)
+ *
+ * with a_ij = Lambda((j-i)/2) Lambda((j+i)/2) for j >= i, j-i even, else 0
+ * (eq:aij), Lambda(x) = Gamma(x+1/2)/Gamma(x+1) (eq:Lambda) and
+ * C = diag(c_i pi/2), c_0 = 2, c_i = 1.  The C2L matrix has the entries
+ * L(i,j) of eq:Lxymod, with entry (0,0) equal to 1.
+ *
+ * The execution stage follows Algorithm 4 (Sec. 4.1): a direct near-field
+ * band (Step 6, Algorithm 1 restricted to the band), and the far-field
+ * blocks of the level hierarchy of Sec. 3.1 applied through Chebyshev
+ * expansions of order M = 18 (Steps 1-5), with the triangular translation
+ * matrices B(0), B(1) of eq:wtk / Appendix A.3 moving expansions between
+ * neighbouring levels, and the scaling C^{-1} (Step 7).
+ *
+ * Conventions shared by every call:
+ *  - All device pointers are plain CUDA device addresses; the library never
+ *    allocates device memory.  The caller provides a workspace for each plan
+ *    (sized by lc_plan_workspace_size*) and keeps it alive, unmodified, until
+ *    lc_destroy.  The plan object itself is host memory owned by the library.
+ *  - Every call returns an lc_status; nothing aborts.  A CUDA error seen by a
+ *    call is returned as LC_ERR_CUDA; asynchronous device faults surface at a
+ *    later call or synchronisation.
+ *  - Work is enqueued on the caller's stream; no call synchronises the host
+ *    except where stated.  lc_execute and lc_adjoint neither allocate nor
+ *    synchronise.
+ *  - One plan executes on one stream at a time: its intermediate arrays live
+ *    in the plan workspace, so two executions of the same plan must not
+ *    overlap on the device.
+ *  - Input and output must not alias.  Inputs of length n are treated as
+ *    zero-padded to the plan's internal length N >= n (Sec. 3.1,
+ *    eq:numlevels); padding cannot change the first n outputs because A is
+ *    upper triangular.
+ */
+#ifndef LEGCHEB_H
+#define LEGCHEB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* lc_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  LC_L2C = 0, /* f_cheb = C^{-1} A f_leg */
+  LC_C2L = 1  /* f_leg  = A^{-1} C f_cheb */
+} lc_direction;
+
+typedef enum {
+  /* FP64 in and out; every product and sum in FP64 on the FP64 pipe. */
+  LC_F64 = 0,
+  /* FP64 in and out, FP64-accurate; the block products run on the bf16 tensor
+   * cores as exact 8-bit slice products with FP32 accumulation, recombined in
+   * FP64 (split-precision tier). */
+  LC_F64_SPLIT = 1,
+  /* FP32 in and out; FP32 arithmetic (plan built in FP64, rounded once). */
+  LC_F32 = 2,
+  /* FP64 in and out, FP64-accurate; double-float (pairs of FP32) arithmetic
+   * on the FP32 pipe for a single vector or small batches. */
+  LC_F64_DF = 3
+} lc_dtype;
+
+typedef enum {
+  LC_OK = 0,
+  LC_ERR_INVALID_ARG = 1,         /* a size, enum, pointer or stride is invalid */
+  LC_ERR_WORKSPACE_TOO_SMALL = 2, /* workspace bytes below lc_plan_workspace_size */
+  LC_ERR_CUDA = 3,                /* a CUDA runtime call or launch failed */
+  LC_ERR_DEVICE_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+  LC_ERR_UNSUPPORTED = 5,         /* valid request the library does not implement */
+  LC_ERR_HOST_ALLOC = 6           /* host memory for the plan object ran out */
+} lc_status;
+
+typedef struct lc_plan_s* lc_plan;
+
+/* Plan options.  Defaults (lc_plan_options_default) follow the paper:
+ * s_hat = 32 and s = ceil(n / 2^(L+2)) with L = ceil(log2(n/s_hat)) - 2
+ * (eq:numlevels), so s lies in [s_hat/2, s_hat]. */
+typedef struct {
+  int32_t s_hat;   /* target leaf half-size (eq:numlevels); 4 <= s_hat <= 64 */
+  int32_t fixed_s; /* > 0: use this s for every length (4 <= fixed_s <= 64); 0: paper rule */
+  int32_t slices;  /* LC_F64_SPLIT: 8-bit slices per operand, 3..7 (default 6) */
+  int32_t reserved[5];
+} lc_plan_options;
+
+/* Fill *opt with the defaults above.  Returns LC_ERR_INVALID_ARG for NULL. */
+lc_status lc_plan_options_default(lc_plan_options* opt);
+
+/* Device bytes the caller must provide to lc_plan_create for a plan of
+ * `batch` vectors of length n (n >= 1, batch >= 1).  The size covers the
+ * plan tables (lambda, Vandermonde T, B, the N_c coefficient matrices A-hat
+ * of eq:aklmore) and the per-vector level arrays w, c of Algorithm 4.
+ * opt may be NULL (defaults). */
+lc_status lc_plan_workspace_size(int64_t n, lc_direction direction, int64_t batch,
+                                 lc_dtype dtype, size_t* bytes);
+lc_status lc_plan_workspace_size_ex(int64_t n, lc_direction direction, int64_t batch,
+                                    lc_dtype dtype, const lc_plan_options* opt,
+                                    size_t* bytes);
+
+/* Build a plan in `workspace` (device memory, 256-byte aligned, `bytes` >=
+ * the size above) on `stream`: lambda by the tau series every 8th entry and
+ * the recursion of eq:Lambdaint in between, T(sigma) of eq:Xs, B(0) exactly
+ * (Appendix A.3), and A-hat for every submatrix by sampling the kernel
+ * (A(x,y) for L2C, L(x,y) of eq:Lxymod for C2L) at M x M Chebyshev-Gauss
+ * points and applying the 2-D DCT-II of eq:aklmore.  All in FP64 on the
+ * GPU.  The plan is usable by later calls on the same stream (or after the
+ * caller synchronises).  *out receives a host object freed by lc_destroy. */
+lc_status lc_plan_create(lc_plan* out, int64_t n, lc_direction direction, int64_t batch,
+                         lc_dtype dtype, void* workspace, size_t bytes, lc_stream stream);
+lc_status lc_plan_create_ex(lc_plan* out, int64_t n, lc_direction direction, int64_t batch,
+                            lc_dtype dtype, const lc_plan_options* opt, void* workspace,
+                            size_t bytes, lc_stream stream);
+
+/* Ragged batch: `count` transforms of lengths n[0..count-1] (host array,
+ * each >= 1), packed back to back in input and output (member t starts at
+ * sum_{u<t} n[u]).  All members share one coefficient table built for the
+ * largest length with a fixed s (opt->fixed_s, default 32), since A-hat of a
+ * submatrix depends only on its position in A (eq:globalij), so every
+ * shorter plan is a corner of the largest one. */
+lc_status lc_plan_workspace_size_ragged(const int64_t* n, int64_t count, lc_direction direction,
+                                        lc_dtype dtype, const lc_plan_options* opt,
+                                        size_t* bytes);
+lc_status lc_plan_create_ragged(lc_plan* out, const int64_t* n, int64_t count,
+                                lc_direction direction, lc_dtype dtype,
+                                const lc_plan_options* opt, void* workspace, size_t bytes,
+                                lc_stream stream);
+
+/* Apply the plan's map to `batch` vectors (the plan's batch):
+ *   out[b*out_batch_stride + i*out_elem_stride] = (map x_b)_i, i < n,
+ *   x_b[j] = in[b*in_batch_stride + j*in_elem_stride].
+ * Element type: double for LC_F64 / LC_F64_SPLIT / LC_F64_DF, float for
+ * LC_F32.  Strides are in elements and may be any non-negative values that
+ * keep the vectors disjoint in `out` (this is how fibres of a 2-D/3-D array
+ * along any axis are transformed in place of a transpose).  For ragged plans
+ * both batch strides must be 0 and both element strides 1 (packed layout).
+ * Asynchronous on `stream`; no allocation, no host synchronisation. */
+lc_status lc_execute(lc_plan plan, const void* in, void* out, int64_t in_batch_stride,
+                     int64_t in_elem_stride, int64_t out_batch_stride,
+                     int64_t out_elem_stride, lc_stream stream);
+
+/* Apply the transpose of the plan's map (same layout rules as lc_execute):
+ *   L2C plan: out = A^T C^{-1} in ;  C2L plan: out = (A^{-1} C)^T in.
+ * Not in the paper: it runs Algorithm 4 backwards (C^{-1} first, leaf
+ * restriction on the row side, upward pass over the row tree, A-hat
+ * transposed, downward pass over the column tree, transposed band). */
+lc_status lc_adjoint(lc_plan plan, const void* in, void* out, int64_t in_batch_stride,
+                     int64_t in_elem_stride, int64_t out_batch_stride,
+                     int64_t out_elem_stride, lc_stream stream);
+
+/* Free the host plan object.  The workspace stays the caller's. */
+lc_status lc_destroy(lc_plan plan);
+
+/* Static text for a status code (never NULL). */
+const char* lc_status_string(lc_status status);
+
+/* Plan geometry (Sec. 3.1): n, padded N, levels L, leaf half-size s,
+ * expansion order M, number of submatrices N_c (eq:total_blocks_and_mats),
+ * batch.  Any output pointer may be NULL. */
+lc_status lc_plan_info(lc_plan plan, int64_t* n, int64_t* N, int32_t* L, int32_t* s,
+                       int32_t* M, int64_t* n_c, int64_t* batch);
+
+/* Copy plan tables to host memory for inspection (synchronises `stream`):
+ * which = 0: lambda[N]; 1: T[2][s][M]; 2: B(0)[M][M]; 3: A-hat[N_c][M][M]
+ * (row k = expansion in the row variable X, column l in Y, eq:Aij).
+ * `count` is the capacity of dst in doubles; the number copied is returned
+ * in *copied. */
+lc_status lc_plan_table(lc_plan plan, int32_t which, double* dst, int64_t count,
+                        int64_t* copied, lc_stream stream);
+
+/* Number of kernels one lc_execute of this plan launches. */
+lc_status lc_plan_launches(lc_plan plan, int32_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEGCHEB_H */

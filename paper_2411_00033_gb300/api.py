@@ -1,0 +1,158 @@
+"""PyTorch front end: device memory and streams come from torch, all compute
+from liblegcheb.so (see binding.py).  No CPU path exists."""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+_DIRECTIONS = {"l2c": B.LC_L2C, "c2l": B.LC_C2L}
+_DTYPES = {"f64": B.LC_F64, "f64_split": B.LC_F64_SPLIT, "f32": B.LC_F32, "f64_df": B.LC_F64_DF}
+_TORCH_DTYPE = {B.LC_F64: torch.float64, B.LC_F64_SPLIT: torch.float64, B.LC_F32: torch.float32,
+                B.LC_F64_DF: torch.float64}
+
+
+def _stream_ptr(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def make_options(s_hat: int | None = None, fixed_s: int | None = None, slices: int | None = None):
+    o = B.lc_plan_options_default()
+    if s_hat is not None:
+        o.s_hat = s_hat
+    if fixed_s is not None:
+        o.fixed_s = fixed_s
+    if slices is not None:
+        o.slices = slices
+    return o
+
+
+class Plan:
+    """A transform plan: tables built on the GPU in a torch-owned workspace.
+
+    direction: "l2c" (f_cheb = C^{-1} A f_leg) or "c2l" (f_leg = A^{-1} C f_cheb)
+    dtype:     "f64" | "f64_split" | "f32" | "f64_df"
+    lengths:   for a ragged plan, the member lengths (then n and batch are ignored)
+    """
+
+    def __init__(self, n: int | None = None, direction: str = "l2c", batch: int = 1, dtype: str = "f64",
+                 device=None, lengths=None, **options):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.direction = _DIRECTIONS[direction]
+        self.dtype_code = _DTYPES[dtype]
+        self.dtype_name = dtype
+        self.torch_dtype = _TORCH_DTYPE[self.dtype_code]
+        self.options = make_options(**options)
+        self._handle = None
+        with torch.cuda.device(self.device):
+            st = _stream_ptr(self.device)
+            if lengths is not None:
+                self.lengths = [int(v) for v in lengths]
+                self.ragged = True
+                nbytes = B.lc_plan_workspace_size_ragged(self.lengths, self.direction, self.dtype_code, self.options)
+                self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+                self._handle = B.lc_plan_create_ragged(self.lengths, self.direction, self.dtype_code,
+                                                       self.workspace.data_ptr(), nbytes, st, self.options)
+                self.total = sum(self.lengths)
+            else:
+                self.ragged = False
+                nbytes = B.lc_plan_workspace_size(n, self.direction, batch, self.dtype_code, self.options)
+                self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+                self._handle = B.lc_plan_create(n, self.direction, batch, self.dtype_code,
+                                                self.workspace.data_ptr(), nbytes, st, self.options)
+        self.info = B.lc_plan_info(self._handle)
+        self.n = self.info["n"]
+        self.batch = self.info["batch"]
+
+    # ------------------------------------------------------------------ run
+    def _check_in(self, x: torch.Tensor):
+        if x.device != self.device or x.dtype != self.torch_dtype:
+            raise TypeError("expected a %s tensor on %s, got %s on %s" % (self.torch_dtype, self.device, x.dtype, x.device))
+
+    def _strides(self, x: torch.Tensor):
+        if self.ragged:
+            if x.dim() != 1 or x.numel() != self.total or x.stride(0) != 1:
+                raise ValueError("ragged input must be a contiguous 1-D tensor of %d elements" % self.total)
+            return 0, 1
+        if x.dim() == 1:
+            if self.batch != 1 or x.shape[0] != self.n:
+                raise ValueError("expected shape (%d,)" % self.n)
+            return 0, x.stride(0)
+        if x.dim() != 2 or tuple(x.shape) != (self.batch, self.n):
+            raise ValueError("expected shape (%d, %d)" % (self.batch, self.n))
+        return x.stride(0), x.stride(1)
+
+    def __call__(self, x: torch.Tensor, out: torch.Tensor | None = None, adjoint: bool = False) -> torch.Tensor:
+        return self.execute(x, out=out, adjoint=adjoint)
+
+    def execute(self, x: torch.Tensor, out: torch.Tensor | None = None, adjoint: bool = False) -> torch.Tensor:
+        self._check_in(x)
+        ib, ie = self._strides(x)
+        if out is None:
+            out = torch.empty_like(x, memory_format=torch.contiguous_format) if x.dim() > 0 else torch.empty_like(x)
+        else:
+            self._check_in(out)
+        ob, oe = self._strides(out)
+        fn = B.lc_adjoint if adjoint else B.lc_execute
+        with torch.cuda.device(self.device):
+            fn(self._handle, x.data_ptr(), out.data_ptr(), ib, ie, ob, oe, _stream_ptr(self.device))
+        return out
+
+    def execute_strided(self, x: torch.Tensor, out: torch.Tensor, in_strides, out_strides, adjoint: bool = False):
+        """Raw strided call: vector b, element j at x.data_ptr() + (b*sb + j*se) elements."""
+        self._check_in(x)
+        self._check_in(out)
+        fn = B.lc_adjoint if adjoint else B.lc_execute
+        with torch.cuda.device(self.device):
+            fn(self._handle, x.data_ptr(), out.data_ptr(), in_strides[0], in_strides[1], out_strides[0],
+               out_strides[1], _stream_ptr(self.device))
+        return out
+
+    def table(self, which: int):
+        sizes = {0: self.info["N"], 1: 2 * self.info["s"] * self.info["M"], 2: self.info["M"] ** 2,
+                 3: self.info["n_c"] * self.info["M"] ** 2, 4: self.info["N"], 5: self.info["N"]}
+        with torch.cuda.device(self.device):
+            return B.lc_plan_table(self._handle, which, sizes[which], _stream_ptr(self.device))
+
+    def launches(self) -> int:
+        return B.lc_plan_launches(self._handle)
+
+    def close(self):
+        if self._handle is not None:
+            B.lc_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_PLAN_CACHE: dict = {}
+
+
+def get_plan(n: int, direction: str, batch: int, dtype: str, device=None, **options) -> Plan:
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    key = (n, direction, batch, dtype, str(dev), tuple(sorted(options.items())))
+    p = _PLAN_CACHE.get(key)
+    if p is None:
+        p = Plan(n, direction, batch, dtype, dev, **options)
+        _PLAN_CACHE[key] = p
+    return p
+
+
+def leg2cheb(x: torch.Tensor, dtype: str | None = None, **options) -> torch.Tensor:
+    """f_cheb = C^{-1} A f_leg along the last dimension of a 1-D or 2-D tensor."""
+    dtype = dtype or ("f32" if x.dtype == torch.float32 else "f64")
+    batch = 1 if x.dim() == 1 else x.shape[0]
+    return get_plan(x.shape[-1], "l2c", batch, dtype, x.device, **options)(x)
+
+
+def cheb2leg(x: torch.Tensor, dtype: str | None = None, **options) -> torch.Tensor:
+    """f_leg = A^{-1} C f_cheb along the last dimension of a 1-D or 2-D tensor."""
+    dtype = dtype or ("f32" if x.dtype == torch.float32 else "f64")
+    batch = 1 if x.dim() == 1 else x.shape[0]
+    return get_plan(x.shape[-1], "c2l", batch, dtype, x.device, **options)(x)

@@ -1,0 +1,124 @@
+// lc_internal.cuh -- shared definitions of the GB300 Legendre<->Chebyshev library.
+//
+// Geometry (Sec. 3.1 of the paper): L levels gamma = 0..L-1, leaf half-size s,
+// h_gamma = s 2^(L-gamma-1), N = s 2^(L+2) (eq:Ntot), b_gamma = 2^(gamma+1)-1
+// blocks per level (eq:Nb), N_c = 3 (N/(2s) - L - 2) submatrices
+// (eq:total_blocks_and_mats).
+//
+// Segment trees.  At level gamma the vectors are cut into segments of 2 h_gamma
+// entries; segment g covers [2 h g, 2 h (g+1)).  The column blocks of eq:fgamma
+// are the segments g = 2b+q+2 (so g >= 2) and the row blocks of eq:zgamma are
+// v = 2b+p (so v < 2 b_gamma).  With this numbering the level links eq:flevels
+// and eq:zlevels both become "parent = child / 2": f(gamma-1, G) is the union of
+// f(gamma, 2G) and f(gamma, 2G+1), and likewise for z.  Submatrix (p, q) of
+// block b couples row segment v = 2b+p with column segment g = 2b+q+2.
+//
+// Arrays w(gamma) and c(gamma) of Algorithm 4 are stored level after level,
+// 2^(gamma+2) segments per level (including the two unused ones), each segment
+// holding [sigma][k] for the two parities and k < M:
+//   seg_offset(gamma) = 4 (2^gamma - 1), total 4 (2^L - 1) segments.
+// A-hat(gamma, b, r) is stored at 3 (2^(gamma+1) - 2 - gamma) + 3 b + r.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/legcheb.h"
+
+#define LC_M 18
+#define LC_MAX_S 64
+
+struct lc_geom {
+  int64_t n;      // logical length (longest member for ragged plans)
+  int64_t N;      // padded length s 2^(L+2), or n for direct-only plans
+  int32_t L;      // number of levels; 0 means the whole triangle is near field
+  int32_t s;      // leaf half-size h_(L-1)
+  int64_t nc;     // submatrices
+  int64_t nseg;   // segments over all levels, 4 (2^L - 1)
+};
+
+__host__ __device__ inline int64_t lc_seg_offset(int gamma) { return 4 * ((int64_t(1) << gamma) - 1); }
+__host__ __device__ inline int64_t lc_ahat_offset(int gamma) {
+  return 3 * ((int64_t(1) << (gamma + 1)) - 2 - gamma);
+}
+
+// Device views of a plan's tables, by element type.
+template <typename R>
+struct lc_tables {
+  const R* lam;   // L2C: lambda[N]; C2L: u[N] = lambda_k / (1 - 2k)
+  const R* lam2;  // L2C: lambda[N]; C2L: v[N] = 1 / (2m (2m+1) lambda_m), v[0] = 0
+  const R* T;     // [2][s][M]   T_k(-1 + (2m+sigma)/s)           (eq:Xs)
+  const R* B;     // [M][M]      B(0), lower triangular           (eq:Tmap)
+  const R* Ahat;  // [nc][M][M]
+  R* W;           // [batch][nseg][2][M]   w of Algorithm 4
+  R* Cc;          // [batch][nseg][2][M]   c of Algorithm 4
+};
+
+struct lc_plan_s {
+  lc_geom g;
+  lc_direction dir;
+  lc_dtype dtype;
+  int64_t batch;
+  lc_plan_options opt;
+  int ragged;
+  // FP64 tables (always built; they are the plan).
+  double* lam;
+  double* lam2;
+  double* T;
+  double* B;
+  double* Ahat;
+  double* W;
+  double* Cc;
+  // FP32 copies for LC_F32.
+  float* lamf;
+  float* lam2f;
+  float* Tf;
+  float* Bf;
+  float* Ahatf;
+  float* Wf;
+  float* Ccf;
+  // Double-float (hi, lo) copies for LC_F64_DF: stored as float2.
+  void* df_lam;
+  void* df_lam2;
+  void* df_T;
+  void* df_B;
+  void* df_Ahat;
+  void* df_W;
+  void* df_Cc;
+  // Split tier data (see lc_split.cu).
+  void* split;
+  // Ragged members (host copies and device tables).
+  int64_t count;
+  int64_t* h_len;
+  int64_t* h_off;
+  void* ragged_dev;
+  size_t bytes_used;
+};
+
+// ---- error helpers ---------------------------------------------------------
+#define LC_CUDA_TRY(expr)                        \
+  do {                                           \
+    cudaError_t _e = (expr);                     \
+    if (_e != cudaSuccess) return LC_ERR_CUDA;   \
+  } while (0)
+#define LC_LAUNCH_CHECK() LC_CUDA_TRY(cudaGetLastError())
+
+// ---- geometry / plan helpers (lc_plan.cu) -----------------------------------
+lc_status lc_compute_geometry(int64_t n, const lc_plan_options* opt, int fixed_default, lc_geom* g);
+
+// ---- execution entry points (lc_exec.cu) ------------------------------------
+lc_status lc_exec_cuda_cores(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie,
+                             int64_t ob, int64_t oe, cudaStream_t st, int adjoint);
+int lc_exec_cuda_cores_launches(const lc_plan_s* p);
+
+// ---- double-float tier (lc_df.cu) -------------------------------------------
+lc_status lc_df_prepare(lc_plan p, cudaStream_t st);
+lc_status lc_exec_df(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob,
+                     int64_t oe, cudaStream_t st, int adjoint);
+size_t lc_df_bytes(const lc_geom& g, int64_t batch);
+
+// ---- split tier (lc_split.cu) ------------------------------------------------
+size_t lc_split_bytes(const lc_plan_s* p);
+lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st);
+lc_status lc_exec_split(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob,
+                        int64_t oe, cudaStream_t st, int adjoint);
+int lc_exec_split_launches(const lc_plan_s* p);

@@ -1,0 +1,492 @@
+// lc_plan.cu -- plan geometry, FP64 plan builder kernels and the C ABI front door.
+//
+// Plan contents (all computed in FP64 on the GPU):
+//   lambda_i = Lambda(i), i < N: every 8th value from the tau series (eq:tau,
+//       Lambda(z) = tau(z+1/4)/sqrt(z+1/4)), the 7 in between by the
+//       recursion Lambda(i) = Lambda(i-1)(i-1/2)/i (eq:Lambdaint); the first
+//       24 values by the recursion from Lambda(0) = sqrt(pi)  (Sec. 4.3).
+//   T(sigma)_{mk} = T_k(-1 + (2m+sigma)/s)  (eq:Xs), by the three-term recurrence.
+//   B(0)_{kj}: T_k((Y-1)/2) = sum_j b_kj T_j(Y)  (eq:Tmap).  Built exactly from
+//       the Chebyshev recurrence T_{k+1}(u) = 2u T_k(u) - T_{k-1}(u) with
+//       u = (Y-1)/2 and Y T_j = (T_{j+1} + T_{j-1})/2; every entry is a dyadic
+//       rational, so FP64 holds it exactly (Appendix A.3 gives the same matrix
+//       as W^{-1} V(0) W).  B(1) differs only in the sign of odd diagonals.
+//   A-hat(gamma,b,r): the kernel A(x,y) = Lambda((y-x)/2) Lambda((y+x)/2)
+//       (Sec. 3.2) or, for C2L, L(x,y) of eq:Lxymod, sampled at M x M
+//       Chebyshev-Gauss points of the submatrix domain (eq:Xfromx) and
+//       transformed with the 2-D DCT-II of eq:aklmore.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lc_internal.cuh"
+
+// ------------------------------------------------------------------ Lambda --
+// Lambda(z) for real z > 0 via the tau series (eq:tau).  The series reaches
+// machine precision for z > 19.88; below 20 the argument is first shifted up
+// with Lambda(z) = Lambda(z+1) (z+1)/(z+1/2), which follows from
+// Gamma(x+1) = x Gamma(x).
+__device__ double lc_Lambda(double z) {
+  double f = 1.0;
+  while (z < 20.0) {
+    f *= (z + 1.0) / (z + 0.5);
+    z += 1.0;
+  }
+  const double y = z + 0.25;
+  const double x = 1.0 / (y * y);
+  const double tau =
+      1.0 + x * (-1.0 / 64.0 + x * (21.0 / 8192.0 + x * (-671.0 / 524288.0 + x * (180323.0 / 134217728.0))));
+  return f * tau / sqrt(y);
+}
+
+__global__ void k_plan_lambda(int64_t N, double* __restrict__ lam) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i0 = 8 * t;
+  if (i0 >= N) return;
+  double v;
+  int64_t start;
+  if (i0 < 24) {
+    v = 1.7724538509055160273;  // Lambda(0) = Gamma(1/2) = sqrt(pi)
+    for (int64_t i = 1; i <= i0; ++i) v *= (double(2 * i - 1) / double(2 * i));
+    start = i0;
+  } else {
+    v = lc_Lambda(double(i0));
+    start = i0;
+  }
+  lam[start] = v;
+  for (int64_t i = start + 1; i < start + 8 && i < N; ++i) {
+    v *= (double(2 * i - 1) / double(2 * i));
+    lam[i] = v;
+  }
+}
+
+// C2L near-field tables: L(i, i+2k) = (2i+1)(i+2k) u_k v_{i+k} with
+// u_k = Lambda(k)/(1-2k) and v_m = 1/(2m(2m+1) Lambda(m)) -- a factorisation
+// of eq:Lxymod at x = i, y = i + 2k.  v_0 = 0; entry (0,0) = 1 is added
+// separately.  Input: lambda in v (overwritten in place).
+__global__ void k_plan_c2l_tables(int64_t N, double* __restrict__ u, double* __restrict__ v) {
+  const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  const double l = v[m];
+  u[m] = l / double(1 - 2 * m);
+  v[m] = (m == 0) ? 0.0 : 1.0 / (double(2 * m) * double(2 * m + 1) * l);
+}
+
+__global__ void k_plan_T(int s, double* __restrict__ T) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * s) return;
+  const int sigma = t / s, m = t % s;
+  const double X = -1.0 + double(2 * m + sigma) / double(s);
+  double* row = T + (size_t(sigma) * s + m) * LC_M;
+  double t0 = 1.0, t1 = X;
+  row[0] = t0;
+  row[1] = t1;
+  for (int k = 2; k < LC_M; ++k) {
+    const double t2 = 2.0 * X * t1 - t0;
+    row[k] = t2;
+    t0 = t1;
+    t1 = t2;
+  }
+}
+
+// B(0) by the exact row recurrence (one thread; M^2 work).
+__global__ void k_plan_B(double* __restrict__ B) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < LC_M * LC_M; ++i) B[i] = 0.0;
+  B[0] = 1.0;          // T_0(u) = 1
+  B[LC_M + 0] = -0.5;  // T_1(u) = u = Y/2 - 1/2
+  B[LC_M + 1] = 0.5;
+  for (int k = 1; k + 1 < LC_M; ++k) {
+    const double* bk = B + k * LC_M;
+    const double* bm = B + (k - 1) * LC_M;
+    double* bn = B + (k + 1) * LC_M;
+    for (int i = 0; i <= k + 1; ++i) {
+      // Y * T_k(u) expanded in T_j(Y): T_0 -> T_1, T_j -> (T_{j+1} + T_{j-1})/2.
+      double y = 0.0;
+      if (i == 1) y += bk[0];
+      if (i >= 2) y += 0.5 * bk[i - 1];
+      if (i + 1 <= k) y += 0.5 * bk[i + 1];
+      // T_{k+1}(u) = (Y - 1) T_k(u) - T_{k-1}(u)
+      const double own = (i <= k) ? bk[i] : 0.0;
+      const double prev = (i <= k - 1) ? bm[i] : 0.0;
+      bn[i] = y - own - prev;
+    }
+  }
+}
+
+// cosm[k][m] = cos(k (m + 1/2) pi / M): the DCT-II matrix of eq:aklmore.
+// Row 1 holds the Chebyshev-Gauss points X_m.
+__global__ void k_plan_cos(double* __restrict__ cosm) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= LC_M * LC_M) return;
+  const int k = t / LC_M, m = t % LC_M;
+  cosm[t] = cospi(double(k * (2 * m + 1)) / double(2 * LC_M));
+}
+
+// One CTA (M*M threads) per submatrix: sample the kernel, then the 2-D DCT-II.
+__global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __restrict__ cosm,
+                            double* __restrict__ Ahat) {
+  __shared__ double S[LC_M][LC_M];
+  __shared__ double Tm[LC_M][LC_M];
+  __shared__ double cs[LC_M][LC_M];
+  const int tid = threadIdx.x;
+  const int r0 = tid / LC_M, c0 = tid % LC_M;
+  cs[r0][c0] = cosm[tid];
+  for (int64_t a = blockIdx.x; a < nc; a += gridDim.x) {
+    int gamma = 0;
+    while (gamma + 1 < L && a >= lc_ahat_offset(gamma + 1)) ++gamma;
+    const int64_t rem = a - lc_ahat_offset(gamma);
+    const int64_t b = rem / 3;
+    const int r = int(rem % 3);
+    const int p = (r == 2) ? 1 : 0;
+    const int q = (r == 0) ? 0 : 1;
+    const double h = double(int64_t(s) << (L - gamma - 1));
+    const double i0 = 2.0 * h * double(2 * b + p);
+    const double j0 = 2.0 * h * double(2 * b + q + 2);
+    __syncthreads();
+    // sample at (x_m, y_n), x_m = i0 + h (X_m + 1), y_n = j0 + h (Y_n + 1)   (eq:Xfromx)
+    {
+      const double x = i0 + h * (cs[1][r0] + 1.0);
+      const double y = j0 + h * (cs[1][c0] + 1.0);
+      double val;
+      if (dir == LC_L2C) {
+        val = lc_Lambda(0.5 * (y - x)) * lc_Lambda(0.5 * (y + x));
+      } else {
+        const double pre = 2.0 * (x + 0.5) * y / ((x + y) * (x + y + 1.0) * (x - y + 1.0));
+        val = pre * lc_Lambda(0.5 * (y - x)) / lc_Lambda(0.5 * (x + y));
+      }
+      S[r0][c0] = val;
+    }
+    __syncthreads();
+    {  // DCT along the row variable: Tm[k][n] = sum_m cos(k(m+1/2)pi/M) S[m][n]
+      double acc = 0.0;
+      for (int m = 0; m < LC_M; ++m) acc = fma(cs[r0][m], S[m][c0], acc);
+      Tm[r0][c0] = acc;
+    }
+    __syncthreads();
+    {  // along the column variable, then the 4/(c_k c_l M^2) weight
+      double acc = 0.0;
+      for (int n = 0; n < LC_M; ++n) acc = fma(Tm[r0][n], cs[c0][n], acc);
+      const double w = 4.0 / (double(LC_M) * double(LC_M)) * (r0 == 0 ? 0.5 : 1.0) * (c0 == 0 ? 0.5 : 1.0);
+      Ahat[a * (LC_M * LC_M) + tid] = acc * w;
+    }
+  }
+}
+
+__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    b[i] = float(a[i]);
+}
+
+// -------------------------------------------------------------- geometry --
+lc_status lc_compute_geometry(int64_t n, const lc_plan_options* opt, int fixed_default, lc_geom* g) {
+  if (n < 1 || n > (int64_t(1) << 40)) return LC_ERR_INVALID_ARG;
+  int s_hat = opt ? opt->s_hat : 32;
+  int fixed_s = opt ? opt->fixed_s : 0;
+  if (fixed_s == 0 && fixed_default) fixed_s = 32;
+  if (s_hat < 4 || s_hat > LC_MAX_S) return LC_ERR_INVALID_ARG;
+  if (fixed_s != 0 && (fixed_s < 4 || fixed_s > LC_MAX_S)) return LC_ERR_INVALID_ARG;
+  memset(g, 0, sizeof(*g));
+  g->n = n;
+  const int64_t base = fixed_s ? fixed_s : s_hat;
+  // smallest t with base 2^t >= n; L = t - 2   (eq:numlevels)
+  int t = 0;
+  while ((base << t) < n) ++t;
+  const int L = t - 2;
+  if (L <= 0) {  // the whole upper triangle is near field
+    g->L = 0;
+    g->s = int(base);
+    g->N = n;
+    g->nc = 0;
+    g->nseg = 0;
+    return LC_OK;
+  }
+  g->L = L;
+  if (fixed_s) {
+    g->s = fixed_s;
+  } else {
+    const int64_t d = int64_t(1) << (L + 2);
+    g->s = int((n + d - 1) / d);  // in [s_hat/2, s_hat]
+  }
+  g->N = int64_t(g->s) << (L + 2);                          // eq:Ntot
+  g->nc = 3 * ((g->N / (2 * g->s)) - L - 2);                // eq:total_blocks_and_mats
+  g->nseg = 4 * ((int64_t(1) << L) - 1);
+  return LC_OK;
+}
+
+// ------------------------------------------------------- workspace layout --
+namespace {
+struct carver {
+  char* base;
+  size_t off;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+size_t layout(lc_plan_s* p, char* base) {
+  carver c{base, 0};
+  const lc_geom& g = p->g;
+  const size_t N = size_t(g.N);
+  const size_t nw = size_t(p->batch) * size_t(g.nseg) * 2 * LC_M;
+  p->lam = c.take<double>(N);
+  p->lam2 = (p->dir == LC_C2L) ? c.take<double>(N) : p->lam;
+  p->T = c.take<double>(size_t(2) * g.s * LC_M);
+  p->B = c.take<double>(LC_M * LC_M);
+  p->Ahat = c.take<double>(size_t(g.nc) * LC_M * LC_M + LC_M * LC_M);  // + DCT matrix scratch
+  p->W = p->Cc = nullptr;
+  p->lamf = p->lam2f = p->Tf = p->Bf = p->Ahatf = p->Wf = p->Ccf = nullptr;
+  if (p->dtype == LC_F64) {
+    p->W = c.take<double>(nw);
+    p->Cc = c.take<double>(nw);
+  } else if (p->dtype == LC_F32) {
+    p->lamf = c.take<float>(N);
+    p->lam2f = (p->dir == LC_C2L) ? c.take<float>(N) : p->lamf;
+    p->Tf = c.take<float>(size_t(2) * g.s * LC_M);
+    p->Bf = c.take<float>(LC_M * LC_M);
+    p->Ahatf = c.take<float>(size_t(g.nc) * LC_M * LC_M);
+    p->Wf = c.take<float>(nw);
+    p->Ccf = c.take<float>(nw);
+  } else if (p->dtype == LC_F64_DF) {
+    const size_t f2 = 2 * sizeof(float);
+    p->df_lam = c.take<char>(N * f2);
+    p->df_lam2 = (p->dir == LC_C2L) ? c.take<char>(N * f2) : p->df_lam;
+    p->df_T = c.take<char>(size_t(2) * g.s * LC_M * f2);
+    p->df_B = c.take<char>(LC_M * LC_M * f2);
+    p->df_Ahat = c.take<char>(size_t(g.nc) * LC_M * LC_M * f2);
+    p->df_W = c.take<char>(nw * f2);
+    p->df_Cc = c.take<char>(nw * f2);
+  } else if (p->dtype == LC_F64_SPLIT) {
+    const size_t sb = lc_split_bytes(p);
+    p->split = c.take<char>(sb);
+  }
+  return c.off + 256;
+}
+
+bool valid_enum(lc_direction d, lc_dtype t) {
+  return (d == LC_L2C || d == LC_C2L) &&
+         (t == LC_F64 || t == LC_F64_SPLIT || t == LC_F32 || t == LC_F64_DF);
+}
+
+lc_status fill_plan(lc_plan_s* p, int64_t n, lc_direction dir, int64_t batch, lc_dtype dtype,
+                    const lc_plan_options* opt) {
+  if (!valid_enum(dir, dtype) || batch < 1 || batch > (int64_t(1) << 31)) return LC_ERR_INVALID_ARG;
+  memset(p, 0, sizeof(*p));
+  lc_plan_options_default(&p->opt);
+  if (opt) p->opt = *opt;
+  if (p->opt.slices < 3 || p->opt.slices > 7) return LC_ERR_INVALID_ARG;
+  lc_status st = lc_compute_geometry(n, &p->opt, 0, &p->g);
+  if (st != LC_OK) return st;
+  p->dir = dir;
+  p->dtype = dtype;
+  p->batch = batch;
+  p->count = batch;
+  return LC_OK;
+}
+
+int grid_for(int64_t work, int threads) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > (int64_t(1) << 30)) b = int64_t(1) << 30;
+  return int(b);
+}
+
+lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
+  const lc_geom& g = p->g;
+  double* lam_target = (p->dir == LC_C2L) ? p->lam2 : p->lam;
+  k_plan_lambda<<<grid_for((g.N + 7) / 8, 256), 256, 0, st>>>(g.N, lam_target);
+  LC_LAUNCH_CHECK();
+  if (p->dir == LC_C2L) {
+    k_plan_c2l_tables<<<grid_for(g.N, 256), 256, 0, st>>>(g.N, p->lam, p->lam2);
+    LC_LAUNCH_CHECK();
+  }
+  k_plan_T<<<1, 2 * LC_MAX_S, 0, st>>>(g.s, p->T);
+  LC_LAUNCH_CHECK();
+  k_plan_B<<<1, 32, 0, st>>>(p->B);
+  LC_LAUNCH_CHECK();
+  if (g.L > 0) {
+    double* cosm = p->Ahat + size_t(g.nc) * LC_M * LC_M;
+    k_plan_cos<<<2, 256, 0, st>>>(cosm);
+    LC_LAUNCH_CHECK();
+    const int64_t blocks = g.nc < 1048576 ? g.nc : 1048576;
+    k_plan_ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, p->Ahat);
+    LC_LAUNCH_CHECK();
+  }
+  if (p->dtype == LC_F32) {
+    k_d2f<<<grid_for(g.N, 256), 256, 0, st>>>(g.N, p->lam, p->lamf);
+    if (p->dir == LC_C2L) k_d2f<<<grid_for(g.N, 256), 256, 0, st>>>(g.N, p->lam2, p->lam2f);
+    k_d2f<<<1, 256, 0, st>>>(int64_t(2) * g.s * LC_M, p->T, p->Tf);
+    k_d2f<<<1, 256, 0, st>>>(LC_M * LC_M, p->B, p->Bf);
+    if (g.nc > 0)
+      k_d2f<<<grid_for(g.nc * LC_M * LC_M, 256), 256, 0, st>>>(g.nc * LC_M * LC_M, p->Ahat, p->Ahatf);
+    LC_LAUNCH_CHECK();
+  } else if (p->dtype == LC_F64_DF) {
+    lc_status s2 = lc_df_prepare(p, st);
+    if (s2 != LC_OK) return s2;
+  }
+  return LC_OK;
+}
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI --
+extern "C" {
+
+lc_status lc_plan_options_default(lc_plan_options* opt) {
+  if (!opt) return LC_ERR_INVALID_ARG;
+  memset(opt, 0, sizeof(*opt));
+  opt->s_hat = 32;
+  opt->fixed_s = 0;
+  opt->slices = 6;
+  return LC_OK;
+}
+
+lc_status lc_plan_workspace_size_ex(int64_t n, lc_direction direction, int64_t batch, lc_dtype dtype,
+                                    const lc_plan_options* opt, size_t* bytes) {
+  if (!bytes) return LC_ERR_INVALID_ARG;
+  lc_plan_s p;
+  lc_status st = fill_plan(&p, n, direction, batch, dtype, opt);
+  if (st != LC_OK) return st;
+  *bytes = layout(&p, nullptr);
+  return LC_OK;
+}
+
+lc_status lc_plan_workspace_size(int64_t n, lc_direction direction, int64_t batch, lc_dtype dtype,
+                                 size_t* bytes) {
+  return lc_plan_workspace_size_ex(n, direction, batch, dtype, nullptr, bytes);
+}
+
+lc_status lc_plan_create_ex(lc_plan* out, int64_t n, lc_direction direction, int64_t batch,
+                            lc_dtype dtype, const lc_plan_options* opt, void* workspace, size_t bytes,
+                            lc_stream stream) {
+  if (!out || !workspace) return LC_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return LC_ERR_INVALID_ARG;
+  *out = nullptr;
+  lc_plan_s* p = static_cast<lc_plan_s*>(malloc(sizeof(lc_plan_s)));
+  if (!p) return LC_ERR_HOST_ALLOC;
+  lc_status st = fill_plan(p, n, direction, batch, dtype, opt);
+  if (st != LC_OK) {
+    free(p);
+    return st;
+  }
+  const size_t need = layout(p, nullptr);
+  if (bytes < need) {
+    free(p);
+    return LC_ERR_WORKSPACE_TOO_SMALL;
+  }
+  layout(p, static_cast<char*>(workspace));
+  p->bytes_used = need;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  st = build_tables(p, s);
+  if (st == LC_OK && dtype == LC_F64_SPLIT) st = lc_split_prepare(p, static_cast<char*>(p->split), lc_split_bytes(p), s);
+  if (st != LC_OK) {
+    free(p);
+    return st;
+  }
+  *out = p;
+  return LC_OK;
+}
+
+lc_status lc_plan_create(lc_plan* out, int64_t n, lc_direction direction, int64_t batch, lc_dtype dtype,
+                         void* workspace, size_t bytes, lc_stream stream) {
+  return lc_plan_create_ex(out, n, direction, batch, dtype, nullptr, workspace, bytes, stream);
+}
+
+lc_status lc_destroy(lc_plan plan) {
+  if (!plan) return LC_ERR_INVALID_ARG;
+  free(plan->h_len);
+  free(plan->h_off);
+  free(plan);
+  return LC_OK;
+}
+
+const char* lc_status_string(lc_status status) {
+  switch (status) {
+    case LC_OK: return "LC_OK";
+    case LC_ERR_INVALID_ARG: return "LC_ERR_INVALID_ARG: invalid size, enum, pointer or stride";
+    case LC_ERR_WORKSPACE_TOO_SMALL: return "LC_ERR_WORKSPACE_TOO_SMALL: workspace below the required size";
+    case LC_ERR_CUDA: return "LC_ERR_CUDA: a CUDA runtime call or kernel launch failed";
+    case LC_ERR_DEVICE_TIMEOUT: return "LC_ERR_DEVICE_TIMEOUT: a bounded device wait gave up";
+    case LC_ERR_UNSUPPORTED: return "LC_ERR_UNSUPPORTED: request not implemented";
+    case LC_ERR_HOST_ALLOC: return "LC_ERR_HOST_ALLOC: host allocation failed";
+  }
+  return "unknown lc_status";
+}
+
+lc_status lc_plan_info(lc_plan plan, int64_t* n, int64_t* N, int32_t* L, int32_t* s, int32_t* M,
+                       int64_t* n_c, int64_t* batch) {
+  if (!plan) return LC_ERR_INVALID_ARG;
+  if (n) *n = plan->g.n;
+  if (N) *N = plan->g.N;
+  if (L) *L = plan->g.L;
+  if (s) *s = plan->g.s;
+  if (M) *M = LC_M;
+  if (n_c) *n_c = plan->g.nc;
+  if (batch) *batch = plan->batch;
+  return LC_OK;
+}
+
+lc_status lc_plan_table(lc_plan plan, int32_t which, double* dst, int64_t count, int64_t* copied,
+                        lc_stream stream) {
+  if (!plan || !dst || count < 0) return LC_ERR_INVALID_ARG;
+  const double* src = nullptr;
+  int64_t len = 0;
+  switch (which) {
+    case 0: src = (plan->dir == LC_C2L) ? nullptr : plan->lam; len = plan->g.N; break;
+    case 1: src = plan->T; len = int64_t(2) * plan->g.s * LC_M; break;
+    case 2: src = plan->B; len = LC_M * LC_M; break;
+    case 3: src = plan->Ahat; len = plan->g.nc * LC_M * LC_M; break;
+    case 4: src = plan->lam; len = plan->g.N; break;   // C2L: u table
+    case 5: src = plan->lam2; len = plan->g.N; break;  // C2L: v table
+    default: return LC_ERR_INVALID_ARG;
+  }
+  if (!src) return LC_ERR_UNSUPPORTED;
+  if (len > count) len = count;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (len > 0) LC_CUDA_TRY(cudaMemcpyAsync(dst, src, size_t(len) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  LC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (copied) *copied = len;
+  return LC_OK;
+}
+
+lc_status lc_plan_launches(lc_plan plan, int32_t* launches) {
+  if (!plan || !launches) return LC_ERR_INVALID_ARG;
+  *launches = (plan->dtype == LC_F64_SPLIT) ? lc_exec_split_launches(plan) : lc_exec_cuda_cores_launches(plan);
+  return LC_OK;
+}
+
+static lc_status dispatch(lc_plan plan, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob,
+                          int64_t oe, lc_stream stream, int adjoint) {
+  if (!plan || !in || !out) return LC_ERR_INVALID_ARG;
+  if (ib < 0 || ie < 0 || ob < 0 || oe < 0) return LC_ERR_INVALID_ARG;
+  if (plan->ragged) {
+    if (ib != 0 || ob != 0 || ie != 1 || oe != 1) return LC_ERR_INVALID_ARG;
+  } else {
+    if (oe == 0 && plan->g.n > 1) return LC_ERR_INVALID_ARG;
+    if (ob == 0 && plan->batch > 1) return LC_ERR_INVALID_ARG;
+  }
+  if (in == out) return LC_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  switch (plan->dtype) {
+    case LC_F64:
+    case LC_F32: return lc_exec_cuda_cores(plan, in, out, ib, ie, ob, oe, s, adjoint);
+    case LC_F64_DF: return lc_exec_df(plan, in, out, ib, ie, ob, oe, s, adjoint);
+    case LC_F64_SPLIT: return lc_exec_split(plan, in, out, ib, ie, ob, oe, s, adjoint);
+  }
+  return LC_ERR_INVALID_ARG;
+}
+
+lc_status lc_execute(lc_plan plan, const void* in, void* out, int64_t in_batch_stride, int64_t in_elem_stride,
+                     int64_t out_batch_stride, int64_t out_elem_stride, lc_stream stream) {
+  return dispatch(plan, in, out, in_batch_stride, in_elem_stride, out_batch_stride, out_elem_stride, stream, 0);
+}
+
+lc_status lc_adjoint(lc_plan plan, const void* in, void* out, int64_t in_batch_stride, int64_t in_elem_stride,
+                     int64_t out_batch_stride, int64_t out_elem_stride, lc_stream stream) {
+  return dispatch(plan, in, out, in_batch_stride, in_elem_stride, out_batch_stride, out_elem_stride, stream, 1);
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+"""CPU checks of the C ABI: the library loads and exports every function that
+include/*.h declares; the host-side validation paths that need no GPU."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def _declared_functions():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = h.read_text()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:lc_status|const char\s*\*)\s+(lc_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    path = __graft_entry__._build_module().build()
+    return ctypes.CDLL(str(path))
+
+
+def test_header_declares_api():
+    names = _declared_functions()
+    for required in ("lc_plan_workspace_size", "lc_plan_create", "lc_execute", "lc_adjoint", "lc_destroy",
+                     "lc_plan_create_ragged", "lc_status_string"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    from paper_2411_00033_gb300 import binding
+    assert set(binding.EXPORTED) >= set(_declared_functions()) - {"lc_status_string"} or True
+    assert set(_declared_functions()) <= set(binding.EXPORTED) | {"lc_status_string"}
+
+
+def test_workspace_size_and_validation():
+    from paper_2411_00033_gb300 import binding as B
+    assert B.lc_plan_workspace_size(1024, B.LC_L2C, 1, B.LC_F64) > 0
+    # N = 1e6 plan: A-hat dominates (N_c * 324 doubles)
+    big = B.lc_plan_workspace_size(1_000_000, B.LC_L2C, 1, B.LC_F64)
+    assert 49107 * 324 * 8 < big < 49107 * 324 * 8 + 40_000_000
+    for bad in [(0, 0, 1, 0), (10, 2, 1, 0), (10, 0, 0, 0), (10, 0, 1, 9)]:
+        with pytest.raises(B.LegChebError) as e:
+            B.lc_plan_workspace_size(*bad)
+        assert e.value.status == 1
+    opts = B.lc_plan_options_default()
+    assert (opts.s_hat, opts.fixed_s, opts.slices) == (32, 0, 6)
+    assert "INVALID" in B.lc_status_string(1)
+
+
+def test_plan_create_rejects_small_workspace_without_touching_gpu():
+    from paper_2411_00033_gb300 import binding as B
+    with pytest.raises(B.LegChebError) as e:
+        B.lc_plan_create(1024, B.LC_L2C, 1, B.LC_F64, 256, 16, 0)
+    assert e.value.status == 2
+    with pytest.raises(B.LegChebError) as e:
+        B.lc_plan_create(1024, B.LC_L2C, 1, B.LC_F64, 0, 1 << 30, 0)
+    assert e.value.status == 1
+    with pytest.raises(B.LegChebError) as e:   # misaligned workspace
+        B.lc_plan_create(1024, B.LC_L2C, 1, B.LC_F64, 1 << 20 | 8, 1 << 30, 0)
+    assert e.value.status == 1
+
+
+def test_null_plan_calls_fail_cleanly(lib):
+    from paper_2411_00033_gb300 import binding as B
+    B.load()
+    with pytest.raises(B.LegChebError):
+        B.lc_execute(None, 1, 2, 0, 1, 0, 1, 0)
+    with pytest.raises(B.LegChebError):
+        B.lc_destroy(None)

@@ -1,0 +1,149 @@
+"""GPU parity against the CPU oracle (plain FP64 and FP32 tiers).
+
+Tolerances: normwise relative error (E_2) <= 1e-13 for n <= 1e5 and <= 1e-12
+at n = 1e6 for FP64 output; <= 2e-6 for the FP32 tier.  E_inf (eq:Einf) is
+checked with the same bounds for L2C and a looser bound for C2L, whose
+far-field approximation of L(x,y) is the weaker one (Table 1 of the paper
+reports C2L errors growing to 2e-13 at N = 32768 for undecaying input).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_util import rel_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DIRS = [("l2c", oracle.L2C), ("c2l", oracle.C2L)]
+
+
+@pytest.fixture(scope="module")
+def lc():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_00033_gb300 as m
+    return m
+
+
+def _run(lc, x, direction, dtype="f64", batch=1, **opts):
+    dev = torch.device("cuda", 0)
+    xt = torch.as_tensor(x, device=dev, dtype=torch.float32 if dtype == "f32" else torch.float64)
+    plan = lc.Plan(x.shape[-1], direction, batch, dtype, dev, **opts)
+    out = plan(xt)
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy(), plan
+
+
+def _input(n, seed=0):
+    if n <= 4096:
+        return workloads.uniform_vector(n, seed=seed)
+    return workloads.decaying_vector(n, seed=seed, r=0.5)
+
+
+SIZES = [1, 2, 3, 5, 17, 64, 127, 128, 129, 200, 255, 256, 257, 500, 1000, 1023, 1024, 1025, 2047, 4096, 5000,
+         16384, 33333]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_f64_matches_oracle(lc, n, direction, code):
+    x = _input(n, seed=n)
+    z, plan = _run(lc, x, direction)
+    ref = oracle.apply(code, x)
+    e2, einf = rel_errors(z, ref)
+    assert e2 <= 1e-13, (n, direction, e2, einf, plan.info)
+    assert einf <= (1e-13 if code == oracle.L2C else 3e-13), (n, direction, e2, einf)
+
+
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_config_n1024_uniform(lc, direction, code):
+    x = workloads.uniform_vector(1024, seed=0)
+    z, plan = _run(lc, x, direction)
+    assert plan.info["L"] == 3 and plan.info["s"] == 32 and plan.info["n_c"] == 33
+    e2, einf = rel_errors(z, oracle.apply(code, x))
+    assert e2 <= 1e-13 and einf <= 1e-13, (e2, einf)
+
+
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_config_n1e6_sampled_rows(lc, direction, code):
+    n = 1_000_000
+    x = workloads.decaying_vector(n, seed=1, r=1.0)
+    z, plan = _run(lc, x, direction)
+    assert (plan.info["L"], plan.info["s"], plan.info["N"]) == (13, 31, 1_015_808)
+    rows = workloads.sample_rows(n, 4096)
+    ref = oracle.apply(code, x, rows=rows)
+    e2, einf = rel_errors(z[rows], ref)
+    assert e2 <= 1e-12 and einf <= 1e-12, (e2, einf)
+
+
+@pytest.mark.parametrize("n", [100, 1024, 40000])
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_f32_tier(lc, n, direction, code):
+    x = _input(n, seed=3)
+    z, _ = _run(lc, x, direction, dtype="f32")
+    ref = oracle.apply(code, x.astype(np.float32).astype(np.float64))
+    e2, einf = rel_errors(z, ref)
+    assert e2 <= 2e-6, (e2, einf)
+
+
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_batched_strided_fibres(lc, direction, code):
+    n, batch = 3001, 3
+    X = np.stack([_input(n, seed=40 + b) for b in range(batch)], axis=1)  # (n, batch): fibres along axis 0
+    dev = torch.device("cuda", 0)
+    xt = torch.as_tensor(X, device=dev)
+    plan = lc.Plan(n, direction, batch, "f64", dev)
+    out = torch.empty((batch, n), dtype=torch.float64, device=dev)
+    plan.execute_strided(xt, out, (1, batch), (n, 1))
+    z = out.cpu().numpy()
+    for b in range(batch):
+        e2, einf = rel_errors(z[b], oracle.apply(code, X[:, b]))
+        assert e2 <= 1e-13, (b, e2)
+
+
+@pytest.mark.parametrize("n", [1, 2, 100, 129, 1024, 5000])
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_adjoint_matches_oracle_transpose(lc, n, direction, code):
+    r = _input(n, seed=7 + n)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, direction, 1, "f64", dev)
+    g = plan(torch.as_tensor(r, device=dev), adjoint=True).cpu().numpy()
+    ref = oracle.apply(code, r, adjoint=True)
+    e2, einf = rel_errors(g, ref)
+    assert e2 <= 1e-13, (e2, einf)
+
+
+@pytest.mark.parametrize("direction", ["l2c", "c2l"])
+def test_adjoint_dot_product(lc, direction):
+    n = 20000
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(n) / np.arange(1, n + 1)
+    y = rng.standard_normal(n) / np.arange(1, n + 1)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, direction, 1, "f64", dev)
+    Ax = plan(torch.as_tensor(x, device=dev)).cpu().numpy()
+    Aty = plan(torch.as_tensor(y, device=dev), adjoint=True).cpu().numpy()
+    lhs, rhs = Ax @ y, x @ Aty
+    assert abs(lhs - rhs) <= 1e-13 * (np.abs(Ax) @ np.abs(y))
+
+
+def test_round_trip_l2c_c2l(lc):
+    n = 65536
+    x = workloads.decaying_vector(n, seed=12, r=0.5)
+    dev = torch.device("cuda", 0)
+    z = lc.Plan(n, "l2c", 1, "f64", dev)(torch.as_tensor(x, device=dev))
+    back = lc.Plan(n, "c2l", 1, "f64", dev)(z).cpu().numpy()
+    assert np.abs(back - x).max() <= 1e-13 * np.abs(x).max()
+
+
+def test_fixed_s_option_same_map(lc):
+    n = 10000
+    x = _input(n, seed=2)
+    for code, direction in ((oracle.L2C, "l2c"), (oracle.C2L, "c2l")):
+        ref = oracle.apply(code, x)
+        for opts in ({"fixed_s": 32}, {"fixed_s": 20}, {"s_hat": 24}, {"fixed_s": 16}):
+            z, plan = _run(lc, x, direction, **opts)
+            e2, _ = rel_errors(z, ref)
+            assert e2 <= 1e-13, (opts, plan.info, e2)
