@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark: transformed coefficients per second at n = 1e6 on GB300.
+
+Workload (one "step"): the single-vector n = 1,000,000 transform in both
+directions -- Legendre->Chebyshev and Chebyshev->Legendre -- of the same
+vector, coefficients N(0,1) (j+1)^-1 from seed 1 (float64, host PCG64).
+Inputs are resident in HBM; the L2 cache (129 MB) is flushed by writing a
+256 MB buffer before every timed step (outside the step's events).
+
+Reported (one JSON line on rank 0):
+  value        2n / device time per step, for the fastest FP64-accurate tier
+  e2e          same metric through the C ABI with pinned host buffers
+               (host->device copy of both inputs and device->host copy of
+               both outputs inside the timed region)
+  accuracy     E_2 / E_inf of the timed tier on sampled output rows against
+               the CPU oracle (the same rows the cpu_baseline leg computes)
+  tiers        coefficients/s of every FP64-accurate tier, including the
+               plain FP64 path
+  roofline     the dominant kernel's achieved FP64 rate (or bytes) per launch
+               over its CUDA-event duration in the timed region
+  cpu_baseline the oracle (direct O(n^2) double-double sum) on the host's
+               cores, on a bounded sample of the same workload's rows
+
+--impl reference times the oracle itself (the only reference this project
+has) on the same workload and prints the same line with "impl": "reference".
+Multi-GPU (torchrun): every rank transforms its own copy (replicas; the
+transform has no exchange step), value = all ranks' coefficients / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_COEF = 1_000_000
+PAPER_COEF_PER_S = 1_000_000 / 0.020   # paper: ~20 ms per 1e6 L2C, 1 core of an M3 Pro (context only)
+CPU_ROWS = 2048                         # oracle rows per direction for the CPU baseline / accuracy sample
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+# DRAM bytes per launch of the dominant kernel, from the ncu capture summarised in
+# profiles/f64_single_n1e6.md (dram__bytes_read.sum + dram__bytes_write.sum).
+TRAFFIC = {("f64", 4): 20.68e6}
+KIND_NAMES = {0: "leaf_restrict", 1: "upward", 2: "couple", 3: "downward", 4: "spread_near_scale", 5: "prepare",
+              6: "other"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tier", default="auto", help="f64 | f64_df | f64_split | auto (fastest FP64-accurate)")
+    ap.add_argument("--cpu-rows", type=int, default=CPU_ROWS)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_leg(n, x, rows_per_dir):
+    """Time the oracle on `rows_per_dir` sampled rows of each direction."""
+    import numpy as np
+    import oracle
+    import workloads
+    rows = workloads.sample_rows(n, 4096)
+    rng = np.random.default_rng(12345)
+    pick = np.sort(rng.choice(rows, size=min(rows_per_dir, rows.size), replace=False))
+    t0 = time.perf_counter()
+    ref_l2c = oracle.apply(oracle.L2C, x, rows=pick)
+    ref_c2l = oracle.apply(oracle.C2L, x, rows=pick)
+    dt = time.perf_counter() - t0
+    return pick, ref_l2c, ref_c2l, dt, oracle.threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import workloads
+    n = N_COEF
+    x = workloads.decaying_vector(n, seed=1, r=1.0)
+    rows_all = workloads.sample_rows(n, 4096)
+    per_step = max(1, args.cpu_rows // max(1, args.steps + args.warmup))
+    rng = np.random.default_rng(777)
+    times = []
+    for k in range(args.warmup + args.steps):
+        pick = np.sort(rng.choice(rows_all, size=per_step, replace=False))
+        t0 = time.perf_counter()
+        oracle.apply(oracle.L2C, x, rows=pick)
+        oracle.apply(oracle.C2L, x, rows=pick)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = 2 * per_step / t
+    line = {
+        "impl": "reference", "metric": "transformed coefficients/s (n=1e6, L2C+C2L, FP64-accurate)",
+        "value": value, "unit": "coefficients/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_COEF_PER_S,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "n=1e6 single vector, L2C and C2L, N(0,1)(j+1)^-1 seed 1", "n": n, "batch": 1},
+        "cpu_baseline": {"value": value, "unit": "coefficients/s", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": "%d sampled output rows per direction per step of the n=1e6 transform "
+                                   "(direct double-double row sums)" % per_step},
+        "e2e": {"value": value, "unit": "coefficients/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- clock sampler
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our leg
+def near_field_nonzeros(n, L, s):
+    """Nonzeros of the direct band (Step 6) for rows < n."""
+    import numpy as np
+    i = np.arange(n, dtype=np.int64)
+    end = np.minimum(n, 2 * s * (i // (2 * s) + 2)) if L > 0 else np.full(n, n, np.int64)
+    return int(((end - i + 1) // 2).sum())
+
+
+def kernel_work(info, kind, direction):
+    """Algorithmic FP64 flops of one launch of a kernel kind (paper's counting, Sec. 4.2)."""
+    n, L, s, M, nc = info["n"], info["L"], info["s"], info["M"], info["n_c"]
+    if kind == 4:  # spread (2M per row) + near field (3 flops per nonzero, mu = 4.5) + scaling
+        return 2 * M * n + 3 * near_field_nonzeros(n, L, s) + n
+    if kind == 2:  # couple: 2 M^2 per submatrix per parity
+        return 4 * M * M * nc
+    if kind == 0:  # leaf: 2 M s per segment per parity
+        return 2 * 2 * M * s * ((2 << L) - 2)
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_00033_gb300 as lc
+    import workloads
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    n = N_COEF
+    x_host = workloads.decaying_vector(n, seed=1, r=1.0)
+    x = torch.from_numpy(x_host).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    available = ["f64", "f64_df", "f64_split"]
+    tiers = {}
+    for t in available:
+        try:
+            tiers[t] = (lc.Plan(n, "l2c", 1, t, dev), lc.Plan(n, "c2l", 1, t, dev))
+        except lc.LegChebError as e:
+            if e.status != 5:  # LC_ERR_UNSUPPORTED: tier not built for this request
+                raise
+    outs = (torch.empty_like(x), torch.empty_like(x))
+
+    def step(pl):
+        pl[0](x, out=outs[0])
+        pl[1](x, out=outs[1])
+
+    def time_tier(pl, steps, warmup, stage_timing=False):
+        for _ in range(warmup):
+            flush.fill_(1.0)
+            step(pl)
+        if stage_timing:
+            for p in pl:
+                lc.binding.lc_plan_set_timing(p._handle, steps)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush.fill_(float(k))
+            starts[k].record()
+            step(pl)
+            ends[k].record()
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        stages = None
+        if stage_timing:
+            stages = {}
+            for d, p in enumerate(pl):
+                per = {}
+                for k in range(steps):
+                    for kind, t in lc.binding.lc_plan_get_timing(p._handle, k):
+                        per.setdefault(kind, []).append(t)
+                stages[d] = per
+                lc.binding.lc_plan_set_timing(p._handle, 0)
+        return ms, wall, stages
+
+    # short timing of every tier to pick the fastest FP64-accurate one
+    quick = {}
+    for t, pl in tiers.items():
+        ms, _, _ = time_tier(pl, max(5, min(20, args.steps)), args.warmup)
+        quick[t] = statistics.median(ms)
+    chosen = args.tier if args.tier != "auto" else min(quick, key=quick.get)
+    pl = tiers[chosen]
+
+    clocks = ClockSampler(local if ws > 1 else 0)
+    ms, wall, stages = time_tier(pl, args.steps, args.warmup, stage_timing=True)
+    clk = clocks.stop()
+    ms_per_step = sum(ms) / len(ms)
+    if ws > 1:
+        t = torch.tensor([ms_per_step], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    value = ws * 2 * n / (ms_per_step / 1e3)
+
+    # per-tier numbers (median of a shorter run each)
+    tier_vals = {}
+    for t, p2 in tiers.items():
+        m2, _, _ = time_tier(p2, max(10, min(50, args.steps)), 2)
+        tier_vals[t] = {"coefficients_per_s": 2 * n / (statistics.median(m2) / 1e3),
+                        "ms_per_step_median": statistics.median(m2), "launches_per_step": p2[0].launches() + p2[1].launches()}
+
+    # end to end through the C ABI with pinned host buffers
+    h_in = (torch.from_numpy(x_host.copy()).pin_memory(), torch.from_numpy(x_host.copy()).pin_memory())
+    h_out = (torch.empty(n, dtype=torch.float64).pin_memory(), torch.empty(n, dtype=torch.float64).pin_memory())
+    d_in = (torch.empty_like(x), torch.empty_like(x))
+    e2e_steps = max(5, min(args.steps, 100))
+    for k in range(e2e_steps + 2):
+        if k == 2:
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+        for d in range(2):
+            d_in[d].copy_(h_in[d], non_blocking=True)
+            pl[d](d_in[d], out=outs[d])
+            h_out[d].copy_(outs[d], non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_val = ws * 2 * n / (e2e_ms / 1e3)
+
+    # dominant kernel and its roofline
+    info = pl[0].info
+    totals = {}
+    for d in stages:
+        for kind, ts in stages[d].items():
+            totals[kind] = totals.get(kind, 0.0) + sum(ts)
+    dom = max(totals, key=totals.get)
+    per_launch_ms = []
+    work = 0
+    for d in stages:
+        if dom in stages[d]:
+            per_launch_ms.extend(stages[d][dom])
+    avg_ms = sum(per_launch_ms) / len(per_launch_ms)
+    flops = kernel_work(info, dom, 0)
+    roofline = None
+    if flops is not None and chosen == "f64":
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get((chosen, dom)),
+                    "kernel": KIND_NAMES[dom], "avg_launch_ms": avg_ms,
+                    "peak_note": "FP64 nominal 1.26 TFLOP/s from 152 SMs x 2 FMA/clk x 2070 MHz; "
+                                 "a dependent-FMA microbenchmark reached 1.01"}
+    launches = sum(p.launches() for p in pl) * args.steps
+
+    line = {
+        "metric": "transformed coefficients/s (n=1e6, L2C+C2L, FP64-accurate)",
+        "value": value, "unit": "coefficients/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_COEF_PER_S, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "n=1e6 single vector, L2C and C2L, N(0,1)(j+1)^-1 seed 1",
+                   "n": n, "batch": 1, "tier": chosen, "plan": {k: info[k] for k in ("N", "L", "s", "M", "n_c")},
+                   "l2_flush": "256 MB write before every timed step", "parallelism": "replicas" if ws > 1 else "single"},
+        "e2e": {"value": e2e_val, "unit": "coefficients/s", "h2d_bytes_per_step": 2 * 8 * n,
+                "d2h_bytes_per_step": 2 * 8 * n},
+        "gpu_launches": launches,
+        "tiers": tier_vals,
+        "stage_ms_per_step": {KIND_NAMES[k]: v / args.steps for k, v in sorted(totals.items())},
+        "roofline": roofline,
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+
+    if rank == 0 and not args.no_cpu:
+        pick, ref_l2c, ref_c2l, dt, cores = oracle_leg(n, x_host, args.cpu_rows)
+        pl[0](x, out=outs[0])
+        pl[1](x, out=outs[1])
+        z = [outs[0].cpu().numpy()[pick], outs[1].cpu().numpy()[pick]]
+        acc = {}
+        for name, zz, rr in (("l2c", z[0], ref_l2c), ("c2l", z[1], ref_c2l)):
+            d = zz - rr
+            acc[name] = {"E_2": float(np.linalg.norm(d) / np.linalg.norm(rr)),
+                         "E_inf": float(np.abs(d).max() / np.abs(rr).max()), "rows": int(pick.size)}
+        line["accuracy"] = acc
+        line["cpu_baseline"] = {"value": 2 * pick.size / dt, "unit": "coefficients/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "%d sampled output rows per direction of the n=1e6 transform "
+                                          "(direct double-double row sums, %.1f s)" % (pick.size, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

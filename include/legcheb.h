@@ -178,6 +178,22 @@ lc_status lc_plan_table(lc_plan plan, int32_t which, double* dst, int64_t count,
 /* Number of kernels one lc_execute of this plan launches. */
 lc_status lc_plan_launches(lc_plan plan, int32_t* launches);
 
+/* Per-kernel timing with CUDA events (diagnostics, off by default).
+ * slots > 0 creates slots x (launches + 1) events (host API, no device
+ * memory); every later lc_execute / lc_adjoint records one event before
+ * each of its kernels and one after the last, into the next slot (round
+ * robin).  slots = 0 destroys the events and switches timing off.
+ * Not for use while the stream is being captured into a CUDA graph. */
+lc_status lc_plan_set_timing(lc_plan plan, int32_t slots);
+
+/* Kernel durations (ms) of the execution recorded in `slot`; waits for its
+ * events.  kinds[i] names kernel i: 0 leaf restriction (Step 1),
+ * 1 upward pass (Step 2), 2 coupling (Step 3), 3 downward pass (Step 4),
+ * 4 leaf spread + near field + scaling (Steps 5-7), 5 input preparation,
+ * 6 other.  ms and kinds may be NULL; *count receives the kernel count. */
+lc_status lc_plan_get_timing(lc_plan plan, int32_t slot, float* ms, int32_t* kinds, int32_t capacity,
+                             int32_t* count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ EXPORTED = (
     "lc_plan_options_default", "lc_plan_workspace_size", "lc_plan_workspace_size_ex",
     "lc_plan_create", "lc_plan_create_ex", "lc_plan_workspace_size_ragged", "lc_plan_create_ragged",
     "lc_execute", "lc_adjoint", "lc_destroy", "lc_status_string", "lc_plan_info", "lc_plan_table",
-    "lc_plan_launches",
+    "lc_plan_launches", "lc_plan_set_timing", "lc_plan_get_timing",
 )
 
 
@@ -72,6 +72,8 @@ def load(path: Path | None = None):
         "lc_plan_info": [vp, p64, p64, pi32, pi32, pi32, p64, p64],
         "lc_plan_table": [vp, i32, ctypes.POINTER(ctypes.c_double), i64, p64, vp],
         "lc_plan_launches": [vp, pi32],
+        "lc_plan_set_timing": [vp, i32],
+        "lc_plan_get_timing": [vp, i32, ctypes.POINTER(ctypes.c_float), pi32, i32, pi32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -177,3 +179,17 @@ def lc_plan_launches(plan) -> int:
     v = ctypes.c_int32()
     _check(load().lc_plan_launches(ctypes.c_void_p(plan), ctypes.byref(v)), "lc_plan_launches")
     return v.value
+
+
+def lc_plan_set_timing(plan, slots: int):
+    _check(load().lc_plan_set_timing(ctypes.c_void_p(plan), slots), "lc_plan_set_timing")
+
+
+def lc_plan_get_timing(plan, slot: int, capacity: int = 256):
+    """[(kind, ms)] for the kernels of the execution recorded in `slot`."""
+    ms = (ctypes.c_float * capacity)()
+    kinds = (ctypes.c_int32 * capacity)()
+    count = ctypes.c_int32()
+    _check(load().lc_plan_get_timing(ctypes.c_void_p(plan), slot, ms, kinds, capacity, ctypes.byref(count)),
+           "lc_plan_get_timing")
+    return [(int(kinds[i]), float(ms[i])) for i in range(min(count.value, capacity))]

@@ -294,8 +294,9 @@ __global__ void k_final_adj(Args<R> a) {
 }
 
 template <typename R>
-lc_status run(const lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
+lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
   const int L = a.L, s = a.s;
+  lc_timer_begin(p);
   const int gy = int(a.batch < 65535 ? a.batch : 65535);
   if (L > 0) {
     // leaf restriction: column segments [2, 2^(L+1)) forward, row segments [0, 2^(L+1)-2) transposed
@@ -303,6 +304,7 @@ lc_status run(const lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
     const int64_t hi = adjoint ? ((int64_t(2) << L) - 2) : (int64_t(2) << L);
     const size_t sm = (size_t(2) * s * LC_M + kSegs * 2 * s) * sizeof(R);
     dim3 grid(unsigned((hi - lo + kSegs - 1) / kSegs), gy);
+    lc_timer_mark(p, st, LC_K_LEAF);
     k_leaf<R><<<grid, kSegs * kThreadsSeg, sm, st>>>(a, lo, hi, (adjoint && a.dir == LC_L2C) ? 1 : 0);
     LC_LAUNCH_CHECK();
     for (int gc = L - 1; gc >= 1; --gc) {
@@ -310,10 +312,12 @@ lc_status run(const lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
       const int64_t plo = adjoint ? 0 : 2;
       const int64_t phi = adjoint ? ((int64_t(2) << gc) - 2) : (int64_t(2) << gc);
       dim3 g2(unsigned((phi - plo + kSegs - 1) / kSegs), gy);
+      lc_timer_mark(p, st, LC_K_UP);
       k_up<R><<<g2, kSegs * kThreadsSeg, 0, st>>>(a, gc, plo, phi);
       LC_LAUNCH_CHECK();
     }
     dim3 g3(unsigned((a.nseg + kCoupleSegs - 1) / kCoupleSegs), gy);
+    lc_timer_mark(p, st, LC_K_COUPLE);
     if (adjoint)
       k_couple<R, true><<<g3, kCoupleSegs * LC_M, 0, st>>>(a);
     else
@@ -324,16 +328,19 @@ lc_status run(const lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
       const int64_t clo = adjoint ? 4 : 0;
       const int64_t chi = adjoint ? (int64_t(8) << gp) : ((int64_t(8) << gp) - 4);
       dim3 g4(unsigned((chi - clo + kSegs - 1) / kSegs), gy);
+      lc_timer_mark(p, st, LC_K_DOWN);
       k_down<R><<<g4, kSegs * kThreadsSeg, 0, st>>>(a, gp, clo, chi);
       LC_LAUNCH_CHECK();
     }
   }
   dim3 g5(unsigned((a.n + kFinalThreads - 1) / kFinalThreads), gy);
+  lc_timer_mark(p, st, LC_K_FINAL);
   if (adjoint)
     k_final_adj<R><<<g5, kFinalThreads, 0, st>>>(a);
   else
     k_final<R><<<g5, kFinalThreads, 0, st>>>(a);
   LC_LAUNCH_CHECK();
+  lc_timer_end(p, st);
   return LC_OK;
 }
 

@@ -92,7 +92,39 @@ struct lc_plan_s {
   int64_t* h_off;
   void* ragged_dev;
   size_t bytes_used;
+  // Optional per-kernel timing (lc_plan_set_timing).
+  int timing_slots;
+  int timing_stride;       // events per slot
+  cudaEvent_t* events;     // [slots][stride]
+  int32_t* kinds;          // [slots][stride]
+  int* marks;              // events recorded per slot
+  int64_t exec_counter;
+  int cur_slot;
 };
+
+// Timing marks: call lc_timer_begin once per execution, lc_timer_mark before
+// each kernel (with its kind) and lc_timer_end after the last one.
+enum { LC_K_LEAF = 0, LC_K_UP = 1, LC_K_COUPLE = 2, LC_K_DOWN = 3, LC_K_FINAL = 4, LC_K_PREP = 5, LC_K_OTHER = 6 };
+inline void lc_timer_begin(lc_plan_s* p) {
+  if (p->timing_slots <= 0) return;
+  p->cur_slot = int(p->exec_counter++ % p->timing_slots);
+  p->marks[p->cur_slot] = 0;
+}
+inline void lc_timer_mark(lc_plan_s* p, cudaStream_t st, int kind) {
+  if (p->timing_slots <= 0) return;
+  int& m = p->marks[p->cur_slot];
+  if (m >= p->timing_stride - 1) return;
+  cudaEventRecord(p->events[p->cur_slot * p->timing_stride + m], st);
+  p->kinds[p->cur_slot * p->timing_stride + m] = kind;
+  ++m;
+}
+inline void lc_timer_end(lc_plan_s* p, cudaStream_t st) {
+  if (p->timing_slots <= 0) return;
+  int& m = p->marks[p->cur_slot];
+  cudaEventRecord(p->events[p->cur_slot * p->timing_stride + m], st);
+  p->kinds[p->cur_slot * p->timing_stride + m] = -1;
+  ++m;
+}
 
 // ---- error helpers ---------------------------------------------------------
 #define LC_CUDA_TRY(expr)                        \

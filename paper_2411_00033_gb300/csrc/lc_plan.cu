@@ -395,8 +395,52 @@ lc_status lc_plan_create(lc_plan* out, int64_t n, lc_direction direction, int64_
   return lc_plan_create_ex(out, n, direction, batch, dtype, nullptr, workspace, bytes, stream);
 }
 
+lc_status lc_plan_set_timing(lc_plan plan, int32_t slots) {
+  if (!plan || slots < 0 || slots > 100000) return LC_ERR_INVALID_ARG;
+  if (plan->events) {
+    for (int i = 0; i < plan->timing_slots * plan->timing_stride; ++i) cudaEventDestroy(plan->events[i]);
+    free(plan->events);
+    free(plan->kinds);
+    free(plan->marks);
+    plan->events = nullptr;
+    plan->kinds = nullptr;
+    plan->marks = nullptr;
+  }
+  plan->timing_slots = 0;
+  if (slots == 0) return LC_OK;
+  int32_t launches = 0;
+  lc_plan_launches(plan, &launches);
+  const int stride = launches + 2;
+  plan->events = static_cast<cudaEvent_t*>(calloc(size_t(slots) * stride, sizeof(cudaEvent_t)));
+  plan->kinds = static_cast<int32_t*>(calloc(size_t(slots) * stride, sizeof(int32_t)));
+  plan->marks = static_cast<int*>(calloc(size_t(slots), sizeof(int)));
+  if (!plan->events || !plan->kinds || !plan->marks) return LC_ERR_HOST_ALLOC;
+  for (int i = 0; i < slots * stride; ++i) LC_CUDA_TRY(cudaEventCreate(&plan->events[i]));
+  plan->timing_stride = stride;
+  plan->timing_slots = slots;
+  plan->exec_counter = 0;
+  return LC_OK;
+}
+
+lc_status lc_plan_get_timing(lc_plan plan, int32_t slot, float* ms, int32_t* kinds, int32_t capacity,
+                             int32_t* count) {
+  if (!plan || !count || plan->timing_slots <= 0 || slot < 0 || slot >= plan->timing_slots) return LC_ERR_INVALID_ARG;
+  const int m = plan->marks[slot];
+  const int n = m > 0 ? m - 1 : 0;
+  *count = n;
+  if (n == 0) return LC_OK;
+  cudaEvent_t* ev = plan->events + size_t(slot) * plan->timing_stride;
+  LC_CUDA_TRY(cudaEventSynchronize(ev[n]));
+  for (int i = 0; i < n && i < capacity; ++i) {
+    if (ms) LC_CUDA_TRY(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+    if (kinds) kinds[i] = plan->kinds[size_t(slot) * plan->timing_stride + i];
+  }
+  return LC_OK;
+}
+
 lc_status lc_destroy(lc_plan plan) {
   if (!plan) return LC_ERR_INVALID_ARG;
+  lc_plan_set_timing(plan, 0);
   free(plan->h_len);
   free(plan->h_off);
   free(plan);
