@@ -194,6 +194,34 @@ lc_status lc_plan_set_timing(lc_plan plan, int32_t slots);
 lc_status lc_plan_get_timing(lc_plan plan, int32_t slot, float* ms, int32_t* kinds, int32_t capacity,
                              int32_t* count);
 
+/* ---- Transform without any device allocation ------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory (a plugin inside an application whose memory
+ * pool owns the device, a latency-critical loop that cannot afford the
+ * device-wide synchronisation cudaMalloc may cause, a deployment that
+ * reserves all memory at load time).  It computes the same maps as
+ * lc_execute, out[b][i] = (M x_b)_i for i < n with M = C^{-1}A (LC_L2C) or
+ * A^{-1}C (LC_C2L), FP64 in and out, by the direct O(n^2) sum over the whole
+ * upper triangle.  Its scratch (the Lambda table) lives in a file-scope
+ * __device__ array of LC_STATIC_MAX_N x 2 doubles (256 KiB) that every GPU
+ * loading the library holds until the process exits; it calls no cudaMalloc
+ * or cudaFree.
+ *  - n > LC_STATIC_MAX_N (or n < 1, batch < 1, NULL or aliased pointers,
+ *    negative strides) returns LC_ERR_INVALID_ARG and launches nothing.
+ *  - Pointers, strides and batch follow lc_execute; x and out are device
+ *    memory of the caller.
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress (once per device, with that device current); make
+ *    that first call before any stream capture begins.
+ *  - All calls share the one array: calls whose executions overlap on the
+ *    GPU (different streams, or concurrent host threads) race on it and give
+ *    wrong results.  Calls ordered on one stream are safe; each call rewrites
+ *    the part of the table it reads before reading it. */
+#define LC_STATIC_MAX_N 16384
+lc_status lc_direct_static(lc_direction direction, int64_t n, int64_t batch, const double* in, double* out,
+                           int64_t in_batch_stride, int64_t in_elem_stride, int64_t out_batch_stride,
+                           int64_t out_elem_stride, lc_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ EXPORTED = (
     "lc_plan_options_default", "lc_plan_workspace_size", "lc_plan_workspace_size_ex",
     "lc_plan_create", "lc_plan_create_ex", "lc_plan_workspace_size_ragged", "lc_plan_create_ragged",
     "lc_execute", "lc_adjoint", "lc_destroy", "lc_status_string", "lc_plan_info", "lc_plan_table",
-    "lc_plan_launches", "lc_plan_set_timing", "lc_plan_get_timing",
+    "lc_plan_launches", "lc_plan_set_timing", "lc_plan_get_timing", "lc_direct_static",
 )
 
 
@@ -193,3 +193,14 @@ def lc_plan_get_timing(plan, slot: int, capacity: int = 256):
     _check(load().lc_plan_get_timing(ctypes.c_void_p(plan), slot, ms, kinds, capacity, ctypes.byref(count)),
            "lc_plan_get_timing")
     return [(int(kinds[i]), float(ms[i])) for i in range(min(count.value, capacity))]
+
+
+def lc_direct_static(direction, n, batch, in_ptr, out_ptr, ib, ie, ob, oe, stream_ptr):
+    """Direct transform whose only scratch is a static device array (no allocation)."""
+    lib = load()
+    f = lib.lc_direct_static
+    f.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(direction, n, batch, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), ib, ie, ob, oe,
+             ctypes.c_void_p(stream_ptr)), "lc_direct_static")
