@@ -154,3 +154,4 @@ lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st)
 lc_status lc_exec_split(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob,
                         int64_t oe, cudaStream_t st, int adjoint);
 int lc_exec_split_launches(const lc_plan_s* p);
+void lc_split_release(lc_plan p);

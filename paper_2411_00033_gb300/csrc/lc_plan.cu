@@ -288,6 +288,39 @@ lc_status fill_plan(lc_plan_s* p, int64_t n, lc_direction dir, int64_t batch, lc
   return LC_OK;
 }
 
+lc_status fill_ragged(lc_plan_s* p, const int64_t* n, int64_t count, lc_direction dir, lc_dtype dtype,
+                      const lc_plan_options* opt) {
+  if (!n || count < 1 || count > (int64_t(1) << 31)) return LC_ERR_INVALID_ARG;
+  if (!valid_enum(dir, dtype)) return LC_ERR_INVALID_ARG;
+  if (dtype != LC_F64_SPLIT) return LC_ERR_UNSUPPORTED;
+  memset(p, 0, sizeof(*p));
+  lc_plan_options_default(&p->opt);
+  if (opt) p->opt = *opt;
+  if (p->opt.fixed_s == 0) p->opt.fixed_s = 32;  // one s shared by every member
+  if (p->opt.slices < 3 || p->opt.slices > 7) return LC_ERR_INVALID_ARG;
+  int64_t nmax = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    if (n[i] < 1) return LC_ERR_INVALID_ARG;
+    if (n[i] > nmax) nmax = n[i];
+  }
+  lc_status st = lc_compute_geometry(nmax, &p->opt, 1, &p->g);
+  if (st != LC_OK) return st;
+  p->dir = dir;
+  p->dtype = dtype;
+  p->batch = count;
+  p->count = count;
+  p->ragged = 1;
+  p->h_len = static_cast<int64_t*>(malloc(sizeof(int64_t) * size_t(count)));
+  p->h_off = static_cast<int64_t*>(malloc(sizeof(int64_t) * size_t(count + 1)));
+  if (!p->h_len || !p->h_off) return LC_ERR_HOST_ALLOC;
+  p->h_off[0] = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    p->h_len[i] = n[i];
+    p->h_off[i + 1] = p->h_off[i] + n[i];
+  }
+  return LC_OK;
+}
+
 int grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -383,6 +416,7 @@ lc_status lc_plan_create_ex(lc_plan* out, int64_t n, lc_direction direction, int
   st = build_tables(p, s);
   if (st == LC_OK && dtype == LC_F64_SPLIT) st = lc_split_prepare(p, static_cast<char*>(p->split), lc_split_bytes(p), s);
   if (st != LC_OK) {
+    lc_split_release(p);
     free(p);
     return st;
   }
@@ -441,6 +475,7 @@ lc_status lc_plan_get_timing(lc_plan plan, int32_t slot, float* ms, int32_t* kin
 lc_status lc_destroy(lc_plan plan) {
   if (!plan) return LC_ERR_INVALID_ARG;
   lc_plan_set_timing(plan, 0);
+  lc_split_release(plan);
   free(plan->h_len);
   free(plan->h_off);
   free(plan);
@@ -458,6 +493,47 @@ const char* lc_status_string(lc_status status) {
     case LC_ERR_HOST_ALLOC: return "LC_ERR_HOST_ALLOC: host allocation failed";
   }
   return "unknown lc_status";
+}
+
+lc_status lc_plan_workspace_size_ragged(const int64_t* n, int64_t count, lc_direction direction, lc_dtype dtype,
+                                        const lc_plan_options* opt, size_t* bytes) {
+  if (!bytes) return LC_ERR_INVALID_ARG;
+  lc_plan_s p;
+  lc_status st = fill_ragged(&p, n, count, direction, dtype, opt);
+  if (st == LC_OK) *bytes = layout(&p, nullptr);
+  free(p.h_len);
+  free(p.h_off);
+  return st;
+}
+
+lc_status lc_plan_create_ragged(lc_plan* out, const int64_t* n, int64_t count, lc_direction direction,
+                                lc_dtype dtype, const lc_plan_options* opt, void* workspace, size_t bytes,
+                                lc_stream stream) {
+  if (!out || !workspace) return LC_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return LC_ERR_INVALID_ARG;
+  *out = nullptr;
+  lc_plan_s* p = static_cast<lc_plan_s*>(malloc(sizeof(lc_plan_s)));
+  if (!p) return LC_ERR_HOST_ALLOC;
+  lc_status st = fill_ragged(p, n, count, direction, dtype, opt);
+  if (st == LC_OK) {
+    const size_t need = layout(p, nullptr);
+    if (bytes < need) st = LC_ERR_WORKSPACE_TOO_SMALL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (st == LC_OK) {
+    p->bytes_used = layout(p, static_cast<char*>(workspace));
+    st = build_tables(p, s);
+  }
+  if (st == LC_OK) st = lc_split_prepare(p, static_cast<char*>(p->split), lc_split_bytes(p), s);
+  if (st != LC_OK) {
+    lc_split_release(p);
+    free(p->h_len);
+    free(p->h_off);
+    free(p);
+    return st;
+  }
+  *out = p;
+  return LC_OK;
 }
 
 lc_status lc_plan_info(lc_plan plan, int64_t* n, int64_t* N, int32_t* L, int32_t* s, int32_t* M,

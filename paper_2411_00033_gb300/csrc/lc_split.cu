@@ -1,20 +1,991 @@
-// lc_split.cu -- split-precision tensor-core tier, LC_F64_SPLIT.
+// lc_split.cu -- split-precision tensor-core tier (LC_F64_SPLIT) for batches.
+//
+// When many vectors share one plan, every step of Algorithm 4 becomes a
+// matrix product whose left operand holds one row per vector:
+//   leaf    W(g)      = F(g) T(sigma)                  (Step 1, eq:wMM)
+//   up      W(G)      = [W(2G) W(2G+1)] [B(0) B(1)]^T   (Step 2, eq:wtk)
+//   couple  C(v)      = [W(v+2) W(v+3)] [A-hat A-hat]^T (Step 3)
+//   down    C(v)     += C(v/2) B(v mod 2)              (Step 4)
+//   final   Z(strip)  = C(v) T(sigma)^T + F(strip) E^T (Steps 5-6), then C^{-1} (Step 7)
+// (E = the near-field block of the strip.)  Each product runs on the bf16
+// tensor cores (mma.sync m16n8k16, FP32 accumulation) as an exact
+// multi-word product: every operand row/column is scaled by a power of two
+// and cut into S signed 8-bit slices (|q| <= 128, exact in bf16), so each
+// slice product is an exact integer below 2^14 and every FP32 partial sum
+// over K <= 64 terms and <= S slice pairs stays below 2^24 -- exact.  The
+// slice pairs (s, t) with s + t <= S + 1 are accumulated per diagonal
+// u = s + t and recombined by a Horner sum in base 2^8 in double-float
+// (pairs of FP32).  Shared matrices are sliced once at plan time (FP64).
+//
+// Per-vector intermediates are stored as "block floating" double-float rows:
+// 18 (hi, lo) pairs scaled into [-1/2, 1/2] plus one power-of-two exponent
+// per row, so the next product slices them without another scan.  Only the
+// final output conversion touches the FP64 pipe (one add per coefficient).
+//
+// Batches: members are sorted by length (descending).  At every level the
+// members owning a segment form a prefix of that order, so each CTA takes
+// one (segment, parity, 64-member tile).  A uniform batch is the special
+// case of equal lengths; a ragged batch shares one coefficient table built
+// for its longest member with a fixed s (A-hat depends only on the position
+// of a submatrix in A, eq:globalij).
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "lc_internal.cuh"
 
-size_t lc_split_bytes(const lc_plan_s*) { return 0; }
-lc_status lc_split_prepare(lc_plan, char*, size_t, cudaStream_t) { return LC_ERR_UNSUPPORTED; }
-lc_status lc_exec_split(lc_plan, const void*, void*, int64_t, int64_t, int64_t, int64_t, cudaStream_t, int) {
-  return LC_ERR_UNSUPPORTED;
-}
-int lc_exec_split_launches(const lc_plan_s*) { return 0; }
+namespace {
 
-extern "C" {
-lc_status lc_plan_workspace_size_ragged(const int64_t*, int64_t, lc_direction, lc_dtype, const lc_plan_options*,
-                                        size_t*) {
-  return LC_ERR_UNSUPPORTED;
+constexpr int kRows = 64;       // members per CTA tile (4 warps x 16 rows)
+constexpr int kThreads = 128;
+constexpr int kNP18 = 24;       // 18 outputs padded to 3 n8 tiles
+
+enum YKind { Y_LEAF = 0, Y_SPREAD = 1, Y_UP = 2, Y_DOWN = 3, Y_COUPLE = 4, Y_NEAR = 5, Y_KINDS = 6 };
+
+struct YTable {
+  int items, K, KP, NP;  // KP: K rounded up to 16; NP: padded outputs
+  size_t off_q, off_e;   // byte offsets in the split region: bf16 [items][S][NP][KP], int32 [items][NP]
+};
+
+struct Work {
+  int32_t d, seg, tile;
+};
+
+struct SplitHost {
+  int S, s, Lmax;
+  int64_t count, Nmax, nstrips;
+  std::vector<int64_t> len_sorted, orig, off_sorted;  // sorted order
+  std::vector<int32_t> Lm;
+  std::vector<int64_t> Lcount;                        // [Lmax + 2]
+  std::vector<int64_t> cntN;                          // [nstrips]
+  std::vector<int64_t> rowbase;                       // concatenated over d
+  int64_t rows;
+  YTable y[Y_KINDS];
+  // work lists: launches in execution order
+  std::vector<Work> work;
+  std::vector<int64_t> launch_off;   // [launches + 1]
+  std::vector<int> launch_kind;      // LC_K_*
+  std::vector<int> launch_level;     // d for up/down
+  // device byte offsets
+  size_t off_len, off_orig, off_off, off_Lcount, off_cntN, off_rowbase, off_work;
+  size_t off_W, off_We, off_C, off_Ce;
+  size_t total;
+};
+
+// cnt(d, g): members owning segment g at relative level d (levels counted
+// from the leaves), given Lcount[l] = #members with L_m >= l.
+inline int64_t seg_threshold(int d, int64_t g) {
+  int lg = 0;
+  while ((int64_t(2) << lg) <= g) ++lg;  // floor(log2 g) for g >= 1
+  if (g < 1) lg = 0;
+  return d + (lg > 1 ? lg : 1);
 }
-lc_status lc_plan_create_ragged(lc_plan*, const int64_t*, int64_t, lc_direction, lc_dtype, const lc_plan_options*,
-                                void*, size_t, lc_stream) {
-  return LC_ERR_UNSUPPORTED;
+
+int member_levels(int64_t n, int s) {
+  if (n <= 4 * int64_t(s)) return 0;
+  int t = 0;
+  while ((int64_t(s) << t) < n) ++t;
+  return t - 2;
 }
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Build all host tables and the byte layout of the split region.
+void build_host(const lc_plan_s* p, SplitHost& h) {
+  h.S = p->opt.slices;
+  h.s = p->g.s;
+  h.Lmax = p->g.L;
+  h.Nmax = p->g.N;
+  h.count = p->count;
+  std::vector<int64_t> len(h.count), off(h.count);
+  int64_t acc = 0;
+  for (int64_t m = 0; m < h.count; ++m) {
+    len[m] = p->ragged ? p->h_len[m] : p->g.n;
+    off[m] = acc;
+    acc += len[m];
+  }
+  std::vector<int64_t> order(h.count);
+  for (int64_t m = 0; m < h.count; ++m) order[m] = m;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return len[a] > len[b]; });
+  h.len_sorted.resize(h.count);
+  h.orig.resize(h.count);
+  h.off_sorted.resize(h.count);
+  h.Lm.resize(h.count);
+  for (int64_t r = 0; r < h.count; ++r) {
+    h.orig[r] = order[r];
+    h.len_sorted[r] = len[order[r]];
+    h.off_sorted[r] = off[order[r]];
+    h.Lm[r] = (h.Lmax > 0) ? member_levels(h.len_sorted[r], h.s) : 0;
+  }
+  h.Lcount.assign(h.Lmax + 2, 0);
+  for (int64_t r = 0; r < h.count; ++r)
+    for (int l = 0; l <= h.Lm[r] && l < h.Lmax + 2; ++l) h.Lcount[l]++;
+  auto cnt = [&](int d, int64_t g) -> int64_t {
+    const int64_t th = seg_threshold(d, g);
+    return th < int64_t(h.Lcount.size()) ? h.Lcount[th] : 0;
+  };
+  h.nstrips = (h.Nmax + 2 * h.s - 1) / (2 * h.s);
+  h.cntN.assign(h.nstrips, 0);
+  for (int64_t t = 0; t < h.nstrips; ++t) {
+    int64_t c = 0;
+    while (c < h.count && h.len_sorted[c] > 2 * int64_t(h.s) * t) ++c;
+    h.cntN[t] = c;
+  }
+  // row bases: per d, per g < 2^(Lmax+1-d): 2 x cnt(d, g) rows (sigma-major)
+  h.rowbase.clear();
+  h.rows = 0;
+  for (int d = 0; d < h.Lmax; ++d) {
+    const int64_t nseg = int64_t(1) << (h.Lmax + 1 - d);
+    for (int64_t g = 0; g < nseg; ++g) {
+      h.rowbase.push_back(h.rows);
+      h.rows += 2 * cnt(d, g);
+    }
+  }
+  if (h.rowbase.empty()) h.rowbase.push_back(0);
+  // work lists
+  h.work.clear();
+  h.launch_off.assign(1, 0);
+  h.launch_kind.clear();
+  h.launch_level.clear();
+  auto add_items = [&](int d, int64_t seg, int64_t members) {
+    for (int64_t t0 = 0; t0 < members; t0 += kRows) h.work.push_back(Work{d, int32_t(seg), int32_t(t0 / kRows)});
+  };
+  auto close_launch = [&](int kind, int level) {
+    h.launch_off.push_back(int64_t(h.work.size()));
+    h.launch_kind.push_back(kind);
+    h.launch_level.push_back(level);
+  };
+  if (h.Lmax > 0) {
+    for (int64_t g = 2; g < (int64_t(2) << h.Lmax); ++g) add_items(0, g, cnt(0, g));
+    close_launch(LC_K_LEAF, 0);
+    for (int d = 0; d + 1 < h.Lmax; ++d) {  // parents at d+1
+      for (int64_t G = 2; G < (int64_t(1) << (h.Lmax - d)); ++G) add_items(d + 1, G, cnt(d + 1, G));
+      close_launch(LC_K_UP, d);
+    }
+    for (int d = 0; d < h.Lmax; ++d)
+      for (int64_t v = 0; v + 2 < (int64_t(1) << (h.Lmax + 1 - d)); ++v) add_items(d, v, cnt(d, v + 2));
+    close_launch(LC_K_COUPLE, 0);
+    for (int d = h.Lmax - 2; d >= 0; --d) {  // children at d
+      for (int64_t v = 0; v + 4 < (int64_t(1) << (h.Lmax + 1 - d)); ++v) add_items(d, v, cnt(d, v + 4));
+      close_launch(LC_K_DOWN, d);
+    }
+  }
+  for (int64_t t = 0; t < h.nstrips; ++t) add_items(0, t, h.cntN[t]);
+  close_launch(LC_K_FINAL, 0);
+
+  // Y tables
+  const int s = h.s;
+  auto ktab = [&](YKind k, int items, int K, int NP) {
+    h.y[k].items = items;
+    h.y[k].K = K;
+    h.y[k].KP = std::max(32, (K + 15) / 16 * 16);
+    h.y[k].NP = NP;
+  };
+  int64_t nrowseg = 0;
+  for (int G = 0; G < h.Lmax; ++G) nrowseg += (int64_t(4) << G) - 2;
+  ktab(Y_LEAF, 2, s, kNP18);
+  ktab(Y_SPREAD, 2, LC_M, 32);
+  ktab(Y_UP, 1, 2 * LC_M, kNP18);
+  ktab(Y_DOWN, 2, LC_M, kNP18);
+  ktab(Y_COUPLE, int(nrowseg), 2 * LC_M, kNP18);
+  ktab(Y_NEAR, int(2 * h.nstrips), 2 * s, 32);
+
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    o = align256(o);
+    size_t r = o;
+    o += bytes;
+    return r;
+  };
+  for (int k = 0; k < Y_KINDS; ++k) {
+    YTable& y = h.y[k];
+    y.off_q = take(size_t(y.items) * h.S * y.NP * y.KP * 2);
+    y.off_e = take(size_t(y.items) * y.NP * 4);
+  }
+  h.off_len = take(size_t(h.count) * 8);
+  h.off_orig = take(size_t(h.count) * 8);
+  h.off_off = take(size_t(h.count) * 8);
+  h.off_Lcount = take(h.Lcount.size() * 8);
+  h.off_cntN = take(size_t(h.nstrips) * 8);
+  h.off_rowbase = take(h.rowbase.size() * 8);
+  h.off_work = take(h.work.size() * sizeof(Work));
+  h.off_W = take(size_t(h.rows) * LC_M * 8);
+  h.off_We = take(size_t(h.rows) * 4);
+  h.off_C = take(size_t(h.rows) * LC_M * 8);
+  h.off_Ce = take(size_t(h.rows) * 4);
+  h.total = align256(o) + 256;
 }
+
+// ------------------------------------------------------------ device helpers
+__device__ __forceinline__ float pow2f(int k) {
+  return (k < -126) ? 0.0f : (k > 127 ? __int_as_float(0x7f800000) : __uint_as_float(uint32_t(k + 127) << 23));
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+// Exponent k of a positive normal float v with v in [2^(k-1), 2^k).
+__device__ __forceinline__ int exp_of(float v) { return int((__float_as_uint(v) >> 23) & 0xff) - 126; }
+
+// x * 2^-e_row as a double-float, built from the bit pattern (no FP64 op).
+// Subnormal doubles and results below 2^-126 are flushed to zero.
+__device__ __forceinline__ void d2df_scaled(double x, int e_row, float& hi, float& lo) {
+  const uint64_t u = __double_as_longlong(x);
+  const int E = int((u >> 52) & 0x7ff);
+  if (E == 0) {
+    hi = lo = 0.0f;
+    return;
+  }
+  const uint64_t m = (u & ((uint64_t(1) << 52) - 1)) | (uint64_t(1) << 52);
+  const int k = E - 1075 - e_row;  // value = m * 2^k
+  const uint32_t mh = uint32_t(m >> 29);
+  const uint32_t ml = uint32_t(m & 0x1fffffffu);
+  const int eh = k + 29 + 23 + 127;
+  const uint32_t sgn = uint32_t(u >> 63) << 31;
+  hi = (eh >= 1 && eh <= 254) ? __uint_as_float(sgn | (uint32_t(eh) << 23) | (mh & 0x7fffffu)) : 0.0f;
+  float l = __uint2float_rn(ml) * pow2f(k);
+  lo = (sgn ? -l : l);
+  if (eh < 1) lo = 0.0f;
+}
+
+// f * 2^E as a double (exact for normal f), from the bit pattern.
+__device__ __forceinline__ double f2d_scaled(float f, int E) {
+  const uint32_t u = __float_as_uint(f);
+  const int ef = int((u >> 23) & 0xff);
+  if (ef == 0) return 0.0;
+  const int64_t ed = int64_t(ef) - 127 + 1023 + E;
+  if (ed <= 0) return 0.0;
+  const uint64_t sgn = uint64_t(u >> 31) << 63;
+  if (ed >= 2047) return __longlong_as_double(sgn | (uint64_t(2047) << 52));
+  return __longlong_as_double(sgn | (uint64_t(ed) << 52) | (uint64_t(u & 0x7fffffu) << 29));
+}
+
+__device__ __forceinline__ uint16_t bf16_of_int(float q) { return uint16_t(__float_as_uint(q) >> 16); }
+
+// Cut a double-float x (|x| <= 1/2) into S slices q_1..q_S in [-128, 128]:
+// x = sum_s q_s 2^(-8 s) + r, |r| <= 2^(-8S-1).  dst[s * stride] = bf16(q_s).
+__device__ __forceinline__ void slice_df(float hi, float lo, int S, uint16_t* dst, int stride) {
+  for (int s = 0; s < S; ++s) {
+    const float th = hi * 256.0f, tl = lo * 256.0f;
+    const float q = rintf(th);
+    const float rh = th - q;  // exact
+    two_sum(rh, tl, hi, lo);
+    dst[s * stride] = bf16_of_int(q);
+  }
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// Sliced product of this warp's 16 rows of X (smem [S][kRows][xs]) with Y
+// (smem [S][NT*8][ys]) over KT k16 tiles.  Result per fragment element:
+// hi + lo = sum_u P_u 2^(-8(u-2)), i.e. the product times 2^16 in units of
+// 2^(e_x + e_y).
+template <int KT, int NT>
+__device__ __forceinline__ void warp_ozaki(const uint16_t* Xs, int xs, const uint16_t* Ys, int ys, int S,
+                                           float (&hi)[NT][4], float (&lo)[NT][4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int xslice = kRows * xs, yslice = NT * 8 * ys;
+  const uint16_t* xw = Xs + warp * 16 * xs;
+  for (int u = S + 1; u >= 2; --u) {
+    float p[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) p[nt][i] = 0.0f;
+    const int s0 = (u - S > 1) ? u - S : 1;
+    const int s1 = (u - 1 < S) ? u - 1 : S;
+    for (int sx = s0; sx <= s1; ++sx) {
+      const uint16_t* xa = xw + (sx - 1) * xslice;
+      const uint16_t* yb = Ys + (u - sx - 1) * yslice;
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) {
+        const int kc = kt * 16 + 2 * t;
+        const uint32_t a0 = ld32(xa + g * xs + kc);
+        const uint32_t a1 = ld32(xa + (g + 8) * xs + kc);
+        const uint32_t a2 = ld32(xa + g * xs + kc + 8);
+        const uint32_t a3 = ld32(xa + (g + 8) * xs + kc + 8);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const uint16_t* yr = yb + (nt * 8 + g) * ys + kc;
+          mma_bf16(p[nt], a0, a1, a2, a3, ld32(yr), ld32(yr + 8));
+        }
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (u == S + 1) {
+          hi[nt][i] = p[nt][i];
+          lo[nt][i] = 0.0f;
+        } else {
+          float sh, se;
+          two_sum(hi[nt][i] * (1.0f / 256.0f), p[nt][i], sh, se);
+          fast_two_sum(sh, lo[nt][i] * (1.0f / 256.0f) + se, hi[nt][i], lo[nt][i]);
+        }
+      }
+  }
+}
+
+// Copy the Y slices of one table item into smem [S][NP][KP+8] plus exponents.
+__device__ __forceinline__ void load_y(const uint16_t* __restrict__ q, const int* __restrict__ e, int S, int NP,
+                                       int KP, uint16_t* Ys, int ys, int* Ye) {
+  const int per = KP / 2;  // 32-bit words per row
+  const int total = S * NP * per;
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(q);
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int row = i / per, w = i % per;
+    reinterpret_cast<uint32_t*>(Ys + row * ys)[w] = src[i];
+  }
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) Ye[i] = e[i];
+}
+
+struct Dev {
+  int S, s, Lmax;
+  int64_t count, Nmax, nstrips;
+  const int64_t* len;
+  const int64_t* orig;
+  const int64_t* off;
+  const int64_t* Lcount;
+  const int64_t* cntN;
+  const int64_t* rowbase;
+  const Work* work;
+  float2* W;
+  int* We;
+  float2* C;
+  int* Ce;
+  const uint16_t* yq[Y_KINDS];
+  const int* ye[Y_KINDS];
+  int yKP[Y_KINDS], yNP[Y_KINDS];
+  int dir;
+  int ragged;
+  // I/O
+  const double* in;
+  double* out;
+  int64_t ib, ie, ob, oe;
+};
+
+__device__ __forceinline__ int64_t dcnt(const Dev& D, int d, int64_t g) {
+  int lg = 0;
+  int64_t gg = g;
+  while (gg >= 2) {
+    gg >>= 1;
+    ++lg;
+  }
+  const int th = d + (lg > 1 ? lg : 1);
+  return th <= D.Lmax + 1 ? D.Lcount[th] : 0;
+}
+__device__ __forceinline__ int64_t drow(const Dev& D, int d, int64_t g, int sigma, int64_t r) {
+  const int64_t db = (int64_t(4) << D.Lmax) - (int64_t(4) << (D.Lmax - d));  // sum_{d'<d} 2^(Lmax+1-d')
+  return D.rowbase[db + g] + sigma * dcnt(D, d, g) + r;
+}
+__device__ __forceinline__ const double* in_base(const Dev& D, int64_t r) {
+  return D.in + (D.ragged ? D.off[r] : D.orig[r] * D.ib);
+}
+__device__ __forceinline__ double* out_base(const Dev& D, int64_t r) {
+  return D.out + (D.ragged ? D.off[r] : D.orig[r] * D.ob);
+}
+
+// Load one 18-wide double-float row pair (two segments) into a common
+// exponent frame and slice it into Xs: columns [c*18, c*18+18) from row c.
+// Rows beyond `valid` are zero.
+__device__ __forceinline__ void stage_rows_df(const Dev& D, const float2* A, const int* Ae, int64_t rowA0,
+                                              int64_t rowA1, int two, int64_t tile0, int64_t valid, int KP,
+                                              uint16_t* Xs, int xs, int* Xe) {
+  // one warp per 16 rows, lane = column
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int lr = warp * 16; lr < warp * 16 + 16; ++lr) {
+    const int64_t r = tile0 + lr;
+    const bool ok = r < valid;
+    int e0 = -100000, e1 = -100000;
+    if (ok) {
+      e0 = Ae[rowA0 + r];
+      if (two) e1 = Ae[rowA1 + r];
+    }
+    const int e = max(e0, e1);
+    for (int c = lane; c < KP; c += 32) {
+      float hi = 0.0f, lo = 0.0f;
+      if (ok && c < LC_M * (two ? 2 : 1)) {
+        const int part = c / LC_M, col = c % LC_M;
+        const float2 v = A[((part ? rowA1 : rowA0) + r) * LC_M + col];
+        const float sc = pow2f((part ? e1 : e0) - e);
+        hi = v.x * sc;
+        lo = v.y * sc;
+      }
+      slice_df(hi, lo, D.S, Xs + lr * xs + c, kRows * xs);
+    }
+    if (lane == 0) Xe[lr] = ok ? e : 0;
+  }
+}
+
+// Value frame of a fragment row: scale so the row max lies in [1/4, 1/2).
+// hi/lo hold P * 2^16 in units of 2^(e_x + e_y(col)); returns e_row and
+// rescales hi/lo in place to value * 2^-e_row for the 18 real columns.
+template <int NT>
+__device__ __forceinline__ void frame_rows(float (&hi)[NT][4], float (&lo)[NT][4], const int* Ye, int ex0, int ex1,
+                                           int& er0, int& er1) {
+  const int t = threadIdx.x & 3;
+  float m0 = 0.0f, m1 = 0.0f;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int col = nt * 8 + 2 * t + (i & 1);
+      if (col >= LC_M) continue;
+      const float a = fabsf(hi[nt][i]) * pow2f(Ye[col]);
+      if (i < 2) m0 = fmaxf(m0, a); else m1 = fmaxf(m1, a);
+    }
+  m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 1));
+  m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 2));
+  m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 1));
+  m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 2));
+  const int k0 = (m0 > 0.0f) ? exp_of(m0) : 0;
+  const int k1 = (m1 > 0.0f) ? exp_of(m1) : 0;
+  er0 = ex0 - 16 + k0 + 1;
+  er1 = ex1 - 16 + k1 + 1;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int col = nt * 8 + 2 * t + (i & 1);
+      const float sc = (col < LC_M) ? pow2f(Ye[col] - ((i < 2) ? k0 : k1) - 1) : 0.0f;
+      hi[nt][i] *= sc;
+      lo[nt][i] *= sc;
+    }
+}
+
+// smem layout shared by the stage kernels
+struct Smem {
+  uint16_t* Xs;
+  int xs;
+  uint16_t* Ys;
+  int ys;
+  int* Xe;
+  int* Ye;
+};
+__device__ __forceinline__ Smem carve(unsigned char* base, int S, int KP, int NP) {
+  Smem m;
+  m.xs = KP + 8;
+  m.ys = KP + 8;
+  m.Xs = reinterpret_cast<uint16_t*>(base);
+  m.Ys = m.Xs + S * kRows * m.xs;
+  m.Xe = reinterpret_cast<int*>(m.Ys + S * NP * m.ys);
+  m.Ye = m.Xe + kRows;
+  return m;
+}
+size_t smem_bytes(int S, int KP, int NP) {
+  return size_t(S) * kRows * (KP + 8) * 2 + size_t(S) * NP * (KP + 8) * 2 + (kRows + NP) * 4 + 16;
+}
+
+// Store a framed fragment row pair to a double-float row array.
+template <int NT>
+__device__ __forceinline__ void store_rows(float2* Out, int* OutE, int64_t row_base, int64_t tile0, int64_t valid,
+                                           float (&hi)[NT][4], float (&lo)[NT][4], int er0, int er1) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t r0 = tile0 + warp * 16 + g, r1 = r0 + 8;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int col = nt * 8 + 2 * t + (i & 1);
+      const int64_t r = (i < 2) ? r0 : r1;
+      if (col < LC_M && r < valid) Out[(row_base + r) * LC_M + col] = make_float2(hi[nt][i], lo[nt][i]);
+    }
+  if (t == 0) {
+    if (r0 < valid) OutE[row_base + r0] = er0;
+    if (r1 < valid) OutE[row_base + r1] = er1;
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+// Step 1: W(0, g, sigma) = F(g, sigma) T(sigma).
+__global__ void __launch_bounds__(kThreads) k_s_leaf(Dev D, int64_t w0) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const Work it = D.work[w0 + blockIdx.x];
+  const int sigma = blockIdx.y;
+  const int KP = D.yKP[Y_LEAF], NP = D.yNP[Y_LEAF];
+  Smem m = carve(sm_raw, D.S, KP, NP);
+  const int64_t g = it.seg, tile0 = int64_t(it.tile) * kRows;
+  const int64_t valid = dcnt(D, 0, g);
+  load_y(D.yq[Y_LEAF] + size_t(sigma) * D.S * NP * KP, D.ye[Y_LEAF] + sigma * NP, D.S, NP, KP, m.Ys, m.ys, m.Ye);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int s = D.s;
+  for (int lr = warp * 16; lr < warp * 16 + 16; ++lr) {
+    const int64_t r = tile0 + lr;
+    double x = 0.0;
+    if (r < valid && lane < s) {
+      const int64_t j = 2 * int64_t(s) * g + 2 * lane + sigma;
+      if (j < D.len[r]) x = in_base(D, r)[j * D.ie];
+    }
+    int E = int((__double_as_longlong(x) >> 52) & 0x7ff);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+    const int er = E - 1021;
+    float hi, lo;
+    d2df_scaled(x, er, hi, lo);
+    slice_df(hi, lo, D.S, m.Xs + lr * m.xs + lane, kRows * m.xs);
+    if (lane == 0) m.Xe[lr] = er;
+  }
+  __syncthreads();
+  float hi[3][4], lo[3][4];
+  warp_ozaki<2, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
+  const int g8 = lane >> 2;
+  int er0, er1;
+  frame_rows<3>(hi, lo, m.Ye, m.Xe[warp * 16 + g8], m.Xe[warp * 16 + g8 + 8], er0, er1);
+  store_rows<3>(D.W, D.We, drow(D, 0, g, sigma, 0), tile0, valid, hi, lo, er0, er1);
+}
+
+// Step 2: W(d+1, G) = [W(d, 2G) W(d, 2G+1)] [B(0) B(1)]^T.
+__global__ void __launch_bounds__(kThreads) k_s_up(Dev D, int64_t w0) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const Work it = D.work[w0 + blockIdx.x];
+  const int sigma = blockIdx.y;
+  const int KP = D.yKP[Y_UP], NP = D.yNP[Y_UP];
+  Smem m = carve(sm_raw, D.S, KP, NP);
+  const int dp = it.d;  // parent level
+  const int64_t G = it.seg, tile0 = int64_t(it.tile) * kRows;
+  const int64_t valid = dcnt(D, dp, G);
+  load_y(D.yq[Y_UP], D.ye[Y_UP], D.S, NP, KP, m.Ys, m.ys, m.Ye);
+  stage_rows_df(D, D.W, D.We, drow(D, dp - 1, 2 * G, sigma, 0), drow(D, dp - 1, 2 * G + 1, sigma, 0), 1, tile0,
+                valid, KP, m.Xs, m.xs, m.Xe);
+  __syncthreads();
+  float hi[3][4], lo[3][4];
+  warp_ozaki<3, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2;
+  int er0, er1;
+  frame_rows<3>(hi, lo, m.Ye, m.Xe[warp * 16 + g8], m.Xe[warp * 16 + g8 + 8], er0, er1);
+  store_rows<3>(D.W, D.We, drow(D, dp, G, sigma, 0), tile0, valid, hi, lo, er0, er1);
+}
+
+// Step 3: C(d, v) = [W(d, v+2) W(d, v+3)] [A-hat(b,0) A-hat(b,1)]^T (v even),
+//                  W(d, v+2) A-hat(b,2)^T (v odd).
+__global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const Work it = D.work[w0 + blockIdx.x];
+  const int sigma = blockIdx.y;
+  const int KP = D.yKP[Y_COUPLE], NP = D.yNP[Y_COUPLE];
+  Smem m = carve(sm_raw, D.S, KP, NP);
+  const int d = it.d;
+  const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;
+  const int64_t valid = dcnt(D, d, v + 2);
+  const int Gam = D.Lmax - 1 - d;  // level in the shared table
+  const int64_t item = (int64_t(4) * ((int64_t(1) << Gam) - 1) - 2 * Gam) + v;
+  load_y(D.yq[Y_COUPLE] + size_t(item) * D.S * NP * KP, D.ye[Y_COUPLE] + item * NP, D.S, NP, KP, m.Ys, m.ys, m.Ye);
+  const int two = ((v & 1) == 0) ? 1 : 0;
+  stage_rows_df(D, D.W, D.We, drow(D, d, v + 2, sigma, 0), two ? drow(D, d, v + 3, sigma, 0) : 0, two, tile0, valid,
+                KP, m.Xs, m.xs, m.Xe);
+  __syncthreads();
+  float hi[3][4], lo[3][4];
+  warp_ozaki<3, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2;
+  int er0, er1;
+  frame_rows<3>(hi, lo, m.Ye, m.Xe[warp * 16 + g8], m.Xe[warp * 16 + g8 + 8], er0, er1);
+  store_rows<3>(D.C, D.Ce, drow(D, d, v, sigma, 0), tile0, valid, hi, lo, er0, er1);
+}
+
+// Step 4: C(d, v) += C(d+1, v/2) B(v mod 2).
+__global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const Work it = D.work[w0 + blockIdx.x];
+  const int sigma = blockIdx.y;
+  const int KP = D.yKP[Y_DOWN], NP = D.yNP[Y_DOWN];
+  Smem m = carve(sm_raw, D.S, KP, NP);
+  const int d = it.d;
+  const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;
+  const int64_t valid = dcnt(D, d, v + 4);
+  const int p = int(v & 1);
+  load_y(D.yq[Y_DOWN] + size_t(p) * D.S * NP * KP, D.ye[Y_DOWN] + p * NP, D.S, NP, KP, m.Ys, m.ys, m.Ye);
+  stage_rows_df(D, D.C, D.Ce, drow(D, d + 1, v >> 1, sigma, 0), 0, 0, tile0, valid, KP, m.Xs, m.xs, m.Xe);
+  __syncthreads();
+  float hi[3][4], lo[3][4];
+  warp_ozaki<2, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2, t = lane & 3;
+  int er0, er1;
+  frame_rows<3>(hi, lo, m.Ye, m.Xe[warp * 16 + g8], m.Xe[warp * 16 + g8 + 8], er0, er1);
+  // add the existing row (couple result) in a common frame
+  const int64_t base = drow(D, d, v, sigma, 0);
+  const int64_t r0 = tile0 + warp * 16 + g8, r1 = r0 + 8;
+  int eo0 = 0, eo1 = 0;
+  if (r0 < valid) eo0 = D.Ce[base + r0];
+  if (r1 < valid) eo1 = D.Ce[base + r1];
+  const int F0 = max(er0, eo0) + 1, F1 = max(er1, eo1) + 1;
+  const float sa0 = pow2f(er0 - F0), sb0 = pow2f(eo0 - F0), sa1 = pow2f(er1 - F1), sb1 = pow2f(eo1 - F1);
+#pragma unroll
+  for (int nt = 0; nt < 3; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int col = nt * 8 + 2 * t + (i & 1);
+      const int64_t r = (i < 2) ? r0 : r1;
+      if (col >= LC_M || r >= valid) continue;
+      const float2 o = D.C[(base + r) * LC_M + col];
+      const float sa = (i < 2) ? sa0 : sa1, sb = (i < 2) ? sb0 : sb1;
+      float sh, se;
+      two_sum(hi[nt][i] * sa, o.x * sb, sh, se);
+      float nh, nl;
+      fast_two_sum(sh, se + lo[nt][i] * sa + o.y * sb, nh, nl);
+      D.C[(base + r) * LC_M + col] = make_float2(nh, nl);
+    }
+  if (t == 0) {
+    if (r0 < valid) D.Ce[base + r0] = F0;
+    if (r1 < valid) D.Ce[base + r1] = F1;
+  }
+}
+
+// Steps 5-7 for strip t: Z = C(0, t) T(sigma)^T + F(strip) E^T, C^{-1}, store.
+__global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const Work it = D.work[w0 + blockIdx.x];
+  const int sigma = blockIdx.y;
+  const int s = D.s;
+  const int64_t t = it.seg, tile0 = int64_t(it.tile) * kRows;
+  const int64_t validN = D.cntN[t];
+  const int64_t validF = (D.Lmax > 0 && t + 2 < (int64_t(2) << D.Lmax)) ? dcnt(D, 0, t + 2) : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2, tq = lane & 3;
+  // ---- near field
+  const int KPn = D.yKP[Y_NEAR], NPn = D.yNP[Y_NEAR];
+  Smem m = carve(sm_raw, D.S, KPn, NPn);
+  const int64_t item = 2 * t + sigma;
+  load_y(D.yq[Y_NEAR] + size_t(item) * D.S * NPn * KPn, D.ye[Y_NEAR] + item * NPn, D.S, NPn, KPn, m.Ys, m.ys,
+         m.Ye);
+  for (int lr = warp * 16; lr < warp * 16 + 16; ++lr) {
+    const int64_t r = tile0 + lr;
+    double x0 = 0.0, x1 = 0.0;
+    if (r < validN) {
+      const double* f = in_base(D, r);
+      const int64_t n = D.len[r];
+      const int64_t j0 = 2 * int64_t(s) * t + 2 * lane + sigma;
+      const int64_t j1 = j0 + 64;
+      if (lane < 2 * s && j0 < n) x0 = f[j0 * D.ie];
+      if (lane + 32 < 2 * s && j1 < n) x1 = f[j1 * D.ie];
+    }
+    int E = max(int((__double_as_longlong(x0) >> 52) & 0x7ff), int((__double_as_longlong(x1) >> 52) & 0x7ff));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+    const int er = E - 1021;
+    float hi, lo;
+    d2df_scaled(x0, er, hi, lo);
+    slice_df(hi, lo, D.S, m.Xs + lr * m.xs + lane, kRows * m.xs);
+    if (lane + 32 < KPn) {
+      d2df_scaled(x1, er, hi, lo);
+      slice_df(hi, lo, D.S, m.Xs + lr * m.xs + lane + 32, kRows * m.xs);
+    }
+    if (lane == 0) m.Xe[lr] = er;
+  }
+  __syncthreads();
+  float nh[4][4], nl[4][4];
+  if (KPn == 64)
+    warp_ozaki<4, 4>(m.Xs, m.xs, m.Ys, m.ys, D.S, nh, nl);
+  else if (KPn == 48)
+    warp_ozaki<3, 4>(m.Xs, m.xs, m.Ys, m.ys, D.S, nh, nl);
+  else
+    warp_ozaki<2, 4>(m.Xs, m.xs, m.Ys, m.ys, D.S, nh, nl);
+  int enx0 = m.Xe[warp * 16 + g8], enx1 = m.Xe[warp * 16 + g8 + 8];
+  int eny[4][2];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    eny[nt][0] = m.Ye[nt * 8 + 2 * tq];
+    eny[nt][1] = m.Ye[nt * 8 + 2 * tq + 1];
+  }
+  __syncthreads();
+  // ---- far field (spread)
+  float fh[4][4], fl[4][4];
+  int efx0 = 0, efx1 = 0, efy[4][2];
+  const bool any_far = validF > tile0;
+  if (any_far) {
+    const int KPs = D.yKP[Y_SPREAD], NPs = D.yNP[Y_SPREAD];
+    Smem m2 = carve(sm_raw, D.S, KPs, NPs);
+    load_y(D.yq[Y_SPREAD] + size_t(sigma) * D.S * NPs * KPs, D.ye[Y_SPREAD] + sigma * NPs, D.S, NPs, KPs, m2.Ys,
+           m2.ys, m2.Ye);
+    stage_rows_df(D, D.C, D.Ce, drow(D, 0, t, sigma, 0), 0, 0, tile0, validF, KPs, m2.Xs, m2.xs, m2.Xe);
+    __syncthreads();
+    warp_ozaki<2, 4>(m2.Xs, m2.xs, m2.Ys, m2.ys, D.S, fh, fl);
+    efx0 = m2.Xe[warp * 16 + g8];
+    efx1 = m2.Xe[warp * 16 + g8 + 8];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      efy[nt][0] = m2.Ye[nt * 8 + 2 * tq];
+      efy[nt][1] = m2.Ye[nt * 8 + 2 * tq + 1];
+    }
+  } else {
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) fh[nt][i] = fl[nt][i] = 0.0f;
+      efy[nt][0] = efy[nt][1] = 0;
+    }
+  }
+  // ---- combine, scale, store
+  const int64_t r0 = tile0 + warp * 16 + g8, r1 = r0 + 8;
+  const bool l2c = (D.dir == LC_L2C);
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int col = nt * 8 + 2 * tq + (i & 1);  // local row m of the strip
+      const int64_t r = (i < 2) ? r0 : r1;
+      if (col >= s || r >= validN) continue;
+      const int64_t row_i = 2 * int64_t(s) * t + 2 * col + sigma;
+      if (row_i >= D.len[r]) continue;
+      const bool far = r < validF;
+      const int E1 = ((i < 2) ? enx0 : enx1) + eny[nt][i & 1] - 16;
+      const int E2 = ((i < 2) ? efx0 : efx1) + efy[nt][i & 1] - 16;
+      const int F = far ? max(E1, E2) : E1;
+      const float s1 = pow2f(E1 - F), s2 = far ? pow2f(E2 - F) : 0.0f;
+      float zh, ze;
+      two_sum(nh[nt][i] * s1, fh[nt][i] * s2, zh, ze);
+      float zl = ze + nl[nt][i] * s1 + fl[nt][i] * s2;
+      fast_two_sum(zh, zl, zh, zl);
+      if (l2c) {  // Step 7: times 2/pi (1/pi for row 0) in double-float
+        const float ch = (row_i == 0) ? 0.31830987334251404f : 0.6366197466850281f;
+        const float cl = (row_i == 0) ? 1.2841276486597053e-08f : 2.5682552973194106e-08f;
+        const float ph = zh * ch;
+        float pe = fmaf(zh, ch, -ph);
+        pe = fmaf(zh, cl, fmaf(zl, ch, pe));
+        fast_two_sum(ph, pe, zh, zl);
+      }
+      out_base(D, r)[row_i * D.oe] = f2d_scaled(zh, F) + f2d_scaled(zl, F);
+    }
+}
+
+// ------------------------------------------------------------ plan kernels
+__device__ double y_value(int kind, int64_t item, int k, int n, const lc_plan_s& P, int s, int L, int64_t N,
+                          int dir) {
+  switch (kind) {
+    case Y_LEAF:  // Y[m][k'] = T[sigma][m][k']
+      return (n < LC_M && k < s) ? P.T[(item * s + k) * LC_M + n] : 0.0;
+    case Y_SPREAD:  // Y[k'][m] = T[sigma][m][k']
+      return (k < LC_M && n < s) ? P.T[(item * s + n) * LC_M + k] : 0.0;
+    case Y_UP: {  // Y[c*18+j][k'] = B(c)[k'][j]
+      if (n >= LC_M || k >= 2 * LC_M) return 0.0;
+      const int c = k / LC_M, j = k % LC_M;
+      const double b = P.B[n * LC_M + j];
+      return (c == 1 && ((n - j) & 1)) ? -b : b;
+    }
+    case Y_DOWN: {  // Y[j][k'] = B(p)[j][k']
+      if (n >= LC_M || k >= LC_M) return 0.0;
+      const double b = P.B[k * LC_M + n];
+      return (item == 1 && ((k - n) & 1)) ? -b : b;
+    }
+    case Y_COUPLE: {
+      if (n >= LC_M || k >= 2 * LC_M) return 0.0;
+      int G = 0;
+      while (G + 1 < L && item >= 4 * ((int64_t(1) << (G + 1)) - 1) - 2 * (G + 1)) ++G;
+      const int64_t v = item - (4 * ((int64_t(1) << G) - 1) - 2 * G);
+      const int64_t b = v >> 1;
+      const int64_t aoff = lc_ahat_offset(G);
+      if ((v & 1) == 0) {
+        const int c = k / LC_M, l = k % LC_M;
+        return P.Ahat[(aoff + 3 * b + c) * (LC_M * LC_M) + n * LC_M + l];
+      }
+      if (k >= LC_M) return 0.0;
+      return P.Ahat[(aoff + 3 * b + 2) * (LC_M * LC_M) + n * LC_M + k];
+    }
+    case Y_NEAR: {  // Y[jj][m] = E(t, sigma)[m][jj]
+      if (n >= s || k >= 2 * s) return 0.0;
+      const int64_t t = item >> 1;
+      const int sigma = int(item & 1);
+      const int64_t i = 2 * int64_t(s) * t + 2 * n + sigma;
+      const int64_t j = 2 * int64_t(s) * t + 2 * k + sigma;
+      if (j < i || j >= N || i >= N) return 0.0;
+      const int64_t kk = (j - i) / 2;
+      if (dir == LC_L2C) return P.lam[kk] * P.lam2[i + kk];
+      double e = double(2 * i + 1) * double(j) * P.lam[kk] * P.lam2[i + kk];
+      if (i == 0 && j == 0) e += 1.0;
+      return e;
+    }
+  }
+  return 0.0;
+}
+
+__global__ void k_make_y(int kind, int items, int K, int KP, int NP, int S, lc_plan_s P, int s, int L, int64_t N,
+                         int dir, uint16_t* __restrict__ q, int* __restrict__ e) {
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (tid >= int64_t(items) * NP) return;
+  const int64_t item = tid / NP;
+  const int n = int(tid % NP);
+  double mx = 0.0;
+  for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(y_value(kind, item, k, n, P, s, L, N, dir)));
+  int ey = 0;
+  if (mx > 0.0) {
+    int ex;
+    frexp(mx, &ex);  // mx in [2^(ex-1), 2^ex)
+    ey = ex + 1;
+  }
+  e[item * NP + n] = ey;
+  uint16_t* dst = q + (size_t(item) * S * NP + n) * KP;
+  for (int k = 0; k < KP; ++k) {
+    double y = (k < K) ? ldexp(y_value(kind, item, k, n, P, s, L, N, dir), -ey) : 0.0;
+    for (int sl = 0; sl < S; ++sl) {
+      const double tt = y * 256.0;
+      const double qq = rint(tt);
+      y = tt - qq;
+      dst[size_t(sl) * NP * KP + k] = uint16_t(__float_as_uint(float(qq)) >> 16);
+    }
+  }
+}
+
+Dev make_dev(const lc_plan_s* p, const SplitHost& h) {
+  char* base = static_cast<char*>(p->split);
+  Dev D;
+  memset(&D, 0, sizeof(D));
+  D.S = h.S;
+  D.s = h.s;
+  D.Lmax = h.Lmax;
+  D.count = h.count;
+  D.Nmax = h.Nmax;
+  D.nstrips = h.nstrips;
+  D.len = reinterpret_cast<const int64_t*>(base + h.off_len);
+  D.orig = reinterpret_cast<const int64_t*>(base + h.off_orig);
+  D.off = reinterpret_cast<const int64_t*>(base + h.off_off);
+  D.Lcount = reinterpret_cast<const int64_t*>(base + h.off_Lcount);
+  D.cntN = reinterpret_cast<const int64_t*>(base + h.off_cntN);
+  D.rowbase = reinterpret_cast<const int64_t*>(base + h.off_rowbase);
+  D.work = reinterpret_cast<const Work*>(base + h.off_work);
+  D.W = reinterpret_cast<float2*>(base + h.off_W);
+  D.We = reinterpret_cast<int*>(base + h.off_We);
+  D.C = reinterpret_cast<float2*>(base + h.off_C);
+  D.Ce = reinterpret_cast<int*>(base + h.off_Ce);
+  for (int k = 0; k < Y_KINDS; ++k) {
+    D.yq[k] = reinterpret_cast<const uint16_t*>(base + h.y[k].off_q);
+    D.ye[k] = reinterpret_cast<const int*>(base + h.y[k].off_e);
+    D.yKP[k] = h.y[k].KP;
+    D.yNP[k] = h.y[k].NP;
+  }
+  D.dir = int(p->dir);
+  D.ragged = p->ragged;
+  return D;
+}
+
+}  // namespace
+
+size_t lc_split_bytes(const lc_plan_s* p) {
+  SplitHost h;
+  build_host(p, h);
+  return h.total;
+}
+
+lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st) {
+  if (p->g.s > 32) return LC_ERR_UNSUPPORTED;  // K tiles sized for s <= 32
+  SplitHost* h = new (std::nothrow) SplitHost;
+  if (!h) return LC_ERR_HOST_ALLOC;
+  build_host(p, *h);
+  if (h->total > bytes) {
+    delete h;
+    return LC_ERR_WORKSPACE_TOO_SMALL;
+  }
+  p->ragged_dev = h;  // host tables stay alive with the plan (freed by lc_split_release)
+  auto up = [&](size_t off, const void* src, size_t n) -> lc_status {
+    if (n) LC_CUDA_TRY(cudaMemcpyAsync(base + off, src, n, cudaMemcpyHostToDevice, st));
+    return LC_OK;
+  };
+  lc_status s2;
+  if ((s2 = up(h->off_len, h->len_sorted.data(), h->count * 8)) != LC_OK) return s2;
+  if ((s2 = up(h->off_orig, h->orig.data(), h->count * 8)) != LC_OK) return s2;
+  if ((s2 = up(h->off_off, h->off_sorted.data(), h->count * 8)) != LC_OK) return s2;
+  if ((s2 = up(h->off_Lcount, h->Lcount.data(), h->Lcount.size() * 8)) != LC_OK) return s2;
+  if ((s2 = up(h->off_cntN, h->cntN.data(), h->cntN.size() * 8)) != LC_OK) return s2;
+  if ((s2 = up(h->off_rowbase, h->rowbase.data(), h->rowbase.size() * 8)) != LC_OK) return s2;
+  if ((s2 = up(h->off_work, h->work.data(), h->work.size() * sizeof(Work))) != LC_OK) return s2;
+  const int Ks[Y_KINDS] = {h->s, LC_M, 2 * LC_M, LC_M, 2 * LC_M, 2 * h->s};
+  for (int k = 0; k < Y_KINDS; ++k) {
+    const YTable& y = h->y[k];
+    if (y.items == 0) continue;
+    const int64_t threads = int64_t(y.items) * y.NP;
+    k_make_y<<<unsigned((threads + 127) / 128), 128, 0, st>>>(
+        k, y.items, Ks[k], y.KP, y.NP, h->S, *p, h->s, h->Lmax, h->Nmax, int(p->dir),
+        reinterpret_cast<uint16_t*>(base + y.off_q), reinterpret_cast<int*>(base + y.off_e));
+    LC_LAUNCH_CHECK();
+  }
+  const size_t big = smem_bytes(h->S, 64, 32);
+  LC_CUDA_TRY(cudaFuncSetAttribute(k_s_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
+  LC_CUDA_TRY(cudaFuncSetAttribute(k_s_up, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
+  LC_CUDA_TRY(cudaFuncSetAttribute(k_s_couple, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
+  LC_CUDA_TRY(cudaFuncSetAttribute(k_s_down, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
+  LC_CUDA_TRY(cudaFuncSetAttribute(k_s_final, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
+  return LC_OK;
+}
+
+void lc_split_release(lc_plan p) {
+  if (p && p->dtype == LC_F64_SPLIT && p->ragged_dev) {
+    delete static_cast<SplitHost*>(p->ragged_dev);
+    p->ragged_dev = nullptr;
+  }
+}
+
+int lc_exec_split_launches(const lc_plan_s* p) {
+  const SplitHost* h = static_cast<const SplitHost*>(p->ragged_dev);
+  return h ? int(h->launch_kind.size()) : 0;
+}
+
+lc_status lc_exec_split(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob, int64_t oe,
+                        cudaStream_t st, int adjoint) {
+  if (adjoint) return LC_ERR_UNSUPPORTED;
+  const SplitHost* h = static_cast<const SplitHost*>(p->ragged_dev);
+  if (!h) return LC_ERR_INVALID_ARG;
+  Dev D = make_dev(p, *h);
+  D.in = static_cast<const double*>(in);
+  D.out = static_cast<double*>(out);
+  D.ib = ib;
+  D.ie = ie;
+  D.ob = ob;
+  D.oe = oe;
+  lc_timer_begin(p);
+  for (size_t l = 0; l < h->launch_kind.size(); ++l) {
+    const int64_t w0 = h->launch_off[l], nitems = h->launch_off[l + 1] - w0;
+    if (nitems <= 0) continue;
+    const int kind = h->launch_kind[l];
+    dim3 grid(unsigned(nitems), 2);
+    lc_timer_mark(p, st, kind);
+    switch (kind) {
+      case LC_K_LEAF: {
+        const YTable& y = h->y[Y_LEAF];
+        k_s_leaf<<<grid, kThreads, smem_bytes(h->S, y.KP, y.NP), st>>>(D, w0);
+        break;
+      }
+      case LC_K_UP: {
+        const YTable& y = h->y[Y_UP];
+        k_s_up<<<grid, kThreads, smem_bytes(h->S, y.KP, y.NP), st>>>(D, w0);
+        break;
+      }
+      case LC_K_COUPLE: {
+        const YTable& y = h->y[Y_COUPLE];
+        k_s_couple<<<grid, kThreads, smem_bytes(h->S, y.KP, y.NP), st>>>(D, w0);
+        break;
+      }
+      case LC_K_DOWN: {
+        const YTable& y = h->y[Y_DOWN];
+        k_s_down<<<grid, kThreads, smem_bytes(h->S, y.KP, y.NP), st>>>(D, w0);
+        break;
+      }
+      case LC_K_FINAL: {
+        const YTable& y = h->y[Y_NEAR];
+        k_s_final<<<grid, kThreads, smem_bytes(h->S, y.KP, y.NP), st>>>(D, w0);
+        break;
+      }
+    }
+    LC_LAUNCH_CHECK();
+  }
+  lc_timer_end(p, st);
+  return LC_OK;
+}
+

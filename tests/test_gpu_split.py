@@ -1,0 +1,101 @@
+"""Split-precision tensor-core tier (LC_F64_SPLIT): parity with the oracle.
+
+Tolerance: the tier is FP64-accurate through exact 8-bit slice products;
+with S = 6 slices the normwise relative error stays <= 1e-12 (the gate for
+this tier), with S = 7 <= 1e-13 (the FP64 gate for n <= 1e5).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_util import rel_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DIRS = [("l2c", oracle.L2C), ("c2l", oracle.C2L)]
+
+
+@pytest.fixture(scope="module")
+def lc():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_00033_gb300 as m
+    return m
+
+
+def _batch(n, batch, seed, r=0.5):
+    return np.stack([workloads.decaying_vector(n, seed=seed + b, r=r) for b in range(batch)])
+
+
+@pytest.mark.parametrize("n,batch", [(1, 2), (7, 3), (100, 5), (128, 2), (129, 3), (1000, 64), (1024, 65),
+                                     (4097, 7), (20000, 3)])
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_split_uniform_batch(lc, n, batch, direction, code):
+    X = _batch(n, batch, seed=1000 + n)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, direction, batch, "f64_split", dev)
+    Z = plan(torch.as_tensor(X, device=dev)).cpu().numpy()
+    worst = 0.0
+    for b in range(batch):
+        e2, _ = rel_errors(Z[b], oracle.apply(code, X[b]))
+        worst = max(worst, e2)
+    assert worst <= 1e-12, (n, batch, worst)
+
+
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_split_seven_slices_fp64_gate(lc, direction, code):
+    n, batch = 5000, 4
+    X = _batch(n, batch, seed=77)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, direction, batch, "f64_split", dev, slices=7)
+    Z = plan(torch.as_tensor(X, device=dev)).cpu().numpy()
+    for b in range(batch):
+        e2, einf = rel_errors(Z[b], oracle.apply(code, X[b]))
+        assert e2 <= 1e-13, (b, e2, einf)
+
+
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_split_ragged(lc, direction, code):
+    rng = np.random.default_rng(5)
+    lengths = [1, 2, 3, 64, 100, 128, 129, 130, 500, 1000, 1024, 1025, 3000, 5000] + \
+        list(workloads.ragged_lengths(40, 64, 8192, seed=9))
+    rng.shuffle(lengths)
+    x = workloads.ragged_batch(lengths, seed=3)
+    offs = workloads.ragged_offsets(lengths)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(direction=direction, dtype="f64_split", device=dev, lengths=lengths)
+    z = plan(torch.as_tensor(x, device=dev)).cpu().numpy()
+    worst = 0.0
+    for i, n in enumerate(lengths):
+        a, b = offs[i], offs[i + 1]
+        e2, _ = rel_errors(z[a:b], oracle.apply(code, x[a:b]))
+        worst = max(worst, e2)
+    assert worst <= 1e-12, worst
+
+
+def test_split_strided_fibres(lc):
+    n, batch = 512, 96
+    X = _batch(n, batch, seed=21, r=1.0).T.copy()  # (n, batch): fibres along axis 0
+    dev = torch.device("cuda", 0)
+    xt = torch.as_tensor(X, device=dev)
+    out = torch.empty((batch, n), dtype=torch.float64, device=dev)
+    plan = lc.Plan(n, "l2c", batch, "f64_split", dev)
+    plan.execute_strided(xt, out, (1, batch), (n, 1))
+    Z = out.cpu().numpy()
+    for b in range(0, batch, 7):
+        e2, _ = rel_errors(Z[b], oracle.apply(oracle.L2C, X[:, b]))
+        assert e2 <= 1e-12, (b, e2)
+
+
+def test_split_matches_f64_tier_large(lc):
+    n, batch = 65536, 3
+    X = _batch(n, batch, seed=31)
+    dev = torch.device("cuda", 0)
+    xt = torch.as_tensor(X, device=dev)
+    for direction in ("l2c", "c2l"):
+        zs = lc.Plan(n, direction, batch, "f64_split", dev)(xt).cpu().numpy()
+        zf = lc.Plan(n, direction, batch, "f64", dev)(xt).cpu().numpy()
+        for b in range(batch):
+            e2, _ = rel_errors(zs[b], zf[b])
+            assert e2 <= 1e-12, (direction, b, e2)
