@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--tier", default="auto", help="f64 | f64_df | f64_split | auto (fastest FP64-accurate)")
     ap.add_argument("--cpu-rows", type=int, default=CPU_ROWS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (profiling runs)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched workloads")
     return ap.parse_args()
 
 
@@ -188,6 +189,90 @@ def kernel_work(info, kind, direction):
     return None
 
 
+def graph_step(fn):
+    """Capture fn (library launches on the current stream) into a CUDA graph."""
+    import torch
+    fn()  # warm (plans, lazy module loads)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g.replay
+
+
+def time_fn(fn, flush, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        flush.fill_(1.0)
+        fn()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.fill_(float(k))
+        evs[k][0].record()
+        fn()
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+
+def batched_leg(lc, dev, flush, args):
+    """Batched workloads sharing one plan: split-precision tensor-core tier
+    (one CUDA graph replay per step) against the plain FP64 tier."""
+    import numpy as np
+    import torch
+    import workloads
+    out = {}
+    steps = max(3, min(10, args.steps))
+    # (a) uniform batch: 256 vectors of n = 65536 (the differentiable-fit shape), L2C
+    n, B = 65536, 256
+    X = torch.as_tensor(workloads.decaying_vector(n, seed=5, r=1.0, batch=B), device=dev)
+    Z = torch.empty_like(X)
+    res = {}
+    ref = None
+    for tier in ("f64_split", "f64"):
+        plan = lc.Plan(n, "l2c", B, tier, dev)
+        step = graph_step(lambda: plan(X, out=Z))
+        ms = time_fn(step, flush, steps, 2)
+        res[tier] = {"coefficients_per_s": n * B / (ms / 1e3), "ms": ms,
+                     "launches": plan.launches()}
+        if tier == "f64":
+            ref = Z.clone()
+        else:
+            got = Z.clone()
+        del plan
+    d = (got - ref).double()
+    res["split_vs_f64_E2"] = float(torch.linalg.norm(d) / torch.linalg.norm(ref))
+    res["speedup_split_over_f64_batched"] = res["f64_split"]["coefficients_per_s"] / res["f64"]["coefficients_per_s"]
+    out["uniform_65536x256_l2c"] = res
+    del X, Z
+    # (b) ragged batch: 4096 transforms, n log-uniform in [64, 65536]
+    lengths = workloads.ragged_lengths(4096, seed=2)
+    x = torch.as_tensor(workloads.ragged_batch(lengths, seed=3), device=dev)
+    z = torch.empty_like(x)
+    t0 = time.perf_counter()
+    plan = lc.Plan(direction="l2c", dtype="f64_split", device=dev, lengths=lengths)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    step = graph_step(lambda: plan(x, out=z))
+    ms = time_fn(step, flush, steps, 2)
+    out["ragged_4096_l2c"] = {"coefficients_per_s": float(lengths.sum()) / (ms / 1e3), "ms": ms,
+                              "coefficients": int(lengths.sum()), "plan_s": plan_s, "launches": plan.launches()}
+    del plan, x, z
+    # (c) 512^3 array, Legendre->Chebyshev along axis 0 (strided fibres) and axis 2 (contiguous)
+    N3 = 512
+    cube = torch.as_tensor(workloads.cube(N3, seed=4), device=dev)
+    outc = torch.empty((N3 * N3, N3), dtype=torch.float64, device=dev)
+    plan = lc.Plan(N3, "l2c", N3 * N3, "f64_split", dev)
+    for axis, strides in ((0, (1, N3 * N3)), (2, (N3, 1))):
+        step = graph_step(lambda: plan.execute_strided(cube, outc, strides, (N3, 1)))
+        ms = time_fn(step, flush, max(3, steps // 2), 1)
+        out["cube512_axis%d_l2c" % axis] = {"coefficients_per_s": N3 ** 3 / (ms / 1e3), "ms": ms}
+    del plan, cube, outc
+    torch.cuda.synchronize()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -212,7 +297,7 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.barrier()
 
-    available = ["f64", "f64_df", "f64_split"]
+    available = ["f64", "f64_df"]  # the split tier is for batches (reported under "batched")
     tiers = {}
     for t in available:
         try:
@@ -347,6 +432,9 @@ def run_ours(args):
         "clocks": clk,
         "wall_s_timed": wall,
     }
+
+    if not args.no_batched:
+        line["batched"] = batched_leg(lc, dev, flush, args)
 
     if rank == 0 and not args.no_cpu:
         pick, ref_l2c, ref_c2l, dt, cores = oracle_leg(n, x_host, args.cpu_rows)

@@ -1,8 +1,75 @@
-// lc_df.cu -- double-float (FP32 pair) tier, LC_F64_DF.
-#include "lc_internal.cuh"
+// lc_df.cu -- LC_F64_DF: FP64 input and output, Algorithm 4 in double-float
+// arithmetic on the FP32 pipe (the kernels of lc_exec_kernels.cuh with
+// R = lc_df).  The plan tables are rounded once from the FP64 plan to
+// double-float pairs.
+#include "lc_df.cuh"
+#include "lc_exec_kernels.cuh"
+
+namespace lc_exec {
+template <>
+struct lc_io<lc_df> {
+  typedef double type;
+};
+template <>
+__device__ __forceinline__ lc_df lc_ld<lc_df, double>(const double* p) {
+  return lc_df_from_double(*p);
+}
+template <>
+__device__ __forceinline__ void lc_st<lc_df, double>(double* p, const lc_df& v) {
+  *p = lc_df_to_double(v);
+}
+template <>
+__device__ __forceinline__ lc_df cinv<lc_df>(int64_t i) {
+  // 1/pi and 2/pi as double-floats
+  return i == 0 ? lc_df(0.31830987334251404f, 1.2841276486597053e-08f)
+                : lc_df(0.6366197466850281f, 2.5682552973194106e-08f);
+}
+}  // namespace lc_exec
+
+using namespace lc_exec;
+
+namespace {
+__global__ void k_d2df(int64_t n, const double* __restrict__ a, lc_df* __restrict__ b) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double x = a[i];
+    const float h = float(x);
+    b[i] = lc_df(h, float(x - double(h)));
+  }
+}
+unsigned blocks_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 65535 * 16) b = 65535 * 16;
+  return unsigned(b);
+}
+}  // namespace
 
 size_t lc_df_bytes(const lc_geom&, int64_t) { return 0; }
-lc_status lc_df_prepare(lc_plan, cudaStream_t) { return LC_ERR_UNSUPPORTED; }
-lc_status lc_exec_df(lc_plan, const void*, void*, int64_t, int64_t, int64_t, int64_t, cudaStream_t, int) {
-  return LC_ERR_UNSUPPORTED;
+
+lc_status lc_df_prepare(lc_plan p, cudaStream_t st) {
+  const lc_geom& g = p->g;
+  k_d2df<<<blocks_for(g.N), 256, 0, st>>>(g.N, p->lam, static_cast<lc_df*>(p->df_lam));
+  if (p->dir == LC_C2L) k_d2df<<<blocks_for(g.N), 256, 0, st>>>(g.N, p->lam2, static_cast<lc_df*>(p->df_lam2));
+  k_d2df<<<1, 256, 0, st>>>(int64_t(2) * g.s * LC_M, p->T, static_cast<lc_df*>(p->df_T));
+  k_d2df<<<1, 256, 0, st>>>(LC_M * LC_M, p->B, static_cast<lc_df*>(p->df_B));
+  if (g.nc > 0) k_d2df<<<blocks_for(g.nc * LC_M * LC_M), 256, 0, st>>>(g.nc * LC_M * LC_M, p->Ahat,
+                                                                      static_cast<lc_df*>(p->df_Ahat));
+  LC_LAUNCH_CHECK();
+  return LC_OK;
+}
+
+lc_status lc_exec_df(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob, int64_t oe,
+                     cudaStream_t st, int adjoint) {
+  if (p->ragged) return LC_ERR_UNSUPPORTED;
+  Args<lc_df> a;
+  a.in = static_cast<const double*>(in);
+  a.out = static_cast<double*>(out);
+  a.ib = ib; a.ie = ie; a.ob = ob; a.oe = oe;
+  a.n = p->g.n; a.N = p->g.N; a.L = p->g.L; a.s = p->g.s; a.nseg = p->g.nseg;
+  a.batch = p->batch; a.dir = int(p->dir);
+  a.t = lc_tables<lc_df>{static_cast<const lc_df*>(p->df_lam), static_cast<const lc_df*>(p->df_lam2),
+                         static_cast<const lc_df*>(p->df_T), static_cast<const lc_df*>(p->df_B),
+                         static_cast<const lc_df*>(p->df_Ahat), static_cast<lc_df*>(p->df_W),
+                         static_cast<lc_df*>(p->df_Cc)};
+  return run<lc_df>(p, a, st, adjoint);
 }

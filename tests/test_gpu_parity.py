@@ -46,31 +46,34 @@ SIZES = [1, 2, 3, 5, 17, 64, 127, 128, 129, 200, 255, 256, 257, 500, 1000, 1023,
          16384, 33333]
 
 
+@pytest.mark.parametrize("tier", ["f64", "f64_df"])
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("direction,code", DIRS)
-def test_f64_matches_oracle(lc, n, direction, code):
+def test_f64_matches_oracle(lc, n, direction, code, tier):
     x = _input(n, seed=n)
-    z, plan = _run(lc, x, direction)
+    z, plan = _run(lc, x, direction, dtype=tier)
     ref = oracle.apply(code, x)
     e2, einf = rel_errors(z, ref)
     assert e2 <= 1e-13, (n, direction, e2, einf, plan.info)
     assert einf <= (1e-13 if code == oracle.L2C else 3e-13), (n, direction, e2, einf)
 
 
+@pytest.mark.parametrize("tier", ["f64", "f64_df"])
 @pytest.mark.parametrize("direction,code", DIRS)
-def test_config_n1024_uniform(lc, direction, code):
+def test_config_n1024_uniform(lc, direction, code, tier):
     x = workloads.uniform_vector(1024, seed=0)
-    z, plan = _run(lc, x, direction)
+    z, plan = _run(lc, x, direction, dtype=tier)
     assert plan.info["L"] == 3 and plan.info["s"] == 32 and plan.info["n_c"] == 33
     e2, einf = rel_errors(z, oracle.apply(code, x))
     assert e2 <= 1e-13 and einf <= 1e-13, (e2, einf)
 
 
+@pytest.mark.parametrize("tier", ["f64", "f64_df"])
 @pytest.mark.parametrize("direction,code", DIRS)
-def test_config_n1e6_sampled_rows(lc, direction, code):
+def test_config_n1e6_sampled_rows(lc, direction, code, tier):
     n = 1_000_000
     x = workloads.decaying_vector(n, seed=1, r=1.0)
-    z, plan = _run(lc, x, direction)
+    z, plan = _run(lc, x, direction, dtype=tier)
     assert (plan.info["L"], plan.info["s"], plan.info["N"]) == (13, 31, 1_015_808)
     rows = workloads.sample_rows(n, 4096)
     ref = oracle.apply(code, x, rows=rows)
@@ -88,13 +91,14 @@ def test_f32_tier(lc, n, direction, code):
     assert e2 <= 2e-6, (e2, einf)
 
 
+@pytest.mark.parametrize("tier", ["f64", "f64_df"])
 @pytest.mark.parametrize("direction,code", DIRS)
-def test_batched_strided_fibres(lc, direction, code):
+def test_batched_strided_fibres(lc, direction, code, tier):
     n, batch = 3001, 3
     X = np.stack([_input(n, seed=40 + b) for b in range(batch)], axis=1)  # (n, batch): fibres along axis 0
     dev = torch.device("cuda", 0)
     xt = torch.as_tensor(X, device=dev)
-    plan = lc.Plan(n, direction, batch, "f64", dev)
+    plan = lc.Plan(n, direction, batch, tier, dev)
     out = torch.empty((batch, n), dtype=torch.float64, device=dev)
     plan.execute_strided(xt, out, (1, batch), (n, 1))
     z = out.cpu().numpy()
@@ -103,12 +107,13 @@ def test_batched_strided_fibres(lc, direction, code):
         assert e2 <= 1e-13, (b, e2)
 
 
+@pytest.mark.parametrize("tier", ["f64", "f64_df"])
 @pytest.mark.parametrize("n", [1, 2, 100, 129, 1024, 5000])
 @pytest.mark.parametrize("direction,code", DIRS)
-def test_adjoint_matches_oracle_transpose(lc, n, direction, code):
+def test_adjoint_matches_oracle_transpose(lc, n, direction, code, tier):
     r = _input(n, seed=7 + n)
     dev = torch.device("cuda", 0)
-    plan = lc.Plan(n, direction, 1, "f64", dev)
+    plan = lc.Plan(n, direction, 1, tier, dev)
     g = plan(torch.as_tensor(r, device=dev), adjoint=True).cpu().numpy()
     ref = oracle.apply(code, r, adjoint=True)
     e2, einf = rel_errors(g, ref)

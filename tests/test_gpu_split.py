@@ -99,3 +99,26 @@ def test_split_matches_f64_tier_large(lc):
         for b in range(batch):
             e2, _ = rel_errors(zs[b], zf[b])
             assert e2 <= 1e-12, (direction, b, e2)
+
+
+def test_split_graph_capture_replay(lc):
+    # lc_execute neither allocates nor synchronises, so it can be captured into
+    # a CUDA graph and replayed with new input values.
+    n, batch = 3000, 70
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, "c2l", batch, "f64_split", dev)
+    X = torch.as_tensor(_batch(n, batch, seed=90), device=dev)
+    Z = torch.empty_like(X)
+    plan(X, out=Z)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan(X, out=Z)
+    X2 = _batch(n, batch, seed=91)
+    X.copy_(torch.as_tensor(X2, device=dev))
+    g.replay()
+    torch.cuda.synchronize()
+    Zd = plan(torch.as_tensor(X2, device=dev)).cpu().numpy()
+    assert np.array_equal(Z.cpu().numpy(), Zd)
+    e2, _ = rel_errors(Zd[0], oracle.apply(oracle.C2L, X2[0]))
+    assert e2 <= 1e-12
