@@ -88,7 +88,11 @@ typedef struct {
   int32_t s_hat;   /* target leaf half-size (eq:numlevels); 4 <= s_hat <= 64 */
   int32_t fixed_s; /* > 0: use this s for every length (4 <= fixed_s <= 64); 0: paper rule */
   int32_t slices;  /* LC_F64_SPLIT: 8-bit slices per operand, 3..7 (default 6) */
-  int32_t reserved[5];
+  /* Testing only (0 in normal use).  Bit 0: the coupling kernel withholds
+   * one of its bulk copies, so its bounded wait runs out and the execution
+   * reports LC_ERR_DEVICE_TIMEOUT through lc_plan_check. */
+  int32_t debug_flags;
+  int32_t reserved[4];
 } lc_plan_options;
 
 /* Fill *opt with the defaults above.  Returns LC_ERR_INVALID_ARG for NULL. */
@@ -154,6 +158,13 @@ lc_status lc_execute(lc_plan plan, const void* in, void* out, int64_t in_batch_s
 lc_status lc_adjoint(lc_plan plan, const void* in, void* out, int64_t in_batch_stride,
                      int64_t in_elem_stride, int64_t out_batch_stride,
                      int64_t out_elem_stride, lc_stream stream);
+
+/* Device-side status of the plan's earlier executions.  Kernels that wait on
+ * an asynchronous copy (mbarrier) give up after about one second, record the
+ * failure in a status word of the workspace and exit.  This call
+ * synchronises `stream`, returns LC_ERR_DEVICE_TIMEOUT if any such failure
+ * was recorded since the last check (and clears it), else LC_OK. */
+lc_status lc_plan_check(lc_plan plan, lc_stream stream);
 
 /* Free the host plan object.  The workspace stays the caller's. */
 lc_status lc_destroy(lc_plan plan);

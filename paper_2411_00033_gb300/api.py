@@ -16,8 +16,11 @@ def _stream_ptr(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
 
-def make_options(s_hat: int | None = None, fixed_s: int | None = None, slices: int | None = None):
+def make_options(s_hat: int | None = None, fixed_s: int | None = None, slices: int | None = None,
+                 debug_flags: int | None = None):
     o = B.lc_plan_options_default()
+    if debug_flags is not None:
+        o.debug_flags = debug_flags
     if s_hat is not None:
         o.s_hat = s_hat
     if fixed_s is not None:
@@ -115,6 +118,11 @@ class Plan:
                  3: self.info["n_c"] * self.info["M"] ** 2, 4: self.info["N"], 5: self.info["N"]}
         with torch.cuda.device(self.device):
             return B.lc_plan_table(self._handle, which, sizes[which], _stream_ptr(self.device))
+
+    def check(self):
+        """Raise if a bounded device-side wait of an earlier execution ran out."""
+        with torch.cuda.device(self.device):
+            B.lc_plan_check(self._handle, _stream_ptr(self.device))
 
     def launches(self) -> int:
         return B.lc_plan_launches(self._handle)

@@ -23,7 +23,7 @@ EXPORTED = (
     "lc_plan_options_default", "lc_plan_workspace_size", "lc_plan_workspace_size_ex",
     "lc_plan_create", "lc_plan_create_ex", "lc_plan_workspace_size_ragged", "lc_plan_create_ragged",
     "lc_execute", "lc_adjoint", "lc_destroy", "lc_status_string", "lc_plan_info", "lc_plan_table",
-    "lc_plan_launches", "lc_plan_set_timing", "lc_plan_get_timing", "lc_direct_static",
+    "lc_plan_launches", "lc_plan_set_timing", "lc_plan_get_timing", "lc_plan_check", "lc_direct_static",
 )
 
 
@@ -35,7 +35,7 @@ class LegChebError(RuntimeError):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("s_hat", ctypes.c_int32), ("fixed_s", ctypes.c_int32), ("slices", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("debug_flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -73,6 +73,7 @@ def load(path: Path | None = None):
         "lc_plan_table": [vp, i32, ctypes.POINTER(ctypes.c_double), i64, p64, vp],
         "lc_plan_launches": [vp, pi32],
         "lc_plan_set_timing": [vp, i32],
+        "lc_plan_check": [vp, vp],
         "lc_plan_get_timing": [vp, i32, ctypes.POINTER(ctypes.c_float), pi32, i32, pi32],
     }
     for name, args in sig.items():
@@ -179,6 +180,11 @@ def lc_plan_launches(plan) -> int:
     v = ctypes.c_int32()
     _check(load().lc_plan_launches(ctypes.c_void_p(plan), ctypes.byref(v)), "lc_plan_launches")
     return v.value
+
+
+def lc_plan_check(plan, stream_ptr):
+    """Raise LegChebError(LC_ERR_DEVICE_TIMEOUT) if a bounded device wait ran out."""
+    _check(load().lc_plan_check(ctypes.c_void_p(plan), ctypes.c_void_p(stream_ptr)), "lc_plan_check")
 
 
 def lc_plan_set_timing(plan, slots: int):

@@ -24,6 +24,35 @@ __device__ __forceinline__ lc_df cinv<lc_df>(int64_t i) {
   return i == 0 ? lc_df(0.31830987334251404f, 1.2841276486597053e-08f)
                 : lc_df(0.6366197466850281f, 2.5682552973194106e-08f);
 }
+// Lean accumulation: the product's error terms and the TwoSum error are
+// gathered in acc.lo without renormalising; finish() normalises once.
+template <>
+__device__ __forceinline__ lc_df acc2<lc_df>(const lc_df& acc, const lc_df& a, const lc_df& b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  const float s = acc.hi + p;
+  const float bb = s - acc.hi;
+  const float t = (acc.hi - (s - bb)) + (p - bb);
+  return lc_df(s, acc.lo + (t + e));
+}
+template <>
+__device__ __forceinline__ lc_df acc3<lc_df>(const lc_df& acc, const lc_df& a, const lc_df& b, const lc_df& c) {
+  const float p1 = a.hi * b.hi;
+  float e1 = fmaf(a.hi, b.hi, -p1);
+  e1 = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e1));
+  const float p2 = p1 * c.hi;
+  float e2 = fmaf(p1, c.hi, -p2);
+  e2 = fmaf(p1, c.lo, fmaf(e1, c.hi, e2));
+  const float s = acc.hi + p2;
+  const float bb = s - acc.hi;
+  const float t = (acc.hi - (s - bb)) + (p2 - bb);
+  return lc_df(s, acc.lo + (t + e2));
+}
+template <>
+__device__ __forceinline__ lc_df finish<lc_df>(const lc_df& acc) {
+  return lc_df_fast2(acc.hi, acc.lo);
+}
 }  // namespace lc_exec
 
 using namespace lc_exec;
@@ -34,6 +63,18 @@ __global__ void k_d2df(int64_t n, const double* __restrict__ a, lc_df* __restric
     const double x = a[i];
     const float h = float(x);
     b[i] = lc_df(h, float(x - double(h)));
+  }
+}
+// A-hat copies for the double-float tier are stored transposed, [m][l][k].
+__global__ void k_d2df_T(int64_t nm, const double* __restrict__ a, lc_df* __restrict__ b) {
+  const int64_t total = nm * LC_M * LC_M;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t m = i / (LC_M * LC_M);
+    const int r = int(i % (LC_M * LC_M));
+    const int k = r / LC_M, l = r % LC_M;
+    const double x = a[i];
+    const float h = float(x);
+    b[m * (LC_M * LC_M) + l * LC_M + k] = lc_df(h, float(x - double(h)));
   }
 }
 unsigned blocks_for(int64_t n) {
@@ -52,8 +93,8 @@ lc_status lc_df_prepare(lc_plan p, cudaStream_t st) {
   if (p->dir == LC_C2L) k_d2df<<<blocks_for(g.N), 256, 0, st>>>(g.N, p->lam2, static_cast<lc_df*>(p->df_lam2));
   k_d2df<<<1, 256, 0, st>>>(int64_t(2) * g.s * LC_M, p->T, static_cast<lc_df*>(p->df_T));
   k_d2df<<<1, 256, 0, st>>>(LC_M * LC_M, p->B, static_cast<lc_df*>(p->df_B));
-  if (g.nc > 0) k_d2df<<<blocks_for(g.nc * LC_M * LC_M), 256, 0, st>>>(g.nc * LC_M * LC_M, p->Ahat,
-                                                                      static_cast<lc_df*>(p->df_Ahat));
+  if (g.nc > 0) k_d2df_T<<<blocks_for(g.nc * LC_M * LC_M), 256, 0, st>>>(g.nc, p->Ahat,
+                                                                        static_cast<lc_df*>(p->df_Ahat));
   LC_LAUNCH_CHECK();
   return LC_OK;
 }
@@ -70,6 +111,6 @@ lc_status lc_exec_df(lc_plan p, const void* in, void* out, int64_t ib, int64_t i
   a.t = lc_tables<lc_df>{static_cast<const lc_df*>(p->df_lam), static_cast<const lc_df*>(p->df_lam2),
                          static_cast<const lc_df*>(p->df_T), static_cast<const lc_df*>(p->df_B),
                          static_cast<const lc_df*>(p->df_Ahat), static_cast<lc_df*>(p->df_W),
-                         static_cast<lc_df*>(p->df_Cc)};
+                         static_cast<lc_df*>(p->df_Cc), p->err, p->opt.debug_flags};
   return run<lc_df>(p, a, st, adjoint);
 }

@@ -6,7 +6,7 @@
 using namespace lc_exec;
 
 
-int lc_exec_cuda_cores_launches(const lc_plan_s* p) { return p->g.L > 0 ? 2 * p->g.L + 1 : 1; }
+int lc_exec_cuda_cores_launches(const lc_plan_s* p) { return launches_for<double>(p->g.L); }
 
 lc_status lc_exec_cuda_cores(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob,
                              int64_t oe, cudaStream_t st, int adjoint) {
@@ -18,7 +18,7 @@ lc_status lc_exec_cuda_cores(lc_plan p, const void* in, void* out, int64_t ib, i
     a.ib = ib; a.ie = ie; a.ob = ob; a.oe = oe;
     a.n = p->g.n; a.N = p->g.N; a.L = p->g.L; a.s = p->g.s; a.nseg = p->g.nseg;
     a.batch = p->batch; a.dir = int(p->dir);
-    a.t = lc_tables<double>{p->lam, p->lam2, p->T, p->B, p->Ahat, p->W, p->Cc};
+    a.t = lc_tables<double>{p->lam, p->lam2, p->T, p->B, p->Ahat, p->W, p->Cc, p->err, p->opt.debug_flags};
     return run<double>(p, a, st, adjoint);
   } else {
     Args<float> a;
@@ -27,7 +27,7 @@ lc_status lc_exec_cuda_cores(lc_plan p, const void* in, void* out, int64_t ib, i
     a.ib = ib; a.ie = ie; a.ob = ob; a.oe = oe;
     a.n = p->g.n; a.N = p->g.N; a.L = p->g.L; a.s = p->g.s; a.nseg = p->g.nseg;
     a.batch = p->batch; a.dir = int(p->dir);
-    a.t = lc_tables<float>{p->lamf, p->lam2f, p->Tf, p->Bf, p->Ahatf, p->Wf, p->Ccf};
+    a.t = lc_tables<float>{p->lamf, p->lam2f, p->Tf, p->Bf, p->Ahatf, p->Wf, p->Ccf, p->err, p->opt.debug_flags};
     return run<float>(p, a, st, adjoint);
   }
 }

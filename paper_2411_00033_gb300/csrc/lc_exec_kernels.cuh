@@ -13,20 +13,27 @@
 // j in [i, min(N, 2s(floor(i/2s)+2))), j - i even: the part of the upper
 // triangle that no submatrix of eq:globalij covers.
 //
-// The transposed pass runs the same kernels with the roles of row and column
-// segments exchanged (leaf restriction over row segments, the row tree
-// upwards, A-hat transposed, the column tree downwards, spread over column
-// segments, transposed band).
+// Launch structure: the levels are cut into chunks and each CTA owns the
+// subtree of one node of a chunk's top level, so consecutive levels never
+// need a grid-wide barrier inside a chunk:
+//   up chunks (bottom to top): the first one restricts the input over
+//     2^5 leaf segments and climbs 5 levels; each later one climbs up to 4
+//     more levels from the previous chunk's top level;
+//   down chunks (top to bottom): each adds, level by level, the parent's
+//     contribution of Step 4 to the coupling result of Step 3; the last chunk
+//     ends at the leaves and also does the spread, the near-field band with
+//     its operands staged in shared memory, and the scaling.
+// The coupling of Step 3 for all levels is one launch between the two passes.
+// For L = 13 (n = 1e6) that is 7 launches instead of 2L+1 = 27.
+//
+// The transposed pass (lc_adjoint) runs the same kernels with the roles of
+// the trees exchanged: restriction over row segments and the row tree
+// upwards, A-hat transposed in the coupling, the column tree downwards,
+// spread over column segments and the transposed band.
 #pragma once
 #include "lc_internal.cuh"
 
 namespace lc_exec {
-
-
-constexpr int kSegs = 4;                 // segments per CTA in leaf/up/down kernels
-constexpr int kThreadsSeg = 2 * LC_M;    // (sigma, k) pairs per segment
-constexpr int kCoupleSegs = 8;
-constexpr int kFinalThreads = 128;
 
 // Element conversions between the I/O type and the arithmetic type R.
 template <typename R, typename IO>
@@ -57,302 +64,499 @@ __device__ __forceinline__ R cinv(int64_t i) {
 template <typename R>
 __device__ __forceinline__ R negate(const R& v) { return -v; }
 
-// Leaf restriction (Step 1) over segments [lo, hi) of the leaf level.
-// scale_rows: multiply the input by C^{-1} first (transposed L2C pass).
+// Dot-product accumulation.  Generic: fused multiply-add in R.  The
+// double-float tier specialises these to keep an unnormalised error word and
+// normalise once at the end (see lc_df.cu).
 template <typename R>
-__global__ void k_leaf(Args<R> a, int64_t lo, int64_t hi, int scale_rows) {
-  extern __shared__ unsigned char smem_raw[];
-  R* Ts = reinterpret_cast<R*>(smem_raw);               // [2][s][M]
-  R* fs = Ts + 2 * a.s * LC_M;                           // [kSegs][2s]
-  const int s = a.s, L = a.L;
-  for (int i = threadIdx.x; i < 2 * s * LC_M; i += blockDim.x) Ts[i] = a.t.T[i];
-  const int64_t g0 = lo + int64_t(blockIdx.x) * kSegs;
-  const int seg = threadIdx.x / kThreadsSeg;
-  const int sigma = (threadIdx.x % kThreadsSeg) / LC_M;
-  const int k = threadIdx.x % LC_M;
-  for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSegs * 2 * s; i += blockDim.x) {
-      const int64_t g = g0 + i / (2 * s);
-      const int64_t j = g * 2 * s + i % (2 * s);
-      R v = R(0);
-      if (g < hi && j < a.n) {
-        v = lc_ld<R>(a.in + b * a.ib + j * a.ie);
-        if (scale_rows) v *= cinv<R>(j);
-      }
-      fs[i] = v;
-    }
-    __syncthreads();
-    const int64_t g = g0 + seg;
-    if (seg < kSegs && g < hi) {
-      const R* fseg = fs + seg * 2 * s;
-      R acc = R(0);
-      for (int m = 0; m < s; ++m) acc = fma(fseg[2 * m + sigma], Ts[(sigma * s + m) * LC_M + k], acc);
-      a.t.W[((b * a.nseg) + lc_seg_offset(L - 1) + g) * (2 * LC_M) + sigma * LC_M + k] = acc;
-    }
-  }
+__device__ __forceinline__ R acc2(const R& acc, const R& a, const R& b) { return fma(a, b, acc); }
+template <typename R>
+__device__ __forceinline__ R acc3(const R& acc, const R& a, const R& b, const R& c) { return fma(a * b, c, acc); }
+template <typename R>
+__device__ __forceinline__ R finish(const R& acc) { return acc; }
+// A-hat(m)[k][l]: the FP64 table keeps row-major [k][l]; the FP32 and
+// double-float copies are stored transposed, [l][k], so that threads that
+// own consecutive k read consecutive addresses.
+template <typename R>
+__device__ __forceinline__ const R& ahat_at(const R* Ah, int64_t m, int k, int l) {
+  return Ah[m * (LC_M * LC_M) + l * LC_M + k];
+}
+template <>
+__device__ __forceinline__ const double& ahat_at<double>(const double* Ah, int64_t m, int k, int l) {
+  return Ah[m * (LC_M * LC_M) + k * LC_M + l];
 }
 
-// Upward pass (Step 2): level gc -> gc-1 for parents P in [lo, hi):
-//   w(gc-1, P) = B(0) w(gc, 2P) + B(1) w(gc, 2P+1), by Algorithm a.1:
-//   z0 = w_left + w_right, z1 = w_left - w_right,
-//   out_k = sum_{j<=k} b_kj z_{(k-j) mod 2, j}.
+constexpr int kThreads = 256;
+constexpr int kLeafDepth = 4;   // levels climbed by the first up chunk / descended by the last down chunk
+constexpr int kChunkDepth = 4;  // levels per middle chunk
+constexpr int kSeg = 2 * LC_M;  // values per segment: [sigma][k]
+
+// Node x at level gamma of the column tree (segments g >= 2) or of the row
+// tree (segments v < 2 b_gamma).
+__device__ __forceinline__ bool node_valid(bool col, int gamma, int64_t x) {
+  const int64_t n = int64_t(4) << gamma;
+  return col ? (x >= 2 && x < n) : (x >= 0 && x < n - 2);
+}
+
+// Offsets (in R elements) of level d inside a subtree buffer.
+__device__ __forceinline__ int sub_off(int d) { return ((1 << d) - 1) * kSeg; }
+
+// ---------------------------------------------------------------- up chunk
+// Root x0 = blockIdx.x at level rho; bottom level rho + depth.  leaf != 0:
+// the bottom level is the leaf level, computed from the input (Step 1).
 template <typename R>
-__global__ void k_up(Args<R> a, int gc, int64_t lo, int64_t hi) {
+__global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int depth, int leaf, int adj) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* nodes = reinterpret_cast<R*>(smem_raw);                 // (2^(depth+1) - 1) segments
+  R* zt = nodes + sub_off(depth + 1);                         // 2 x 2^(depth-1) segments
+  R* Ts = zt + 2 * (1 << (depth > 0 ? depth - 1 : 0)) * kSeg;  // [2][s][M]
+  R* fs = Ts + 2 * a.s * LC_M;                                // [2^depth][2s]
   __shared__ R Bs[LC_M * LC_M];
-  __shared__ R z[kSegs][2][2][LC_M];  // [seg][z0/z1][sigma][j]
+  const bool col = !adj;
+  const int s = a.s, L = a.L;
+  const int64_t x0 = blockIdx.x;
+  const int gb = rho + depth;
+  const int nb = 1 << depth;
   for (int i = threadIdx.x; i < LC_M * LC_M; i += blockDim.x) Bs[i] = a.t.B[i];
-  const int seg = threadIdx.x / kThreadsSeg;
-  const int sigma = (threadIdx.x % kThreadsSeg) / LC_M;
-  const int k = threadIdx.x % LC_M;
-  const int64_t P = lo + int64_t(blockIdx.x) * kSegs + seg;
+  if (leaf)
+    for (int i = threadIdx.x; i < 2 * s * LC_M; i += blockDim.x) Ts[i] = a.t.T[i];
   for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
+    R* Wb = a.t.W + b * a.nseg * kSeg;
     __syncthreads();
-    if (seg < kSegs && P < hi) {
-      const R* wc = a.t.W + ((b * a.nseg) + lc_seg_offset(gc) + 2 * P) * (2 * LC_M);
-      const R l = wc[sigma * LC_M + k], r = wc[2 * LC_M + sigma * LC_M + k];
-      z[seg][0][sigma][k] = l + r;
-      z[seg][1][sigma][k] = l - r;
+    if (leaf) {
+      const int64_t p0 = (x0 << depth) * 2 * s;
+      const typename lc_io<R>::type* f = a.in + b * a.ib;
+      const bool scale = adj && a.dir == LC_L2C;  // transposed L2C starts with C^{-1}
+      for (int i = threadIdx.x; i < nb * 2 * s; i += blockDim.x) {
+        const int64_t j = p0 + i;
+        R v = R(0);
+        if (j < a.n) {
+          v = lc_ld<R>(f + j * a.ie);
+          if (scale) v *= cinv<R>(j);
+        }
+        fs[i] = v;
+      }
+      __syncthreads();
+      R* lev = nodes + sub_off(depth);
+      for (int t = threadIdx.x; t < nb * kSeg; t += blockDim.x) {
+        const int j = t / kSeg, sigma = (t % kSeg) / LC_M, k = t % LC_M;
+        const int64_t x = (x0 << depth) + j;
+        R acc = R(0);
+        if (node_valid(col, gb, x)) {
+          const R* fseg = fs + j * 2 * s;
+          for (int m = 0; m < s; ++m) acc = acc2(acc, fseg[2 * m + sigma], Ts[(sigma * s + m) * LC_M + k]);
+          acc = finish(acc);
+          Wb[(lc_seg_offset(gb) + x) * kSeg + sigma * LC_M + k] = acc;
+        }
+        lev[t] = acc;
+      }
+    } else {
+      R* lev = nodes + sub_off(depth);
+      for (int t = threadIdx.x; t < nb * kSeg; t += blockDim.x) {
+        const int64_t x = (x0 << depth) + t / kSeg;
+        lev[t] = node_valid(col, gb, x) ? Wb[(lc_seg_offset(gb) + x) * kSeg + t % kSeg] : R(0);
+      }
     }
-    __syncthreads();
-    if (seg < kSegs && P < hi) {
-      R acc = R(0);
-      for (int j = 0; j <= k; ++j) acc = fma(Bs[k * LC_M + j], z[seg][(k - j) & 1][sigma][j], acc);
-      a.t.W[((b * a.nseg) + lc_seg_offset(gc - 1) + P) * (2 * LC_M) + sigma * LC_M + k] = acc;
+    for (int d = depth - 1; d >= 0; --d) {
+      __syncthreads();
+      const int gamma = rho + d;
+      const int nd = 1 << d;
+      const R* ch = nodes + sub_off(d + 1);
+      // z0 = w(2x) + w(2x+1), z1 = w(2x) - w(2x+1)   (Algorithm a.1)
+      for (int t = threadIdx.x; t < nd * kSeg; t += blockDim.x) {
+        const int j = t / kSeg, e = t % kSeg;
+        const R l = ch[(2 * j) * kSeg + e], r = ch[(2 * j + 1) * kSeg + e];
+        zt[t] = l + r;
+        zt[nd * kSeg + t] = l - r;
+      }
+      __syncthreads();
+      R* lev = nodes + sub_off(d);
+      for (int t = threadIdx.x; t < nd * kSeg; t += blockDim.x) {
+        const int j = t / kSeg, sigma = (t % kSeg) / LC_M, k = t % LC_M;
+        const int64_t x = (x0 << d) + j;
+        R acc = R(0);
+        if (node_valid(col, gamma, x)) {
+          const R* z0 = zt + j * kSeg + sigma * LC_M;
+          const R* z1 = z0 + nd * kSeg;
+          for (int jj = 0; jj <= k; ++jj) acc = acc2(acc, Bs[k * LC_M + jj], ((k - jj) & 1) ? z1[jj] : z0[jj]);
+          acc = finish(acc);
+          Wb[(lc_seg_offset(gamma) + x) * kSeg + sigma * LC_M + k] = acc;
+        }
+        lev[t] = acc;
+      }
     }
   }
 }
 
-// Coupling (Step 3), all levels in one launch.  Forward: one output row
-// segment v per group of 18 threads:
-//   v even: c = A-hat(b,0) w(2b+2) + A-hat(b,1) w(2b+3);  v odd: c = A-hat(b,2) w(2b+3).
-// Transposed: one output column segment g:
-//   g even: c = A-hat(b,0)^T w(2b), b = (g-2)/2;
-//   g odd:  c = A-hat(b,1)^T w(2b) + A-hat(b,2)^T w(2b+1), b = (g-3)/2.
-template <typename R, bool kAdj>
-__global__ void k_couple(Args<R> a) {
-  const int seg = threadIdx.x / LC_M;
-  const int k = threadIdx.x % LC_M;
-  const int64_t t = int64_t(blockIdx.x) * kCoupleSegs + seg;
-  if (seg >= kCoupleSegs || t >= a.nseg) return;
+// ------------------------------------------------------------- coupling
+// Step 3 for every level in one launch.  Each CTA takes kCBlocks consecutive
+// blocks b of one level; their 3 kCBlocks A-hat matrices are contiguous in
+// the plan, so they are staged into shared memory with coalesced loads
+// before the products.  Block b couples
+//   forward:    rows 2b, 2b+1 with columns 2b+2, 2b+3:
+//     c(2b) = A(b,0) w(2b+2) + A(b,1) w(2b+3),  c(2b+1) = A(b,2) w(2b+3);
+//   transposed: columns 2b+2, 2b+3 with rows 2b, 2b+1:
+//     c(2b+2) = A(b,0)^T w(2b),  c(2b+3) = A(b,1)^T w(2b) + A(b,2)^T w(2b+1).
+constexpr int kCBlocks = 4;
+
+// Bulk copy global -> shared (TMA, no tensor map), completing on an mbarrier.
+// Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  const uint32_t d = uint32_t(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               :: "r"(d), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
+  uint32_t done;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
+  return done != 0;
+}
+// Wait for the phase with a deadline of about one second; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+  const long long t0 = clock64();
+  while (!mbar_try(mbar, phase)) {
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+  return true;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  R* As = reinterpret_cast<R*>(smem_raw);          // [3 kCBlocks][M][M]
+  R* Ws = As + 3 * kCBlocks * LC_M * LC_M;          // [2 kCBlocks][2][M]
+  // locate (level, first block) of this CTA
   int gamma = 0;
-  while (gamma + 1 < a.L && t >= lc_seg_offset(gamma + 1)) ++gamma;
-  const int64_t v = t - lc_seg_offset(gamma);
-  const int64_t nrow = (int64_t(4) << gamma) - 2;  // 2 b_gamma
-  const int64_t aoff = lc_ahat_offset(gamma);
-  const R* Ah = a.t.Ahat;
-  for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
-    const R* Wl = a.t.W + ((b * a.nseg) + lc_seg_offset(gamma)) * (2 * LC_M);
-    R* Cl = a.t.Cc + ((b * a.nseg) + lc_seg_offset(gamma)) * (2 * LC_M);
-    R c0 = R(0), c1 = R(0);
-    if (!kAdj) {
-      if (v >= nrow) continue;
-      const int64_t bb = v >> 1;
-      if ((v & 1) == 0) {
-        const R* A0 = Ah + (aoff + 3 * bb + 0) * (LC_M * LC_M) + k * LC_M;
-        const R* A1 = Ah + (aoff + 3 * bb + 1) * (LC_M * LC_M) + k * LC_M;
-        const R* w0 = Wl + (v + 2) * (2 * LC_M);
-        const R* w1 = Wl + (v + 3) * (2 * LC_M);
-        for (int l = 0; l < LC_M; ++l) {
-          c0 = fma(A0[l], w0[l], c0);
-          c1 = fma(A0[l], w0[LC_M + l], c1);
-          c0 = fma(A1[l], w1[l], c0);
-          c1 = fma(A1[l], w1[LC_M + l], c1);
-        }
-      } else {
-        const R* A2 = Ah + (aoff + 3 * bb + 2) * (LC_M * LC_M) + k * LC_M;
-        const R* w0 = Wl + (v + 2) * (2 * LC_M);
-        for (int l = 0; l < LC_M; ++l) {
-          c0 = fma(A2[l], w0[l], c0);
-          c1 = fma(A2[l], w0[LC_M + l], c1);
-        }
+  int64_t first = blockIdx.x, per;
+  for (;;) {
+    per = ((int64_t(2) << gamma) - 1 + kCBlocks - 1) / kCBlocks;
+    if (first < per || gamma + 1 >= a.L) break;
+    first -= per;
+    ++gamma;
+  }
+  const int64_t nblk = (int64_t(2) << gamma) - 1;  // b_gamma
+  const int64_t b0 = first * kCBlocks;
+  const int nb = int(nblk - b0 < kCBlocks ? nblk - b0 : kCBlocks);
+  if (nb <= 0) return;
+  const int64_t m0 = lc_ahat_offset(gamma) + 3 * b0;
+  const uint32_t bytesA = uint32_t(3 * nb * LC_M * LC_M * sizeof(R));
+  const uint32_t bytesW = uint32_t(2 * nb * kSeg * sizeof(R));
+  const uint32_t mb = uint32_t(__cvta_generic_to_shared(&mbar));
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  uint32_t phase = 0;
+  for (int64_t bt = blockIdx.y; bt < a.batch; bt += gridDim.y) {
+    const R* Wl = a.t.W + (bt * a.nseg + lc_seg_offset(gamma)) * kSeg;
+    R* Cl = a.t.Cc + (bt * a.nseg + lc_seg_offset(gamma)) * kSeg;
+    // source segments: forward columns 2b0+2 .., transposed rows 2b0 ..
+    const int64_t s0 = adj ? 2 * b0 : 2 * b0 + 2;
+    const bool loadA = (bt == blockIdx.y);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      const uint32_t bytes = bytesW + (loadA ? bytesA : 0u);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" :: "r"(mb), "r"(bytes) : "memory");
+      if (loadA && !(a.t.debug & 1)) bulk_g2s(As, a.t.Ahat + m0 * (LC_M * LC_M), bytesA, mb);
+      bulk_g2s(Ws, Wl + s0 * kSeg, bytesW, mb);
+    }
+    bool ok = mbar_wait_bounded(mb, phase);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(a.t.err, 1);
+        mbar_wait_bounded(mb, phase);  // let a late copy land before the CTA exits
       }
-    } else {
-      const int64_t g = v;
-      if (g < 2) continue;
-      if ((g & 1) == 0) {
-        const int64_t bb = (g - 2) >> 1;
-        const R* A0 = Ah + (aoff + 3 * bb + 0) * (LC_M * LC_M) + k;
-        const R* w0 = Wl + (2 * bb) * (2 * LC_M);
-        for (int l = 0; l < LC_M; ++l) {
-          c0 = fma(A0[l * LC_M], w0[l], c0);
-          c1 = fma(A0[l * LC_M], w0[LC_M + l], c1);
+      return;
+    }
+    phase ^= 1u;
+    for (int t = threadIdx.x; t < 2 * nb * kSeg; t += blockDim.x) {
+      const int jb = t / (2 * kSeg);            // block within the group
+      const int half = (t / kSeg) & 1;          // which of the two output segments
+      const int sigma = (t % kSeg) / LC_M, k = t % LC_M;
+      const R* A0 = As + (3 * jb) * (LC_M * LC_M);
+      const R* w0 = Ws + (2 * jb) * kSeg + sigma * LC_M;
+      const R* w1 = w0 + kSeg;
+      R c = R(0);
+      if (!adj) {
+        if (half == 0) {
+          for (int l = 0; l < LC_M; ++l) {
+            c = acc2(c, ahat_at(A0, 0, k, l), w0[l]);
+            c = acc2(c, ahat_at(A0, 1, k, l), w1[l]);
+          }
+        } else {
+          for (int l = 0; l < LC_M; ++l) c = acc2(c, ahat_at(A0, 2, k, l), w1[l]);
         }
+        Cl[(2 * (b0 + jb) + half) * kSeg + sigma * LC_M + k] = finish(c);
       } else {
-        const int64_t bb = (g - 3) >> 1;
-        const R* A1 = Ah + (aoff + 3 * bb + 1) * (LC_M * LC_M) + k;
-        const R* A2 = Ah + (aoff + 3 * bb + 2) * (LC_M * LC_M) + k;
-        const R* w0 = Wl + (2 * bb) * (2 * LC_M);
-        const R* w1 = Wl + (2 * bb + 1) * (2 * LC_M);
-        for (int l = 0; l < LC_M; ++l) {
-          c0 = fma(A1[l * LC_M], w0[l], c0);
-          c1 = fma(A1[l * LC_M], w0[LC_M + l], c1);
-          c0 = fma(A2[l * LC_M], w1[l], c0);
-          c1 = fma(A2[l * LC_M], w1[LC_M + l], c1);
+        if (half == 0) {
+          for (int l = 0; l < LC_M; ++l) c = acc2(c, ahat_at(A0, 0, l, k), w0[l]);
+        } else {
+          for (int l = 0; l < LC_M; ++l) {
+            c = acc2(c, ahat_at(A0, 1, l, k), w0[l]);
+            c = acc2(c, ahat_at(A0, 2, l, k), w1[l]);
+          }
         }
+        Cl[(2 * (b0 + jb) + 2 + half) * kSeg + sigma * LC_M + k] = finish(c);
       }
     }
-    Cl[v * (2 * LC_M) + k] = c0;
-    Cl[v * (2 * LC_M) + LC_M + k] = c1;
   }
 }
 
-// Downward pass (Step 4): level gp -> gp+1 for children v in [lo, hi):
-//   c(gp+1, v) += B(v mod 2)^T c(gp, v/2), with b(1)_jk = (-1)^(j-k) b(0)_jk.
 template <typename R>
-__global__ void k_down(Args<R> a, int gp, int64_t lo, int64_t hi) {
+inline int64_t couple_ctas(int L) {
+  int64_t n = 0;
+  for (int g = 0; g < L; ++g) n += ((int64_t(2) << g) - 1 + kCBlocks - 1) / kCBlocks;
+  return n;
+}
+
+// Shared-memory sizes (bytes) of the chunk kernels.
+template <typename R>
+inline size_t up_smem(int depth, int s, int leaf) {
+  size_t v = size_t((2 << depth) - 1) * kSeg + 2 * size_t(1 << (depth > 0 ? depth - 1 : 0)) * kSeg;
+  if (leaf) v += size_t(2) * s * LC_M + size_t(1 << depth) * 2 * s;
+  return v * sizeof(R) + 16;
+}
+template <typename R>
+inline size_t down_smem(int depth, int s, int fin, int64_t nrows_direct) {
+  size_t v = size_t((2 << depth) - 1) * kSeg;
+  if (fin) {
+    const size_t rows = nrows_direct > 0 ? size_t(nrows_direct) : (size_t(1) << depth) * 2 * s;
+    v += size_t(2) * s * LC_M;             // T
+    v += rows + 4 * size_t(s) + 8;         // operand tile
+    v += 2 * size_t(s) + 8;                // lambda_k
+    v += rows + 2 * size_t(s) + 8;         // lambda_(i+k)
+    if (nrows_direct > 0) v += 2 * rows;   // direct-only plans: full triangle tables
+  }
+  return v * sizeof(R) + 16;
+}
+
+// -------------------------------------------------------------- down chunk
+// Root x0 = blockIdx.x at level rho; levels rho .. rho + depth, each node:
+//   c(gamma, x) = couple(gamma, x) + [parent valid] B(x mod 2)^T c(gamma-1, x/2).
+// fin != 0: the bottom level is the leaf level; finish with Steps 5-7 for the
+// rows (forward) or columns (transposed) of the subtree.  L == 0: direct-only
+// plan, one CTA computes the whole triangle.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_down_chunk(Args<R> a, int rho, int depth, int fin, int adj) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ R Bs[LC_M * LC_M];
-  __shared__ R par[kSegs][2][LC_M];
+  const bool col = adj;  // forward: row tree; transposed: column tree
+  const int s = a.s, L = a.L;
+  const int64_t two_s = 2 * int64_t(s);
+  const int64_t x0 = blockIdx.x;
+  R* nodes = reinterpret_cast<R*>(smem_raw);
+  R* Ts = nodes + sub_off(depth + 1);
   for (int i = threadIdx.x; i < LC_M * LC_M; i += blockDim.x) Bs[i] = a.t.B[i];
-  const int seg = threadIdx.x / kThreadsSeg;
-  const int sigma = (threadIdx.x % kThreadsSeg) / LC_M;
-  const int k = threadIdx.x % LC_M;
-  const int64_t v = lo + int64_t(blockIdx.x) * kSegs + seg;
+  if (fin)
+    for (int i = threadIdx.x; i < 2 * s * LC_M; i += blockDim.x) Ts[i] = a.t.T[i];
   for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
-    __syncthreads();
-    if (seg < kSegs && v < hi)
-      par[seg][sigma][k] = a.t.Cc[((b * a.nseg) + lc_seg_offset(gp) + (v >> 1)) * (2 * LC_M) + sigma * LC_M + k];
-    __syncthreads();
-    if (seg < kSegs && v < hi) {
-      R acc = R(0);
-      const bool odd = (v & 1) != 0;
-      for (int j = k; j < LC_M; ++j) {
-        const R bjk = Bs[j * LC_M + k];
-        acc = fma((odd && ((j - k) & 1)) ? negate(bjk) : bjk, par[seg][sigma][j], acc);
+    R* Cb = a.t.Cc + b * a.nseg * kSeg;
+    if (L > 0) {
+      for (int d = 0; d <= depth; ++d) {
+        __syncthreads();
+        const int gamma = rho + d;
+        const int nd = 1 << d;
+        R* lev = nodes + sub_off(d);
+        for (int t = threadIdx.x; t < nd * kSeg; t += blockDim.x) {
+          const int j = t / kSeg, sigma = (t % kSeg) / LC_M, k = t % LC_M;
+          const int64_t x = (x0 << d) + j;
+          R c = R(0);
+          if (node_valid(col, gamma, x)) {
+            c = Cb[(lc_seg_offset(gamma) + x) * kSeg + sigma * LC_M + k];  // Step 3 result (k_couple_blocks)
+            if (gamma > 0 && node_valid(col, gamma - 1, x >> 1)) {
+              const R* pv = (d == 0) ? Cb + (lc_seg_offset(gamma - 1) + (x >> 1)) * kSeg + sigma * LC_M
+                                     : nodes + sub_off(d - 1) + (j >> 1) * kSeg + sigma * LC_M;
+              const bool odd = (x & 1) != 0;
+              for (int jj = k; jj < LC_M; ++jj) {
+                const R bjk = Bs[jj * LC_M + k];
+                c = acc2(c, (odd && ((jj - k) & 1)) ? negate(bjk) : bjk, pv[jj]);
+              }
+            }
+            c = finish(c);
+          }
+          lev[t] = c;
+        }
       }
-      a.t.Cc[((b * a.nseg) + lc_seg_offset(gp + 1) + v) * (2 * LC_M) + sigma * LC_M + k] += acc;
+      if (!fin) {
+        __syncthreads();
+        const int gamma = rho + depth;
+        const R* lev = nodes + sub_off(depth);
+        for (int t = threadIdx.x; t < (1 << depth) * kSeg; t += blockDim.x) {
+          const int64_t x = (x0 << depth) + t / kSeg;
+          if (node_valid(col, gamma, x)) Cb[(lc_seg_offset(gamma) + x) * kSeg + t % kSeg] = lev[t];
+        }
+        continue;
+      }
     }
-  }
-}
-
-// Steps 5-7 for the forward pass: one thread per output row i < n.
-template <typename R>
-__global__ void k_final(Args<R> a) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const int s = a.s, L = a.L;
-  const int64_t two_s = 2 * int64_t(s);
-  const int64_t v = i / two_s;
-  const int l = int(i - v * two_s);
-  const int m = l >> 1, sigma = l & 1;
-  const int64_t nleaf_rows = (int64_t(2) << L) - 2;
-  const int64_t end = (L > 0) ? min(a.n, two_s * (v + 2)) : a.n;
-  const R* Trow = a.t.T + (sigma * s + m) * LC_M;
-  for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
+    // ---------------- Steps 5-7 for this subtree's rows (forward) or columns (transposed)
+    const R* leafc = nodes + sub_off(depth);
+    const int64_t lo = (L > 0) ? (x0 << depth) * two_s : 0;
+    const int64_t hi_raw = (L > 0) ? ((x0 + 1) << depth) * two_s : a.n;
+    const int64_t hi = hi_raw < a.n ? hi_raw : a.n;
+    if (lo >= hi) continue;
     const typename lc_io<R>::type* f = a.in + b * a.ib;
-    R far = R(0);
-    if (L > 0 && v < nleaf_rows) {
-      const R* c = a.t.Cc + ((b * a.nseg) + lc_seg_offset(L - 1) + v) * (2 * LC_M) + sigma * LC_M;
-      for (int k = 0; k < LC_M; ++k) far = fma(c[k], Trow[k], far);
-    }
-    R near = R(0);
-    R res;
-    if (a.dir == LC_L2C) {
-      // a_{i,i+2k} = lambda_k lambda_{i+k}   (eq:hik)
-      int64_t kk = 0;
-      for (int64_t j = i; j < end; j += 2, ++kk) near = fma(a.t.lam[kk] * a.t.lam2[i + kk], lc_ld<R>(f + j * a.ie), near);
-      res = cinv<R>(i) * (far + near);
+    R* opnd = Ts + 2 * s * LC_M;  // operand tile (input values, pre-scaled)
+    int64_t olo, ohi;             // operand index range
+    if (!adj) {
+      olo = lo;
+      ohi = (L > 0) ? hi + 2 * two_s : a.n;
     } else {
-      // L(i, i+2k) = (2i+1)(i+2k) u_k v_{i+k}; L(0,0) = 1   (eq:Lxymod)
-      int64_t kk = 0;
-      for (int64_t j = i; j < end; j += 2, ++kk)
-        near = fma(a.t.lam[kk] * a.t.lam2[i + kk], R(j) * lc_ld<R>(f + j * a.ie), near);
-      near *= R(2 * i + 1);
-      if (i == 0) near += lc_ld<R>(f);
-      res = far + near;
+      olo = (L > 0) ? (lo - two_s > 0 ? lo - two_s : 0) : 0;
+      ohi = hi;
     }
-    lc_st<R>(a.out + b * a.ob + i * a.oe, res);
+    if (ohi > a.n) ohi = a.n;
+    const int64_t olen = ohi - olo;
+    R* lamk = opnd + olen + 8;       // lambda_k (L2C) / u_k (C2L), k < kmax
+    const int64_t kmax = (L > 0) ? two_s : (a.n + 1) / 2;
+    R* lamm = lamk + kmax + 8;       // lambda_m / v_m for m in [mlo, mhi)
+    const int64_t mlo = adj ? (olo + lo) / 2 : lo;
+    const int64_t mhi = adj ? hi : (hi + ohi) / 2 + 1;
+    const int64_t mcap = mhi < a.N ? mhi : a.N;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < olen; i += blockDim.x) {
+      const int64_t q = olo + i;
+      R v = lc_ld<R>(f + q * a.ie);
+      if (!adj) {
+        if (a.dir == LC_C2L) v = R(q) * v;                // L(i, j) = (2i+1) j u v: scale column j
+      } else {
+        v = (a.dir == LC_L2C) ? cinv<R>(q) * v : R(2 * q + 1) * v;  // C^{-1} r or (2i+1) r
+      }
+      opnd[i] = v;
+    }
+    for (int64_t k = threadIdx.x; k < kmax; k += blockDim.x) lamk[k] = (k < a.N) ? a.t.lam[k] : R(0);
+    for (int64_t m = mlo + threadIdx.x; m < mhi; m += blockDim.x) lamm[m - mlo] = (m < mcap) ? a.t.lam2[m] : R(0);
+    __syncthreads();
+    const bool l2c = (a.dir == LC_L2C);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const int64_t v = i / two_s;
+      const int l = int(i - v * two_s);
+      const int m = l >> 1, sigma = l & 1;
+      R far = R(0);
+      if (L > 0 && node_valid(col, L - 1, v)) {
+        const R* c = leafc + (v - (x0 << depth)) * kSeg + sigma * LC_M;
+        const R* Trow = Ts + (sigma * s + m) * LC_M;
+        for (int k = 0; k < LC_M; ++k) far = acc2(far, c[k], Trow[k]);
+        far = finish(far);
+      }
+      R near = R(0);
+      if (!adj) {
+        // row i: sum over j = i + 2k in the band  (eq:hik, eq:Lxymod)
+        const int64_t end = (L > 0) ? (two_s * (v + 2) < a.n ? two_s * (v + 2) : a.n) : a.n;
+        const R* fo = opnd + (i - olo);
+        const R* lm = lamm + (i - mlo);
+        int64_t kk = 0;
+        for (int64_t j = i; j < end; j += 2, ++kk) near = acc3(near, lamk[kk], lm[kk], fo[2 * kk]);
+        near = finish(near);
+        R res;
+        if (l2c) {
+          res = cinv<R>(i) * (far + near);
+        } else {
+          // (2i+1) u_k v_(i+k) (j f_j) summed; entry (0,0) = 1 adds f_0 (eq:Lxymod)
+          res = far + R(2 * i + 1) * near;
+          if (i == 0) res += lc_ld<R>(f);
+        }
+        lc_st<R>(a.out + b * a.ob + i * a.oe, res);
+      } else {
+        // column j = i: sum over rows r <= j in the band
+        int64_t st = (L > 0) ? (two_s * (v - 1) > 0 ? two_s * (v - 1) : 0) : 0;
+        if ((st & 1) != (i & 1)) ++st;
+        for (int64_t r = st; r <= i; r += 2) {
+          const int64_t k = (i - r) >> 1;
+          near = acc3(near, lamk[k], lamm[(r + i) / 2 - mlo], opnd[r - olo]);
+        }
+        near = finish(near);
+        if (!l2c) {
+          near = R(i) * near;
+          if (i == 0) near += lc_ld<R>(f);
+        }
+        lc_st<R>(a.out + b * a.ob + i * a.oe, far + near);
+      }
+    }
   }
 }
 
-// Transposed Steps 7-5: one thread per output column j < n:
-//   g_j = [spread of c over column segment j/2s] + sum_{band rows i of column j} M_ij r_i
-// with r scaled by C^{-1} for L2C.  Band rows of column j: i <= j, same
-// parity, floor(i/2s) >= floor(j/2s) - 1.
+// ------------------------------------------------------------------ driver
 template <typename R>
-__global__ void k_final_adj(Args<R> a) {
-  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= a.n) return;
-  const int s = a.s, L = a.L;
-  const int64_t two_s = 2 * int64_t(s);
-  const int64_t g = j / two_s;
-  const int l = int(j - g * two_s);
-  const int m = l >> 1, sigma = l & 1;
-  int64_t start = (L > 0) ? max(int64_t(0), two_s * (g - 1)) : 0;
-  if ((start & 1) != (j & 1)) ++start;
-  const R* Trow = a.t.T + (sigma * s + m) * LC_M;
-  for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
-    const typename lc_io<R>::type* r = a.in + b * a.ib;
-    R far = R(0);
-    if (L > 0 && g >= 2) {
-      const R* c = a.t.Cc + ((b * a.nseg) + lc_seg_offset(L - 1) + g) * (2 * LC_M) + sigma * LC_M;
-      for (int k = 0; k < LC_M; ++k) far = fma(c[k], Trow[k], far);
-    }
-    R near = R(0);
-    if (a.dir == LC_L2C) {
-      for (int64_t i = start; i <= j; i += 2) {
-        const int64_t k = (j - i) >> 1;
-        near = fma(a.t.lam[k] * a.t.lam2[i + k], cinv<R>(i) * lc_ld<R>(r + i * a.ie), near);
-      }
-    } else {
-      for (int64_t i = start; i <= j; i += 2) {
-        const int64_t k = (j - i) >> 1;
-        near = fma(a.t.lam[k] * a.t.lam2[i + k], R(2 * i + 1) * lc_ld<R>(r + i * a.ie), near);
-      }
-      near *= R(j);
-      if (j == 0) near += lc_ld<R>(r);
-    }
-    lc_st<R>(a.out + b * a.ob + j * a.oe, far + near);
+inline void chunk_roots(int L, int* roots, int* count) {
+  // roots[0] = top level of the first up chunk, then up to 4 levels per chunk
+  int n = 0;
+  int r = L - 1 - kLeafDepth;
+  if (r < 0) r = 0;
+  roots[n++] = r;
+  while (r > 0) {
+    r = r - kChunkDepth > 0 ? r - kChunkDepth : 0;
+    roots[n++] = r;
   }
+  *count = n;
+}
+
+template <typename R>
+inline int launches_for(int L) {
+  if (L <= 0) return 1;
+  int roots[32], nr;
+  chunk_roots<R>(L, roots, &nr);
+  return 2 * nr + 1;
+}
+
+template <typename R>
+lc_status set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) LC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+  return LC_OK;
 }
 
 template <typename R>
 lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
   const int L = a.L, s = a.s;
+  const unsigned gy = unsigned(a.batch < 65535 ? a.batch : 65535);
   lc_timer_begin(p);
-  const int gy = int(a.batch < 65535 ? a.batch : 65535);
-  if (L > 0) {
-    // leaf restriction: column segments [2, 2^(L+1)) forward, row segments [0, 2^(L+1)-2) transposed
-    const int64_t lo = adjoint ? 0 : 2;
-    const int64_t hi = adjoint ? ((int64_t(2) << L) - 2) : (int64_t(2) << L);
-    const size_t sm = (size_t(2) * s * LC_M + kSegs * 2 * s) * sizeof(R);
-    dim3 grid(unsigned((hi - lo + kSegs - 1) / kSegs), gy);
-    lc_timer_mark(p, st, LC_K_LEAF);
-    k_leaf<R><<<grid, kSegs * kThreadsSeg, sm, st>>>(a, lo, hi, (adjoint && a.dir == LC_L2C) ? 1 : 0);
+  if (L <= 0) {
+    const size_t sm = down_smem<R>(0, s, 1, a.n);
+    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R>), sm);
+    if (e != LC_OK) return e;
+    lc_timer_mark(p, st, LC_K_FINAL);
+    k_down_chunk<R><<<dim3(1, gy), kThreads, sm, st>>>(a, 0, 0, 1, adjoint);
     LC_LAUNCH_CHECK();
-    for (int gc = L - 1; gc >= 1; --gc) {
-      // parents at level gc-1: [2, 2^(gc+1)) forward (column tree), [0, 2^(gc+1)-2) transposed (row tree)
-      const int64_t plo = adjoint ? 0 : 2;
-      const int64_t phi = adjoint ? ((int64_t(2) << gc) - 2) : (int64_t(2) << gc);
-      dim3 g2(unsigned((phi - plo + kSegs - 1) / kSegs), gy);
-      lc_timer_mark(p, st, LC_K_UP);
-      k_up<R><<<g2, kSegs * kThreadsSeg, 0, st>>>(a, gc, plo, phi);
-      LC_LAUNCH_CHECK();
-    }
-    dim3 g3(unsigned((a.nseg + kCoupleSegs - 1) / kCoupleSegs), gy);
-    lc_timer_mark(p, st, LC_K_COUPLE);
-    if (adjoint)
-      k_couple<R, true><<<g3, kCoupleSegs * LC_M, 0, st>>>(a);
-    else
-      k_couple<R, false><<<g3, kCoupleSegs * LC_M, 0, st>>>(a);
-    LC_LAUNCH_CHECK();
-    for (int gp = 0; gp + 1 <= L - 1; ++gp) {
-      // children at level gp+1: [0, 2^(gp+3)-4) forward (row tree), [4, 2^(gp+3)) transposed (column tree)
-      const int64_t clo = adjoint ? 4 : 0;
-      const int64_t chi = adjoint ? (int64_t(8) << gp) : ((int64_t(8) << gp) - 4);
-      dim3 g4(unsigned((chi - clo + kSegs - 1) / kSegs), gy);
-      lc_timer_mark(p, st, LC_K_DOWN);
-      k_down<R><<<g4, kSegs * kThreadsSeg, 0, st>>>(a, gp, clo, chi);
-      LC_LAUNCH_CHECK();
-    }
+    lc_timer_end(p, st);
+    return LC_OK;
   }
-  dim3 g5(unsigned((a.n + kFinalThreads - 1) / kFinalThreads), gy);
-  lc_timer_mark(p, st, LC_K_FINAL);
-  if (adjoint)
-    k_final_adj<R><<<g5, kFinalThreads, 0, st>>>(a);
-  else
-    k_final<R><<<g5, kFinalThreads, 0, st>>>(a);
-  LC_LAUNCH_CHECK();
+  int roots[32], nr;
+  chunk_roots<R>(L, roots, &nr);
+  // up chunks: first from the leaves to roots[0], then roots[k-1] -> roots[k]
+  for (int c = 0; c < nr; ++c) {
+    const int rho = roots[c];
+    const int depth = (c == 0) ? (L - 1 - rho) : (roots[c - 1] - rho);
+    if (c > 0 && depth == 0) continue;
+    const int leaf = (c == 0);
+    const size_t sm = up_smem<R>(depth, s, leaf);
+    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_up_chunk<R>), sm);
+    if (e != LC_OK) return e;
+    lc_timer_mark(p, st, leaf ? LC_K_LEAF : LC_K_UP);
+    k_up_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, st>>>(a, rho, depth, leaf, adjoint);
+    LC_LAUNCH_CHECK();
+  }
+  {  // coupling, all levels
+    const size_t sm = (size_t(3) * kCBlocks * LC_M * LC_M + size_t(2) * kCBlocks * kSeg) * sizeof(R) + 16;
+    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_couple_blocks<R>), sm);
+    if (e != LC_OK) return e;
+    lc_timer_mark(p, st, LC_K_COUPLE);
+    k_couple_blocks<R><<<dim3(unsigned(couple_ctas<R>(L)), gy), kThreads, sm, st>>>(a, adjoint);
+    LC_LAUNCH_CHECK();
+  }
+  // down chunks: top chunk first; chunk c covers levels [roots[c], roots[c-1] - 1]
+  for (int c = nr - 1; c >= 0; --c) {
+    const int rho = roots[c];
+    const int fin = (c == 0);
+    const int depth = fin ? (L - 1 - rho) : (roots[c - 1] - 1 - rho);
+    if (!fin && depth < 0) continue;
+    const size_t sm = down_smem<R>(depth, s, fin, 0);
+    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R>), sm);
+    if (e != LC_OK) return e;
+    lc_timer_mark(p, st, fin ? LC_K_FINAL : LC_K_DOWN);
+    k_down_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, st>>>(a, rho, depth, fin, adjoint);
+    LC_LAUNCH_CHECK();
+  }
   lc_timer_end(p, st);
   return LC_OK;
 }

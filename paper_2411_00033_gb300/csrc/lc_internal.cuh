@@ -51,6 +51,8 @@ struct lc_tables {
   const R* Ahat;  // [nc][M][M]
   R* W;           // [batch][nseg][2][M]   w of Algorithm 4
   R* Cc;          // [batch][nseg][2][M]   c of Algorithm 4
+  int* err;       // device status word (bounded waits that ran out)
+  int debug;      // lc_plan_options.debug_flags
 };
 
 struct lc_plan_s {
@@ -92,6 +94,7 @@ struct lc_plan_s {
   int64_t* h_off;
   void* ragged_dev;
   size_t bytes_used;
+  int* err;  // device status word in the workspace
   // Optional per-kernel timing (lc_plan_set_timing).
   int timing_slots;
   int timing_stride;       // events per slot

@@ -173,6 +173,16 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
   }
 }
 
+// FP32 copy of A-hat, stored transposed per matrix: [m][l][k].
+__global__ void k_d2f_T(int64_t nm, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t total = nm * LC_M * LC_M;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t m = i / (LC_M * LC_M);
+    const int r = int(i % (LC_M * LC_M));
+    b[m * (LC_M * LC_M) + (r % LC_M) * LC_M + r / LC_M] = float(a[i]);
+  }
+}
+
 __global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     b[i] = float(a[i]);
@@ -235,6 +245,7 @@ size_t layout(lc_plan_s* p, char* base) {
   const size_t nw = size_t(p->batch) * size_t(g.nseg) * 2 * LC_M;
   p->lam = c.take<double>(N);
   p->lam2 = (p->dir == LC_C2L) ? c.take<double>(N) : p->lam;
+  p->err = c.take<int>(64);
   p->T = c.take<double>(size_t(2) * g.s * LC_M);
   p->B = c.take<double>(LC_M * LC_M);
   p->Ahat = c.take<double>(size_t(g.nc) * LC_M * LC_M + LC_M * LC_M);  // + DCT matrix scratch
@@ -330,6 +341,7 @@ int grid_for(int64_t work, int threads) {
 
 lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
   const lc_geom& g = p->g;
+  LC_CUDA_TRY(cudaMemsetAsync(p->err, 0, 64 * sizeof(int), st));
   double* lam_target = (p->dir == LC_C2L) ? p->lam2 : p->lam;
   k_plan_lambda<<<grid_for((g.N + 7) / 8, 256), 256, 0, st>>>(g.N, lam_target);
   LC_LAUNCH_CHECK();
@@ -355,7 +367,7 @@ lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
     k_d2f<<<1, 256, 0, st>>>(int64_t(2) * g.s * LC_M, p->T, p->Tf);
     k_d2f<<<1, 256, 0, st>>>(LC_M * LC_M, p->B, p->Bf);
     if (g.nc > 0)
-      k_d2f<<<grid_for(g.nc * LC_M * LC_M, 256), 256, 0, st>>>(g.nc * LC_M * LC_M, p->Ahat, p->Ahatf);
+      k_d2f_T<<<grid_for(g.nc * LC_M * LC_M, 256), 256, 0, st>>>(g.nc, p->Ahat, p->Ahatf);
     LC_LAUNCH_CHECK();
   } else if (p->dtype == LC_F64_DF) {
     lc_status s2 = lc_df_prepare(p, st);
@@ -533,6 +545,20 @@ lc_status lc_plan_create_ragged(lc_plan* out, const int64_t* n, int64_t count, l
     return st;
   }
   *out = p;
+  return LC_OK;
+}
+
+lc_status lc_plan_check(lc_plan plan, lc_stream stream) {
+  if (!plan) return LC_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int h = 0;
+  LC_CUDA_TRY(cudaMemcpyAsync(&h, plan->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h != 0) {
+    LC_CUDA_TRY(cudaMemsetAsync(plan->err, 0, sizeof(int), s));
+    LC_CUDA_TRY(cudaStreamSynchronize(s));
+    return LC_ERR_DEVICE_TIMEOUT;
+  }
   return LC_OK;
 }
 
