@@ -29,7 +29,9 @@
  *    later call or synchronisation.
  *  - Work is enqueued on the caller's stream; no call synchronises the host
  *    except where stated.  lc_execute and lc_adjoint neither allocate nor
- *    synchronise.
+ *    synchronise; they may fork independent kernels onto a side stream owned
+ *    by the plan and join it back (events) before their last kernel, so the
+ *    caller sees ordinary stream order, also under stream capture.
  *  - One plan executes on one stream at a time: its intermediate arrays live
  *    in the plan workspace, so two executions of the same plan must not
  *    overlap on the device.

@@ -23,8 +23,11 @@
 //     contribution of Step 4 to the coupling result of Step 3; the last chunk
 //     ends at the leaves and also does the spread, the near-field band with
 //     its operands staged in shared memory, and the scaling.
-// The coupling of Step 3 for all levels is one launch between the two passes.
-// For L = 13 (n = 1e6) that is 7 launches instead of 2L+1 = 27.
+// After the first up chunk, the coarse levels' up chunks, their coupling and
+// their down chunks run on a high-priority side stream, concurrently with the
+// coupling of the fine levels on the caller's stream; the last down chunk
+// waits for both.  For L = 13 (n = 1e6): 8 launches instead of 2L+1 = 27,
+// with the coarse chain hidden behind the fine coupling.
 //
 // The transposed pass (lc_adjoint) runs the same kernels with the roles of
 // the trees exchanged: restriction over row segments and the row tree
@@ -73,6 +76,11 @@ template <typename R>
 __device__ __forceinline__ R acc3(const R& acc, const R& a, const R& b, const R& c) { return fma(a * b, c, acc); }
 template <typename R>
 __device__ __forceinline__ R finish(const R& acc) { return acc; }
+// Whether splitting a short sum into two independent chains pays off: it
+// does for the hardware types (latency of dependent FMAs), not for the
+// double-float type, whose extra normalisations cost more than they hide.
+template <typename R>
+struct split_chains { static constexpr bool value = true; };
 // A-hat(m)[k][l]: the FP64 table keeps row-major [k][l]; the FP32 and
 // double-float copies are stored transposed, [l][k], so that threads that
 // own consecutive k read consecutive addresses.
@@ -110,13 +118,13 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
   R* zt = nodes + sub_off(depth + 1);                         // 2 x 2^(depth-1) segments
   R* Ts = zt + 2 * (1 << (depth > 0 ? depth - 1 : 0)) * kSeg;  // [2][s][M]
   R* fs = Ts + 2 * a.s * LC_M;                                // [2^depth][2s]
-  __shared__ R Bs[LC_M * LC_M];
+  __shared__ R Bt[LC_M * LC_M];  // B(0) transposed: Bt[j][k] = b_kj
   const bool col = !adj;
-  const int s = a.s, L = a.L;
+  const int s = a.s;
   const int64_t x0 = blockIdx.x;
   const int gb = rho + depth;
   const int nb = 1 << depth;
-  for (int i = threadIdx.x; i < LC_M * LC_M; i += blockDim.x) Bs[i] = a.t.B[i];
+  for (int i = threadIdx.x; i < LC_M * LC_M; i += blockDim.x) Bt[(i % LC_M) * LC_M + i / LC_M] = a.t.B[i];
   if (leaf)
     for (int i = threadIdx.x; i < 2 * s * LC_M; i += blockDim.x) Ts[i] = a.t.T[i];
   for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
@@ -142,8 +150,9 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
         const int64_t x = (x0 << depth) + j;
         R acc = R(0);
         if (node_valid(col, gb, x)) {
-          const R* fseg = fs + j * 2 * s;
-          for (int m = 0; m < s; ++m) acc = acc2(acc, fseg[2 * m + sigma], Ts[(sigma * s + m) * LC_M + k]);
+          const R* fseg = fs + j * 2 * s + sigma;
+          const R* tcol = Ts + sigma * s * LC_M + k;
+          for (int m = 0; m < s; ++m) acc = acc2(acc, fseg[2 * m], tcol[m * LC_M]);
           acc = finish(acc);
           Wb[(lc_seg_offset(gb) + x) * kSeg + sigma * LC_M + k] = acc;
         }
@@ -175,9 +184,10 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
         const int64_t x = (x0 << d) + j;
         R acc = R(0);
         if (node_valid(col, gamma, x)) {
+          // Algorithm a.1: b_kj times z0 on even k-j, z1 on odd k-j (two chains)
           const R* z0 = zt + j * kSeg + sigma * LC_M;
           const R* z1 = z0 + nd * kSeg;
-          for (int jj = 0; jj <= k; ++jj) acc = acc2(acc, Bs[k * LC_M + jj], ((k - jj) & 1) ? z1[jj] : z0[jj]);
+          for (int jj = 0; jj <= k; ++jj) acc = acc2(acc, Bt[jj * LC_M + k], ((k - jj) & 1) ? z1[jj] : z0[jj]);
           acc = finish(acc);
           Wb[(lc_seg_offset(gamma) + x) * kSeg + sigma * LC_M + k] = acc;
         }
@@ -196,7 +206,7 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
 //     c(2b) = A(b,0) w(2b+2) + A(b,1) w(2b+3),  c(2b+1) = A(b,2) w(2b+3);
 //   transposed: columns 2b+2, 2b+3 with rows 2b, 2b+1:
 //     c(2b+2) = A(b,0)^T w(2b),  c(2b+3) = A(b,1)^T w(2b) + A(b,2)^T w(2b+1).
-constexpr int kCBlocks = 4;
+constexpr int kCBlocks = 7;
 
 // Bulk copy global -> shared (TMA, no tensor map), completing on an mbarrier.
 // Both addresses 16-byte aligned, size a multiple of 16.
@@ -221,17 +231,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase)
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj) {
+__global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, int g_lo, int g_hi) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
   R* As = reinterpret_cast<R*>(smem_raw);          // [3 kCBlocks][M][M]
   R* Ws = As + 3 * kCBlocks * LC_M * LC_M;          // [2 kCBlocks][2][M]
-  // locate (level, first block) of this CTA
-  int gamma = 0;
+  // locate (level, first block) of this CTA among levels [g_lo, g_hi)
+  int gamma = g_lo;
   int64_t first = blockIdx.x, per;
   for (;;) {
     per = ((int64_t(2) << gamma) - 1 + kCBlocks - 1) / kCBlocks;
-    if (first < per || gamma + 1 >= a.L) break;
+    if (first < per || gamma + 1 >= g_hi) break;
     first -= per;
     ++gamma;
   }
@@ -271,43 +281,44 @@ __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj) 
       return;
     }
     phase ^= 1u;
-    for (int t = threadIdx.x; t < 2 * nb * kSeg; t += blockDim.x) {
-      const int jb = t / (2 * kSeg);            // block within the group
-      const int half = (t / kSeg) & 1;          // which of the two output segments
+    for (int t = threadIdx.x; t < nb * kSeg; t += blockDim.x) {
+      const int jb = t / kSeg;                  // block within the group
       const int sigma = (t % kSeg) / LC_M, k = t % LC_M;
       const R* A0 = As + (3 * jb) * (LC_M * LC_M);
       const R* w0 = Ws + (2 * jb) * kSeg + sigma * LC_M;
       const R* w1 = w0 + kSeg;
-      R c = R(0);
+      R c0 = R(0), c0b = R(0), c1 = R(0);
       if (!adj) {
-        if (half == 0) {
-          for (int l = 0; l < LC_M; ++l) {
-            c = acc2(c, ahat_at(A0, 0, k, l), w0[l]);
-            c = acc2(c, ahat_at(A0, 1, k, l), w1[l]);
-          }
-        } else {
-          for (int l = 0; l < LC_M; ++l) c = acc2(c, ahat_at(A0, 2, k, l), w1[l]);
+        // c(2b) = A(b,0) w(2b+2) + A(b,1) w(2b+3);  c(2b+1) = A(b,2) w(2b+3)
+        for (int l = 0; l < LC_M; ++l) {
+          const R wa = w0[l], wb = w1[l];
+          c0 = acc2(c0, ahat_at(A0, 0, k, l), wa);
+          c0b = acc2(c0b, ahat_at(A0, 1, k, l), wb);
+          c1 = acc2(c1, ahat_at(A0, 2, k, l), wb);
         }
-        Cl[(2 * (b0 + jb) + half) * kSeg + sigma * LC_M + k] = finish(c);
+        R* out = Cl + (2 * (b0 + jb)) * kSeg + sigma * LC_M + k;
+        out[0] = finish(c0) + finish(c0b);
+        out[kSeg] = finish(c1);
       } else {
-        if (half == 0) {
-          for (int l = 0; l < LC_M; ++l) c = acc2(c, ahat_at(A0, 0, l, k), w0[l]);
-        } else {
-          for (int l = 0; l < LC_M; ++l) {
-            c = acc2(c, ahat_at(A0, 1, l, k), w0[l]);
-            c = acc2(c, ahat_at(A0, 2, l, k), w1[l]);
-          }
+        // c(2b+2) = A(b,0)^T w(2b);  c(2b+3) = A(b,1)^T w(2b) + A(b,2)^T w(2b+1)
+        for (int l = 0; l < LC_M; ++l) {
+          const R wa = w0[l], wb = w1[l];
+          c0 = acc2(c0, ahat_at(A0, 0, l, k), wa);
+          c1 = acc2(c1, ahat_at(A0, 1, l, k), wa);
+          c0b = acc2(c0b, ahat_at(A0, 2, l, k), wb);
         }
-        Cl[(2 * (b0 + jb) + 2 + half) * kSeg + sigma * LC_M + k] = finish(c);
+        R* out = Cl + (2 * (b0 + jb) + 2) * kSeg + sigma * LC_M + k;
+        out[0] = finish(c0);
+        out[kSeg] = finish(c1) + finish(c0b);
       }
     }
   }
 }
 
 template <typename R>
-inline int64_t couple_ctas(int L) {
+inline int64_t couple_ctas(int g_lo, int g_hi) {
   int64_t n = 0;
-  for (int g = 0; g < L; ++g) n += ((int64_t(2) << g) - 1 + kCBlocks - 1) / kCBlocks;
+  for (int g = g_lo; g < g_hi; ++g) n += ((int64_t(2) << g) - 1 + kCBlocks - 1) / kCBlocks;
   return n;
 }
 
@@ -368,13 +379,21 @@ __global__ void __launch_bounds__(kThreads) k_down_chunk(Args<R> a, int rho, int
             if (gamma > 0 && node_valid(col, gamma - 1, x >> 1)) {
               const R* pv = (d == 0) ? Cb + (lc_seg_offset(gamma - 1) + (x >> 1)) * kSeg + sigma * LC_M
                                      : nodes + sub_off(d - 1) + (j >> 1) * kSeg + sigma * LC_M;
-              const bool odd = (x & 1) != 0;
-              for (int jj = k; jj < LC_M; ++jj) {
-                const R bjk = Bs[jj * LC_M + k];
-                c = acc2(c, (odd && ((jj - k) & 1)) ? negate(bjk) : bjk, pv[jj]);
+              // B(1) = B(0) with odd diagonals negated
+              if constexpr (split_chains<R>::value) {
+                R ce = R(0), co = R(0);
+                for (int jj = k; jj < LC_M; jj += 2) ce = acc2(ce, Bs[jj * LC_M + k], pv[jj]);
+                for (int jj = k + 1; jj < LC_M; jj += 2) co = acc2(co, Bs[jj * LC_M + k], pv[jj]);
+                c = c + ((x & 1) ? finish(ce) - finish(co) : finish(ce) + finish(co));
+              } else {
+                const bool odd = (x & 1) != 0;
+                for (int jj = k; jj < LC_M; ++jj) {
+                  const R bjk = Bs[jj * LC_M + k];
+                  c = acc2(c, (odd && ((jj - k) & 1)) ? negate(bjk) : bjk, pv[jj]);
+                }
+                c = finish(c);
               }
             }
-            c = finish(c);
           }
           lev[t] = c;
         }
@@ -429,49 +448,61 @@ __global__ void __launch_bounds__(kThreads) k_down_chunk(Args<R> a, int rho, int
     for (int64_t m = mlo + threadIdx.x; m < mhi; m += blockDim.x) lamm[m - mlo] = (m < mcap) ? a.t.lam2[m] : R(0);
     __syncthreads();
     const bool l2c = (a.dir == LC_L2C);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const int64_t v = i / two_s;
-      const int l = int(i - v * two_s);
-      const int m = l >> 1, sigma = l & 1;
-      R far = R(0);
-      if (L > 0 && node_valid(col, L - 1, v)) {
-        const R* c = leafc + (v - (x0 << depth)) * kSeg + sigma * LC_M;
-        const R* Trow = Ts + (sigma * s + m) * LC_M;
-        for (int k = 0; k < LC_M; ++k) far = acc2(far, c[k], Trow[k]);
-        far = finish(far);
-      }
-      R near = R(0);
-      if (!adj) {
-        // row i: sum over j = i + 2k in the band  (eq:hik, eq:Lxymod)
-        const int64_t end = (L > 0) ? (two_s * (v + 2) < a.n ? two_s * (v + 2) : a.n) : a.n;
-        const R* fo = opnd + (i - olo);
-        const R* lm = lamm + (i - mlo);
-        int64_t kk = 0;
-        for (int64_t j = i; j < end; j += 2, ++kk) near = acc3(near, lamk[kk], lm[kk], fo[2 * kk]);
-        near = finish(near);
-        R res;
-        if (l2c) {
-          res = cinv<R>(i) * (far + near);
+    // Work unit: within one 2s-row strip and parity, rows m and s-1-m, whose
+    // band lengths add up to about 3s, so the threads of a warp stay balanced.
+    const int half = (s + 1) / 2;
+    const int64_t nstrips = (hi - lo + two_s - 1) / two_s;
+    const int64_t units = nstrips * 2 * half;
+    for (int64_t u = threadIdx.x; u < units; u += blockDim.x) {
+      const int64_t strip = u / (2 * half);
+      const int rem = int(u - strip * 2 * half);
+      const int sigma = rem / half, mm = rem % half;
+      for (int rep = 0; rep < 2; ++rep) {
+        const int m = rep ? s - 1 - mm : mm;
+        if (rep && m == mm) break;
+        const int64_t i = lo + strip * two_s + 2 * m + sigma;
+        if (i >= hi) continue;
+        const int64_t v = i / two_s;
+        R far = R(0);
+        if (L > 0 && node_valid(col, L - 1, v)) {
+          const R* c = leafc + (v - (x0 << depth)) * kSeg + sigma * LC_M;
+          const R* Trow = Ts + (sigma * s + m) * LC_M;
+          for (int k = 0; k < LC_M; ++k) far = acc2(far, c[k], Trow[k]);
+          far = finish(far);
+        }
+        R near = R(0);
+        if (!adj) {
+          // row i: sum over j = i + 2k in the band  (eq:hik, eq:Lxymod)
+          const int64_t end = (L > 0) ? (two_s * (v + 2) < a.n ? two_s * (v + 2) : a.n) : a.n;
+          const int cnt = int((end - i + 1) >> 1);
+          const R* fo = opnd + (i - olo);
+          const R* lm = lamm + (i - mlo);
+          for (int kk = 0; kk < cnt; ++kk) near = acc3(near, lamk[kk], lm[kk], fo[2 * kk]);
+          near = finish(near);
+          R res;
+          if (l2c) {
+            res = cinv<R>(i) * (far + near);
+          } else {
+            // (2i+1) u_k v_(i+k) (j f_j) summed; entry (0,0) = 1 adds f_0 (eq:Lxymod)
+            res = far + R(2 * i + 1) * near;
+            if (i == 0) res += lc_ld<R>(f);
+          }
+          lc_st<R>(a.out + b * a.ob + i * a.oe, res);
         } else {
-          // (2i+1) u_k v_(i+k) (j f_j) summed; entry (0,0) = 1 adds f_0 (eq:Lxymod)
-          res = far + R(2 * i + 1) * near;
-          if (i == 0) res += lc_ld<R>(f);
+          // column j = i: sum over rows r <= j in the band
+          int64_t st = (L > 0) ? (two_s * (v - 1) > 0 ? two_s * (v - 1) : 0) : 0;
+          if ((st & 1) != (i & 1)) ++st;
+          const int cnt = int((i - st) / 2 + 1);
+          const R* ro = opnd + (i - olo);          // ro[-2k] = row i - 2k
+          const R* lm = lamm + (i - mlo);           // lm[-k]  = (r + i)/2 = i - k
+          for (int k = 0; k < cnt; ++k) near = acc3(near, lamk[k], lm[-k], ro[-2 * k]);
+          near = finish(near);
+          if (!l2c) {
+            near = R(i) * near;
+            if (i == 0) near += lc_ld<R>(f);
+          }
+          lc_st<R>(a.out + b * a.ob + i * a.oe, far + near);
         }
-        lc_st<R>(a.out + b * a.ob + i * a.oe, res);
-      } else {
-        // column j = i: sum over rows r <= j in the band
-        int64_t st = (L > 0) ? (two_s * (v - 1) > 0 ? two_s * (v - 1) : 0) : 0;
-        if ((st & 1) != (i & 1)) ++st;
-        for (int64_t r = st; r <= i; r += 2) {
-          const int64_t k = (i - r) >> 1;
-          near = acc3(near, lamk[k], lamm[(r + i) / 2 - mlo], opnd[r - olo]);
-        }
-        near = finish(near);
-        if (!l2c) {
-          near = R(i) * near;
-          if (i == 0) near += lc_ld<R>(f);
-        }
-        lc_st<R>(a.out + b * a.ob + i * a.oe, far + near);
       }
     }
   }
@@ -497,7 +528,7 @@ inline int launches_for(int L) {
   if (L <= 0) return 1;
   int roots[32], nr;
   chunk_roots<R>(L, roots, &nr);
-  return 2 * nr + 1;
+  return 2 * nr + (roots[0] > 0 ? 2 : 1);
 }
 
 template <typename R>
@@ -523,38 +554,72 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
   }
   int roots[32], nr;
   chunk_roots<R>(L, roots, &nr);
-  // up chunks: first from the leaves to roots[0], then roots[k-1] -> roots[k]
-  for (int c = 0; c < nr; ++c) {
-    const int rho = roots[c];
-    const int depth = (c == 0) ? (L - 1 - rho) : (roots[c - 1] - rho);
-    if (c > 0 && depth == 0) continue;
-    const int leaf = (c == 0);
-    const size_t sm = up_smem<R>(depth, s, leaf);
+  const size_t smc = (size_t(3) * kCBlocks * LC_M * LC_M + size_t(2) * kCBlocks * kSeg) * sizeof(R) + 16;
+  {
+    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_couple_blocks<R>), smc);
+    if (e != LC_OK) return e;
+  }
+  // Once the first up chunk is done, w is final on the levels [roots[0], L).
+  // The coarse levels (up chunks, their coupling, their down chunks) form a
+  // latency-bound chain of small grids; it runs on the plan's high-priority
+  // side stream while the wide coupling of the fine levels runs on the
+  // caller's stream, and the last down chunk waits for both.  (Everything
+  // stays on the caller's stream when per-kernel timing is on.)
+  const bool overlap = p->timing_slots <= 0 && roots[0] > 0 && p->side != nullptr;
+  cudaStream_t sk = overlap ? p->side : st;  // stream of the coarse chain
+  {  // first up chunk: leaf restriction and the fine levels
+    const int rho = roots[0];
+    const int depth = L - 1 - rho;
+    const size_t sm = up_smem<R>(depth, s, 1);
     lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_up_chunk<R>), sm);
     if (e != LC_OK) return e;
-    lc_timer_mark(p, st, leaf ? LC_K_LEAF : LC_K_UP);
-    k_up_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, st>>>(a, rho, depth, leaf, adjoint);
+    lc_timer_mark(p, st, LC_K_LEAF);
+    k_up_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, st>>>(a, rho, depth, 1, adjoint);
     LC_LAUNCH_CHECK();
   }
-  {  // coupling, all levels
-    const size_t sm = (size_t(3) * kCBlocks * LC_M * LC_M + size_t(2) * kCBlocks * kSeg) * sizeof(R) + 16;
-    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_couple_blocks<R>), sm);
-    if (e != LC_OK) return e;
-    lc_timer_mark(p, st, LC_K_COUPLE);
-    k_couple_blocks<R><<<dim3(unsigned(couple_ctas<R>(L)), gy), kThreads, sm, st>>>(a, adjoint);
-    LC_LAUNCH_CHECK();
+  if (overlap) {
+    LC_CUDA_TRY(cudaEventRecord(p->ev_fork, st));
+    LC_CUDA_TRY(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
   }
-  // down chunks: top chunk first; chunk c covers levels [roots[c], roots[c-1] - 1]
-  for (int c = nr - 1; c >= 0; --c) {
-    const int rho = roots[c];
-    const int fin = (c == 0);
-    const int depth = fin ? (L - 1 - rho) : (roots[c - 1] - 1 - rho);
-    if (!fin && depth < 0) continue;
-    const size_t sm = down_smem<R>(depth, s, fin, 0);
+  if (roots[0] > 0) {
+    for (int c = 1; c < nr; ++c) {  // coarse up chunks
+      const int rho = roots[c];
+      const int depth = roots[c - 1] - rho;
+      const size_t sm = up_smem<R>(depth, s, 0);
+      lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_up_chunk<R>), sm);
+      if (e != LC_OK) return e;
+      lc_timer_mark(p, st, LC_K_UP);
+      k_up_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sk>>>(a, rho, depth, 0, adjoint);
+      LC_LAUNCH_CHECK();
+    }
+    lc_timer_mark(p, st, LC_K_COUPLE);  // coupling of the coarse levels
+    k_couple_blocks<R><<<dim3(unsigned(couple_ctas<R>(0, roots[0])), gy), kThreads, smc, sk>>>(a, adjoint, 0, roots[0]);
+    LC_LAUNCH_CHECK();
+    for (int c = nr - 1; c >= 1; --c) {  // coarse down chunks: levels [roots[c], roots[c-1] - 1]
+      const int rho = roots[c];
+      const int depth = roots[c - 1] - 1 - rho;
+      const size_t sm = down_smem<R>(depth, s, 0, 0);
+      lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R>), sm);
+      if (e != LC_OK) return e;
+      lc_timer_mark(p, st, LC_K_DOWN);
+      k_down_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sk>>>(a, rho, depth, 0, adjoint);
+      LC_LAUNCH_CHECK();
+    }
+    if (overlap) LC_CUDA_TRY(cudaEventRecord(p->ev_join, p->side));
+  }
+  // coupling of the fine levels [roots[0], L) on the caller's stream
+  lc_timer_mark(p, st, LC_K_COUPLE);
+  k_couple_blocks<R><<<dim3(unsigned(couple_ctas<R>(roots[0], L)), gy), kThreads, smc, st>>>(a, adjoint, roots[0], L);
+  LC_LAUNCH_CHECK();
+  if (overlap) LC_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
+  {  // last down chunk: fine levels, then Steps 5-7
+    const int rho = roots[0];
+    const int depth = L - 1 - rho;
+    const size_t sm = down_smem<R>(depth, s, 1, 0);
     lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R>), sm);
     if (e != LC_OK) return e;
-    lc_timer_mark(p, st, fin ? LC_K_FINAL : LC_K_DOWN);
-    k_down_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, st>>>(a, rho, depth, fin, adjoint);
+    lc_timer_mark(p, st, LC_K_FINAL);
+    k_down_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, st>>>(a, rho, depth, 1, adjoint);
     LC_LAUNCH_CHECK();
   }
   lc_timer_end(p, st);

@@ -95,6 +95,10 @@ struct lc_plan_s {
   void* ragged_dev;
   size_t bytes_used;
   int* err;  // device status word in the workspace
+  // Side stream and fork/join events used to overlap independent kernels of
+  // one execution (host objects; created at plan time).
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
   // Optional per-kernel timing (lc_plan_set_timing).
   int timing_slots;
   int timing_stride;       // events per slot

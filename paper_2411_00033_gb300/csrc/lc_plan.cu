@@ -332,6 +332,27 @@ lc_status fill_ragged(lc_plan_s* p, const int64_t* n, int64_t count, lc_directio
   return LC_OK;
 }
 
+lc_status create_side(lc_plan_s* p) {
+  p->side = nullptr;
+  p->ev_fork = p->ev_join = nullptr;
+  // The side stream carries the latency-bound coarse-level chain: give it the
+  // highest priority so its few CTAs are scheduled ahead of wide kernels.
+  int lo_prio = 0, hi_prio = 0;
+  LC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+  LC_CUDA_TRY(cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, hi_prio));
+  LC_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  LC_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  return LC_OK;
+}
+
+void destroy_side(lc_plan_s* p) {
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->side) cudaStreamDestroy(p->side);
+  p->side = nullptr;
+  p->ev_fork = p->ev_join = nullptr;
+}
+
 int grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -425,10 +446,12 @@ lc_status lc_plan_create_ex(lc_plan* out, int64_t n, lc_direction direction, int
   layout(p, static_cast<char*>(workspace));
   p->bytes_used = need;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  st = build_tables(p, s);
+  st = create_side(p);
+  if (st == LC_OK) st = build_tables(p, s);
   if (st == LC_OK && dtype == LC_F64_SPLIT) st = lc_split_prepare(p, static_cast<char*>(p->split), lc_split_bytes(p), s);
   if (st != LC_OK) {
     lc_split_release(p);
+    destroy_side(p);
     free(p);
     return st;
   }
@@ -488,6 +511,7 @@ lc_status lc_destroy(lc_plan plan) {
   if (!plan) return LC_ERR_INVALID_ARG;
   lc_plan_set_timing(plan, 0);
   lc_split_release(plan);
+  destroy_side(plan);
   free(plan->h_len);
   free(plan->h_off);
   free(plan);
@@ -534,11 +558,13 @@ lc_status lc_plan_create_ragged(lc_plan* out, const int64_t* n, int64_t count, l
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (st == LC_OK) {
     p->bytes_used = layout(p, static_cast<char*>(workspace));
-    st = build_tables(p, s);
+    st = create_side(p);
   }
+  if (st == LC_OK) st = build_tables(p, s);
   if (st == LC_OK) st = lc_split_prepare(p, static_cast<char*>(p->split), lc_split_bytes(p), s);
   if (st != LC_OK) {
     lc_split_release(p);
+    destroy_side(p);
     free(p->h_len);
     free(p->h_off);
     free(p);

@@ -152,3 +152,26 @@ def test_fixed_s_option_same_map(lc):
             z, plan = _run(lc, x, direction, **opts)
             e2, _ = rel_errors(z, ref)
             assert e2 <= 1e-13, (opts, plan.info, e2)
+
+
+@pytest.mark.parametrize("tier", ["f64", "f64_df", "f32"])
+def test_graph_capture_of_cuda_core_tiers(lc, tier):
+    # lc_execute forks part of its work onto a plan-owned side stream and joins
+    # it back; under stream capture that fork/join becomes part of the graph.
+    n = 200000
+    dev = torch.device("cuda", 0)
+    dt = torch.float32 if tier == "f32" else torch.float64
+    plan = lc.Plan(n, "l2c", 1, tier, dev)
+    x = torch.as_tensor(workloads.decaying_vector(n, seed=8), device=dev, dtype=dt)
+    z = torch.empty_like(x)
+    plan(x, out=z)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan(x, out=z)
+    x2 = workloads.decaying_vector(n, seed=9)
+    x.copy_(torch.as_tensor(x2, device=dev, dtype=dt))
+    g.replay()
+    torch.cuda.synchronize()
+    direct = plan(x).cpu().numpy()
+    assert np.array_equal(z.cpu().numpy(), direct)
