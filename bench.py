@@ -44,9 +44,13 @@ N_COEF = 1_000_000
 PAPER_COEF_PER_S = 1_000_000 / 0.020   # paper: ~20 ms per 1e6 L2C, 1 core of an M3 Pro (context only)
 CPU_ROWS = 2048                         # oracle rows per direction for the CPU baseline / accuracy sample
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+# Double-float tier: one FP64-equivalent multiply-add costs 12 FP32-pipe
+# instructions (TwoProd with fma, cross terms, TwoSum accumulation); the FP32
+# issue limit is 152 SMs x 128 lanes x 2070 MHz.
+DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 # DRAM bytes per launch of the dominant kernel, from the ncu capture summarised in
 # profiles/f64_single_n1e6.md (dram__bytes_read.sum + dram__bytes_write.sum).
-TRAFFIC = {("f64", 4): 20.68e6}
+TRAFFIC = {}
 KIND_NAMES = {0: "leaf_restrict", 1: "upward", 2: "couple", 3: "downward", 4: "spread_near_scale", 5: "prepare",
               6: "other"}
 
@@ -179,9 +183,18 @@ def near_field_nonzeros(n, L, s):
 
 def kernel_work(info, kind, direction):
     """Algorithmic FP64 flops of one launch of a kernel kind (paper's counting, Sec. 4.2)."""
-    n, L, s, M, nc = info["n"], info["L"], info["s"], info["M"], info["n_c"]
-    if kind == 4:  # spread (2M per row) + near field (3 flops per nonzero, mu = 4.5) + scaling
-        return 2 * M * n + 3 * near_field_nonzeros(n, L, s) + n
+    n, L, s, M, nc, N = info["n"], info["L"], info["s"], info["M"], info["n_c"], info["N"]
+    if kind == 4:
+        # last down chunk: Step 4 on the fine levels [max(0, L-5), L) (a triangular
+        # M x M product, M(M+1) flops per node and parity), then the spread
+        # (2M per row with a far field), the near field (3 flops per band
+        # nonzero, mu = 4.5) and the scaling (1 per row)
+        rho = max(0, L - 1 - 4)
+        nodes = 0
+        for g in range(rho, L):
+            nodes += ((4 << g) - 4) if g > 0 else 0
+        rows_far = min(n, N - 4 * s) if L > 0 else 0
+        return 2 * M * (M + 1) * nodes + 2 * M * rows_far + 3 * near_field_nonzeros(n, L, s) + n
     if kind == 2:  # couple: 2 M^2 per submatrix per parity
         return 4 * M * M * nc
     if kind == 0:  # leaf: 2 M s per segment per parity
@@ -230,19 +243,19 @@ def batched_leg(lc, dev, flush, args):
     Z = torch.empty_like(X)
     res = {}
     ref = None
-    for tier in ("f64_split", "f64"):
+    for tier in ("f64_split", "f64_df", "f64"):
         plan = lc.Plan(n, "l2c", B, tier, dev)
         step = graph_step(lambda: plan(X, out=Z))
         ms = time_fn(step, flush, steps, 2)
         res[tier] = {"coefficients_per_s": n * B / (ms / 1e3), "ms": ms,
                      "launches": plan.launches()}
-        if tier == "f64":
-            ref = Z.clone()
-        else:
-            got = Z.clone()
+        outs_b = locals().setdefault("outs_b", {})
+        outs_b[tier] = Z.clone()
         del plan
-    d = (got - ref).double()
-    res["split_vs_f64_E2"] = float(torch.linalg.norm(d) / torch.linalg.norm(ref))
+    ref = outs_b["f64"]
+    for t in ("f64_split", "f64_df"):
+        d = (outs_b[t] - ref).double()
+        res[t + "_vs_f64_E2"] = float(torch.linalg.norm(d) / torch.linalg.norm(ref))
     res["speedup_split_over_f64_batched"] = res["f64_split"]["coefficients_per_s"] / res["f64"]["coefficients_per_s"]
     out["uniform_65536x256_l2c"] = res
     del X, Z
@@ -353,8 +366,12 @@ def run_ours(args):
     pl = tiers[chosen]
 
     clocks = ClockSampler(local if ws > 1 else 0)
-    ms, wall, stages = time_tier(pl, args.steps, args.warmup, stage_timing=True)
+    ms, wall, _ = time_tier(pl, args.steps, args.warmup)
     clk = clocks.stop()
+    # Per-kernel durations: the same steps again with CUDA events between the
+    # library's kernels (in this mode each execution stays on one stream, so the
+    # overlap of the coarse levels with the coupling is off).
+    _, _, stages = time_tier(pl, args.steps, 2, stage_timing=True)
     ms_per_step = sum(ms) / len(ms)
     if ws > 1:
         t = torch.tensor([ms_per_step], device=dev, dtype=torch.float64)
@@ -406,13 +423,17 @@ def run_ours(args):
     avg_ms = sum(per_launch_ms) / len(per_launch_ms)
     flops = kernel_work(info, dom, 0)
     roofline = None
-    if flops is not None and chosen == "f64":
+    if flops is not None and chosen in ("f64", "f64_df"):
         achieved = flops / (avg_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get((chosen, dom)),
-                    "kernel": KIND_NAMES[dom], "avg_launch_ms": avg_ms,
-                    "peak_note": "FP64 nominal 1.26 TFLOP/s from 152 SMs x 2 FMA/clk x 2070 MHz; "
-                                 "a dependent-FMA microbenchmark reached 1.01"}
+        peak = FP64_PEAK_TFLOPS if chosen == "f64" else DF_PEAK_TFLOPS
+        note = ("FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz = 1.26 TFLOP/s (a dependent-FMA "
+                "microbenchmark reached 1.01)") if chosen == "f64" else (
+                "double-float on the FP32 pipe: 152 SMs x 128 lanes x 2070 MHz / 12 instructions per "
+                "FP64-equivalent multiply-add x 2 flop = 6.71 TFLOP/s FP64-equivalent")
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": TRAFFIC.get((chosen, dom)),
+                    "kernel": KIND_NAMES[dom], "avg_launch_ms": avg_ms, "flops_per_launch": flops,
+                    "peak_note": note}
     launches = sum(p.launches() for p in pl) * args.steps
 
     line = {
