@@ -35,6 +35,7 @@
 // spread over column segments and the transposed band.
 #pragma once
 #include "lc_internal.cuh"
+#include "lc_tma.cuh"
 
 namespace lc_exec {
 
@@ -208,28 +209,6 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
 //     c(2b+2) = A(b,0)^T w(2b),  c(2b+3) = A(b,1)^T w(2b) + A(b,2)^T w(2b+1).
 constexpr int kCBlocks = 7;
 
-// Bulk copy global -> shared (TMA, no tensor map), completing on an mbarrier.
-// Both addresses 16-byte aligned, size a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint32_t mbar) {
-  const uint32_t d = uint32_t(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
-               :: "r"(d), "l"(src), "r"(bytes), "r"(mbar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
-  uint32_t done;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-               : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
-  return done != 0;
-}
-// Wait for the phase with a deadline of about one second; false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
-  const long long t0 = clock64();
-  while (!mbar_try(mbar, phase)) {
-    if (clock64() - t0 > (1ll << 31)) return false;
-  }
-  return true;
-}
-
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, int g_lo, int g_hi) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -254,8 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, 
   const uint32_t bytesW = uint32_t(2 * nb * kSeg * sizeof(R));
   const uint32_t mb = uint32_t(__cvta_generic_to_shared(&mbar));
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(mb) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    lc_mbar_init(mb);
   }
   uint32_t phase = 0;
   for (int64_t bt = blockIdx.y; bt < a.batch; bt += gridDim.y) {
@@ -266,17 +244,17 @@ __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, 
     const bool loadA = (bt == blockIdx.y);
     __syncthreads();
     if (threadIdx.x == 0) {
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      lc_fence_proxy_async();
       const uint32_t bytes = bytesW + (loadA ? bytesA : 0u);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" :: "r"(mb), "r"(bytes) : "memory");
-      if (loadA && !(a.t.debug & 1)) bulk_g2s(As, a.t.Ahat + m0 * (LC_M * LC_M), bytesA, mb);
-      bulk_g2s(Ws, Wl + s0 * kSeg, bytesW, mb);
+      lc_mbar_expect(mb, bytes);
+      if (loadA && !(a.t.debug & 1)) lc_bulk_g2s(As, a.t.Ahat + m0 * (LC_M * LC_M), bytesA, mb);
+      lc_bulk_g2s(Ws, Wl + s0 * kSeg, bytesW, mb);
     }
-    bool ok = mbar_wait_bounded(mb, phase);
+    bool ok = lc_mbar_wait_bounded(mb, phase);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicOr(a.t.err, 1);
-        mbar_wait_bounded(mb, phase);  // let a late copy land before the CTA exits
+        lc_mbar_wait_bounded(mb, phase);  // let a late copy land before the CTA exits
       }
       return;
     }

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "lc_internal.cuh"
+#include "lc_tma.cuh"
 
 namespace {
 
@@ -201,7 +202,7 @@ void build_host(const lc_plan_s* p, SplitHost& h) {
   };
   for (int k = 0; k < Y_KINDS; ++k) {
     YTable& y = h.y[k];
-    y.off_q = take(size_t(y.items) * h.S * y.NP * y.KP * 2);
+    y.off_q = take(size_t(y.items) * h.S * y.NP * (y.KP + 8) * 2);  // rows padded as in shared memory
     y.off_e = take(size_t(y.items) * y.NP * 4);
   }
   h.off_len = take(size_t(h.count) * 8);
@@ -271,6 +272,37 @@ __device__ __forceinline__ double f2d_scaled(float f, int E) {
 
 __device__ __forceinline__ uint16_t bf16_of_int(float q) { return uint16_t(__float_as_uint(q) >> 16); }
 
+// Same digits as slice_df for a normalised double-float (|lo| <= ulp(hi)),
+// cheaper: the first two digits come from hi alone (its 24 bits are exact
+// under the 8-bit shifts), lo joins once through TwoSum, and after the third
+// digit the residual fits one float.  Digits stay within [-129, 129].
+__device__ __forceinline__ void slice_df_fast(float hi, float lo, int S, uint16_t* dst, int stride) {
+  float r = hi;
+  int sl = 0;
+  for (; sl < 2 && sl < S; ++sl) {
+    const float t = r * 256.0f;
+    const float q = rintf(t);
+    r = t - q;
+    dst[sl * stride] = bf16_of_int(q);
+  }
+  if (sl >= S) return;
+  float rh, rl;
+  two_sum(r, lo * 65536.0f, rh, rl);  // residual after two digits, lo brought to the same scale
+  {
+    const float th = rh * 256.0f, tl = rl * 256.0f;
+    const float q = rintf(th);
+    r = (th - q) + tl;  // the rest fits one float
+    dst[sl * stride] = bf16_of_int(q);
+    ++sl;
+  }
+  for (; sl < S; ++sl) {
+    const float t = r * 256.0f;
+    const float q = rintf(t);
+    r = t - q;
+    dst[sl * stride] = bf16_of_int(q);
+  }
+}
+
 // Cut a double-float x (|x| <= 1/2) into S slices q_1..q_S in [-128, 128]:
 // x = sum_s q_s 2^(-8 s) + r, |r| <= 2^(-8S-1).  dst[s * stride] = bf16(q_s).
 __device__ __forceinline__ void slice_df(float hi, float lo, int S, uint16_t* dst, int stride) {
@@ -285,7 +317,7 @@ __device__ __forceinline__ void slice_df(float hi, float lo, int S, uint16_t* ds
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -298,13 +330,28 @@ __device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpre
 // (smem [S][NT*8][ys]) over KT k16 tiles.  Result per fragment element:
 // hi + lo = sum_u P_u 2^(-8(u-2)), i.e. the product times 2^16 in units of
 // 2^(e_x + e_y).
+__device__ __forceinline__ void ldsm_x4(const uint16_t* p, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  const uint32_t a = uint32_t(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(const uint16_t* p, uint32_t& r0, uint32_t& r1) {
+  const uint32_t a = uint32_t(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
+// Sliced product of this warp's 16 rows of X (smem [S][kRows][xs]) with Y
+// (smem [S][NT*8][ys]) over KT k16 tiles.  Result per fragment element:
+// hi + lo = sum_u P_u 2^(-8(u-2)), i.e. the product times 2^16 in units of
+// 2^(e_x + e_y).  Fragments are loaded with ldmatrix (rows 16-byte aligned).
 template <int KT, int NT>
 __device__ __forceinline__ void warp_ozaki(const uint16_t* Xs, int xs, const uint16_t* Ys, int ys, int S,
                                            float (&hi)[NT][4], float (&lo)[NT][4]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
   const int xslice = kRows * xs, yslice = NT * 8 * ys;
-  const uint16_t* xw = Xs + warp * 16 * xs;
+  // ldmatrix row addresses of this lane
+  const uint16_t* xw = Xs + (warp * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * xs + (lane >> 4) * 8;
+  const int yrow = (lane & 7) + (lane >> 4) * 8, ycol = ((lane >> 3) & 1) * 8;
   for (int u = S + 1; u >= 2; --u) {
     float p[NT][4];
 #pragma unroll
@@ -315,18 +362,22 @@ __device__ __forceinline__ void warp_ozaki(const uint16_t* Xs, int xs, const uin
     const int s1 = (u - 1 < S) ? u - 1 : S;
     for (int sx = s0; sx <= s1; ++sx) {
       const uint16_t* xa = xw + (sx - 1) * xslice;
-      const uint16_t* yb = Ys + (u - sx - 1) * yslice;
+      const uint16_t* yb = Ys + (u - sx - 1) * yslice + yrow * ys + ycol;
 #pragma unroll
       for (int kt = 0; kt < KT; ++kt) {
-        const int kc = kt * 16 + 2 * t;
-        const uint32_t a0 = ld32(xa + g * xs + kc);
-        const uint32_t a1 = ld32(xa + (g + 8) * xs + kc);
-        const uint32_t a2 = ld32(xa + g * xs + kc + 8);
-        const uint32_t a3 = ld32(xa + (g + 8) * xs + kc + 8);
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(xa + kt * 16, a0, a1, a2, a3);
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          const uint16_t* yr = yb + (nt * 8 + g) * ys + kc;
-          mma_bf16(p[nt], a0, a1, a2, a3, ld32(yr), ld32(yr + 8));
+        for (int nt = 0; nt + 1 < NT; nt += 2) {
+          uint32_t b0, b1, b2, b3;
+          ldsm_x4(yb + nt * 8 * ys + kt * 16, b0, b1, b2, b3);
+          mma_bf16(p[nt], a0, a1, a2, a3, b0, b1);
+          mma_bf16(p[nt + 1], a0, a1, a2, a3, b2, b3);
+        }
+        if (NT & 1) {
+          uint32_t b0, b1;
+          ldsm_x2(yb + (NT - 1) * 8 * ys + kt * 16, b0, b1);
+          mma_bf16(p[NT - 1], a0, a1, a2, a3, b0, b1);
         }
       }
     }
@@ -346,17 +397,24 @@ __device__ __forceinline__ void warp_ozaki(const uint16_t* Xs, int xs, const uin
   }
 }
 
-// Copy the Y slices of one table item into smem [S][NP][KP+8] plus exponents.
-__device__ __forceinline__ void load_y(const uint16_t* __restrict__ q, const int* __restrict__ e, int S, int NP,
-                                       int KP, uint16_t* Ys, int ys, int* Ye) {
-  const int per = KP / 2;  // 32-bit words per row
-  const int total = S * NP * per;
-  const uint32_t* src = reinterpret_cast<const uint32_t*>(q);
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int row = i / per, w = i % per;
-    reinterpret_cast<uint32_t*>(Ys + row * ys)[w] = src[i];
+// Bring the Y slices of one table item ([S][NP][KP+8] bf16, padded like the
+// shared-memory layout) and its NP exponents into shared memory with two bulk
+// copies.  Must be called by all threads; returns false if the bounded wait
+// ran out (the caller records the failure and exits).
+__device__ __forceinline__ bool load_y(const uint16_t* __restrict__ q, const int* __restrict__ e, int S, int NP,
+                                       int KP, uint16_t* Ys, int* Ye, uint64_t* mbar) {
+  const uint32_t mb = uint32_t(__cvta_generic_to_shared(mbar));
+  const uint32_t bq = uint32_t(S) * NP * (KP + 8) * 2, be = uint32_t(NP) * 4;
+  if (threadIdx.x == 0) {
+    lc_mbar_init(mb);
+    lc_fence_proxy_async();
+    lc_mbar_expect(mb, bq + be);
+    lc_bulk_g2s(Ys, q, bq, mb);
+    lc_bulk_g2s(Ye, e, be, mb);
   }
-  for (int i = threadIdx.x; i < NP; i += blockDim.x) Ye[i] = e[i];
+  __syncthreads();
+  const bool ok = lc_mbar_wait_bounded(mb, 0);
+  return !__syncthreads_or(!ok);
 }
 
 struct Dev {
@@ -378,6 +436,7 @@ struct Dev {
   int yKP[Y_KINDS], yNP[Y_KINDS];
   int dir;
   int ragged;
+  int* err;
   // I/O
   const double* in;
   double* out;
@@ -405,36 +464,112 @@ __device__ __forceinline__ double* out_base(const Dev& D, int64_t r) {
   return D.out + (D.ragged ? D.off[r] : D.orig[r] * D.ob);
 }
 
-// Load one 18-wide double-float row pair (two segments) into a common
-// exponent frame and slice it into Xs: columns [c*18, c*18+18) from row c.
-// Rows beyond `valid` are zero.
+// smem layout shared by the stage kernels
+struct Smem {
+  uint16_t* Xs;
+  int xs;
+  uint16_t* Ys;
+  int ys;
+  int* Xe;
+  int* Ye;
+  int* re;  // [2][kRows] exponents of the staged rows
+};
+__device__ __forceinline__ Smem carve(unsigned char* base, int S, int KP, int NP) {
+  Smem m;
+  m.xs = KP + 8;
+  m.ys = KP + 8;
+  m.Xs = reinterpret_cast<uint16_t*>(base);
+  m.Ys = m.Xs + S * kRows * m.xs;
+  m.Xe = reinterpret_cast<int*>(m.Ys + S * NP * m.ys);
+  m.Ye = m.Xe + kRows;
+  m.re = m.Ye + NP;
+  return m;
+}
+size_t smem_bytes(int S, int KP, int NP) {
+  return size_t(S) * kRows * (KP + 8) * 2 + size_t(S) * NP * (KP + 8) * 2 + (3 * kRows + NP) * 4 + 16;
+}
+
+// Stage up to two 18-wide double-float row blocks (rows A0 and, if two, A1
+// for the same members) side by side as one operand row of 18 or 36 columns,
+// in a common exponent frame, sliced into Xs.  The frame comes from the
+// stored row exponents, so every element is then loaded, rescaled and sliced
+// independently (all loads in flight at once).  Rows beyond `valid` are zero.
 __device__ __forceinline__ void stage_rows_df(const Dev& D, const float2* A, const int* Ae, int64_t rowA0,
                                               int64_t rowA1, int two, int64_t tile0, int64_t valid, int KP,
-                                              uint16_t* Xs, int xs, int* Xe) {
-  // one warp per 16 rows, lane = column
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int lr = warp * 16; lr < warp * 16 + 16; ++lr) {
-    const int64_t r = tile0 + lr;
-    const bool ok = r < valid;
-    int e0 = -100000, e1 = -100000;
-    if (ok) {
-      e0 = Ae[rowA0 + r];
-      if (two) e1 = Ae[rowA1 + r];
-    }
-    const int e = max(e0, e1);
-    for (int c = lane; c < KP; c += 32) {
-      float hi = 0.0f, lo = 0.0f;
-      if (ok && c < LC_M * (two ? 2 : 1)) {
-        const int part = c / LC_M, col = c % LC_M;
-        const float2 v = A[((part ? rowA1 : rowA0) + r) * LC_M + col];
-        const float sc = pow2f((part ? e1 : e0) - e);
-        hi = v.x * sc;
-        lo = v.y * sc;
-      }
-      slice_df(hi, lo, D.S, Xs + lr * xs + c, kRows * xs);
-    }
-    if (lane == 0) Xe[lr] = ok ? e : 0;
+                                              Smem& m) {
+  const int parts = two ? 2 : 1;
+  for (int i = threadIdx.x; i < kRows * parts; i += blockDim.x) {
+    const int part = i / kRows, rr = i % kRows;
+    const int64_t r = tile0 + rr;
+    m.re[i] = (r < valid) ? Ae[(part ? rowA1 : rowA0) + r] : -100000;
   }
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x)
+    m.Xe[rr] = two ? max(m.re[rr], m.re[kRows + rr]) : m.re[rr];
+  __syncthreads();
+#pragma unroll 4
+  for (int i = threadIdx.x; i < kRows * KP; i += blockDim.x) {
+    const int rr = i / KP, c = i % KP;
+    float hi = 0.0f, lo = 0.0f;
+    if (c < LC_M * parts && tile0 + rr < valid) {
+      const int part = c / LC_M;
+      const float2 v = A[((part ? rowA1 : rowA0) + tile0 + rr) * LC_M + (c - part * LC_M)];
+      const float sc = pow2f(m.re[part * kRows + rr] - m.Xe[rr]);
+      hi = v.x * sc;
+      lo = v.y * sc;
+    }
+    slice_df_fast(hi, lo, D.S, m.Xs + rr * m.xs + c, kRows * m.xs);
+  }
+  __syncthreads();
+}
+
+// Stage the strip/segment of FP64 input: column c < ncols of member row rr
+// is f_r[j0 + 2c] (zero beyond the member's length).  Pass 1 finds each row's
+// exponent (max over the warp's lanes of the same row, then one shared atomic
+// per row); pass 2 reloads the values (L1 hits), frames and slices them.
+__device__ __forceinline__ void stage_input(const Dev& D, int64_t tile0, int64_t valid, int64_t j0, int ncols,
+                                            int KP, Smem& m, const int64_t* rbase, const int64_t* rlen) {
+  for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) m.Xe[rr] = 0;
+  __syncthreads();
+  const int n = kRows * KP;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int rr = i / KP, c = i - rr * KP;
+    double x = 0.0;
+    const int64_t j = j0 + 2 * c;
+    if (c < ncols && tile0 + rr < valid && j < rlen[rr]) x = D.in[rbase[rr] + j * D.ie];
+    // max over the lanes of this warp that hold the same row, one atomic per row
+    const unsigned grp = __match_any_sync(0xffffffffu, rr);
+    const unsigned E = __reduce_max_sync(grp, unsigned((__double_as_longlong(x) >> 52) & 0x7ff));
+    if ((threadIdx.x & 31) == __ffs(grp) - 1 && E > 0) atomicMax(&m.Xe[rr], int(E));
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int rr = i / KP, c = i - rr * KP;
+    double x = 0.0;
+    const int64_t j = j0 + 2 * c;
+    if (c < ncols && tile0 + rr < valid && j < rlen[rr]) x = D.in[rbase[rr] + j * D.ie];
+    float hi, lo;
+    d2df_scaled(x, m.Xe[rr] - 1021, hi, lo);
+    slice_df_fast(hi, lo, D.S, m.Xs + rr * m.xs + c, kRows * m.xs);
+  }
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) m.Xe[rr] -= 1021;
+  __syncthreads();
+}
+
+// Per-row input/output bases and lengths of a member tile.
+__device__ __forceinline__ void row_info(const Dev& D, int64_t tile0, int64_t valid, int64_t* rbase, int64_t* obase,
+                                         int64_t* rlen) {
+  for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) {
+    const int64_t r = tile0 + rr;
+    const bool ok = r < valid;
+    rbase[rr] = ok ? (D.ragged ? D.off[r] : D.orig[r] * D.ib) : 0;
+    if (obase) obase[rr] = ok ? (D.ragged ? D.off[r] : D.orig[r] * D.ob) : 0;
+    rlen[rr] = ok ? D.len[r] : 0;
+  }
+  __syncthreads();
 }
 
 // Value frame of a fragment row: scale so the row max lies in [1/4, 1/2).
@@ -473,29 +608,6 @@ __device__ __forceinline__ void frame_rows(float (&hi)[NT][4], float (&lo)[NT][4
     }
 }
 
-// smem layout shared by the stage kernels
-struct Smem {
-  uint16_t* Xs;
-  int xs;
-  uint16_t* Ys;
-  int ys;
-  int* Xe;
-  int* Ye;
-};
-__device__ __forceinline__ Smem carve(unsigned char* base, int S, int KP, int NP) {
-  Smem m;
-  m.xs = KP + 8;
-  m.ys = KP + 8;
-  m.Xs = reinterpret_cast<uint16_t*>(base);
-  m.Ys = m.Xs + S * kRows * m.xs;
-  m.Xe = reinterpret_cast<int*>(m.Ys + S * NP * m.ys);
-  m.Ye = m.Xe + kRows;
-  return m;
-}
-size_t smem_bytes(int S, int KP, int NP) {
-  return size_t(S) * kRows * (KP + 8) * 2 + size_t(S) * NP * (KP + 8) * 2 + (kRows + NP) * 4 + 16;
-}
-
 // Store a framed fragment row pair to a double-float row array.
 template <int NT>
 __device__ __forceinline__ void store_rows(float2* Out, int* OutE, int64_t row_base, int64_t tile0, int64_t valid,
@@ -520,33 +632,23 @@ __device__ __forceinline__ void store_rows(float2* Out, int* OutE, int64_t row_b
 // ------------------------------------------------------------------ kernels
 // Step 1: W(0, g, sigma) = F(g, sigma) T(sigma).
 __global__ void __launch_bounds__(kThreads) k_s_leaf(Dev D, int64_t w0) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t mbar;
   const Work it = D.work[w0 + blockIdx.x];
   const int sigma = blockIdx.y;
   const int KP = D.yKP[Y_LEAF], NP = D.yNP[Y_LEAF];
   Smem m = carve(sm_raw, D.S, KP, NP);
   const int64_t g = it.seg, tile0 = int64_t(it.tile) * kRows;
   const int64_t valid = dcnt(D, 0, g);
-  load_y(D.yq[Y_LEAF] + size_t(sigma) * D.S * NP * KP, D.ye[Y_LEAF] + sigma * NP, D.S, NP, KP, m.Ys, m.ys, m.Ye);
+  if (!load_y(D.yq[Y_LEAF] + size_t(sigma) * D.S * NP * (KP + 8), D.ye[Y_LEAF] + sigma * NP, D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
+    if (threadIdx.x == 0) atomicOr(D.err, 1);
+    return;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int s = D.s;
-  for (int lr = warp * 16; lr < warp * 16 + 16; ++lr) {
-    const int64_t r = tile0 + lr;
-    double x = 0.0;
-    if (r < valid && lane < s) {
-      const int64_t j = 2 * int64_t(s) * g + 2 * lane + sigma;
-      if (j < D.len[r]) x = in_base(D, r)[j * D.ie];
-    }
-    int E = int((__double_as_longlong(x) >> 52) & 0x7ff);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-    const int er = E - 1021;
-    float hi, lo;
-    d2df_scaled(x, er, hi, lo);
-    slice_df(hi, lo, D.S, m.Xs + lr * m.xs + lane, kRows * m.xs);
-    if (lane == 0) m.Xe[lr] = er;
-  }
-  __syncthreads();
+  __shared__ int64_t rbase[kRows], rlen[kRows];
+  row_info(D, tile0, valid, rbase, nullptr, rlen);
+  stage_input(D, tile0, valid, 2 * int64_t(s) * g + sigma, s, KP, m, rbase, rlen);
   float hi[3][4], lo[3][4];
   warp_ozaki<2, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
   const int g8 = lane >> 2;
@@ -557,7 +659,8 @@ __global__ void __launch_bounds__(kThreads) k_s_leaf(Dev D, int64_t w0) {
 
 // Step 2: W(d+1, G) = [W(d, 2G) W(d, 2G+1)] [B(0) B(1)]^T.
 __global__ void __launch_bounds__(kThreads) k_s_up(Dev D, int64_t w0) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t mbar;
   const Work it = D.work[w0 + blockIdx.x];
   const int sigma = blockIdx.y;
   const int KP = D.yKP[Y_UP], NP = D.yNP[Y_UP];
@@ -565,10 +668,12 @@ __global__ void __launch_bounds__(kThreads) k_s_up(Dev D, int64_t w0) {
   const int dp = it.d;  // parent level
   const int64_t G = it.seg, tile0 = int64_t(it.tile) * kRows;
   const int64_t valid = dcnt(D, dp, G);
-  load_y(D.yq[Y_UP], D.ye[Y_UP], D.S, NP, KP, m.Ys, m.ys, m.Ye);
+  if (!load_y(D.yq[Y_UP], D.ye[Y_UP], D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
+    if (threadIdx.x == 0) atomicOr(D.err, 1);
+    return;
+  }
   stage_rows_df(D, D.W, D.We, drow(D, dp - 1, 2 * G, sigma, 0), drow(D, dp - 1, 2 * G + 1, sigma, 0), 1, tile0,
-                valid, KP, m.Xs, m.xs, m.Xe);
-  __syncthreads();
+                valid, KP, m);
   float hi[3][4], lo[3][4];
   warp_ozaki<3, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2;
@@ -580,7 +685,8 @@ __global__ void __launch_bounds__(kThreads) k_s_up(Dev D, int64_t w0) {
 // Step 3: C(d, v) = [W(d, v+2) W(d, v+3)] [A-hat(b,0) A-hat(b,1)]^T (v even),
 //                  W(d, v+2) A-hat(b,2)^T (v odd).
 __global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t mbar;
   const Work it = D.work[w0 + blockIdx.x];
   const int sigma = blockIdx.y;
   const int KP = D.yKP[Y_COUPLE], NP = D.yNP[Y_COUPLE];
@@ -590,11 +696,13 @@ __global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) {
   const int64_t valid = dcnt(D, d, v + 2);
   const int Gam = D.Lmax - 1 - d;  // level in the shared table
   const int64_t item = (int64_t(4) * ((int64_t(1) << Gam) - 1) - 2 * Gam) + v;
-  load_y(D.yq[Y_COUPLE] + size_t(item) * D.S * NP * KP, D.ye[Y_COUPLE] + item * NP, D.S, NP, KP, m.Ys, m.ys, m.Ye);
+  if (!load_y(D.yq[Y_COUPLE] + size_t(item) * D.S * NP * (KP + 8), D.ye[Y_COUPLE] + item * NP, D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
+    if (threadIdx.x == 0) atomicOr(D.err, 1);
+    return;
+  }
   const int two = ((v & 1) == 0) ? 1 : 0;
   stage_rows_df(D, D.W, D.We, drow(D, d, v + 2, sigma, 0), two ? drow(D, d, v + 3, sigma, 0) : 0, two, tile0, valid,
-                KP, m.Xs, m.xs, m.Xe);
-  __syncthreads();
+                KP, m);
   float hi[3][4], lo[3][4];
   warp_ozaki<3, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2;
@@ -605,7 +713,8 @@ __global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) {
 
 // Step 4: C(d, v) += C(d+1, v/2) B(v mod 2).
 __global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t mbar;
   const Work it = D.work[w0 + blockIdx.x];
   const int sigma = blockIdx.y;
   const int KP = D.yKP[Y_DOWN], NP = D.yNP[Y_DOWN];
@@ -614,9 +723,11 @@ __global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) {
   const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;
   const int64_t valid = dcnt(D, d, v + 4);
   const int p = int(v & 1);
-  load_y(D.yq[Y_DOWN] + size_t(p) * D.S * NP * KP, D.ye[Y_DOWN] + p * NP, D.S, NP, KP, m.Ys, m.ys, m.Ye);
-  stage_rows_df(D, D.C, D.Ce, drow(D, d + 1, v >> 1, sigma, 0), 0, 0, tile0, valid, KP, m.Xs, m.xs, m.Xe);
-  __syncthreads();
+  if (!load_y(D.yq[Y_DOWN] + size_t(p) * D.S * NP * (KP + 8), D.ye[Y_DOWN] + p * NP, D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
+    if (threadIdx.x == 0) atomicOr(D.err, 1);
+    return;
+  }
+  stage_rows_df(D, D.C, D.Ce, drow(D, d + 1, v >> 1, sigma, 0), 0, 0, tile0, valid, KP, m);
   float hi[3][4], lo[3][4];
   warp_ozaki<2, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2, t = lane & 3;
@@ -651,55 +762,30 @@ __global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) {
   }
 }
 
-// Steps 5-7 for strip t: Z = C(0, t) T(sigma)^T + F(strip) E^T, C^{-1}, store.
-__global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const Work it = D.work[w0 + blockIdx.x];
-  const int sigma = blockIdx.y;
+// Steps 5-7 for strip t and parity sigma, 64 members per CTA:
+//   Z = F(strip) E^T + C(0, t) T(sigma)^T, then C^{-1}, store.
+// Two sliced products (near field, K = 2s; spread, K = 18) that reuse the
+// same shared memory; their double-float results are added in a common frame.
+template <int KTN>
+__device__ __forceinline__ void final_body(const Dev& D, unsigned char* sm_raw, uint64_t* mbar, int64_t t, int sigma,
+                                           int64_t tile0, int64_t validN, int64_t validF) {
   const int s = D.s;
-  const int64_t t = it.seg, tile0 = int64_t(it.tile) * kRows;
-  const int64_t validN = D.cntN[t];
-  const int64_t validF = (D.Lmax > 0 && t + 2 < (int64_t(2) << D.Lmax)) ? dcnt(D, 0, t + 2) : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2, tq = lane & 3;
+  __shared__ int64_t rbase[kRows], obase[kRows], rlen[kRows];
+  row_info(D, tile0, validN, rbase, obase, rlen);
   // ---- near field
-  const int KPn = D.yKP[Y_NEAR], NPn = D.yNP[Y_NEAR];
+  const int KPn = KTN * 16, NPn = D.yNP[Y_NEAR];
   Smem m = carve(sm_raw, D.S, KPn, NPn);
   const int64_t item = 2 * t + sigma;
-  load_y(D.yq[Y_NEAR] + size_t(item) * D.S * NPn * KPn, D.ye[Y_NEAR] + item * NPn, D.S, NPn, KPn, m.Ys, m.ys,
-         m.Ye);
-  for (int lr = warp * 16; lr < warp * 16 + 16; ++lr) {
-    const int64_t r = tile0 + lr;
-    double x0 = 0.0, x1 = 0.0;
-    if (r < validN) {
-      const double* f = in_base(D, r);
-      const int64_t n = D.len[r];
-      const int64_t j0 = 2 * int64_t(s) * t + 2 * lane + sigma;
-      const int64_t j1 = j0 + 64;
-      if (lane < 2 * s && j0 < n) x0 = f[j0 * D.ie];
-      if (lane + 32 < 2 * s && j1 < n) x1 = f[j1 * D.ie];
-    }
-    int E = max(int((__double_as_longlong(x0) >> 52) & 0x7ff), int((__double_as_longlong(x1) >> 52) & 0x7ff));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-    const int er = E - 1021;
-    float hi, lo;
-    d2df_scaled(x0, er, hi, lo);
-    slice_df(hi, lo, D.S, m.Xs + lr * m.xs + lane, kRows * m.xs);
-    if (lane + 32 < KPn) {
-      d2df_scaled(x1, er, hi, lo);
-      slice_df(hi, lo, D.S, m.Xs + lr * m.xs + lane + 32, kRows * m.xs);
-    }
-    if (lane == 0) m.Xe[lr] = er;
+  if (!load_y(D.yq[Y_NEAR] + size_t(item) * D.S * NPn * (KPn + 8), D.ye[Y_NEAR] + item * NPn, D.S, NPn, KPn, m.Ys,
+              m.Ye, mbar)) {
+    if (threadIdx.x == 0) atomicOr(D.err, 1);
+    return;
   }
-  __syncthreads();
+  stage_input(D, tile0, validN, 2 * int64_t(s) * t + sigma, 2 * s, KPn, m, rbase, rlen);
   float nh[4][4], nl[4][4];
-  if (KPn == 64)
-    warp_ozaki<4, 4>(m.Xs, m.xs, m.Ys, m.ys, D.S, nh, nl);
-  else if (KPn == 48)
-    warp_ozaki<3, 4>(m.Xs, m.xs, m.Ys, m.ys, D.S, nh, nl);
-  else
-    warp_ozaki<2, 4>(m.Xs, m.xs, m.Ys, m.ys, D.S, nh, nl);
-  int enx0 = m.Xe[warp * 16 + g8], enx1 = m.Xe[warp * 16 + g8 + 8];
+  warp_ozaki<KTN, 4>(m.Xs, m.xs, m.Ys, m.ys, D.S, nh, nl);
+  const int enx0 = m.Xe[warp * 16 + g8], enx1 = m.Xe[warp * 16 + g8 + 8];
   int eny[4][2];
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt) {
@@ -710,14 +796,15 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
   // ---- far field (spread)
   float fh[4][4], fl[4][4];
   int efx0 = 0, efx1 = 0, efy[4][2];
-  const bool any_far = validF > tile0;
-  if (any_far) {
+  if (validF > tile0) {
     const int KPs = D.yKP[Y_SPREAD], NPs = D.yNP[Y_SPREAD];
     Smem m2 = carve(sm_raw, D.S, KPs, NPs);
-    load_y(D.yq[Y_SPREAD] + size_t(sigma) * D.S * NPs * KPs, D.ye[Y_SPREAD] + sigma * NPs, D.S, NPs, KPs, m2.Ys,
-           m2.ys, m2.Ye);
-    stage_rows_df(D, D.C, D.Ce, drow(D, 0, t, sigma, 0), 0, 0, tile0, validF, KPs, m2.Xs, m2.xs, m2.Xe);
-    __syncthreads();
+    if (!load_y(D.yq[Y_SPREAD] + size_t(sigma) * D.S * NPs * (KPs + 8), D.ye[Y_SPREAD] + sigma * NPs, D.S, NPs, KPs,
+                m2.Ys, m2.Ye, mbar)) {
+      if (threadIdx.x == 0) atomicOr(D.err, 1);
+      return;
+    }
+    stage_rows_df(D, D.C, D.Ce, drow(D, 0, t, sigma, 0), 0, 0, tile0, validF, KPs, m2);
     warp_ozaki<2, 4>(m2.Xs, m2.xs, m2.Ys, m2.ys, D.S, fh, fl);
     efx0 = m2.Xe[warp * 16 + g8];
     efx1 = m2.Xe[warp * 16 + g8 + 8];
@@ -742,10 +829,11 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int col = nt * 8 + 2 * tq + (i & 1);  // local row m of the strip
+      const int rr = warp * 16 + g8 + ((i < 2) ? 0 : 8);
       const int64_t r = (i < 2) ? r0 : r1;
       if (col >= s || r >= validN) continue;
       const int64_t row_i = 2 * int64_t(s) * t + 2 * col + sigma;
-      if (row_i >= D.len[r]) continue;
+      if (row_i >= rlen[rr]) continue;
       const bool far = r < validF;
       const int E1 = ((i < 2) ? enx0 : enx1) + eny[nt][i & 1] - 16;
       const int E2 = ((i < 2) ? efx0 : efx1) + efy[nt][i & 1] - 16;
@@ -763,8 +851,25 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
         pe = fmaf(zh, cl, fmaf(zl, ch, pe));
         fast_two_sum(ph, pe, zh, zl);
       }
-      out_base(D, r)[row_i * D.oe] = f2d_scaled(zh, F) + f2d_scaled(zl, F);
+      D.out[obase[rr] + row_i * D.oe] = f2d_scaled(zh, F) + f2d_scaled(zl, F);
     }
+}
+
+__global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  const Work it = D.work[w0 + blockIdx.x];
+  const int sigma = blockIdx.y;
+  const int64_t t = it.seg, tile0 = int64_t(it.tile) * kRows;
+  const int64_t validN = D.cntN[t];
+  const int64_t validF = (D.Lmax > 0 && t + 2 < (int64_t(2) << D.Lmax)) ? dcnt(D, 0, t + 2) : 0;
+  const int KPn = D.yKP[Y_NEAR];
+  if (KPn == 64)
+    final_body<4>(D, sm_raw, &mbar, t, sigma, tile0, validN, validF);
+  else if (KPn == 48)
+    final_body<3>(D, sm_raw, &mbar, t, sigma, tile0, validN, validF);
+  else
+    final_body<2>(D, sm_raw, &mbar, t, sigma, tile0, validN, validF);
 }
 
 // ------------------------------------------------------------ plan kernels
@@ -832,14 +937,15 @@ __global__ void k_make_y(int kind, int items, int K, int KP, int NP, int S, lc_p
     ey = ex + 1;
   }
   e[item * NP + n] = ey;
-  uint16_t* dst = q + (size_t(item) * S * NP + n) * KP;
-  for (int k = 0; k < KP; ++k) {
+  const int KS = KP + 8;  // row stride of the shared-memory layout
+  uint16_t* dst = q + (size_t(item) * S * NP + n) * KS;
+  for (int k = 0; k < KS; ++k) {
     double y = (k < K) ? ldexp(y_value(kind, item, k, n, P, s, L, N, dir), -ey) : 0.0;
     for (int sl = 0; sl < S; ++sl) {
       const double tt = y * 256.0;
       const double qq = rint(tt);
       y = tt - qq;
-      dst[size_t(sl) * NP * KP + k] = uint16_t(__float_as_uint(float(qq)) >> 16);
+      dst[size_t(sl) * NP * KS + k] = uint16_t(__float_as_uint(float(qq)) >> 16);
     }
   }
 }
@@ -873,6 +979,7 @@ Dev make_dev(const lc_plan_s* p, const SplitHost& h) {
   }
   D.dir = int(p->dir);
   D.ragged = p->ragged;
+  D.err = p->err;
   return D;
 }
 
