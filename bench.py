@@ -75,6 +75,22 @@ def dist_env():
     return ws, rank, local
 
 
+# ------------------------------------------------------------ multi-rank
+def replica_throughput(ms_local, coef_per_rank, device=None):
+    """Whole-job throughput of N independent replicas (the transform has no
+    exchange step): every rank transforms its own copy; the job time is the
+    slowest rank's.  Returns (ms_max, coefficients/s over all ranks)."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = float(ms_local)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ws * coef_per_rank / (ms / 1e3)
+
+
 # ---------------------------------------------------------------- oracle leg
 def oracle_leg(n, x, rows_per_dir):
     """Time the oracle on `rows_per_dir` sampled rows of each direction."""
@@ -272,16 +288,66 @@ def batched_leg(lc, dev, flush, args):
     out["ragged_4096_l2c"] = {"coefficients_per_s": float(lengths.sum()) / (ms / 1e3), "ms": ms,
                               "coefficients": int(lengths.sum()), "plan_s": plan_s, "launches": plan.launches()}
     del plan, x, z
-    # (c) 512^3 array, Legendre->Chebyshev along axis 0 (strided fibres) and axis 2 (contiguous)
+    # (b') the plain per-vector FP64 and double-float paths on a sample of 128 members
+    sample = np.random.default_rng(6).choice(len(lengths), 128, replace=False)
+    offs = workloads.ragged_offsets(lengths)
+    xs = torch.as_tensor(workloads.ragged_batch(lengths, seed=3), device=dev)
+    for tier in ("f64", "f64_df"):
+        plans = [(lc.Plan(int(lengths[i]), "l2c", 1, tier, dev), int(offs[i]), int(lengths[i])) for i in sample]
+        zs = torch.empty_like(xs)
+
+        def per_vector():
+            for pl_, a, m in plans:
+                pl_(xs[a:a + m], out=zs[a:a + m])
+        step = graph_step(per_vector)
+        ms = time_fn(step, flush, max(3, steps // 2), 1)
+        cnt = int(sum(m for _, _, m in plans))
+        out["ragged_4096_l2c"]["per_vector_%s_sample128" % tier] = {"coefficients_per_s": cnt / (ms / 1e3), "ms": ms,
+                                                                     "coefficients": cnt}
+        del plans
+    del xs
+    # (c) 512^3 array, Legendre->Chebyshev along each axis; fibres are strided views of the array
     N3 = 512
     cube = torch.as_tensor(workloads.cube(N3, seed=4), device=dev)
     outc = torch.empty((N3 * N3, N3), dtype=torch.float64, device=dev)
-    plan = lc.Plan(N3, "l2c", N3 * N3, "f64_split", dev)
-    for axis, strides in ((0, (1, N3 * N3)), (2, (N3, 1))):
-        step = graph_step(lambda: plan.execute_strided(cube, outc, strides, (N3, 1)))
-        ms = time_fn(step, flush, max(3, steps // 2), 1)
-        out["cube512_axis%d_l2c" % axis] = {"coefficients_per_s": N3 ** 3 / (ms / 1e3), "ms": ms}
-    del plan, cube, outc
+    for tier in ("f64_split", "f64_df"):
+        plan = lc.Plan(N3, "l2c", N3 * N3, tier, dev)
+        res = {}
+        for axis, strides in ((0, (1, N3 * N3)), (2, (N3, 1))):
+            step = graph_step(lambda: plan.execute_strided(cube, outc, strides, (N3, 1)))
+            ms = time_fn(step, flush, max(3, steps // 2), 1)
+            res["axis%d" % axis] = {"coefficients_per_s": N3 ** 3 / (ms / 1e3), "ms": ms}
+        # axis 1: fibre (i, k) runs over j with stride N3; one call per slab i (batch over k)
+        slab = lc.Plan(N3, "l2c", N3, tier, dev)
+        outs = outc.view(N3, N3, N3)
+
+        def axis1():
+            for i in range(N3):
+                slab.execute_strided(cube[i], outs[i], (1, N3), (N3, 1))
+        step = graph_step(axis1)
+        ms = time_fn(step, flush, 3, 1)
+        res["axis1"] = {"coefficients_per_s": N3 ** 3 / (ms / 1e3), "ms": ms, "calls": N3}
+        out["cube512_l2c_" + tier] = res
+        del plan, slab
+    del cube, outc
+    # (d) differentiable least-squares fit: loss = ||leg2cheb(x) - y||^2, n = 65536, batch 256,
+    #     one step = forward transform + hand-written adjoint (autograd backward)
+    x0, y0 = workloads.fit_pair(65536, 256)
+    fit = {}
+    for tier in ("f64_df", "f64", "f32"):
+        dt = torch.float32 if tier == "f32" else torch.float64
+        xt = torch.as_tensor(x0, device=dev, dtype=dt).requires_grad_(True)
+        yt = torch.as_tensor(y0, device=dev, dtype=dt)
+
+        def fit_step():
+            xt.grad = None
+            loss = ((lc.leg2cheb(xt, dtype=tier) - yt) ** 2).sum()
+            loss.backward()
+        ms = time_fn(fit_step, flush, max(3, steps // 2), 2)
+        fit[tier] = {"ms_per_step": ms, "transforms_per_step": 2,
+                     "coefficients_per_s": 2 * 65536 * 256 / (ms / 1e3)}
+        del xt, yt
+    out["fit_65536x256_forward_backward"] = fit
     torch.cuda.synchronize()
     return out
 
@@ -372,12 +438,7 @@ def run_ours(args):
     # library's kernels (in this mode each execution stays on one stream, so the
     # overlap of the coarse levels with the coupling is off).
     _, _, stages = time_tier(pl, args.steps, 2, stage_timing=True)
-    ms_per_step = sum(ms) / len(ms)
-    if ws > 1:
-        t = torch.tensor([ms_per_step], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_per_step = float(t.item())
-    value = ws * 2 * n / (ms_per_step / 1e3)
+    ms_per_step, value = replica_throughput(sum(ms) / len(ms), 2 * n, dev)
 
     # per-tier numbers (median of a shorter run each)
     tier_vals = {}
