@@ -48,9 +48,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2
 # instructions (TwoProd with fma, cross terms, TwoSum accumulation); the FP32
 # issue limit is 152 SMs x 128 lanes x 2070 MHz.
 DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
-# DRAM bytes per launch of the dominant kernel, from the ncu capture summarised in
-# profiles/f64_single_n1e6.md (dram__bytes_read.sum + dram__bytes_write.sum).
-TRAFFIC = {}
+# DRAM bytes per launch of the dominant kernel (the last down chunk: Steps 4-7
+# of the fine levels), dram__bytes_read.sum + dram__bytes_write.sum from the
+# ncu captures summarised in profiles/df_single_n1e6.md and
+# profiles/f64_single_n1e6.md (one L2C launch at n = 1e6).
+TRAFFIC = {("f64_df", 4): 25.342e6, ("f64", 4): 25.350e6}
 KIND_NAMES = {0: "leaf_restrict", 1: "upward", 2: "couple", 3: "downward", 4: "spread_near_scale", 5: "prepare",
               6: "other"}
 
@@ -65,6 +67,8 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=CPU_ROWS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (profiling runs)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workloads")
+    ap.add_argument("--profile", default=None,
+                    help="TIER:DIRECTION:N:BATCH -- build one plan, run it twice, exit (a short target for ncu)")
     return ap.parse_args()
 
 
@@ -539,8 +543,33 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def profile_run(spec):
+    """Two executions of one plan on synthetic data (a small, fixed target for profilers)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_00033_gb300 as lc
+    import workloads
+    tier, direction, n, batch = spec.split(":")
+    n, batch = int(n), int(batch)
+    dev = torch.device("cuda", 0)
+    dt = torch.float32 if tier == "f32" else torch.float64
+    x = workloads.decaying_vector(n, seed=1, r=1.0, batch=None if batch == 1 else batch)
+    xt = torch.as_tensor(x, device=dev, dtype=dt)
+    plan = lc.Plan(n, direction, batch, tier, dev)
+    out = torch.empty_like(xt)
+    for _ in range(2):
+        plan(xt, out=out)
+    torch.cuda.synchronize()
+    plan.check()
+    print(json.dumps({"profile": spec, "launches_per_execute": plan.launches()}))
+
+
 def main():
     args = parse()
+    if args.profile:
+        profile_run(args.profile)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
