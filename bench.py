@@ -382,13 +382,17 @@ def run_ours(args):
 
     available = ["f64", "f64_df"]  # the split tier is for batches (reported under "batched")
     tiers = {}
+    tuned = {}
+    outs = (torch.empty_like(x), torch.empty_like(x))
     for t in available:
         try:
             tiers[t] = (lc.Plan(n, "l2c", 1, t, dev), lc.Plan(n, "c2l", 1, t, dev))
         except lc.LegChebError as e:
             if e.status != 5:  # LC_ERR_UNSUPPORTED: tier not built for this request
                 raise
-    outs = (torch.empty_like(x), torch.empty_like(x))
+            continue
+        # plan setup includes the autotuner's choice of chunk geometry (untimed, like planning)
+        tuned[t] = [list(p.autotune(x, out=outs[0])[:2]) for p in tiers[t]]
 
     def step(pl):
         pl[0](x, out=outs[0])
@@ -508,6 +512,7 @@ def run_ours(args):
         "vs_baseline": value / PAPER_COEF_PER_S, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "n=1e6 single vector, L2C and C2L, N(0,1)(j+1)^-1 seed 1",
                    "n": n, "batch": 1, "tier": chosen, "plan": {k: info[k] for k in ("N", "L", "s", "M", "n_c")},
+                   "autotuned_chunks_l2c_c2l": tuned.get(chosen),
                    "l2_flush": "256 MB write before every timed step", "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": {"value": e2e_val, "unit": "coefficients/s", "h2d_bytes_per_step": 2 * 8 * n,
                 "d2h_bytes_per_step": 2 * 8 * n},

@@ -168,6 +168,25 @@ lc_status lc_adjoint(lc_plan plan, const void* in, void* out, int64_t in_batch_s
  * was recorded since the last check (and clears it), else LC_OK. */
 lc_status lc_plan_check(lc_plan plan, lc_stream stream);
 
+/* Chunk geometry of the CUDA-core tiers (LC_F64, LC_F32, LC_F64_DF).  The
+ * levels of Algorithm 4 are processed in subtrees, one CTA per subtree:
+ * leaf_depth = levels the first upward chunk climbs from the leaves (and the
+ * last downward chunk descends), chunk_depth = levels per coarser chunk;
+ * 1..6 each, defaults 4 and 4.  The results do not depend on them. */
+lc_status lc_plan_set_config(lc_plan plan, int32_t leaf_depth, int32_t chunk_depth);
+
+/* Autotuner (not in the paper): time every candidate chunk geometry
+ * (leaf_depth in {3,4,5} x chunk_depth in {3,4,6}) on the given input with
+ * CUDA events on `stream` (synchronises it; `out` is overwritten, same layout
+ * rules as lc_execute), keep the fastest in the plan, and cache it for this
+ * process under the plan's shape (n, batch, L, s, dtype, direction); plans of
+ * the same shape created later start from the cached choice.  Outputs may be
+ * NULL.  Plans without a tunable geometry (split tier, ragged, L <= 1) return
+ * LC_OK unchanged. */
+lc_status lc_plan_autotune(lc_plan plan, const void* in, void* out, int64_t in_batch_stride,
+                           int64_t in_elem_stride, int64_t out_batch_stride, int64_t out_elem_stride,
+                           lc_stream stream, int32_t* leaf_depth, int32_t* chunk_depth, float* best_ms);
+
 /* Free the host plan object.  The workspace stays the caller's. */
 lc_status lc_destroy(lc_plan plan);
 

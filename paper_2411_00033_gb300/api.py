@@ -119,6 +119,20 @@ class Plan:
         with torch.cuda.device(self.device):
             return B.lc_plan_table(self._handle, which, sizes[which], _stream_ptr(self.device))
 
+    def autotune(self, x: torch.Tensor, out: torch.Tensor | None = None):
+        """Pick the fastest chunk geometry on this input (see lc_plan_autotune)."""
+        self._check_in(x)
+        ib, ie = self._strides(x)
+        if out is None:
+            out = torch.empty_like(x)
+        ob, oe = self._strides(out)
+        with torch.cuda.device(self.device):
+            return B.lc_plan_autotune(self._handle, x.data_ptr(), out.data_ptr(), ib, ie, ob, oe,
+                                      _stream_ptr(self.device))
+
+    def set_config(self, leaf_depth: int, chunk_depth: int):
+        B.lc_plan_set_config(self._handle, leaf_depth, chunk_depth)
+
     def check(self):
         """Raise if a bounded device-side wait of an earlier execution ran out."""
         with torch.cuda.device(self.device):

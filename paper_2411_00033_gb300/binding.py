@@ -24,6 +24,7 @@ EXPORTED = (
     "lc_plan_create", "lc_plan_create_ex", "lc_plan_workspace_size_ragged", "lc_plan_create_ragged",
     "lc_execute", "lc_adjoint", "lc_destroy", "lc_status_string", "lc_plan_info", "lc_plan_table",
     "lc_plan_launches", "lc_plan_set_timing", "lc_plan_get_timing", "lc_plan_check", "lc_direct_static",
+    "lc_plan_set_config", "lc_plan_autotune",
 )
 
 
@@ -74,6 +75,8 @@ def load(path: Path | None = None):
         "lc_plan_launches": [vp, pi32],
         "lc_plan_set_timing": [vp, i32],
         "lc_plan_check": [vp, vp],
+        "lc_plan_set_config": [vp, i32, i32],
+        "lc_plan_autotune": [vp, vp, vp, i64, i64, i64, i64, vp, pi32, pi32, ctypes.POINTER(ctypes.c_float)],
         "lc_plan_get_timing": [vp, i32, ctypes.POINTER(ctypes.c_float), pi32, i32, pi32],
     }
     for name, args in sig.items():
@@ -210,3 +213,16 @@ def lc_direct_static(direction, n, batch, in_ptr, out_ptr, ib, ie, ob, oe, strea
     f.restype = ctypes.c_int
     _check(f(direction, n, batch, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), ib, ie, ob, oe,
              ctypes.c_void_p(stream_ptr)), "lc_direct_static")
+
+
+def lc_plan_set_config(plan, leaf_depth: int, chunk_depth: int):
+    _check(load().lc_plan_set_config(ctypes.c_void_p(plan), leaf_depth, chunk_depth), "lc_plan_set_config")
+
+
+def lc_plan_autotune(plan, in_ptr, out_ptr, ib, ie, ob, oe, stream_ptr):
+    """Time the candidate chunk geometries, keep the fastest: returns (leaf_depth, chunk_depth, ms)."""
+    a, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load().lc_plan_autotune(ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), ib, ie,
+                                   ob, oe, ctypes.c_void_p(stream_ptr), ctypes.byref(a), ctypes.byref(b),
+                                   ctypes.byref(ms)), "lc_plan_autotune")
+    return a.value, b.value, ms.value

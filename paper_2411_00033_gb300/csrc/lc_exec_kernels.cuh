@@ -95,8 +95,9 @@ __device__ __forceinline__ const double& ahat_at<double>(const double* Ah, int64
 }
 
 constexpr int kThreads = 256;
-constexpr int kLeafDepth = 4;   // levels climbed by the first up chunk / descended by the last down chunk
-constexpr int kChunkDepth = 4;  // levels per middle chunk
+// Chunk geometry (per plan, chosen by lc_plan_autotune; defaults 4 and 4):
+// leaf depth = levels climbed by the first up chunk / descended by the last
+// down chunk, chunk depth = levels per coarse chunk.
 constexpr int kSeg = 2 * LC_M;  // values per segment: [sigma][k]
 
 // Node x at level gamma of the column tree (segments g >= 2) or of the row
@@ -488,24 +489,24 @@ __global__ void __launch_bounds__(kThreads) k_down_chunk(Args<R> a, int rho, int
 
 // ------------------------------------------------------------------ driver
 template <typename R>
-inline void chunk_roots(int L, int* roots, int* count) {
-  // roots[0] = top level of the first up chunk, then up to 4 levels per chunk
+inline void chunk_roots(int L, int leaf_depth, int chunk_depth, int* roots, int* count) {
+  // roots[0] = top level of the first up chunk, then up to chunk_depth levels per chunk
   int n = 0;
-  int r = L - 1 - kLeafDepth;
+  int r = L - 1 - leaf_depth;
   if (r < 0) r = 0;
   roots[n++] = r;
   while (r > 0) {
-    r = r - kChunkDepth > 0 ? r - kChunkDepth : 0;
+    r = r - chunk_depth > 0 ? r - chunk_depth : 0;
     roots[n++] = r;
   }
   *count = n;
 }
 
 template <typename R>
-inline int launches_for(int L) {
+inline int launches_for(int L, int leaf_depth, int chunk_depth) {
   if (L <= 0) return 1;
-  int roots[32], nr;
-  chunk_roots<R>(L, roots, &nr);
+  int roots[64], nr;
+  chunk_roots<R>(L, leaf_depth, chunk_depth, roots, &nr);
   return 2 * nr + (roots[0] > 0 ? 2 : 1);
 }
 
@@ -530,8 +531,8 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
     lc_timer_end(p, st);
     return LC_OK;
   }
-  int roots[32], nr;
-  chunk_roots<R>(L, roots, &nr);
+  int roots[64], nr;
+  chunk_roots<R>(L, p->leaf_depth, p->chunk_depth, roots, &nr);
   const size_t smc = (size_t(3) * kCBlocks * LC_M * LC_M + size_t(2) * kCBlocks * kSeg) * sizeof(R) + 16;
   {
     lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_couple_blocks<R>), smc);

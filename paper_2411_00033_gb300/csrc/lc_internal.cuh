@@ -99,6 +99,8 @@ struct lc_plan_s {
   // one execution (host objects; created at plan time).
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
+  // Chunk geometry of the CUDA-core tiers (lc_plan_autotune / lc_plan_set_config).
+  int leaf_depth, chunk_depth;
   // Optional per-kernel timing (lc_plan_set_timing).
   int timing_slots;
   int timing_stride;       // events per slot
@@ -162,3 +164,6 @@ lc_status lc_exec_split(lc_plan p, const void* in, void* out, int64_t ib, int64_
                         int64_t oe, cudaStream_t st, int adjoint);
 int lc_exec_split_launches(const lc_plan_s* p);
 void lc_split_release(lc_plan p);
+
+// ---- autotuning cache (lc_tune.cu) ------------------------------------------
+void lc_tune_apply_cached(lc_plan p);

@@ -296,6 +296,8 @@ lc_status fill_plan(lc_plan_s* p, int64_t n, lc_direction dir, int64_t batch, lc
   p->dtype = dtype;
   p->batch = batch;
   p->count = batch;
+  p->leaf_depth = 4;
+  p->chunk_depth = 4;
   return LC_OK;
 }
 
@@ -455,6 +457,7 @@ lc_status lc_plan_create_ex(lc_plan* out, int64_t n, lc_direction direction, int
     free(p);
     return st;
   }
+  lc_tune_apply_cached(p);
   *out = p;
   return LC_OK;
 }

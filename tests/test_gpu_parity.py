@@ -175,3 +175,33 @@ def test_graph_capture_of_cuda_core_tiers(lc, tier):
     torch.cuda.synchronize()
     direct = plan(x).cpu().numpy()
     assert np.array_equal(z.cpu().numpy(), direct)
+
+
+@pytest.mark.parametrize("tier", ["f64", "f64_df"])
+def test_chunk_geometry_does_not_change_results(lc, tier):
+    # The subtree chunking only reorders independent work: bitwise-equal outputs.
+    n = 300000
+    dev = torch.device("cuda", 0)
+    x = torch.as_tensor(workloads.decaying_vector(n, seed=13), device=dev)
+    for direction in ("l2c", "c2l"):
+        plan = lc.Plan(n, direction, 1, tier, dev)
+        ref = plan(x).cpu().numpy()
+        for leaf, chunk in ((1, 1), (3, 6), (5, 2), (6, 3)):
+            plan.set_config(leaf, chunk)
+            got = plan(x).cpu().numpy()
+            assert np.array_equal(got, ref), (direction, leaf, chunk)
+            got_adj = plan(x, adjoint=True).cpu().numpy()
+            plan.set_config(4, 4)
+            assert np.array_equal(got_adj, plan(x, adjoint=True).cpu().numpy()), (direction, leaf, chunk)
+
+
+def test_autotune_picks_and_caches_a_geometry(lc):
+    n = 500000
+    dev = torch.device("cuda", 0)
+    x = torch.as_tensor(workloads.decaying_vector(n, seed=14), device=dev)
+    plan = lc.Plan(n, "l2c", 1, "f64_df", dev)
+    leaf, chunk, ms = plan.autotune(x)
+    assert leaf in (3, 4, 5) and chunk in (3, 4, 6) and ms > 0
+    z = plan(x).cpu().numpy()
+    e2, _ = rel_errors(z[:2000], oracle.apply(oracle.L2C, x.cpu().numpy(), rows=np.arange(2000)))
+    assert e2 <= 1e-13
