@@ -383,6 +383,7 @@ def run_ours(args):
     available = ["f64", "f64_df"]  # the split tier is for batches (reported under "batched")
     tiers = {}
     tuned = {}
+    plan_ms = {}
     outs = (torch.empty_like(x), torch.empty_like(x))
     for t in available:
         try:
@@ -391,6 +392,16 @@ def run_ours(args):
             if e.status != 5:  # LC_ERR_UNSUPPORTED: tier not built for this request
                 raise
             continue
+        # plan build time (FP64 on the GPU, off the timed path; reported separately)
+        tp = []
+        for d in ("l2c", "c2l"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tmp = lc.Plan(n, d, 1, t, dev)
+            torch.cuda.synchronize()
+            tp.append((time.perf_counter() - t0) * 1e3)
+            del tmp
+        plan_ms[t] = {"l2c": tp[0], "c2l": tp[1]}
         # plan setup includes the autotuner's choice of chunk geometry (untimed, like planning)
         tuned[t] = [list(p.autotune(x, out=outs[0])[:2]) for p in tiers[t]]
 
@@ -518,6 +529,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 2 * 8 * n},
         "gpu_launches": launches,
         "tiers": tier_vals,
+        "plan_ms": plan_ms,
         "stage_ms_per_step": {KIND_NAMES[k]: v / args.steps for k, v in sorted(totals.items())},
         "roofline": roofline,
         "clocks": clk,

@@ -123,10 +123,33 @@ __global__ void k_plan_cos(double* __restrict__ cosm) {
   cosm[t] = cospi(double(k * (2 * m + 1)) / double(2 * LC_M));
 }
 
-// One CTA (M*M threads) per submatrix: sample the kernel, then the 2-D DCT-II.
+// Lambda((y - x)/2) at the M x M Chebyshev-Gauss points of a submatrix
+// depends only on its level and on the offset j0 - i0, which is 4h for
+// (p,q) = (0,0), (1,1) and 6h for (0,1) (eq:globalij): 2 M x M tables per
+// level, shared by every block of the level (Sec. 4.3 reuses Lambda^- the
+// same way).  Table [L][2][M][M].
+__global__ void k_plan_lminus(int L, int s, const double* __restrict__ cosm, double* __restrict__ tab) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(L) * 2 * LC_M * LC_M) return;
+  const int gamma = int(t / (2 * LC_M * LC_M));
+  const int c = int((t / (LC_M * LC_M)) % 2);
+  const int m = int((t / LC_M) % LC_M), n = int(t % LC_M);
+  const double h = double(int64_t(s) << (L - gamma - 1));
+  const double off = (c == 0 ? 4.0 : 6.0) * h;  // j0 - i0
+  // (y_n - x_m)/2 with x_m = i0 + h (X_m + 1), y_n = j0 + h (Y_n + 1)   (eq:Xfromx)
+  tab[t] = lc_Lambda(0.5 * (off + h * (cosm[LC_M + n] - cosm[LC_M + m])));
+}
+
+// One CTA (M*M threads) per submatrix: sample the kernel, then the 2-D DCT-II
+// of eq:aklmore.  Lambda((x+y)/2) is symmetric in (m, n) because X and Y use
+// the same nodes, so only m <= n is evaluated; the DCT matrix satisfies
+// cos(k(M-1-m+1/2)pi/M) = (-1)^k cos(k(m+1/2)pi/M), so each 18-term sum is
+// folded into 9 terms of sums or differences.
 __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __restrict__ cosm,
-                            double* __restrict__ Ahat) {
+                            const double* __restrict__ lminus, double* __restrict__ Ahat) {
+  constexpr int H = LC_M / 2;
   __shared__ double S[LC_M][LC_M];
+  __shared__ double F[2][H][LC_M];  // folded rows: sums (even k) and differences (odd k)
   __shared__ double Tm[LC_M][LC_M];
   __shared__ double cs[LC_M][LC_M];
   const int tid = threadIdx.x;
@@ -143,30 +166,49 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
     const double h = double(int64_t(s) << (L - gamma - 1));
     const double i0 = 2.0 * h * double(2 * b + p);
     const double j0 = 2.0 * h * double(2 * b + q + 2);
+    const double* lm = lminus + (size_t(gamma) * 2 + (r == 1 ? 1 : 0)) * (LC_M * LC_M);
     __syncthreads();
-    // sample at (x_m, y_n), x_m = i0 + h (X_m + 1), y_n = j0 + h (Y_n + 1)   (eq:Xfromx)
+    if (r0 <= c0) {  // Lambda((x_m + y_n)/2), symmetric in (m, n)
+      const double lp = lc_Lambda(0.5 * (i0 + j0 + h * (cs[1][r0] + cs[1][c0] + 2.0)));
+      S[r0][c0] = lp;
+      S[c0][r0] = lp;
+    }
+    __syncthreads();
     {
       const double x = i0 + h * (cs[1][r0] + 1.0);
       const double y = j0 + h * (cs[1][c0] + 1.0);
+      const double lmi = lm[tid];
       double val;
       if (dir == LC_L2C) {
-        val = lc_Lambda(0.5 * (y - x)) * lc_Lambda(0.5 * (y + x));
-      } else {
+        val = lmi * S[r0][c0];  // A(x, y) = Lambda((y-x)/2) Lambda((y+x)/2)
+      } else {                  // L(x, y) of eq:Lxymod
         const double pre = 2.0 * (x + 0.5) * y / ((x + y) * (x + y + 1.0) * (x - y + 1.0));
-        val = pre * lc_Lambda(0.5 * (y - x)) / lc_Lambda(0.5 * (x + y));
+        val = pre * lmi / S[r0][c0];
       }
+      __syncthreads();
       S[r0][c0] = val;
+    }
+    __syncthreads();
+    if (tid < 2 * H * LC_M) {  // fold the row variable
+      const int e = tid / (H * LC_M), mm = (tid / LC_M) % H, n = tid % LC_M;
+      const double u = S[mm][n], v = S[LC_M - 1 - mm][n];
+      F[e][mm][n] = e ? u - v : u + v;
     }
     __syncthreads();
     {  // DCT along the row variable: Tm[k][n] = sum_m cos(k(m+1/2)pi/M) S[m][n]
       double acc = 0.0;
-      for (int m = 0; m < LC_M; ++m) acc = fma(cs[r0][m], S[m][c0], acc);
+      const int e = r0 & 1;
+      for (int mm = 0; mm < H; ++mm) acc = fma(cs[r0][mm], F[e][mm][c0], acc);
       Tm[r0][c0] = acc;
     }
     __syncthreads();
-    {  // along the column variable, then the 4/(c_k c_l M^2) weight
+    {  // along the column variable (folded the same way), then 4/(c_k c_l M^2)
+      const int e = c0 & 1;
       double acc = 0.0;
-      for (int n = 0; n < LC_M; ++n) acc = fma(Tm[r0][n], cs[c0][n], acc);
+      for (int nn = 0; nn < H; ++nn) {
+        const double u = Tm[r0][nn], v = Tm[r0][LC_M - 1 - nn];
+        acc = fma(e ? u - v : u + v, cs[c0][nn], acc);
+      }
       const double w = 4.0 / (double(LC_M) * double(LC_M)) * (r0 == 0 ? 0.5 : 1.0) * (c0 == 0 ? 0.5 : 1.0);
       Ahat[a * (LC_M * LC_M) + tid] = acc * w;
     }
@@ -248,7 +290,8 @@ size_t layout(lc_plan_s* p, char* base) {
   p->err = c.take<int>(64);
   p->T = c.take<double>(size_t(2) * g.s * LC_M);
   p->B = c.take<double>(LC_M * LC_M);
-  p->Ahat = c.take<double>(size_t(g.nc) * LC_M * LC_M + LC_M * LC_M);  // + DCT matrix scratch
+  // + plan scratch: the DCT matrix and the per-level Lambda((y-x)/2) tables
+  p->Ahat = c.take<double>(size_t(g.nc) * LC_M * LC_M + LC_M * LC_M + size_t(2 * (g.L > 0 ? g.L : 1)) * LC_M * LC_M);
   p->W = p->Cc = nullptr;
   p->lamf = p->lam2f = p->Tf = p->Bf = p->Ahatf = p->Wf = p->Ccf = nullptr;
   if (p->dtype == LC_F64) {
@@ -378,10 +421,13 @@ lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
   LC_LAUNCH_CHECK();
   if (g.L > 0) {
     double* cosm = p->Ahat + size_t(g.nc) * LC_M * LC_M;
+    double* lminus = cosm + LC_M * LC_M;
     k_plan_cos<<<2, 256, 0, st>>>(cosm);
     LC_LAUNCH_CHECK();
+    k_plan_lminus<<<unsigned((int64_t(g.L) * 2 * LC_M * LC_M + 255) / 256), 256, 0, st>>>(g.L, g.s, cosm, lminus);
+    LC_LAUNCH_CHECK();
     const int64_t blocks = g.nc < 1048576 ? g.nc : 1048576;
-    k_plan_ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, p->Ahat);
+    k_plan_ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat);
     LC_LAUNCH_CHECK();
   }
   if (p->dtype == LC_F32) {
