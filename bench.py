@@ -48,6 +48,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2
 # instructions (TwoProd with fma, cross terms, TwoSum accumulation); the FP32
 # issue limit is 152 SMs x 128 lanes x 2070 MHz.
 DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
+try:  # measured copy bandwidth of the GB300s
+    HBM_PEAK_GBS = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+except Exception:
+    HBM_PEAK_GBS = 6800.0  # fallback figure for a GB300
 # DRAM bytes per launch of the dominant kernel (the last down chunk: Steps 4-7
 # of the fine levels), dram__bytes_read.sum + dram__bytes_write.sum from the
 # ncu captures summarised in profiles/df_single_n1e6.md and
@@ -201,15 +205,15 @@ def near_field_nonzeros(n, L, s):
     return int(((end - i + 1) // 2).sum())
 
 
-def kernel_work(info, kind, direction):
+def kernel_work(info, kind, direction, leaf_depth=4):
     """Algorithmic FP64 flops of one launch of a kernel kind (paper's counting, Sec. 4.2)."""
     n, L, s, M, nc, N = info["n"], info["L"], info["s"], info["M"], info["n_c"], info["N"]
     if kind == 4:
-        # last down chunk: Step 4 on the fine levels [max(0, L-5), L) (a triangular
+        # last down chunk: Step 4 on the fine levels [max(0, L-1-leaf_depth), L) (a triangular
         # M x M product, M(M+1) flops per node and parity), then the spread
         # (2M per row with a far field), the near field (3 flops per band
         # nonzero, mu = 4.5) and the scaling (1 per row)
-        rho = max(0, L - 1 - 4)
+        rho = max(0, L - 1 - leaf_depth)
         nodes = 0
         for g in range(rho, L):
             nodes += ((4 << g) - 4) if g > 0 else 0
@@ -249,6 +253,53 @@ def time_fn(fn, flush, steps, warmup):
     return statistics.median(a.elapsed_time(b) for a, b in evs)
 
 
+def split_tensor_fractions(lc, dev, X, Z, n, B):
+    """Executed bf16 tensor work of each split-tier kernel kind (mma.m16n8k16 counts
+    from the plan geometry, padding included) over its CUDA-event duration."""
+    plan = lc.Plan(n, "l2c", B, "f64_split", dev)
+    info = plan.info
+    L, s = info["L"], info["s"]
+    S = 6
+    pairs = S * (S + 1) // 2
+    tiles = -(-B // 64)
+    mma = 16 * 8 * 16 * 2
+    per_cta = lambda kt, nt: 4 * pairs * kt * nt  # 4 warps of 16 rows, every slice pair
+    ktiles = lambda K: max(32, -(-K // 16) * 16) // 16  # K padded to 16, at least 32
+    M = info["M"]
+    ctas = {  # tiles of 64 rows x 2 directions sigma, per work item of each launch kind
+        0: ((2 << L) - 2) * tiles * 2,
+        1: sum((1 << (L - d)) - 2 for d in range(L - 1)) * tiles * 2,
+        2: sum((2 << (L - d)) - 2 for d in range(L)) * tiles * 2,
+        3: sum((2 << (L - d)) - 4 for d in range(L - 1)) * tiles * 2,
+        4: (2 << L) * tiles * 2,  # strips of width 2s
+    }
+    kt_nt = {0: per_cta(ktiles(s), 3), 1: per_cta(ktiles(2 * M), 3), 2: per_cta(ktiles(2 * M), 3),
+             3: per_cta(ktiles(M), 3), 4: per_cta(ktiles(2 * s), 4) + per_cta(ktiles(M), 4)}
+    lc.binding.lc_plan_set_timing(plan._handle, 3)
+    for _ in range(3):
+        plan(X, out=Z)
+    import torch
+    torch.cuda.synchronize()
+    tot = {}
+    for slot in range(3):
+        for kind, t in lc.binding.lc_plan_get_timing(plan._handle, slot):
+            tot[kind] = tot.get(kind, 0.0) + t / 3
+    lc.binding.lc_plan_set_timing(plan._handle, 0)
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
+    out = {}
+    for kind, c in ctas.items():
+        if kind in tot and tot[kind] > 0:
+            fl = c * kt_nt[kind] * mma
+            ach = fl / (tot[kind] / 1e3) / 1e12
+            out[KIND_NAMES[kind]] = {"bound": "tensor", "executed_tflop": fl / 1e12, "ms": tot[kind],
+                                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak}
+    del plan
+    return out
+
+
 def batched_leg(lc, dev, flush, args):
     """Batched workloads sharing one plan: split-precision tensor-core tier
     (one CUDA graph replay per step) against the plain FP64 tier."""
@@ -277,6 +328,7 @@ def batched_leg(lc, dev, flush, args):
         d = (outs_b[t] - ref).double()
         res[t + "_vs_f64_E2"] = float(torch.linalg.norm(d) / torch.linalg.norm(ref))
     res["speedup_split_over_f64_batched"] = res["f64_split"]["coefficients_per_s"] / res["f64"]["coefficients_per_s"]
+    res["f64_split_tensor_per_kernel"] = split_tensor_fractions(lc, dev, X, Z, n, B)
     out["uniform_65536x256_l2c"] = res
     del X, Z
     # (b) ragged batch: 4096 transforms, n log-uniform in [64, 65536]
@@ -501,7 +553,7 @@ def run_ours(args):
         if dom in stages[d]:
             per_launch_ms.extend(stages[d][dom])
     avg_ms = sum(per_launch_ms) / len(per_launch_ms)
-    flops = kernel_work(info, dom, 0)
+    flops = kernel_work(info, dom, 0, (tuned.get(chosen) or [[4, 4]])[0][0])
     roofline = None
     if flops is not None and chosen in ("f64", "f64_df"):
         achieved = flops / (avg_ms / 1e3) / 1e12
@@ -514,6 +566,37 @@ def run_ours(args):
                     "frac": achieved / peak, "traffic": TRAFFIC.get((chosen, dom)),
                     "kernel": KIND_NAMES[dom], "avg_launch_ms": avg_ms, "flops_per_launch": flops,
                     "peak_note": note}
+    # Every kernel kind: achieved rate against its own bound.  Coupling: HBM
+    # (A-hat plus the w and c rows it reads and writes); the others: the ALU
+    # peak of the tier, with the paper's flop counts (Sec. 4.2).
+    M, s_, L_, N_, nc_ = info["M"], info["s"], info["L"], info["N"], info["n_c"]
+    ld = (tuned.get(chosen) or [[4, 4]])[0][0]
+    r0 = max(0, L_ - 1 - ld)
+    elem = 8  # FP64 and double-float both store 8 bytes per value
+    nseg_rows = sum((4 << g) - 2 for g in range(L_))
+    kinds_work = {
+        0: ("alu", 2 * 2 * M * s_ * ((2 << L_) - 2) + 2 * M * (M + 1) * sum((4 << g) - 4 for g in range(r0, L_ - 1))),
+        1: ("alu", 2 * M * (M + 1) * sum((4 << g) - 4 for g in range(0, r0))),
+        2: ("hbm", nc_ * M * M * elem + 2 * nseg_rows * 2 * M * elem),
+        3: ("alu", 2 * M * (M + 1) * sum((4 << g) - 4 for g in range(1, max(1, r0)))),
+        4: ("alu", kernel_work(info, 4, 0, ld)),
+    }
+    per_kernel = {}
+    alu_peak = FP64_PEAK_TFLOPS if chosen == "f64" else DF_PEAK_TFLOPS
+    for kind, (bound, work) in kinds_work.items():
+        if kind not in totals:
+            continue
+        t_s = totals[kind] / args.steps / 2 / 1e3   # seconds per direction
+        if t_s <= 0:
+            continue
+        if bound == "hbm":
+            ach = work / t_s / 1e9
+            per_kernel[KIND_NAMES[kind]] = {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                            "frac": ach / HBM_PEAK_GBS, "ms_per_direction": t_s * 1e3}
+        else:
+            ach = work / t_s / 1e12
+            per_kernel[KIND_NAMES[kind]] = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                                            "frac": ach / alu_peak, "ms_per_direction": t_s * 1e3}
     launches = sum(p.launches() for p in pl) * args.steps
 
     line = {
@@ -532,6 +615,7 @@ def run_ours(args):
         "plan_ms": plan_ms,
         "stage_ms_per_step": {KIND_NAMES[k]: v / args.steps for k, v in sorted(totals.items())},
         "roofline": roofline,
+        "roofline_per_kernel": per_kernel,
         "clocks": clk,
         "wall_s_timed": wall,
     }
