@@ -56,9 +56,9 @@ except Exception:
 # of the fine levels), dram__bytes_read.sum + dram__bytes_write.sum from the
 # ncu captures summarised in profiles/df_single_n1e6.md and
 # profiles/f64_single_n1e6.md (one L2C launch at n = 1e6).
-TRAFFIC = {("f64_df", 4): 25.342e6, ("f64", 4): 25.350e6}
-KIND_NAMES = {0: "leaf_restrict", 1: "upward", 2: "couple", 3: "downward", 4: "spread_near_scale", 5: "prepare",
-              6: "other"}
+TRAFFIC = {}
+KIND_NAMES = {0: "leaf_restrict", 1: "upward", 2: "couple", 3: "downward", 4: "spread_sum_scale", 5: "prepare",
+              6: "other", 7: "near_band"}
 
 
 def parse():
@@ -208,17 +208,19 @@ def near_field_nonzeros(n, L, s):
 def kernel_work(info, kind, direction, leaf_depth=4):
     """Algorithmic FP64 flops of one launch of a kernel kind (paper's counting, Sec. 4.2)."""
     n, L, s, M, nc, N = info["n"], info["L"], info["s"], info["M"], info["n_c"], info["N"]
+    if kind == 7:
+        # near-field band: 3 flops per band nonzero (mu = 4.5), scaling 1 per row
+        return 3 * near_field_nonzeros(n, L, s) + n
     if kind == 4:
         # last down chunk: Step 4 on the fine levels [max(0, L-1-leaf_depth), L) (a triangular
         # M x M product, M(M+1) flops per node and parity), then the spread
-        # (2M per row with a far field), the near field (3 flops per band
-        # nonzero, mu = 4.5) and the scaling (1 per row)
+        # (2M per row with a far field) and the sum with the band's part (1 per row)
         rho = max(0, L - 1 - leaf_depth)
         nodes = 0
         for g in range(rho, L):
             nodes += ((4 << g) - 4) if g > 0 else 0
         rows_far = min(n, N - 4 * s) if L > 0 else 0
-        return 2 * M * (M + 1) * nodes + 2 * M * rows_far + 3 * near_field_nonzeros(n, L, s) + n
+        return 2 * M * (M + 1) * nodes + 2 * M * rows_far + n
     if kind == 2:  # couple: 2 M^2 per submatrix per parity
         return 4 * M * M * nc
     if kind == 0:  # leaf: 2 M s per segment per parity
@@ -294,7 +296,7 @@ def split_tensor_fractions(lc, dev, X, Z, n, B):
         if kind in tot and tot[kind] > 0:
             fl = c * kt_nt[kind] * mma
             ach = fl / (tot[kind] / 1e3) / 1e12
-            out[KIND_NAMES[kind]] = {"bound": "tensor", "executed_tflop": fl / 1e12, "ms": tot[kind],
+            out["spread_near_scale" if kind == 4 else KIND_NAMES[kind]] = {"bound": "tensor", "executed_tflop": fl / 1e12, "ms": tot[kind],
                                      "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak}
     del plan
     return out
@@ -580,6 +582,7 @@ def run_ours(args):
         2: ("hbm", nc_ * M * M * elem + 2 * nseg_rows * 2 * M * elem),
         3: ("alu", 2 * M * (M + 1) * sum((4 << g) - 4 for g in range(1, max(1, r0)))),
         4: ("alu", kernel_work(info, 4, 0, ld)),
+        7: ("alu", kernel_work(info, 7, 0, ld)),
     }
     per_kernel = {}
     alu_peak = FP64_PEAK_TFLOPS if chosen == "f64" else DF_PEAK_TFLOPS

@@ -221,8 +221,11 @@ lc_status lc_plan_set_timing(lc_plan plan, int32_t slots);
 /* Kernel durations (ms) of the execution recorded in `slot`; waits for its
  * events.  kinds[i] names kernel i: 0 leaf restriction (Step 1),
  * 1 upward pass (Step 2), 2 coupling (Step 3), 3 downward pass (Step 4),
- * 4 leaf spread + near field + scaling (Steps 5-7), 5 input preparation,
- * 6 other.  ms and kinds may be NULL; *count receives the kernel count. */
+ * 4 leaf spread (Step 5) + far/near sum + scaling, 5 input preparation,
+ * 6 other, 7 near-field band (Steps 6-7; with the split tier, kind 4 also
+ * covers the band).  ms and kinds may be NULL; *count receives the kernel
+ * count.  With timing on, the kernels run one after another on the
+ * caller's stream; without it they overlap on the plan's streams. */
 lc_status lc_plan_get_timing(lc_plan plan, int32_t slot, float* ms, int32_t* kinds, int32_t capacity,
                              int32_t* count);
 

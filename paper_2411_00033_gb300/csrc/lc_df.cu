@@ -53,8 +53,6 @@ template <>
 __device__ __forceinline__ lc_df finish<lc_df>(const lc_df& acc) {
   return lc_df_fast2(acc.hi, acc.lo);
 }
-template <>
-struct split_chains<lc_df> { static constexpr bool value = false; };
 }  // namespace lc_exec
 
 using namespace lc_exec;

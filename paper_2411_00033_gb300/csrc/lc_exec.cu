@@ -6,7 +6,9 @@
 using namespace lc_exec;
 
 
-int lc_exec_cuda_cores_launches(const lc_plan_s* p) { return launches_for<double>(p->g.L, p->leaf_depth, p->chunk_depth); }
+int lc_exec_cuda_cores_launches(const lc_plan_s* p) {
+  return launches_for<double>(p->g.L, p->leaf_depth, p->chunk_depth, p->batch);
+}
 
 lc_status lc_exec_cuda_cores(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob,
                              int64_t oe, cudaStream_t st, int adjoint) {

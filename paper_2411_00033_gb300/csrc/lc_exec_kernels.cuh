@@ -67,6 +67,12 @@ __device__ __forceinline__ R cinv(int64_t i) {
 }
 template <typename R>
 __device__ __forceinline__ R negate(const R& v) { return -v; }
+// Step 4 with one pass per parent for both children (halves the multiplies,
+// halves the parallelism): worth it where the arithmetic pipe binds (FP64).
+template <typename R>
+struct eo_pairs { static constexpr bool value = false; };
+template <>
+struct eo_pairs<double> { static constexpr bool value = true; };
 
 // Dot-product accumulation.  Generic: fused multiply-add in R.  The
 // double-float tier specialises these to keep an unnormalised error word and
@@ -77,11 +83,6 @@ template <typename R>
 __device__ __forceinline__ R acc3(const R& acc, const R& a, const R& b, const R& c) { return fma(a * b, c, acc); }
 template <typename R>
 __device__ __forceinline__ R finish(const R& acc) { return acc; }
-// Whether splitting a short sum into two independent chains pays off: it
-// does for the hardware types (latency of dependent FMAs), not for the
-// double-float type, whose extra normalisations cost more than they hide.
-template <typename R>
-struct split_chains { static constexpr bool value = true; };
 // A-hat(m)[k][l]: the FP64 table keeps row-major [k][l]; the FP32 and
 // double-float copies are stored transposed, [l][k], so that threads that
 // own consecutive k read consecutive addresses.
@@ -99,6 +100,7 @@ constexpr int kThreads = 256;
 // leaf depth = levels climbed by the first up chunk / descended by the last
 // down chunk, chunk depth = levels per coarse chunk.
 constexpr int kSeg = 2 * LC_M;  // values per segment: [sigma][k]
+constexpr int kPadS = 2;        // spare elements per 2s block of the band-sum tiles (even s)
 
 // Node x at level gamma of the column tree (segments g >= 2) or of the row
 // tree (segments v < 2 b_gamma).
@@ -109,6 +111,29 @@ __device__ __forceinline__ bool node_valid(bool col, int gamma, int64_t x) {
 
 // Offsets (in R elements) of level d inside a subtree buffer.
 __device__ __forceinline__ int sub_off(int d) { return ((1 << d) - 1) * kSeg; }
+
+// Tile staging: n elements, element i read by ld(i) and written by st(i, v).
+// Each thread issues up to U reads before its first write, so a tile costs
+// one memory round trip per U elements a thread copies rather than one per
+// element.  U > 1 pays in latency-bound launches of few CTAs (one vector);
+// in launches that fill the GPU many times over (batches) the registers it
+// holds cost more than it saves.
+template <int U = 1, typename Ld, typename St>
+__device__ __forceinline__ void stage(int n, Ld ld, St st) {
+  for (int b0 = threadIdx.x; b0 < n; b0 += U * int(blockDim.x)) {
+    decltype(ld(0)) v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = b0 + u * int(blockDim.x);
+      if (i < n) v[u] = ld(i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = b0 + u * int(blockDim.x);
+      if (i < n) st(i, v[u]);
+    }
+  }
+}
 
 // ---------------------------------------------------------------- up chunk
 // Root x0 = blockIdx.x at level rho; bottom level rho + depth.  leaf != 0:
@@ -309,27 +334,351 @@ inline size_t up_smem(int depth, int s, int leaf) {
   return v * sizeof(R) + 16;
 }
 template <typename R>
-inline size_t down_smem(int depth, int s, int fin, int64_t nrows_direct) {
+inline size_t down_smem(int depth, int s, int fin) {
   size_t v = size_t((2 << depth) - 1) * kSeg;
-  if (fin) {
-    const size_t rows = nrows_direct > 0 ? size_t(nrows_direct) : (size_t(1) << depth) * 2 * s;
-    v += size_t(2) * s * LC_M;             // T
-    v += rows + 4 * size_t(s) + 8;         // operand tile
-    v += 2 * size_t(s) + 8;                // lambda_k
-    v += rows + 2 * size_t(s) + 8;         // lambda_(i+k)
-    if (nrows_direct > 0) v += 2 * rows;   // direct-only plans: full triangle tables
-  }
+  if (fin) v += size_t(2) * s * LC_M;  // T
   return v * sizeof(R) + 16;
+}
+constexpr int kNearStrips = 16;  // strips of 2s rows per CTA of k_near
+// rows: rows of the tile (a multiple of 2s), or, direct != 0, n of a
+// direct-only plan (the whole triangle).
+template <typename R>
+inline size_t near_smem(int s, int64_t nrows, int direct) {
+  const int64_t nrows_direct = direct ? nrows : 0;
+  const size_t rows = size_t(nrows);
+  const size_t pad = (direct || (s & 1)) ? 0 : kPadS;
+  const size_t blocks = rows / (2 * size_t(s)) + 4;
+  size_t v = rows + 4 * size_t(s) + 8 + pad * blocks;               // operand tile
+  v += 2 * size_t(s) + 8;                                            // lambda_k
+  v += (pad ? 2 : 1) * (rows + 2 * size_t(s) + 16 + pad * blocks);  // lambda_(i+k), per parity if padded
+  if (nrows_direct > 0) v += 2 * rows;                               // direct-only plans: whole triangle
+  return v * sizeof(R) + 16;
+}
+
+// ------------------------------------------------- near-field band sums
+// Shared tiles of the band sums for even s: kPadS spare elements after every
+// block of 2s; pad_index maps an offset x >= 0 from the block origin.
+__device__ __forceinline__ int pad_index(int64_t x, int64_t two_s, int pad) {
+  return int(x + (pad ? pad * (x / two_s) : 0));
+}
+// Forward rows i and i + 2 of one parity: row i + 2r takes, at step k, the
+// entry factors lamk[k] and lm[2r + k] (lambda_k, lambda_(i+2r+k), or u, v
+// for C2L) and the operand fo[2(r + k)].  Row i has cnt >= 1 terms, row i + 2
+// one fewer.  fwd_steps runs steps [k, kend) two at a time with the operand
+// and lambda tiles fp, lp; the values of row i + 2 at step k are those of row
+// i at steps k + 1 and k + 2, kept in registers (f0, l0, l1) from step to step.
+template <typename R>
+__device__ __forceinline__ void fwd_steps(const R* __restrict__ lamk, const R* __restrict__ fp,
+                                          const R* __restrict__ lp, int& k, int kend, R& a0, R& a1, R& f0,
+                                          R& l0, R& l1) {
+  int kk = k;
+  R A0 = a0, A1 = a1, F0 = f0, L0 = l0, L1 = l1;
+  const R* pk = lamk + kk;
+  const R* pf = fp + 2 * kk;
+  const R* pl = lp + kk;
+#pragma unroll 1
+  for (; kk + 2 <= kend; kk += 2, pk += 2, pf += 4, pl += 2) {
+    const R k0 = pk[0], k1 = pk[1];
+    const R F1 = pf[2], F2 = pf[4];
+    const R L2 = pl[2], L3 = pl[3];
+    A0 = acc3(A0, k0, L0, F0);
+    A1 = acc3(A1, k0, L2, F1);
+    A0 = acc3(A0, k1, L1, F1);
+    A1 = acc3(A1, k1, L3, F2);
+    F0 = F2;
+    L0 = L2;
+    L1 = L3;
+  }
+  if (kk < kend) {
+    const R k0 = lamk[kk];
+    const R F1 = fp[2 * kk + 2];
+    const R L2 = lp[kk + 2];
+    A0 = acc3(A0, k0, L0, F0);
+    A1 = acc3(A1, k0, L2, F1);
+    F0 = F1;
+    L0 = L1;
+    L1 = L2;
+    ++kk;
+  }
+  k = kk;
+  a0 = A0;
+  a1 = A1;
+  f0 = F0;
+  l0 = L0;
+  l1 = L1;
+}
+// With padded tiles (pad != 0) the operand reads cross into the next block
+// from step kF on and the lambda reads from step kL on (kF <= kL).
+template <typename R>
+__device__ __forceinline__ void near_fwd2(const R* __restrict__ lamk, const R* __restrict__ lm,
+                                          const R* __restrict__ fo, int cnt, int kF, int kL, int pad, R& n0,
+                                          R& n1) {
+  R a0 = R(0), a1 = R(0);
+  R f0 = fo[0], l0 = lm[0], l1 = lm[1];
+  const int last = cnt - 1;
+  int k = 0;
+  if (pad == 0) {
+    fwd_steps(lamk, fo, lm, k, last, a0, a1, f0, l0, l1);
+  } else {
+    fwd_steps(lamk, fo, lm, k, kF < last ? kF : last, a0, a1, f0, l0, l1);
+    fwd_steps(lamk, fo + pad, lm, k, kL < last ? kL : last, a0, a1, f0, l0, l1);
+    fwd_steps(lamk, fo + pad, lm + pad, k, last, a0, a1, f0, l0, l1);
+  }
+  a0 = acc3(a0, lamk[k], l0, f0);  // last term of row i
+  n0 = finish(a0);
+  n1 = finish(a1);
+}
+// Transposed: columns i and i + 2 of one parity; column i sums rows i - 2k for
+// k < cnt, column i + 2 rows i + 2 - 2k for k <= cnt (same first row).  has1
+// is false when column i + 2 lies outside the staged operand range.
+template <typename R>
+__device__ __forceinline__ void adj_steps(const R* __restrict__ lamk, const R* __restrict__ rp,
+                                          const R* __restrict__ lp, int& k, int kend, R& a0, R& a1, R& g1,
+                                          R& l1, R& l2) {
+  int kk = k;
+  R A0 = a0, A1 = a1, G1 = g1, L1 = l1, L2 = l2;
+  const R* pk = lamk + kk;
+  const R* pg = rp - 2 * kk;
+  const R* pl = lp - kk;
+#pragma unroll 1
+  for (; kk + 2 <= kend; kk += 2, pk += 2, pg -= 4, pl -= 2) {
+    const R k0 = pk[0], k1 = pk[1];
+    const R G0 = pg[0], Gm = pg[-2];
+    const R L0 = pl[0], Lm = pl[-1];
+    A0 = acc3(A0, k0, L0, G0);
+    A1 = acc3(A1, k0, L2, G1);
+    A0 = acc3(A0, k1, Lm, Gm);
+    A1 = acc3(A1, k1, L1, G0);
+    G1 = Gm;
+    L2 = L0;
+    L1 = Lm;
+  }
+  if (kk < kend) {
+    const R k0 = lamk[kk];
+    const R G0 = rp[-2 * kk];
+    const R L0 = lp[-kk];
+    A0 = acc3(A0, k0, L0, G0);
+    A1 = acc3(A1, k0, L2, G1);
+    G1 = G0;
+    L2 = L1;
+    L1 = L0;
+    ++kk;
+  }
+  k = kk;
+  a0 = A0;
+  a1 = A1;
+  g1 = G1;
+  l1 = L1;
+  l2 = L2;
+}
+// Padded tiles: operand reads drop into the previous block from step kF on,
+// lambda reads from step kL on.
+template <typename R>
+__device__ __forceinline__ void near_adj2(const R* __restrict__ lamk, const R* __restrict__ lm,
+                                          const R* __restrict__ ro, int cnt, bool has1, int kF, int kL, int pad,
+                                          R& n0, R& n1) {
+  R a0 = R(0), a1 = R(0);
+  R g1 = has1 ? ro[2] : R(0), l1 = lm[1], l2 = lm[2];
+  int k = 0;
+  if (pad == 0) {
+    adj_steps(lamk, ro, lm, k, cnt, a0, a1, g1, l1, l2);
+  } else {
+    adj_steps(lamk, ro, lm, k, kF < cnt ? kF : cnt, a0, a1, g1, l1, l2);
+    adj_steps(lamk, ro - pad, lm, k, kL < cnt ? kL : cnt, a0, a1, g1, l1, l2);
+    adj_steps(lamk, ro - pad, lm - pad, k, cnt, a0, a1, g1, l1, l2);
+  }
+  a1 = acc3(a1, lamk[k], l2, g1);  // first row of the band, column i + 2 only
+  n0 = finish(a0);
+  n1 = finish(a1);
+}
+
+// ----------------------------------------------------------- near field
+// Steps 6 and 7 for the band (eq:hik, eq:Lxymod): CTA x takes the rows
+// (forward) or columns (transposed) of kNearStrips strips of 2s and writes
+// the near-field part of the output, scaled as the output is (C^{-1} for
+// L2C; the (2i+1) and j factors of the C2L entries).  The far-field part is
+// added by the last down chunk.  The band needs only the input and lambda,
+// so this kernel runs beside the far-field chain.  L == 0 (direct-only plan):
+// one CTA, the whole triangle, which is then the complete result.
+// The band for the rows (forward) or columns (transposed) [lo, hi) of batch
+// member b, its tiles at `tile` in shared memory (near_smem bytes).  add == 0:
+// the output receives the band's part; add != 0: it already holds the
+// far-field part of these rows, written by this CTA before a barrier, and the
+// band's part is added.
+template <typename R>
+__device__ __forceinline__ void near_tile(const Args<R>& a, int64_t b, int64_t lo, int64_t hi, int adj,
+                                          unsigned char* tile, int add) {
+  const int s = a.s, L = a.L;
+  const int64_t two_s = 2 * int64_t(s);
+  const bool l2c = (a.dir == LC_L2C);
+  auto put = [&](int64_t i, const R& v) {
+    typename lc_io<R>::type* o = a.out + b * a.ob + i * a.oe;
+    lc_st<R>(o, add ? lc_ld<R>(o) + v : v);
+  };
+  const typename lc_io<R>::type* f = a.in + b * a.ib;
+  R* opnd = reinterpret_cast<R*>(tile);  // operand tile (input values, pre-scaled)
+  int64_t olo, ohi;             // operand index range
+  if (!adj) {
+    olo = lo;
+    ohi = (L > 0) ? hi + 2 * two_s : a.n;
+  } else {
+    olo = (L > 0) ? (lo - two_s > 0 ? lo - two_s : 0) : 0;
+    ohi = hi;
+  }
+  if (ohi > a.n) ohi = a.n;
+  const int64_t olen = ohi - olo;
+  // Even s: the operand and lambda_m tiles keep kPadS spare elements after
+  // every 2s-element block (blocks aligned to strips), so that threads
+  // reading 2s apart hit distinct banks; lambda_m is then kept twice, its
+  // blocks aligned to the rows of each parity.
+  const int pad = (L > 0 && !(s & 1)) ? kPadS : 0;
+  const int64_t pbase = adj ? lo - two_s : lo;  // operand block origin
+  const int64_t lbase = lo - two_s;             // lambda_m block origin (+ sigma)
+  const int ooff = pad_index(olo - pbase, two_s, pad);
+  const int64_t olen_p = olen + (pad ? pad * (olen / two_s + 2) : 0);
+  R* lamk = opnd + olen_p + 8;     // lambda_k (L2C) / u_k (C2L), k < kmax + 2
+  const int64_t kmax = (L > 0) ? two_s : (a.n + 1) / 2;
+  R* lamm = lamk + kmax + 8;       // lambda_m / v_m for m in [mlo, mhi + 2)
+  const int64_t mlo = adj ? (olo + lo) / 2 : lo;
+  const int64_t mhi = adj ? hi : (hi + ohi) / 2 + 1;
+  const int64_t mcap = mhi < a.N ? mhi : a.N;
+  const int64_t mlen = mhi + 2 - mlo;
+  R* lamm1 = lamm + mlen + (pad ? pad * (mlen / two_s + 2) : 0) + 8;  // parity-1 copy (pad != 0)
+  const int moff0 = pad_index(mlo - lbase, two_s, pad);
+  const int moff1 = pad ? pad_index(mlo - lbase - 1, two_s, pad) : 0;
+  typedef typename lc_io<R>::type IO;
+  stage<4>(
+      int(olen), [&](int i) { return f[(olo + i) * a.ie]; },
+      [&](int i, IO x) {
+        const int64_t q = olo + i;
+        R v = lc_ld<R>(&x);
+        if (!adj) {
+          if (a.dir == LC_C2L) v = R(q) * v;  // L(i, j) = (2i+1) j u v: scale column j
+        } else {
+          v = (a.dir == LC_L2C) ? cinv<R>(q) * v : R(2 * q + 1) * v;  // C^{-1} r or (2i+1) r
+        }
+        opnd[pad_index(q - pbase, two_s, pad) - ooff] = v;
+      });
+  stage<4>(int(kmax + 2), [&](int k) { return k < a.N ? a.t.lam[k] : R(0); }, [&](int k, R v) { lamk[k] = v; });
+  stage<4>(
+      int(mlen), [&](int j) { return mlo + j < mcap ? a.t.lam2[mlo + j] : R(0); },
+      [&](int j, R v) {
+        const int64_t m = mlo + j;
+        lamm[pad_index(m - lbase, two_s, pad) - moff0] = v;
+        if (pad) lamm1[pad_index(m - lbase - 1, two_s, pad) - moff1] = v;
+      });
+  __syncthreads();
+  if (L == 0) {
+    // Direct-only plan: every row (column) by itself, the whole triangle.
+    for (int64_t i = threadIdx.x; i < hi; i += blockDim.x) {
+      R near = R(0);
+      if (!adj) {
+        const int cnt = int((a.n - i + 1) >> 1);
+        const R* fo = opnd + (i - olo);
+        const R* lm = lamm + (i - mlo);
+        for (int kk = 0; kk < cnt; ++kk) near = acc3(near, lamk[kk], lm[kk], fo[2 * kk]);
+        near = finish(near);
+        if (l2c) {
+          near = cinv<R>(i) * near;
+        } else {
+          near = R(2 * i + 1) * near;
+          if (i == 0) near += lc_ld<R>(f);
+        }
+      } else {
+        const int cnt = int(i / 2 + 1);
+        const R* ro = opnd + (i - olo);
+        const R* lm = lamm + (i - mlo);
+        for (int k = 0; k < cnt; ++k) near = acc3(near, lamk[k], lm[-k], ro[-2 * k]);
+        near = finish(near);
+        if (!l2c) {
+          near = R(i) * near;
+          if (i == 0) near += lc_ld<R>(f);
+        }
+      }
+      put(i, near);
+    }
+    return;
+  }
+  // Work item: rows (forward) or columns (transposed) m0 = 2g and m0 + 1 of
+  // parity sigma in one 2s-row strip, i.e. i and i + 2, summed together by
+  // near_fwd2 / near_adj2; then the mirrored pair g' = ng - 1 - g, so that
+  // every item has about 3s band terms per row (when that still leaves an item
+  // for every thread; otherwise one pair of rows per item).  Consecutive threads take
+  // consecutive (strip, parity) with the same g: their band lengths agree,
+  // and their shared-memory reads, 2s apart, fall into distinct banks when
+  // s is odd.
+  const int ng = (s + 1) >> 1, npair = (ng + 1) >> 1;
+  const int nstrips = int((hi - lo + two_s - 1) / two_s);
+  const bool mirror = nstrips * 2 * npair >= int(blockDim.x);
+  const int items = nstrips * 2 * (mirror ? npair : ng);
+  for (int u = threadIdx.x; u < items; u += blockDim.x) {
+    const int sigma = u & 1;
+    const int t = (u >> 1) % nstrips;
+    const int pr = (u >> 1) / nstrips;
+    for (int rep = 0; rep < 2; ++rep) {
+      const int g = rep ? ng - 1 - pr : pr;
+      if (rep && (g == pr || !mirror)) break;
+      const int m0 = 2 * g;
+      const int64_t i = lo + t * two_s + 2 * m0 + sigma;
+      if (i >= hi) continue;
+      const bool has1 = (m0 + 1 < s) && (i + 2 < hi);  // second row/column i + 2 in this strip
+      const int64_t v = i / two_s;
+      const R* op = opnd + (pad_index(i - pbase, two_s, pad) - ooff);
+      const R* lm = sigma && pad ? lamm1 + (pad_index(i - lbase - 1, two_s, pad) - moff1)
+                                 : lamm + (pad_index(i - lbase, two_s, pad) - moff0);
+      R n0, n1;
+      if (!adj) {
+        const int64_t e2 = two_s * (v + 2);
+        const int64_t end = e2 < a.n ? e2 : a.n;
+        near_fwd2(lamk, lm, op, int((end - i + 1) >> 1), s - m0 - 1, 2 * s - 2 * m0 - 2, pad, n0, n1);
+        if (l2c) {
+          n0 = cinv<R>(i) * n0;
+          n1 = cinv<R>(i + 2) * n1;
+        } else {
+          // (2i+1) u_k v_(i+k) (j f_j) summed; entry (0,0) = 1 adds f_0 (eq:Lxymod)
+          n0 = R(2 * i + 1) * n0;
+          n1 = R(2 * i + 5) * n1;
+          if (i == 0) n0 += lc_ld<R>(f);
+        }
+      } else {
+        int64_t st = two_s * (v - 1) > 0 ? two_s * (v - 1) : 0;
+        if ((st & 1) != (i & 1)) ++st;
+        near_adj2(lamk, lm, op, int((i - st) / 2 + 1), has1, m0 + 1, 2 * m0 + 1, pad, n0, n1);
+        if (!l2c) {
+          n0 = R(i) * n0;
+          n1 = R(i + 2) * n1;
+          if (i == 0) n0 += lc_ld<R>(f);
+        }
+      }
+      put(i, n0);
+      if (has1) put(i + 2, n1);
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 4) k_near(Args<R> a, int adj) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t two_s = 2 * int64_t(a.s);
+  for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
+    const int64_t lo = (a.L > 0) ? int64_t(blockIdx.x) * kNearStrips * two_s : 0;
+    const int64_t hi_raw = (a.L > 0) ? lo + kNearStrips * two_s : a.n;
+    const int64_t hi = hi_raw < a.n ? hi_raw : a.n;
+    if (lo >= hi) continue;
+    __syncthreads();  // shared tiles of the previous batch member are free
+    near_tile(a, b, lo, hi, adj, smem_raw, 0);
+  }
 }
 
 // -------------------------------------------------------------- down chunk
 // Root x0 = blockIdx.x at level rho; levels rho .. rho + depth, each node:
 //   c(gamma, x) = couple(gamma, x) + [parent valid] B(x mod 2)^T c(gamma-1, x/2).
-// fin != 0: the bottom level is the leaf level; finish with Steps 5-7 for the
-// rows (forward) or columns (transposed) of the subtree.  L == 0: direct-only
-// plan, one CTA computes the whole triangle.
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_down_chunk(Args<R> a, int rho, int depth, int fin, int adj) {
+// fin != 0: the bottom level is the leaf level; finish with Step 5 for the
+// rows (forward) or columns (transposed) of the subtree and add the
+// near-field part that k_near has written to the output (Steps 6-7), or,
+// with fuse (batched plans), compute that part here as well.
+template <typename R, bool fuse>
+__global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a, int rho, int depth, int fin, int adj) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ R Bs[LC_M * LC_M];
   const bool col = adj;  // forward: row tree; transposed: column tree
@@ -338,43 +687,91 @@ __global__ void __launch_bounds__(kThreads) k_down_chunk(Args<R> a, int rho, int
   const int64_t x0 = blockIdx.x;
   R* nodes = reinterpret_cast<R*>(smem_raw);
   R* Ts = nodes + sub_off(depth + 1);
-  for (int i = threadIdx.x; i < LC_M * LC_M; i += blockDim.x) Bs[i] = a.t.B[i];
-  if (fin)
-    for (int i = threadIdx.x; i < 2 * s * LC_M; i += blockDim.x) Ts[i] = a.t.T[i];
+  __shared__ R par[kSeg];  // c of the root's parent
+  constexpr int U = fuse ? 1 : 4;
+  stage<U>(LC_M * LC_M, [&](int i) { return a.t.B[i]; }, [&](int i, R v) { Bs[i] = v; });
+  if (fin) stage<U>(2 * s * LC_M, [&](int i) { return a.t.T[i]; }, [&](int i, R v) { Ts[i] = v; });
   for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
     R* Cb = a.t.Cc + b * a.nseg * kSeg;
-    if (L > 0) {
-      for (int d = 0; d <= depth; ++d) {
-        __syncthreads();
-        const int gamma = rho + d;
-        const int nd = 1 << d;
-        R* lev = nodes + sub_off(d);
-        for (int t = threadIdx.x; t < nd * kSeg; t += blockDim.x) {
-          const int j = t / kSeg, sigma = (t % kSeg) / LC_M, k = t % LC_M;
-          const int64_t x = (x0 << d) + j;
-          R c = R(0);
-          if (node_valid(col, gamma, x)) {
-            c = Cb[(lc_seg_offset(gamma) + x) * kSeg + sigma * LC_M + k];  // Step 3 result (k_couple_blocks)
-            if (gamma > 0 && node_valid(col, gamma - 1, x >> 1)) {
-              const R* pv = (d == 0) ? Cb + (lc_seg_offset(gamma - 1) + (x >> 1)) * kSeg + sigma * LC_M
-                                     : nodes + sub_off(d - 1) + (j >> 1) * kSeg + sigma * LC_M;
-              // B(1) = B(0) with odd diagonals negated
-              if constexpr (split_chains<R>::value) {
-                R ce = R(0), co = R(0);
-                for (int jj = k; jj < LC_M; jj += 2) ce = acc2(ce, Bs[jj * LC_M + k], pv[jj]);
-                for (int jj = k + 1; jj < LC_M; jj += 2) co = acc2(co, Bs[jj * LC_M + k], pv[jj]);
-                c = c + ((x & 1) ? finish(ce) - finish(co) : finish(ce) + finish(co));
-              } else {
-                const bool odd = (x & 1) != 0;
-                for (int jj = k; jj < LC_M; ++jj) {
-                  const R bjk = Bs[jj * LC_M + k];
-                  c = acc2(c, (odd && ((jj - k) & 1)) ? negate(bjk) : bjk, pv[jj]);
-                }
-                c = finish(c);
-              }
+    {
+      __syncthreads();  // shared tiles of the previous batch member are free
+      // Step 3 results of every node of the subtree (zero where the node is not
+      // valid) and of the root's parent, all read before any is used (one
+      // round trip instead of one per level).  Batched plans, whose launches
+      // fill the GPU many times over, read them level by level instead
+      // (except for the FP64 E/O form, which works on the staged copy).
+      const int ntot = sub_off(depth + 1);
+      if (!fuse || eo_pairs<R>::value) stage<U>(
+          ntot + kSeg,
+          [&](int q) {
+            if (q >= ntot) {
+              const int64_t xp = x0 >> 1;
+              return rho > 0 && node_valid(col, rho - 1, xp) ? Cb[(lc_seg_offset(rho - 1) + xp) * kSeg + (q - ntot)]
+                                                             : R(0);
+            }
+            const int d = 31 - __clz((q / kSeg) + 1);  // level of entry q
+            const int64_t x = (x0 << d) + (q - sub_off(d)) / kSeg;
+            return node_valid(col, rho + d, x) ? Cb[(lc_seg_offset(rho + d) + x) * kSeg + (q - sub_off(d)) % kSeg]
+                                               : R(0);
+          },
+          [&](int q, R v) {
+            if (q >= ntot) par[q - ntot] = v;
+            else nodes[q] = v;
+          });
+      // Step 4 level by level.  B(1) is B(0) with its odd diagonals negated.
+      // FP64 (bound by its pipe): one pass over a parent's c gives E (even
+      // diagonals of B(0)^T c) and O (odd diagonals); child 2x receives E + O,
+      // child 2x + 1 receives E - O -- half the multiplies.  Other types
+      // (latency-bound): one thread per child entry, twice the parallelism.
+      if constexpr (eo_pairs<R>::value) {
+        for (int d = 0; d <= depth; ++d) {
+          __syncthreads();
+          const int gamma = rho + d;
+          if (gamma == 0) continue;
+          const int np = d == 0 ? 1 : 1 << (d - 1);  // parents inside the subtree (d == 0: the root's)
+          R* lev = nodes + sub_off(d);
+          for (int t = threadIdx.x; t < np * kSeg; t += blockDim.x) {
+            const int jp = t / kSeg, sigma = (t % kSeg) / LC_M, k = t % LC_M;
+            const int64_t xp = d == 0 ? (x0 >> 1) : (x0 << (d - 1)) + jp;
+            if (!node_valid(col, gamma - 1, xp)) continue;
+            const R* pv = (d == 0 ? par : nodes + sub_off(d - 1) + jp * kSeg) + sigma * LC_M;
+            R e = R(0), o = R(0);
+            for (int jj = k; jj < LC_M; jj += 2) e = acc2(e, Bs[jj * LC_M + k], pv[jj]);
+            for (int jj = k + 1; jj < LC_M; jj += 2) o = acc2(o, Bs[jj * LC_M + k], pv[jj]);
+            e = finish(e);
+            o = finish(o);
+            for (int q = 0; q < 2; ++q) {
+              const int64_t x = 2 * xp + q;
+              if (d == 0 && x != x0) continue;
+              if (!node_valid(col, gamma, x)) continue;
+              R* cc = lev + (d == 0 ? 0 : 2 * jp + q) * kSeg + sigma * LC_M + k;
+              *cc = *cc + (q ? e - o : e + o);
             }
           }
-          lev[t] = c;
+        }
+      } else {
+        for (int d = 0; d <= depth; ++d) {
+          __syncthreads();
+          const int gamma = rho + d;
+          const int nd = 1 << d;
+          R* lev = nodes + sub_off(d);
+          for (int t = threadIdx.x; t < nd * kSeg; t += blockDim.x) {
+            const int j = t / kSeg, sigma = (t % kSeg) / LC_M, k = t % LC_M;
+            const int64_t x = (x0 << d) + j;
+            R c = fuse ? (node_valid(col, gamma, x) ? Cb[(lc_seg_offset(gamma) + x) * kSeg + sigma * LC_M + k] : R(0))
+                       : lev[t];  // Step 3 result (k_couple_blocks)
+            if (gamma > 0 && node_valid(col, gamma, x) && node_valid(col, gamma - 1, x >> 1)) {
+              const R* pv = (d == 0) ? (fuse ? Cb + (lc_seg_offset(gamma - 1) + (x >> 1)) * kSeg : par) + sigma * LC_M
+                                     : nodes + sub_off(d - 1) + (j >> 1) * kSeg + sigma * LC_M;
+              const bool odd = (x & 1) != 0;
+              for (int jj = k; jj < LC_M; ++jj) {
+                const R bjk = Bs[jj * LC_M + k];
+                c = acc2(c, (odd && ((jj - k) & 1)) ? negate(bjk) : bjk, pv[jj]);
+              }
+              c = finish(c);
+            }
+            lev[t] = c;
+          }
         }
       }
       if (!fin) {
@@ -388,99 +785,141 @@ __global__ void __launch_bounds__(kThreads) k_down_chunk(Args<R> a, int rho, int
         continue;
       }
     }
-    // ---------------- Steps 5-7 for this subtree's rows (forward) or columns (transposed)
+    // ---------------- Step 5 for this subtree's rows (forward) or columns (transposed)
+    __syncthreads();  // the leaf level of the subtree is complete
     const R* leafc = nodes + sub_off(depth);
-    const int64_t lo = (L > 0) ? (x0 << depth) * two_s : 0;
-    const int64_t hi_raw = (L > 0) ? ((x0 + 1) << depth) * two_s : a.n;
+    const int64_t lo = (x0 << depth) * two_s;
+    const int64_t hi_raw = ((x0 + 1) << depth) * two_s;
     const int64_t hi = hi_raw < a.n ? hi_raw : a.n;
     if (lo >= hi) continue;
-    const typename lc_io<R>::type* f = a.in + b * a.ib;
-    R* opnd = Ts + 2 * s * LC_M;  // operand tile (input values, pre-scaled)
-    int64_t olo, ohi;             // operand index range
-    if (!adj) {
-      olo = lo;
-      ohi = (L > 0) ? hi + 2 * two_s : a.n;
-    } else {
-      olo = (L > 0) ? (lo - two_s > 0 ? lo - two_s : 0) : 0;
-      ohi = hi;
-    }
-    if (ohi > a.n) ohi = a.n;
-    const int64_t olen = ohi - olo;
-    R* lamk = opnd + olen + 8;       // lambda_k (L2C) / u_k (C2L), k < kmax
-    const int64_t kmax = (L > 0) ? two_s : (a.n + 1) / 2;
-    R* lamm = lamk + kmax + 8;       // lambda_m / v_m for m in [mlo, mhi)
-    const int64_t mlo = adj ? (olo + lo) / 2 : lo;
-    const int64_t mhi = adj ? hi : (hi + ohi) / 2 + 1;
-    const int64_t mcap = mhi < a.N ? mhi : a.N;
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < olen; i += blockDim.x) {
-      const int64_t q = olo + i;
-      R v = lc_ld<R>(f + q * a.ie);
-      if (!adj) {
-        if (a.dir == LC_C2L) v = R(q) * v;                // L(i, j) = (2i+1) j u v: scale column j
-      } else {
-        v = (a.dir == LC_L2C) ? cinv<R>(q) * v : R(2 * q + 1) * v;  // C^{-1} r or (2i+1) r
-      }
-      opnd[i] = v;
-    }
-    for (int64_t k = threadIdx.x; k < kmax; k += blockDim.x) lamk[k] = (k < a.N) ? a.t.lam[k] : R(0);
-    for (int64_t m = mlo + threadIdx.x; m < mhi; m += blockDim.x) lamm[m - mlo] = (m < mcap) ? a.t.lam2[m] : R(0);
-    __syncthreads();
     const bool l2c = (a.dir == LC_L2C);
-    // Work unit: within one 2s-row strip and parity, rows m and s-1-m, whose
-    // band lengths add up to about 3s, so the threads of a warp stay balanced.
-    const int half = (s + 1) / 2;
-    const int64_t nstrips = (hi - lo + two_s - 1) / two_s;
-    const int64_t units = nstrips * 2 * half;
-    for (int64_t u = threadIdx.x; u < units; u += blockDim.x) {
-      const int64_t strip = u / (2 * half);
-      const int rem = int(u - strip * 2 * half);
-      const int sigma = rem / half, mm = rem % half;
-      for (int rep = 0; rep < 2; ++rep) {
-        const int m = rep ? s - 1 - mm : mm;
-        if (rep && m == mm) break;
-        const int64_t i = lo + strip * two_s + 2 * m + sigma;
+    if constexpr (!fuse) {
+      const bool scale = !adj && l2c;  // forward L2C: C^{-1} (far + near)
+      // Item: rows m0 = 2g and m0 + 1 of parity sigma in one strip (they share
+      // the leaf coefficients c), consecutive threads on consecutive strips.
+      const int ng = (s + 1) >> 1;
+      const int nstrips = int((hi - lo + two_s - 1) / two_s);
+      const int items = nstrips * 2 * ng;
+      for (int u = threadIdx.x; u < items; u += blockDim.x) {
+        const int sigma = u & 1;
+        const int t = (u >> 1) % nstrips;
+        const int m0 = 2 * ((u >> 1) / nstrips);
+        const int64_t i = lo + t * two_s + 2 * m0 + sigma;
         if (i >= hi) continue;
-        const int64_t v = i / two_s;
-        R far = R(0);
-        if (L > 0 && node_valid(col, L - 1, v)) {
-          const R* c = leafc + (v - (x0 << depth)) * kSeg + sigma * LC_M;
-          const R* Trow = Ts + (sigma * s + m) * LC_M;
-          for (int k = 0; k < LC_M; ++k) far = acc2(far, c[k], Trow[k]);
-          far = finish(far);
+        const bool has1 = (m0 + 1 < s) && (i + 2 < hi);
+        R far0 = R(0), far1 = R(0);
+        if (node_valid(col, L - 1, (x0 << depth) + t)) {
+          const R* c = leafc + t * kSeg + sigma * LC_M;
+          const R* T0 = Ts + (sigma * s + m0) * LC_M;
+          const R* T1 = (m0 + 1 < s) ? T0 + LC_M : T0;
+#pragma unroll 3
+          for (int k = 0; k < LC_M; ++k) {
+            const R ck = c[k];
+            far0 = acc2(far0, ck, T0[k]);
+            far1 = acc2(far1, ck, T1[k]);
+          }
+          far0 = finish(far0);
+          far1 = finish(far1);
         }
-        R near = R(0);
-        if (!adj) {
-          // row i: sum over j = i + 2k in the band  (eq:hik, eq:Lxymod)
-          const int64_t end = (L > 0) ? (two_s * (v + 2) < a.n ? two_s * (v + 2) : a.n) : a.n;
-          const int cnt = int((end - i + 1) >> 1);
-          const R* fo = opnd + (i - olo);
-          const R* lm = lamm + (i - mlo);
-          for (int kk = 0; kk < cnt; ++kk) near = acc3(near, lamk[kk], lm[kk], fo[2 * kk]);
-          near = finish(near);
-          R res;
-          if (l2c) {
-            res = cinv<R>(i) * (far + near);
+        if (scale) {
+          far0 = cinv<R>(i) * far0;
+          far1 = cinv<R>(i + 2) * far1;
+        }
+        auto* o = a.out + b * a.ob + i * a.oe;
+        lc_st<R>(o, far0 + lc_ld<R>(o));
+        if (has1) lc_st<R>(o + 2 * a.oe, far1 + lc_ld<R>(o + 2 * a.oe));
+      }
+    } else {
+      // Batched plans: Steps 5-7 here, one row (column) per step of a thread,
+      // which keeps register use low enough for many CTAs per SM.
+      typedef typename lc_io<R>::type IO;
+      const IO* f = a.in + b * a.ib;
+      R* opnd = Ts + 2 * s * LC_M;  // operand tile (input values, pre-scaled)
+      int64_t olo, ohi;             // operand index range
+      if (!adj) {
+        olo = lo;
+        ohi = hi + 2 * two_s;
+      } else {
+        olo = lo - two_s > 0 ? lo - two_s : 0;
+        ohi = hi;
+      }
+      if (ohi > a.n) ohi = a.n;
+      const int64_t olen = ohi - olo;
+      R* lamk = opnd + olen + 8;  // lambda_k (L2C) / u_k (C2L), k < 2s
+      R* lamm = lamk + two_s + 8;  // lambda_m / v_m for m in [mlo, mhi)
+      const int64_t mlo = adj ? (olo + lo) / 2 : lo;
+      const int64_t mhi = adj ? hi : (hi + ohi) / 2 + 1;
+      const int64_t mcap = mhi < a.N ? mhi : a.N;
+      stage(
+          int(olen), [&](int i) { return f[(olo + i) * a.ie]; },
+          [&](int i, IO x) {
+            const int64_t q = olo + i;
+            R v = lc_ld<R>(&x);
+            if (!adj) {
+              if (!l2c) v = R(q) * v;  // L(i, j) = (2i+1) j u v: scale column j
+            } else {
+              v = l2c ? cinv<R>(q) * v : R(2 * q + 1) * v;  // C^{-1} r or (2i+1) r
+            }
+            opnd[i] = v;
+          });
+      stage(int(two_s), [&](int k) { return k < a.N ? a.t.lam[k] : R(0); }, [&](int k, R v) { lamk[k] = v; });
+      stage(
+          int(mhi - mlo), [&](int j) { return mlo + j < mcap ? a.t.lam2[mlo + j] : R(0); },
+          [&](int j, R v) { lamm[j] = v; });
+      __syncthreads();
+      // Work unit: within one strip and parity, rows m and s-1-m, whose band
+      // lengths add up to about 3s, so the threads of a warp stay balanced.
+      const int half = (s + 1) / 2;
+      const int units = int((hi - lo + two_s - 1) / two_s) * 2 * half;
+      for (int u = threadIdx.x; u < units; u += blockDim.x) {
+        const int strip = u / (2 * half);
+        const int rem = u - strip * 2 * half;
+        const int sigma = rem / half, mm = rem % half;
+        for (int rep = 0; rep < 2; ++rep) {
+          const int m = rep ? s - 1 - mm : mm;
+          if (rep && m == mm) break;
+          const int64_t i = lo + strip * two_s + 2 * m + sigma;
+          if (i >= hi) continue;
+          const int64_t v = (x0 << depth) + strip;
+          R far = R(0);
+          if (node_valid(col, L - 1, v)) {
+            const R* c = leafc + strip * kSeg + sigma * LC_M;
+            const R* Trow = Ts + (sigma * s + m) * LC_M;
+            for (int k = 0; k < LC_M; ++k) far = acc2(far, c[k], Trow[k]);
+            far = finish(far);
+          }
+          R near = R(0), res;
+          if (!adj) {
+            // row i: sum over j = i + 2k in the band  (eq:hik, eq:Lxymod)
+            const int64_t end = two_s * (v + 2) < a.n ? two_s * (v + 2) : a.n;
+            const int cnt = int((end - i + 1) >> 1);
+            const R* fo = opnd + (i - olo);
+            const R* lm = lamm + (i - mlo);
+            for (int kk = 0; kk < cnt; ++kk) near = acc3(near, lamk[kk], lm[kk], fo[2 * kk]);
+            near = finish(near);
+            if (l2c) {
+              res = cinv<R>(i) * (far + near);
+            } else {
+              // (2i+1) u_k v_(i+k) (j f_j) summed; entry (0,0) = 1 adds f_0 (eq:Lxymod)
+              res = far + R(2 * i + 1) * near;
+              if (i == 0) res += lc_ld<R>(f);
+            }
           } else {
-            // (2i+1) u_k v_(i+k) (j f_j) summed; entry (0,0) = 1 adds f_0 (eq:Lxymod)
-            res = far + R(2 * i + 1) * near;
-            if (i == 0) res += lc_ld<R>(f);
+            // column j = i: sum over rows r <= j in the band
+            int64_t st = two_s * (v - 1) > 0 ? two_s * (v - 1) : 0;
+            if ((st & 1) != (i & 1)) ++st;
+            const int cnt = int((i - st) / 2 + 1);
+            const R* ro = opnd + (i - olo);  // ro[-2k] = row i - 2k
+            const R* lm = lamm + (i - mlo);  // lm[-k]  = (r + i)/2 = i - k
+            for (int k = 0; k < cnt; ++k) near = acc3(near, lamk[k], lm[-k], ro[-2 * k]);
+            near = finish(near);
+            if (!l2c) {
+              near = R(i) * near;
+              if (i == 0) near += lc_ld<R>(f);
+            }
+            res = far + near;
           }
           lc_st<R>(a.out + b * a.ob + i * a.oe, res);
-        } else {
-          // column j = i: sum over rows r <= j in the band
-          int64_t st = (L > 0) ? (two_s * (v - 1) > 0 ? two_s * (v - 1) : 0) : 0;
-          if ((st & 1) != (i & 1)) ++st;
-          const int cnt = int((i - st) / 2 + 1);
-          const R* ro = opnd + (i - olo);          // ro[-2k] = row i - 2k
-          const R* lm = lamm + (i - mlo);           // lm[-k]  = (r + i)/2 = i - k
-          for (int k = 0; k < cnt; ++k) near = acc3(near, lamk[k], lm[-k], ro[-2 * k]);
-          near = finish(near);
-          if (!l2c) {
-            near = R(i) * near;
-            if (i == 0) near += lc_ld<R>(f);
-          }
-          lc_st<R>(a.out + b * a.ob + i * a.oe, far + near);
         }
       }
     }
@@ -503,16 +942,18 @@ inline void chunk_roots(int L, int leaf_depth, int chunk_depth, int* roots, int*
 }
 
 template <typename R>
-inline int launches_for(int L, int leaf_depth, int chunk_depth) {
+inline int launches_for(int L, int leaf_depth, int chunk_depth, int64_t batch) {
   if (L <= 0) return 1;
   int roots[64], nr;
   chunk_roots<R>(L, leaf_depth, chunk_depth, roots, &nr);
-  return 2 * nr + (roots[0] > 0 ? 2 : 1);
+  return 2 * nr + (roots[0] > 0 ? 2 : 1) + (batch > 1 ? 0 : 1);  // + the band (k_near) for one vector
 }
 
 template <typename R>
 lc_status set_smem(const void* fn, size_t bytes) {
-  if (bytes > 48 * 1024) LC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+  // The default limit of 48 KB covers static and dynamic shared memory together;
+  // the kernels' static arrays stay below 4 KB.
+  if (bytes > 44 * 1024) LC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
   return LC_OK;
 }
 
@@ -522,11 +963,11 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
   const unsigned gy = unsigned(a.batch < 65535 ? a.batch : 65535);
   lc_timer_begin(p);
   if (L <= 0) {
-    const size_t sm = down_smem<R>(0, s, 1, a.n);
-    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R>), sm);
+    const size_t sm = near_smem<R>(s, a.n, 1);
+    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_near<R>), sm);
     if (e != LC_OK) return e;
-    lc_timer_mark(p, st, LC_K_FINAL);
-    k_down_chunk<R><<<dim3(1, gy), kThreads, sm, st>>>(a, 0, 0, 1, adjoint);
+    lc_timer_mark(p, st, LC_K_NEAR);
+    k_near<R><<<dim3(1, gy), kThreads, sm, st>>>(a, adjoint);
     LC_LAUNCH_CHECK();
     lc_timer_end(p, st);
     return LC_OK;
@@ -538,14 +979,32 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
     lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_couple_blocks<R>), smc);
     if (e != LC_OK) return e;
   }
-  // Once the first up chunk is done, w is final on the levels [roots[0], L).
-  // The coarse levels (up chunks, their coupling, their down chunks) form a
-  // latency-bound chain of small grids; it runs on the plan's high-priority
-  // side stream while the wide coupling of the fine levels runs on the
-  // caller's stream, and the last down chunk waits for both.  (Everything
-  // stays on the caller's stream when per-kernel timing is on.)
-  const bool overlap = p->timing_slots <= 0 && roots[0] > 0 && p->side != nullptr;
-  cudaStream_t sk = overlap ? p->side : st;  // stream of the coarse chain
+  // Three independent pieces of work: the band (k_near, which needs only the
+  // input), the far-field chain (leaf restriction -> coupling of the fine
+  // levels -> last down chunk) and, once the first up chunk has made w final
+  // on the levels [roots[0], L), the coarse levels (up chunks, their coupling,
+  // their down chunks: a latency-bound chain of small grids).  For one vector
+  // they run on the plan's streams -- coarse chain at the highest priority,
+  // far-field chain next, band at the lowest -- so that the band's CTAs take
+  // the SM slots the latency- and memory-bound far-field kernels leave free;
+  // the last down chunk waits for the other two, the caller's stream for it.
+  // A batch keeps the far-field chain (with the band fused into its last
+  // kernel) on the caller's stream and only the coarse chain beside it.
+  // Per-kernel timing keeps everything on the caller's stream, in order.
+  // A batch fills the GPU from every kernel, so its band rides in the last
+  // down chunk instead (one pass over the output, no separate launch).
+  const bool fused = a.batch > 1;
+  const bool streams = p->timing_slots <= 0 && p->fine && p->nearst && p->side;
+  const bool overlap = streams && !fused;                 // band beside the far-field chain
+  const bool coarse_side = streams && roots[0] > 0;       // coarse chain beside the fine coupling
+  cudaStream_t sf = overlap ? p->fine : st;    // far-field chain
+  cudaStream_t sn = overlap ? p->nearst : st;  // band
+  cudaStream_t sk = coarse_side ? p->side : st;  // coarse chain
+  if (overlap) {
+    LC_CUDA_TRY(cudaEventRecord(p->ev_start, st));
+    LC_CUDA_TRY(cudaStreamWaitEvent(sf, p->ev_start, 0));
+    LC_CUDA_TRY(cudaStreamWaitEvent(sn, p->ev_start, 0));
+  }
   {  // first up chunk: leaf restriction and the fine levels
     const int rho = roots[0];
     const int depth = L - 1 - rho;
@@ -553,14 +1012,24 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
     lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_up_chunk<R>), sm);
     if (e != LC_OK) return e;
     lc_timer_mark(p, st, LC_K_LEAF);
-    k_up_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, st>>>(a, rho, depth, 1, adjoint);
+    k_up_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sf>>>(a, rho, depth, 1, adjoint);
     LC_LAUNCH_CHECK();
   }
-  if (overlap) {
-    LC_CUDA_TRY(cudaEventRecord(p->ev_fork, st));
-    LC_CUDA_TRY(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+  if (!fused) {  // band: rows (columns) of kNearStrips strips per CTA
+    const size_t sm = near_smem<R>(s, int64_t(kNearStrips) * 2 * s, 0);
+    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_near<R>), sm);
+    if (e != LC_OK) return e;
+    const int64_t strips = (a.n + 2 * s - 1) / (2 * s);
+    lc_timer_mark(p, st, LC_K_NEAR);
+    k_near<R><<<dim3(unsigned((strips + kNearStrips - 1) / kNearStrips), gy), kThreads, sm, sn>>>(a, adjoint);
+    LC_LAUNCH_CHECK();
+    if (overlap) LC_CUDA_TRY(cudaEventRecord(p->ev_near, sn));
   }
   if (roots[0] > 0) {
+    if (coarse_side) {
+      LC_CUDA_TRY(cudaEventRecord(p->ev_fork, sf));
+      LC_CUDA_TRY(cudaStreamWaitEvent(sk, p->ev_fork, 0));
+    }
     for (int c = 1; c < nr; ++c) {  // coarse up chunks
       const int rho = roots[c];
       const int depth = roots[c - 1] - rho;
@@ -577,29 +1046,42 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
     for (int c = nr - 1; c >= 1; --c) {  // coarse down chunks: levels [roots[c], roots[c-1] - 1]
       const int rho = roots[c];
       const int depth = roots[c - 1] - 1 - rho;
-      const size_t sm = down_smem<R>(depth, s, 0, 0);
-      lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R>), sm);
+      const size_t sm = down_smem<R>(depth, s, 0);
+      lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R, false>), sm);
       if (e != LC_OK) return e;
       lc_timer_mark(p, st, LC_K_DOWN);
-      k_down_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sk>>>(a, rho, depth, 0, adjoint);
+      k_down_chunk<R, false><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sk>>>(a, rho, depth, 0, adjoint);
       LC_LAUNCH_CHECK();
     }
-    if (overlap) LC_CUDA_TRY(cudaEventRecord(p->ev_join, p->side));
+    if (coarse_side) LC_CUDA_TRY(cudaEventRecord(p->ev_join, sk));
   }
-  // coupling of the fine levels [roots[0], L) on the caller's stream
+  // coupling of the fine levels [roots[0], L)
   lc_timer_mark(p, st, LC_K_COUPLE);
-  k_couple_blocks<R><<<dim3(unsigned(couple_ctas<R>(roots[0], L)), gy), kThreads, smc, st>>>(a, adjoint, roots[0], L);
+  k_couple_blocks<R><<<dim3(unsigned(couple_ctas<R>(roots[0], L)), gy), kThreads, smc, sf>>>(a, adjoint, roots[0], L);
   LC_LAUNCH_CHECK();
-  if (overlap) LC_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
-  {  // last down chunk: fine levels, then Steps 5-7
+  if (coarse_side) LC_CUDA_TRY(cudaStreamWaitEvent(sf, p->ev_join, 0));
+  if (overlap) LC_CUDA_TRY(cudaStreamWaitEvent(sf, p->ev_near, 0));
+  {  // last down chunk: fine levels, then Step 5 plus the band's part
     const int rho = roots[0];
     const int depth = L - 1 - rho;
-    const size_t sm = down_smem<R>(depth, s, 1, 0);
-    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R>), sm);
+    size_t sm = down_smem<R>(depth, s, 1);
+    if (fused) {  // operand, lambda_k and lambda_m tiles of the band
+      const size_t rows = (size_t(1) << depth) * 2 * s;
+      sm += ((rows + 4 * size_t(s) + 8) + (2 * size_t(s) + 8) + (rows + 2 * size_t(s) + 8)) * sizeof(R);
+    }
+    const void* fn = fused ? reinterpret_cast<const void*>(k_down_chunk<R, true>)
+                           : reinterpret_cast<const void*>(k_down_chunk<R, false>);
+    lc_status e = set_smem<R>(fn, sm);
     if (e != LC_OK) return e;
     lc_timer_mark(p, st, LC_K_FINAL);
-    k_down_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, st>>>(a, rho, depth, 1, adjoint);
+    const dim3 grid(unsigned(int64_t(4) << rho), gy);
+    if (fused) k_down_chunk<R, true><<<grid, kThreads, sm, sf>>>(a, rho, depth, 1, adjoint);
+    else k_down_chunk<R, false><<<grid, kThreads, sm, sf>>>(a, rho, depth, 1, adjoint);
     LC_LAUNCH_CHECK();
+  }
+  if (overlap) {
+    LC_CUDA_TRY(cudaEventRecord(p->ev_done, sf));
+    LC_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_done, 0));
   }
   lc_timer_end(p, st);
   return LC_OK;

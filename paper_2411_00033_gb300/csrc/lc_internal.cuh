@@ -97,8 +97,10 @@ struct lc_plan_s {
   int* err;  // device status word in the workspace
   // Side stream and fork/join events used to overlap independent kernels of
   // one execution (host objects; created at plan time).
-  cudaStream_t side;
-  cudaEvent_t ev_fork, ev_join;
+  cudaStream_t side;    // coarse-level chain (highest priority)
+  cudaStream_t fine;    // far-field chain of the fine levels (next priority)
+  cudaStream_t nearst;  // near-field band (lowest priority)
+  cudaEvent_t ev_fork, ev_join, ev_start, ev_near, ev_done;
   // Chunk geometry of the CUDA-core tiers (lc_plan_autotune / lc_plan_set_config).
   int leaf_depth, chunk_depth;
   // Optional per-kernel timing (lc_plan_set_timing).
@@ -113,7 +115,8 @@ struct lc_plan_s {
 
 // Timing marks: call lc_timer_begin once per execution, lc_timer_mark before
 // each kernel (with its kind) and lc_timer_end after the last one.
-enum { LC_K_LEAF = 0, LC_K_UP = 1, LC_K_COUPLE = 2, LC_K_DOWN = 3, LC_K_FINAL = 4, LC_K_PREP = 5, LC_K_OTHER = 6 };
+enum { LC_K_LEAF = 0, LC_K_UP = 1, LC_K_COUPLE = 2, LC_K_DOWN = 3, LC_K_FINAL = 4, LC_K_PREP = 5, LC_K_OTHER = 6,
+       LC_K_NEAR = 7 };
 inline void lc_timer_begin(lc_plan_s* p) {
   if (p->timing_slots <= 0) return;
   p->cur_slot = int(p->exec_counter++ % p->timing_slots);

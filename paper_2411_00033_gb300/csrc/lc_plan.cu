@@ -378,24 +378,34 @@ lc_status fill_ragged(lc_plan_s* p, const int64_t* n, int64_t count, lc_directio
 }
 
 lc_status create_side(lc_plan_s* p) {
-  p->side = nullptr;
-  p->ev_fork = p->ev_join = nullptr;
-  // The side stream carries the latency-bound coarse-level chain: give it the
-  // highest priority so its few CTAs are scheduled ahead of wide kernels.
+  p->side = p->fine = p->nearst = nullptr;
+  p->ev_fork = p->ev_join = p->ev_start = p->ev_near = p->ev_done = nullptr;
+  // Streams of one execution (see run() in lc_exec_kernels.cuh): the
+  // latency-bound coarse-level chain at the highest priority, so that its few
+  // CTAs are scheduled ahead of wide kernels; the far-field chain of the fine
+  // levels next; the near-field band at the lowest, filling free SM slots.
   int lo_prio = 0, hi_prio = 0;
   LC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+  const int mid_prio = hi_prio + 1 <= lo_prio ? hi_prio + 1 : lo_prio;
   LC_CUDA_TRY(cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, hi_prio));
-  LC_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
-  LC_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  LC_CUDA_TRY(cudaStreamCreateWithPriority(&p->fine, cudaStreamNonBlocking, mid_prio));
+  LC_CUDA_TRY(cudaStreamCreateWithPriority(&p->nearst, cudaStreamNonBlocking, lo_prio));
+  cudaEvent_t* evs[] = {&p->ev_fork, &p->ev_join, &p->ev_start, &p->ev_near, &p->ev_done};
+  for (cudaEvent_t* e : evs) LC_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   return LC_OK;
 }
 
 void destroy_side(lc_plan_s* p) {
-  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-  if (p->ev_join) cudaEventDestroy(p->ev_join);
-  if (p->side) cudaStreamDestroy(p->side);
-  p->side = nullptr;
-  p->ev_fork = p->ev_join = nullptr;
+  cudaEvent_t* evs[] = {&p->ev_fork, &p->ev_join, &p->ev_start, &p->ev_near, &p->ev_done};
+  for (cudaEvent_t* e : evs) {
+    if (*e) cudaEventDestroy(*e);
+    *e = nullptr;
+  }
+  cudaStream_t* sts[] = {&p->side, &p->fine, &p->nearst};
+  for (cudaStream_t* q : sts) {
+    if (*q) cudaStreamDestroy(*q);
+    *q = nullptr;
+  }
 }
 
 int grid_for(int64_t work, int threads) {
