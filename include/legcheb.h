@@ -156,7 +156,8 @@ lc_status lc_execute(lc_plan plan, const void* in, void* out, int64_t in_batch_s
  *   L2C plan: out = A^T C^{-1} in ;  C2L plan: out = (A^{-1} C)^T in.
  * Not in the paper: it runs Algorithm 4 backwards (C^{-1} first, leaf
  * restriction on the row side, upward pass over the row tree, A-hat
- * transposed, downward pass over the column tree, transposed band). */
+ * transposed, downward pass over the column tree, transposed band).
+ * Every tier, uniform, strided and ragged plans alike. */
 lc_status lc_adjoint(lc_plan plan, const void* in, void* out, int64_t in_batch_stride,
                      int64_t in_elem_stride, int64_t out_batch_stride,
                      int64_t out_elem_stride, lc_stream stream);
@@ -172,7 +173,8 @@ lc_status lc_plan_check(lc_plan plan, lc_stream stream);
  * levels of Algorithm 4 are processed in subtrees, one CTA per subtree:
  * leaf_depth = levels the first upward chunk climbs from the leaves (and the
  * last downward chunk descends), chunk_depth = levels per coarser chunk;
- * 1..6 each, defaults 4 and 4.  The results do not depend on them. */
+ * leaf_depth 1..6, chunk_depth 1..8, defaults 4 and 4.  The results do not
+ * depend on them. */
 lc_status lc_plan_set_config(lc_plan plan, int32_t leaf_depth, int32_t chunk_depth);
 
 /* Autotuner (not in the paper): time every candidate chunk geometry

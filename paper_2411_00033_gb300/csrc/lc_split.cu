@@ -22,6 +22,17 @@
 // per row, so the next product slices them without another scan.  Only the
 // final output conversion touches the FP64 pipe (one add per coefficient).
 //
+// Transposed pass (lc_adjoint): the same products in reverse roles --
+//   leaf    W'(0, v)  = R(v) T(sigma)                  (row strip v: spread^T)
+//   up      W'(d+1,V) = [W'(d, 2V) W'(d, 2V+1)] [B(0) B(1)]^T   (Step 4^T)
+//   couple  C'(d, g)  = [W'(d, g-2) W'(d, g-3)] [A-hat(b,2) A-hat(b,1)] (g odd),
+//                       W'(d, g-2) A-hat(b,0) (g even)  (Step 3^T)
+//   down    C'(d, g) += C'(d+1, g/2) B(g mod 2)         (Step 2^T)
+//   final   F'(strip) = C'(0, t) T(sigma)^T + R(strips t-1, t) E'^T (Step 1^T, band^T)
+// with R = C^{-1} r for L2C (applied while the input is sliced).  A row
+// segment v is owned by the same members as column segment v + 2, so every
+// row array keeps its slot numbering.
+//
 // Batches: members are sorted by length (descending).  At every level the
 // members owning a segment form a prefix of that order, so each CTA takes
 // one (segment, parity, 64-member tile).  A uniform batch is the special
@@ -43,7 +54,12 @@ constexpr int kRows = 64;       // members per CTA tile (4 warps x 16 rows)
 constexpr int kThreads = 128;
 constexpr int kNP18 = 24;       // 18 outputs padded to 3 n8 tiles
 
-enum YKind { Y_LEAF = 0, Y_SPREAD = 1, Y_UP = 2, Y_DOWN = 3, Y_COUPLE = 4, Y_NEAR = 5, Y_KINDS = 6 };
+enum YKind {
+  Y_LEAF = 0, Y_SPREAD = 1, Y_UP = 2, Y_DOWN = 3, Y_COUPLE = 4, Y_NEAR = 5,
+  Y_COUPLE_T = 6,  // transposed pass: A-hat blocks per column segment
+  Y_NEAR_T = 7,    // transposed pass: band entries per column strip
+  Y_KINDS = 8
+};
 
 struct YTable {
   int items, K, KP, NP;  // KP: K rounded up to 16; NP: padded outputs
@@ -64,13 +80,13 @@ struct SplitHost {
   std::vector<int64_t> rowbase;                       // concatenated over d
   int64_t rows;
   YTable y[Y_KINDS];
-  // work lists: launches in execution order
-  std::vector<Work> work;
-  std::vector<int64_t> launch_off;   // [launches + 1]
-  std::vector<int> launch_kind;      // LC_K_*
-  std::vector<int> launch_level;     // d for up/down
+  // work lists: launches in execution order (forward; a* = transposed pass)
+  std::vector<Work> work, awork;
+  std::vector<int64_t> launch_off, alaunch_off;  // [launches + 1]
+  std::vector<int> launch_kind, alaunch_kind;    // LC_K_*
+  std::vector<int> launch_level;                 // d for up/down
   // device byte offsets
-  size_t off_len, off_orig, off_off, off_Lcount, off_cntN, off_rowbase, off_work;
+  size_t off_len, off_orig, off_off, off_Lcount, off_cntN, off_rowbase, off_work, off_awork;
   size_t off_W, off_We, off_C, off_Ce;
   size_t total;
 };
@@ -175,6 +191,34 @@ void build_host(const lc_plan_s* p, SplitHost& h) {
   }
   for (int64_t t = 0; t < h.nstrips; ++t) add_items(0, t, h.cntN[t]);
   close_launch(LC_K_FINAL, 0);
+  // transposed pass: row tree up, coupling per column segment, column tree down
+  h.awork.clear();
+  h.alaunch_off.assign(1, 0);
+  h.alaunch_kind.clear();
+  auto aadd = [&](int d, int64_t seg, int64_t members) {
+    for (int64_t t0 = 0; t0 < members; t0 += kRows) h.awork.push_back(Work{d, int32_t(seg), int32_t(t0 / kRows)});
+  };
+  auto aclose = [&](int kind) {
+    h.alaunch_off.push_back(int64_t(h.awork.size()));
+    h.alaunch_kind.push_back(kind);
+  };
+  if (h.Lmax > 0) {
+    for (int64_t v = 0; v + 2 < (int64_t(2) << h.Lmax); ++v) aadd(0, v, cnt(0, v + 2));
+    aclose(LC_K_LEAF);
+    for (int d = 0; d + 1 < h.Lmax; ++d) {  // parents at d+1
+      for (int64_t V = 0; V + 2 < (int64_t(1) << (h.Lmax - d)); ++V) aadd(d + 1, V, cnt(d + 1, V + 2));
+      aclose(LC_K_UP);
+    }
+    for (int d = 0; d < h.Lmax; ++d)
+      for (int64_t g = 2; g < (int64_t(1) << (h.Lmax + 1 - d)); ++g) aadd(d, g, cnt(d, g));
+    aclose(LC_K_COUPLE);
+    for (int d = h.Lmax - 2; d >= 0; --d) {  // children at d
+      for (int64_t g = 4; g < (int64_t(1) << (h.Lmax + 1 - d)); ++g) aadd(d, g, cnt(d, g));
+      aclose(LC_K_DOWN);
+    }
+  }
+  for (int64_t t = 0; t < h.nstrips; ++t) aadd(0, t, h.cntN[t]);
+  aclose(LC_K_FINAL);
 
   // Y tables
   const int s = h.s;
@@ -192,6 +236,8 @@ void build_host(const lc_plan_s* p, SplitHost& h) {
   ktab(Y_DOWN, 2, LC_M, kNP18);
   ktab(Y_COUPLE, int(nrowseg), 2 * LC_M, kNP18);
   ktab(Y_NEAR, int(2 * h.nstrips), 2 * s, 32);
+  ktab(Y_COUPLE_T, int(nrowseg), 2 * LC_M, kNP18);
+  ktab(Y_NEAR_T, int(2 * h.nstrips), 2 * s, 32);
 
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -212,6 +258,7 @@ void build_host(const lc_plan_s* p, SplitHost& h) {
   h.off_cntN = take(size_t(h.nstrips) * 8);
   h.off_rowbase = take(h.rowbase.size() * 8);
   h.off_work = take(h.work.size() * sizeof(Work));
+  h.off_awork = take(h.awork.size() * sizeof(Work));
   h.off_W = take(size_t(h.rows) * LC_M * 8);
   h.off_We = take(size_t(h.rows) * 4);
   h.off_C = take(size_t(h.rows) * LC_M * 8);
@@ -272,10 +319,12 @@ __device__ __forceinline__ double f2d_scaled(float f, int E) {
 
 __device__ __forceinline__ uint16_t bf16_of_int(float q) { return uint16_t(__float_as_uint(q) >> 16); }
 
-// Same digits as slice_df for a normalised double-float (|lo| <= ulp(hi)),
-// cheaper: the first two digits come from hi alone (its 24 bits are exact
-// under the 8-bit shifts), lo joins once through TwoSum, and after the third
-// digit the residual fits one float.  Digits stay within [-129, 129].
+// Cut a normalised double-float x = hi + lo (|x| <= 1/2, |lo| <= ulp(hi)) into
+// S base-2^8 digits q_1..q_S (rounded to nearest at each step):
+// x = sum_s q_s 2^(-8 s) + r, |r| <= 2^(-8S-1); dst[s * stride] = bf16(q_s).
+// The first two digits come from hi alone (its 24 bits are exact under the
+// 8-bit shifts), lo joins once through TwoSum, and after the third digit the
+// residual fits one float.  Digits stay within [-129, 129].
 __device__ __forceinline__ void slice_df_fast(float hi, float lo, int S, uint16_t* dst, int stride) {
   float r = hi;
   int sl = 0;
@@ -303,18 +352,6 @@ __device__ __forceinline__ void slice_df_fast(float hi, float lo, int S, uint16_
   }
 }
 
-// Cut a double-float x (|x| <= 1/2) into S slices q_1..q_S in [-128, 128]:
-// x = sum_s q_s 2^(-8 s) + r, |r| <= 2^(-8S-1).  dst[s * stride] = bf16(q_s).
-__device__ __forceinline__ void slice_df(float hi, float lo, int S, uint16_t* dst, int stride) {
-  for (int s = 0; s < S; ++s) {
-    const float th = hi * 256.0f, tl = lo * 256.0f;
-    const float q = rintf(th);
-    const float rh = th - q;  // exact
-    two_sum(rh, tl, hi, lo);
-    dst[s * stride] = bf16_of_int(q);
-  }
-}
-
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
   asm(
@@ -323,8 +360,6 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
-
-__device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
 // Sliced product of this warp's 16 rows of X (smem [S][kRows][xs]) with Y
 // (smem [S][NT*8][ys]) over KT k16 tiles.  Result per fragment element:
@@ -436,6 +471,7 @@ struct Dev {
   int yKP[Y_KINDS], yNP[Y_KINDS];
   int dir;
   int ragged;
+  int adj;  // transposed pass
   int* err;
   // I/O
   const double* in;
@@ -456,12 +492,6 @@ __device__ __forceinline__ int64_t dcnt(const Dev& D, int d, int64_t g) {
 __device__ __forceinline__ int64_t drow(const Dev& D, int d, int64_t g, int sigma, int64_t r) {
   const int64_t db = (int64_t(4) << D.Lmax) - (int64_t(4) << (D.Lmax - d));  // sum_{d'<d} 2^(Lmax+1-d')
   return D.rowbase[db + g] + sigma * dcnt(D, d, g) + r;
-}
-__device__ __forceinline__ const double* in_base(const Dev& D, int64_t r) {
-  return D.in + (D.ragged ? D.off[r] : D.orig[r] * D.ib);
-}
-__device__ __forceinline__ double* out_base(const Dev& D, int64_t r) {
-  return D.out + (D.ragged ? D.off[r] : D.orig[r] * D.ob);
 }
 
 // smem layout shared by the stage kernels
@@ -527,8 +557,16 @@ __device__ __forceinline__ void stage_rows_df(const Dev& D, const float2* A, con
 // is f_r[j0 + 2c] (zero beyond the member's length).  Pass 1 finds each row's
 // exponent (max over the warp's lanes of the same row, then one shared atomic
 // per row); pass 2 reloads the values (L1 hits), frames and slices them.
+// cinv != 0 multiplies each input value by C^{-1} (2/pi, 1/pi at index 0)
+// first (transposed L2C pass); indices below 0 read as zero.
+__device__ __forceinline__ double in_value(const Dev& D, int64_t rb, int64_t j, int64_t len, int cinv) {
+  if (j < 0 || j >= len) return 0.0;
+  const double x = D.in[rb + j * D.ie];
+  return cinv ? x * (j == 0 ? 0.31830988618379067154 : 0.63661977236758134308) : x;
+}
 __device__ __forceinline__ void stage_input(const Dev& D, int64_t tile0, int64_t valid, int64_t j0, int ncols,
-                                            int KP, Smem& m, const int64_t* rbase, const int64_t* rlen) {
+                                            int KP, Smem& m, const int64_t* rbase, const int64_t* rlen,
+                                            int cinv = 0) {
   for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) m.Xe[rr] = 0;
   __syncthreads();
   const int n = kRows * KP;
@@ -537,7 +575,7 @@ __device__ __forceinline__ void stage_input(const Dev& D, int64_t tile0, int64_t
     const int rr = i / KP, c = i - rr * KP;
     double x = 0.0;
     const int64_t j = j0 + 2 * c;
-    if (c < ncols && tile0 + rr < valid && j < rlen[rr]) x = D.in[rbase[rr] + j * D.ie];
+    if (c < ncols && tile0 + rr < valid) x = in_value(D, rbase[rr], j, rlen[rr], cinv);
     // max over the lanes of this warp that hold the same row, one atomic per row
     const unsigned grp = __match_any_sync(0xffffffffu, rr);
     const unsigned E = __reduce_max_sync(grp, unsigned((__double_as_longlong(x) >> 52) & 0x7ff));
@@ -549,7 +587,7 @@ __device__ __forceinline__ void stage_input(const Dev& D, int64_t tile0, int64_t
     const int rr = i / KP, c = i - rr * KP;
     double x = 0.0;
     const int64_t j = j0 + 2 * c;
-    if (c < ncols && tile0 + rr < valid && j < rlen[rr]) x = D.in[rbase[rr] + j * D.ie];
+    if (c < ncols && tile0 + rr < valid) x = in_value(D, rbase[rr], j, rlen[rr], cinv);
     float hi, lo;
     d2df_scaled(x, m.Xe[rr] - 1021, hi, lo);
     slice_df_fast(hi, lo, D.S, m.Xs + rr * m.xs + c, kRows * m.xs);
@@ -638,8 +676,8 @@ __global__ void __launch_bounds__(kThreads) k_s_leaf(Dev D, int64_t w0) {
   const int sigma = blockIdx.y;
   const int KP = D.yKP[Y_LEAF], NP = D.yNP[Y_LEAF];
   Smem m = carve(sm_raw, D.S, KP, NP);
-  const int64_t g = it.seg, tile0 = int64_t(it.tile) * kRows;
-  const int64_t valid = dcnt(D, 0, g);
+  const int64_t g = it.seg, tile0 = int64_t(it.tile) * kRows;  // column segment (transposed: row strip)
+  const int64_t valid = dcnt(D, 0, D.adj ? g + 2 : g);
   if (!load_y(D.yq[Y_LEAF] + size_t(sigma) * D.S * NP * (KP + 8), D.ye[Y_LEAF] + sigma * NP, D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
     if (threadIdx.x == 0) atomicOr(D.err, 1);
     return;
@@ -648,7 +686,7 @@ __global__ void __launch_bounds__(kThreads) k_s_leaf(Dev D, int64_t w0) {
   const int s = D.s;
   __shared__ int64_t rbase[kRows], rlen[kRows];
   row_info(D, tile0, valid, rbase, nullptr, rlen);
-  stage_input(D, tile0, valid, 2 * int64_t(s) * g + sigma, s, KP, m, rbase, rlen);
+  stage_input(D, tile0, valid, 2 * int64_t(s) * g + sigma, s, KP, m, rbase, rlen, D.adj && D.dir == LC_L2C);
   float hi[3][4], lo[3][4];
   warp_ozaki<2, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
   const int g8 = lane >> 2;
@@ -667,7 +705,7 @@ __global__ void __launch_bounds__(kThreads) k_s_up(Dev D, int64_t w0) {
   Smem m = carve(sm_raw, D.S, KP, NP);
   const int dp = it.d;  // parent level
   const int64_t G = it.seg, tile0 = int64_t(it.tile) * kRows;
-  const int64_t valid = dcnt(D, dp, G);
+  const int64_t valid = dcnt(D, dp, D.adj ? G + 2 : G);  // transposed: row tree
   if (!load_y(D.yq[Y_UP], D.ye[Y_UP], D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
     if (threadIdx.x == 0) atomicOr(D.err, 1);
     return;
@@ -692,17 +730,20 @@ __global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) {
   const int KP = D.yKP[Y_COUPLE], NP = D.yNP[Y_COUPLE];
   Smem m = carve(sm_raw, D.S, KP, NP);
   const int d = it.d;
+  // forward: row segment v from column segments v+2 (and v+3);
+  // transposed: column segment g = seg from row segments g-2 (and g-3)
   const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;
-  const int64_t valid = dcnt(D, d, v + 2);
+  const int64_t valid = dcnt(D, d, D.adj ? v : v + 2);
   const int Gam = D.Lmax - 1 - d;  // level in the shared table
-  const int64_t item = (int64_t(4) * ((int64_t(1) << Gam) - 1) - 2 * Gam) + v;
-  if (!load_y(D.yq[Y_COUPLE] + size_t(item) * D.S * NP * (KP + 8), D.ye[Y_COUPLE] + item * NP, D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
+  const int64_t item = (int64_t(4) * ((int64_t(1) << Gam) - 1) - 2 * Gam) + (D.adj ? v - 2 : v);
+  const YKind yk = D.adj ? Y_COUPLE_T : Y_COUPLE;
+  if (!load_y(D.yq[yk] + size_t(item) * D.S * NP * (KP + 8), D.ye[yk] + item * NP, D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
     if (threadIdx.x == 0) atomicOr(D.err, 1);
     return;
   }
-  const int two = ((v & 1) == 0) ? 1 : 0;
-  stage_rows_df(D, D.W, D.We, drow(D, d, v + 2, sigma, 0), two ? drow(D, d, v + 3, sigma, 0) : 0, two, tile0, valid,
-                KP, m);
+  const int two = D.adj ? int(v & 1) : ((v & 1) == 0 ? 1 : 0);
+  const int64_t s0 = D.adj ? v - 2 : v + 2, s1 = D.adj ? v - 3 : v + 3;
+  stage_rows_df(D, D.W, D.We, drow(D, d, s0, sigma, 0), two ? drow(D, d, s1, sigma, 0) : 0, two, tile0, valid, KP, m);
   float hi[3][4], lo[3][4];
   warp_ozaki<3, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2;
@@ -720,8 +761,8 @@ __global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) {
   const int KP = D.yKP[Y_DOWN], NP = D.yNP[Y_DOWN];
   Smem m = carve(sm_raw, D.S, KP, NP);
   const int d = it.d;
-  const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;
-  const int64_t valid = dcnt(D, d, v + 4);
+  const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;  // child (row segment; transposed: column segment)
+  const int64_t valid = dcnt(D, d, D.adj ? v : v + 4);
   const int p = int(v & 1);
   if (!load_y(D.yq[Y_DOWN] + size_t(p) * D.S * NP * (KP + 8), D.ye[Y_DOWN] + p * NP, D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
     if (threadIdx.x == 0) atomicOr(D.err, 1);
@@ -777,12 +818,16 @@ __device__ __forceinline__ void final_body(const Dev& D, unsigned char* sm_raw, 
   const int KPn = KTN * 16, NPn = D.yNP[Y_NEAR];
   Smem m = carve(sm_raw, D.S, KPn, NPn);
   const int64_t item = 2 * t + sigma;
-  if (!load_y(D.yq[Y_NEAR] + size_t(item) * D.S * NPn * (KPn + 8), D.ye[Y_NEAR] + item * NPn, D.S, NPn, KPn, m.Ys,
-              m.Ye, mbar)) {
+  const YKind yk = D.adj ? Y_NEAR_T : Y_NEAR;
+  if (!load_y(D.yq[yk] + size_t(item) * D.S * NPn * (KPn + 8), D.ye[yk] + item * NPn, D.S, NPn, KPn, m.Ys, m.Ye,
+              mbar)) {
     if (threadIdx.x == 0) atomicOr(D.err, 1);
     return;
   }
-  stage_input(D, tile0, validN, 2 * int64_t(s) * t + sigma, 2 * s, KPn, m, rbase, rlen);
+  // forward: columns of strips t, t+1 of the band of rows in strip t;
+  // transposed: rows of strips t-1, t (times C^{-1} for L2C) for columns in strip t
+  stage_input(D, tile0, validN, 2 * int64_t(s) * (D.adj ? t - 1 : t) + sigma, 2 * s, KPn, m, rbase, rlen,
+              D.adj && D.dir == LC_L2C);
   float nh[4][4], nl[4][4];
   warp_ozaki<KTN, 4>(m.Xs, m.xs, m.Ys, m.ys, D.S, nh, nl);
   const int enx0 = m.Xe[warp * 16 + g8], enx1 = m.Xe[warp * 16 + g8 + 8];
@@ -823,7 +868,7 @@ __device__ __forceinline__ void final_body(const Dev& D, unsigned char* sm_raw, 
   }
   // ---- combine, scale, store
   const int64_t r0 = tile0 + warp * 16 + g8, r1 = r0 + 8;
-  const bool l2c = (D.dir == LC_L2C);
+  const bool l2c = (D.dir == LC_L2C) && !D.adj;  // Step 7 (the transposed pass applied C^{-1} first)
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
@@ -862,7 +907,10 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
   const int sigma = blockIdx.y;
   const int64_t t = it.seg, tile0 = int64_t(it.tile) * kRows;
   const int64_t validN = D.cntN[t];
-  const int64_t validF = (D.Lmax > 0 && t + 2 < (int64_t(2) << D.Lmax)) ? dcnt(D, 0, t + 2) : 0;
+  // far field of strip t: row segment t (forward), column segment t (transposed)
+  const int64_t validF = D.Lmax <= 0 ? 0
+                         : D.adj ? ((t >= 2 && t < (int64_t(2) << D.Lmax)) ? dcnt(D, 0, t) : 0)
+                                 : ((t + 2 < (int64_t(2) << D.Lmax)) ? dcnt(D, 0, t + 2) : 0);
   const int KPn = D.yKP[Y_NEAR];
   if (KPn == 64)
     final_body<4>(D, sm_raw, &mbar, t, sigma, tile0, validN, validF);
@@ -904,6 +952,33 @@ __device__ double y_value(int kind, int64_t item, int k, int n, const lc_plan_s&
       }
       if (k >= LC_M) return 0.0;
       return P.Ahat[(aoff + 3 * b + 2) * (LC_M * LC_M) + n * LC_M + k];
+    }
+    case Y_COUPLE_T: {  // column segment g: Y[c*18 + k][l] = A-hat(b, c')[k][l]
+      if (n >= LC_M || k >= 2 * LC_M) return 0.0;
+      int G = 0;
+      while (G + 1 < L && item >= 4 * ((int64_t(1) << (G + 1)) - 1) - 2 * (G + 1)) ++G;
+      const int64_t g = item - (4 * ((int64_t(1) << G) - 1) - 2 * G) + 2;
+      const int64_t aoff = lc_ahat_offset(G);
+      const int c = k / LC_M, kk = k % LC_M;
+      if ((g & 1) == 0) {  // from row segment g-2 (even): A-hat(b, 0), b = (g-2)/2
+        if (c) return 0.0;
+        return P.Ahat[(aoff + 3 * ((g - 2) >> 1)) * (LC_M * LC_M) + kk * LC_M + n];
+      }
+      // from row segments g-2 (odd, A-hat(b, 2)) and g-3 (even, A-hat(b, 1)), b = (g-3)/2
+      return P.Ahat[(aoff + 3 * ((g - 3) >> 1) + (c ? 1 : 2)) * (LC_M * LC_M) + kk * LC_M + n];
+    }
+    case Y_NEAR_T: {  // column strip t: Y[k][m] = entry (row 2s(t-1)+2k+sigma, column 2st+2m+sigma)
+      if (n >= s || k >= 2 * s) return 0.0;
+      const int64_t t = item >> 1;
+      const int sigma = int(item & 1);
+      const int64_t i = 2 * int64_t(s) * (t - 1) + 2 * k + sigma;
+      const int64_t j = 2 * int64_t(s) * t + 2 * n + sigma;
+      if (i < 0 || j < i || j >= N) return 0.0;
+      const int64_t kk = (j - i) / 2;
+      if (dir == LC_L2C) return P.lam[kk] * P.lam2[i + kk];
+      double e = double(2 * i + 1) * double(j) * P.lam[kk] * P.lam2[i + kk];
+      if (i == 0 && j == 0) e += 1.0;
+      return e;
     }
     case Y_NEAR: {  // Y[jj][m] = E(t, sigma)[m][jj]
       if (n >= s || k >= 2 * s) return 0.0;
@@ -979,6 +1054,7 @@ Dev make_dev(const lc_plan_s* p, const SplitHost& h) {
   }
   D.dir = int(p->dir);
   D.ragged = p->ragged;
+  D.adj = 0;
   D.err = p->err;
   return D;
 }
@@ -1013,7 +1089,8 @@ lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st)
   if ((s2 = up(h->off_cntN, h->cntN.data(), h->cntN.size() * 8)) != LC_OK) return s2;
   if ((s2 = up(h->off_rowbase, h->rowbase.data(), h->rowbase.size() * 8)) != LC_OK) return s2;
   if ((s2 = up(h->off_work, h->work.data(), h->work.size() * sizeof(Work))) != LC_OK) return s2;
-  const int Ks[Y_KINDS] = {h->s, LC_M, 2 * LC_M, LC_M, 2 * LC_M, 2 * h->s};
+  if ((s2 = up(h->off_awork, h->awork.data(), h->awork.size() * sizeof(Work))) != LC_OK) return s2;
+  const int Ks[Y_KINDS] = {h->s, LC_M, 2 * LC_M, LC_M, 2 * LC_M, 2 * h->s, 2 * LC_M, 2 * h->s};
   for (int k = 0; k < Y_KINDS; ++k) {
     const YTable& y = h->y[k];
     if (y.items == 0) continue;
@@ -1046,10 +1123,15 @@ int lc_exec_split_launches(const lc_plan_s* p) {
 
 lc_status lc_exec_split(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob, int64_t oe,
                         cudaStream_t st, int adjoint) {
-  if (adjoint) return LC_ERR_UNSUPPORTED;
   const SplitHost* h = static_cast<const SplitHost*>(p->ragged_dev);
   if (!h) return LC_ERR_INVALID_ARG;
   Dev D = make_dev(p, *h);
+  if (adjoint) {
+    D.adj = 1;
+    D.work = reinterpret_cast<const Work*>(static_cast<char*>(p->split) + h->off_awork);
+  }
+  const std::vector<int64_t>& loff = adjoint ? h->alaunch_off : h->launch_off;
+  const std::vector<int>& lkind = adjoint ? h->alaunch_kind : h->launch_kind;
   D.in = static_cast<const double*>(in);
   D.out = static_cast<double*>(out);
   D.ib = ib;
@@ -1057,10 +1139,10 @@ lc_status lc_exec_split(lc_plan p, const void* in, void* out, int64_t ib, int64_
   D.ob = ob;
   D.oe = oe;
   lc_timer_begin(p);
-  for (size_t l = 0; l < h->launch_kind.size(); ++l) {
-    const int64_t w0 = h->launch_off[l], nitems = h->launch_off[l + 1] - w0;
+  for (size_t l = 0; l < lkind.size(); ++l) {
+    const int64_t w0 = loff[l], nitems = loff[l + 1] - w0;
     if (nitems <= 0) continue;
-    const int kind = h->launch_kind[l];
+    const int kind = lkind[l];
     dim3 grid(unsigned(nitems), 2);
     lc_timer_mark(p, st, kind);
     switch (kind) {

@@ -40,7 +40,10 @@ void lc_tune_apply_cached(lc_plan p) {
 extern "C" {
 
 lc_status lc_plan_set_config(lc_plan plan, int32_t leaf_depth, int32_t chunk_depth) {
-  if (!plan || leaf_depth < 1 || leaf_depth > 6 || chunk_depth < 1 || chunk_depth > 6) return LC_ERR_INVALID_ARG;
+  // Depth 8 is the deepest coarse chunk whose subtree (511 nodes of 2M values,
+  // plus the work array of the upward pass) fits the 227 KB of shared memory
+  // of one CTA in the 8-byte types.
+  if (!plan || leaf_depth < 1 || leaf_depth > 6 || chunk_depth < 1 || chunk_depth > 8) return LC_ERR_INVALID_ARG;
   plan->leaf_depth = leaf_depth;
   plan->chunk_depth = chunk_depth;
   return LC_OK;

@@ -23,7 +23,7 @@ def lc():
     return m
 
 
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f64_df", 1e-12)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f64_df", 1e-12), ("f64_split", 1e-12)])
 @pytest.mark.parametrize("fn,code", [("leg2cheb", oracle.L2C), ("cheb2leg", oracle.C2L)])
 def test_fit_gradient_against_oracle_transpose(lc, dtype, tol, fn, code):
     n, batch = 4096, 8

@@ -122,3 +122,62 @@ def test_split_graph_capture_replay(lc):
     assert np.array_equal(Z.cpu().numpy(), Zd)
     e2, _ = rel_errors(Zd[0], oracle.apply(oracle.C2L, X2[0]))
     assert e2 <= 1e-12
+
+
+# ---- transposed pass (lc_adjoint) on the split tier
+@pytest.mark.parametrize("n,batch", [(1, 2), (7, 3), (128, 2), (129, 3), (1000, 64), (1024, 65), (4097, 7),
+                                     (20000, 3)])
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_split_adjoint_uniform_batch(lc, n, batch, direction, code):
+    X = _batch(n, batch, seed=3000 + n)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, direction, batch, "f64_split", dev)
+    Z = plan.execute(torch.as_tensor(X, device=dev), adjoint=True).cpu().numpy()
+    worst = 0.0
+    for b in range(batch):
+        e2, _ = rel_errors(Z[b], oracle.apply(code, X[b], adjoint=True))
+        worst = max(worst, e2)
+    assert worst <= 1e-12, (n, batch, worst)
+
+
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_split_adjoint_ragged(lc, direction, code):
+    rng = np.random.default_rng(6)
+    lengths = [1, 2, 3, 64, 100, 128, 129, 130, 500, 1000, 1024, 1025, 3000, 5000] + \
+        list(workloads.ragged_lengths(40, 64, 8192, seed=10))
+    rng.shuffle(lengths)
+    x = workloads.ragged_batch(lengths, seed=4)
+    offs = workloads.ragged_offsets(lengths)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(direction=direction, dtype="f64_split", device=dev, lengths=lengths)
+    z = plan.execute(torch.as_tensor(x, device=dev), adjoint=True).cpu().numpy()
+    worst = 0.0
+    for i, n in enumerate(lengths):
+        a, b = offs[i], offs[i + 1]
+        e2, _ = rel_errors(z[a:b], oracle.apply(code, x[a:b], adjoint=True))
+        worst = max(worst, e2)
+    assert worst <= 1e-12, worst
+
+
+def test_split_adjoint_dot_test_and_strides(lc):
+    # <A x, y> = <x, A^T y> through the split tier on both sides, and the
+    # transposed pass on strided fibres equals the contiguous one.
+    n, batch = 3000, 16
+    dev = torch.device("cuda", 0)
+    X = torch.as_tensor(_batch(n, batch, seed=41), device=dev)
+    Y = torch.as_tensor(_batch(n, batch, seed=43), device=dev)
+    for direction in ("l2c", "c2l"):
+        plan = lc.Plan(n, direction, batch, "f64_split", dev)
+        ax = plan(X)
+        aty = plan.execute(Y, adjoint=True)
+        lhs = (ax * Y).sum(dim=1)
+        rhs = (X * aty).sum(dim=1)
+        # the sums cancel: measure against |Ax| |y| (and |x| |A^T y|)
+        scale = torch.minimum(ax.norm(dim=1) * Y.norm(dim=1), X.norm(dim=1) * aty.norm(dim=1))
+        rel = ((lhs - rhs).abs() / scale).max().item()
+        assert rel <= 1e-12, (direction, rel)
+        yt = Y.t().contiguous()  # (n, batch): fibres along axis 0
+        out = torch.empty((batch, n), dtype=torch.float64, device=dev)
+        plan.execute_strided(yt, out, (1, batch), (n, 1), adjoint=True)
+        e = ((out - aty).norm() / aty.norm()).item()
+        assert e <= 1e-15, (direction, e)
