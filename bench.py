@@ -392,7 +392,7 @@ def batched_leg(lc, dev, flush, args):
     #     one step = forward transform + hand-written adjoint (autograd backward)
     x0, y0 = workloads.fit_pair(65536, 256)
     fit = {}
-    for tier in ("f64_df", "f64", "f32"):
+    for tier in ("f64_df", "f64_split", "f64", "f32"):
         dt = torch.float32 if tier == "f32" else torch.float64
         xt = torch.as_tensor(x0, device=dev, dtype=dt).requires_grad_(True)
         yt = torch.as_tensor(y0, device=dev, dtype=dt)

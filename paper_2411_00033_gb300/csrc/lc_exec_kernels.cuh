@@ -96,9 +96,6 @@ __device__ __forceinline__ const double& ahat_at<double>(const double* Ah, int64
 }
 
 constexpr int kThreads = 256;
-// Coarse chunks (few CTAs, many levels each) run with wide CTAs: more entries of
-// a level in flight per CTA, fewer barrier-separated rounds.
-constexpr int kWideThreads = 1024;
 // Chunk geometry (per plan, chosen by lc_plan_autotune; defaults 4 and 4):
 // leaf depth = levels climbed by the first up chunk / descended by the last
 // down chunk, chunk depth = levels per coarse chunk.
@@ -141,9 +138,8 @@ __device__ __forceinline__ void stage(int n, Ld ld, St st) {
 // ---------------------------------------------------------------- up chunk
 // Root x0 = blockIdx.x at level rho; bottom level rho + depth.  leaf != 0:
 // the bottom level is the leaf level, computed from the input (Step 1).
-template <typename R, bool wide = false>
-__global__ void __launch_bounds__(wide ? kWideThreads : kThreads) k_up_chunk(Args<R> a, int rho, int depth, int leaf,
-                                                                            int adj) {
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int depth, int leaf, int adj) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* nodes = reinterpret_cast<R*>(smem_raw);                 // (2^(depth+1) - 1) segments
   R* zt = nodes + sub_off(depth + 1);                         // 2 x 2^(depth-1) segments
@@ -191,10 +187,10 @@ __global__ void __launch_bounds__(wide ? kWideThreads : kThreads) k_up_chunk(Arg
       }
     } else {
       R* lev = nodes + sub_off(depth);
-      const R* Wl = Wb + (lc_seg_offset(gb) + (x0 << depth)) * kSeg;
-      stage<wide ? 4 : 1>(
-          nb * kSeg, [&](int t) { return node_valid(col, gb, (x0 << depth) + t / kSeg) ? Wl[t] : R(0); },
-          [&](int t, R v) { lev[t] = v; });
+      for (int t = threadIdx.x; t < nb * kSeg; t += blockDim.x) {
+        const int64_t x = (x0 << depth) + t / kSeg;
+        lev[t] = node_valid(col, gb, x) ? Wb[(lc_seg_offset(gb) + x) * kSeg + t % kSeg] : R(0);
+      }
     }
     for (int d = depth - 1; d >= 0; --d) {
       __syncthreads();
@@ -681,9 +677,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_near(Args<R> a, int adj) {
 // rows (forward) or columns (transposed) of the subtree and add the
 // near-field part that k_near has written to the output (Steps 6-7), or,
 // with fuse (batched plans), compute that part here as well.
-template <typename R, bool fuse, bool wide = false>
-__global__ void __launch_bounds__(wide ? kWideThreads : kThreads, wide ? 1 : (fuse ? 5 : 6))
-    k_down_chunk(Args<R> a, int rho, int depth, int fin, int adj) {
+template <typename R, bool fuse>
+__global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a, int rho, int depth, int fin, int adj) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ R Bs[LC_M * LC_M];
   const bool col = adj;  // forward: row tree; transposed: column tree
@@ -1039,10 +1034,10 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
       const int rho = roots[c];
       const int depth = roots[c - 1] - rho;
       const size_t sm = up_smem<R>(depth, s, 0);
-      lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_up_chunk<R, true>), sm);
+      lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_up_chunk<R>), sm);
       if (e != LC_OK) return e;
       lc_timer_mark(p, st, LC_K_UP);
-      k_up_chunk<R, true><<<dim3(unsigned(int64_t(4) << rho), gy), kWideThreads, sm, sk>>>(a, rho, depth, 0, adjoint);
+      k_up_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sk>>>(a, rho, depth, 0, adjoint);
       LC_LAUNCH_CHECK();
     }
     lc_timer_mark(p, st, LC_K_COUPLE);  // coupling of the coarse levels
@@ -1052,11 +1047,10 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
       const int rho = roots[c];
       const int depth = roots[c - 1] - 1 - rho;
       const size_t sm = down_smem<R>(depth, s, 0);
-      lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R, false, true>), sm);
+      lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R, false>), sm);
       if (e != LC_OK) return e;
       lc_timer_mark(p, st, LC_K_DOWN);
-      k_down_chunk<R, false, true><<<dim3(unsigned(int64_t(4) << rho), gy), kWideThreads, sm, sk>>>(a, rho, depth, 0,
-                                                                                                 adjoint);
+      k_down_chunk<R, false><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sk>>>(a, rho, depth, 0, adjoint);
       LC_LAUNCH_CHECK();
     }
     if (coarse_side) LC_CUDA_TRY(cudaEventRecord(p->ev_join, sk));
