@@ -329,6 +329,10 @@ def batched_leg(lc, dev, flush, args):
     for t in ("f64_split", "f64_df"):
         d = (outs_b[t] - ref).double()
         res[t + "_vs_f64_E2"] = float(torch.linalg.norm(d) / torch.linalg.norm(ref))
+        # per result: normwise error of every member against the FP64 tier
+        per = (torch.linalg.norm(d, dim=1) / torch.linalg.norm(ref.double(), dim=1)).cpu()
+        res[t + "_vs_f64_E2_per_member"] = {"max": float(per.max()), "median": float(per.median()),
+                                            "members": int(per.numel())}
     res["speedup_split_over_f64_batched"] = res["f64_split"]["coefficients_per_s"] / res["f64"]["coefficients_per_s"]
     res["f64_split_tensor_per_kernel"] = split_tensor_fractions(lc, dev, X, Z, n, B)
     out["uniform_65536x256_l2c"] = res
