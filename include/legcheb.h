@@ -29,9 +29,10 @@
  *    later call or synchronisation.
  *  - Work is enqueued on the caller's stream; no call synchronises the host
  *    except where stated.  lc_execute and lc_adjoint neither allocate nor
- *    synchronise; they may fork independent kernels onto a side stream owned
- *    by the plan and join it back (events) before their last kernel, so the
- *    caller sees ordinary stream order, also under stream capture.
+ *    synchronise; they may fork independent kernels onto streams owned by
+ *    the plan (at other priorities) and join them back (events) into the
+ *    caller's stream before returning, so the caller sees ordinary stream
+ *    order, also under stream capture.
  *  - One plan executes on one stream at a time: its intermediate arrays live
  *    in the plan workspace, so two executions of the same plan must not
  *    overlap on the device.

@@ -17,17 +17,20 @@
 // subtree of one node of a chunk's top level, so consecutive levels never
 // need a grid-wide barrier inside a chunk:
 //   up chunks (bottom to top): the first one restricts the input over
-//     2^5 leaf segments and climbs 5 levels; each later one climbs up to 4
-//     more levels from the previous chunk's top level;
+//     2^leaf_depth leaf segments and climbs leaf_depth levels (default 4);
+//     each later one climbs up to chunk_depth more levels;
 //   down chunks (top to bottom): each adds, level by level, the parent's
 //     contribution of Step 4 to the coupling result of Step 3; the last chunk
-//     ends at the leaves and also does the spread, the near-field band with
-//     its operands staged in shared memory, and the scaling.
-// After the first up chunk, the coarse levels' up chunks, their coupling and
-// their down chunks run on a high-priority side stream, concurrently with the
-// coupling of the fine levels on the caller's stream; the last down chunk
-// waits for both.  For L = 13 (n = 1e6): 8 launches instead of 2L+1 = 27,
-// with the coarse chain hidden behind the fine coupling.
+//     ends at the leaves, does the spread and adds it to the band's part;
+//   the band (k_near, Steps 6-7) needs only the input and lambda and runs
+//     beside the whole far-field chain for one vector (batches: inside the
+//     last down chunk).
+// One vector: the first up chunk, the coupling of the fine levels and the
+// last down chunk run on a plan stream; the coarse levels' up chunks, their
+// coupling and their down chunks on a higher-priority one once the first up
+// chunk is done; k_near on a lower-priority one from the start.  The last
+// down chunk waits for all three.  For L = 13 (n = 1e6): 9 launches instead
+// of 2L+2 = 28.
 //
 // The transposed pass (lc_adjoint) runs the same kernels with the roles of
 // the trees exchanged: restriction over row segments and the row tree
