@@ -217,7 +217,16 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
           // Algorithm a.1: b_kj times z0 on even k-j, z1 on odd k-j (two chains)
           const R* z0 = zt + j * kSeg + sigma * LC_M;
           const R* z1 = z0 + nd * kSeg;
-          for (int jj = 0; jj <= k; ++jj) acc = acc2(acc, Bt[jj * LC_M + k], ((k - jj) & 1) ? z1[jj] : z0[jj]);
+          if constexpr (eo_pairs<R>::value) {  // FP64 pipe: only the nonzero b_kj (j <= k)
+            for (int jj = 0; jj <= k; ++jj) acc = acc2(acc, Bt[jj * LC_M + k], ((k - jj) & 1) ? z1[jj] : z0[jj]);
+          } else {
+            // b_kj = 0 exactly for j > k, so all M terms, unrolled: the lanes of a
+            // warp (different k) run the same instructions, with no loop or select
+            const R* ze = (k & 1) ? z1 : z0;  // even j
+            const R* zo = (k & 1) ? z0 : z1;  // odd j
+#pragma unroll
+            for (int jj = 0; jj < LC_M; ++jj) acc = acc2(acc, Bt[jj * LC_M + k], (jj & 1) ? zo[jj] : ze[jj]);
+          }
           acc = finish(acc);
           Wb[(lc_seg_offset(gamma) + x) * kSeg + sigma * LC_M + k] = acc;
         }
@@ -691,8 +700,12 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
   R* nodes = reinterpret_cast<R*>(smem_raw);
   R* Ts = nodes + sub_off(depth + 1);
   __shared__ R par[kSeg];  // c of the root's parent
+  __shared__ R Bs1[eo_pairs<R>::value ? 1 : LC_M * LC_M];  // B(1): B(0) with odd diagonals negated
   constexpr int U = fuse ? 1 : 4;
-  stage<U>(LC_M * LC_M, [&](int i) { return a.t.B[i]; }, [&](int i, R v) { Bs[i] = v; });
+  stage<U>(LC_M * LC_M, [&](int i) { return a.t.B[i]; }, [&](int i, R v) {
+    Bs[i] = v;
+    if constexpr (!eo_pairs<R>::value) Bs1[i] = ((i / LC_M - i % LC_M) & 1) ? negate(v) : v;
+  });
   if (fin) stage<U>(2 * s * LC_M, [&](int i) { return a.t.T[i]; }, [&](int i, R v) { Ts[i] = v; });
   for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
     R* Cb = a.t.Cc + b * a.nseg * kSeg;
@@ -766,11 +779,10 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
             if (gamma > 0 && node_valid(col, gamma, x) && node_valid(col, gamma - 1, x >> 1)) {
               const R* pv = (d == 0) ? (fuse ? Cb + (lc_seg_offset(gamma - 1) + (x >> 1)) * kSeg : par) + sigma * LC_M
                                      : nodes + sub_off(d - 1) + (j >> 1) * kSeg + sigma * LC_M;
-              const bool odd = (x & 1) != 0;
-              for (int jj = k; jj < LC_M; ++jj) {
-                const R bjk = Bs[jj * LC_M + k];
-                c = acc2(c, (odd && ((jj - k) & 1)) ? negate(bjk) : bjk, pv[jj]);
-              }
+              // B(x mod 2); b_jk = 0 exactly for j < k, so all M terms, unrolled
+              const R* Bp = (x & 1) ? Bs1 : Bs;
+#pragma unroll
+              for (int jj = 0; jj < LC_M; ++jj) c = acc2(c, Bp[jj * LC_M + k], pv[jj]);
               c = finish(c);
             }
             lev[t] = c;
