@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
         if (node_valid(col, gb, x)) {
           const R* fseg = fs + j * 2 * s + sigma;
           const R* tcol = Ts + sigma * s * LC_M + k;
+#pragma unroll 4
           for (int m = 0; m < s; ++m) acc = acc2(acc, fseg[2 * m], tcol[m * LC_M]);
           acc = finish(acc);
           Wb[(lc_seg_offset(gb) + x) * kSeg + sigma * LC_M + k] = acc;
@@ -827,7 +828,7 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
           const R* c = leafc + t * kSeg + sigma * LC_M;
           const R* T0 = Ts + (sigma * s + m0) * LC_M;
           const R* T1 = (m0 + 1 < s) ? T0 + LC_M : T0;
-#pragma unroll 3
+#pragma unroll
           for (int k = 0; k < LC_M; ++k) {
             const R ck = c[k];
             far0 = acc2(far0, ck, T0[k]);
@@ -900,6 +901,7 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
           if (node_valid(col, L - 1, v)) {
             const R* c = leafc + strip * kSeg + sigma * LC_M;
             const R* Trow = Ts + (sigma * s + m) * LC_M;
+#pragma unroll
             for (int k = 0; k < LC_M; ++k) far = acc2(far, c[k], Trow[k]);
             far = finish(far);
           }
@@ -910,6 +912,7 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
             const int cnt = int((end - i + 1) >> 1);
             const R* fo = opnd + (i - olo);
             const R* lm = lamm + (i - mlo);
+#pragma unroll 4
             for (int kk = 0; kk < cnt; ++kk) near = acc3(near, lamk[kk], lm[kk], fo[2 * kk]);
             near = finish(near);
             if (l2c) {
@@ -926,6 +929,7 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
             const int cnt = int((i - st) / 2 + 1);
             const R* ro = opnd + (i - olo);  // ro[-2k] = row i - 2k
             const R* lm = lamm + (i - mlo);  // lm[-k]  = (r + i)/2 = i - k
+#pragma unroll 4
             for (int k = 0; k < cnt; ++k) near = acc3(near, lamk[k], lm[-k], ro[-2 * k]);
             near = finish(near);
             if (!l2c) {
