@@ -156,8 +156,9 @@ def test_fixed_s_option_same_map(lc):
 
 @pytest.mark.parametrize("tier", ["f64", "f64_df", "f32"])
 def test_graph_capture_of_cuda_core_tiers(lc, tier):
-    # lc_execute forks part of its work onto a plan-owned side stream and joins
-    # it back; under stream capture that fork/join becomes part of the graph.
+    # lc_execute / lc_adjoint fork the band and the coarse levels onto
+    # plan-owned streams and join them back; under stream capture that
+    # fork/join becomes part of the graph.
     n = 200000
     dev = torch.device("cuda", 0)
     dt = torch.float32 if tier == "f32" else torch.float64
@@ -175,6 +176,15 @@ def test_graph_capture_of_cuda_core_tiers(lc, tier):
     torch.cuda.synchronize()
     direct = plan(x).cpu().numpy()
     assert np.array_equal(z.cpu().numpy(), direct)
+    # the transposed pass as well
+    za = torch.empty_like(x)
+    ga = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(ga):
+        plan.execute(x, out=za, adjoint=True)
+    x.copy_(torch.as_tensor(workloads.decaying_vector(n, seed=10), device=dev, dtype=dt))
+    ga.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(za.cpu().numpy(), plan.execute(x, adjoint=True).cpu().numpy())
 
 
 @pytest.mark.parametrize("tier", ["f64", "f64_df"])
@@ -186,7 +196,7 @@ def test_chunk_geometry_does_not_change_results(lc, tier):
     for direction in ("l2c", "c2l"):
         plan = lc.Plan(n, direction, 1, tier, dev)
         ref = plan(x).cpu().numpy()
-        for leaf, chunk in ((1, 1), (3, 6), (5, 2), (6, 3)):
+        for leaf, chunk in ((1, 1), (3, 6), (5, 2), (6, 3), (4, 8)):
             plan.set_config(leaf, chunk)
             got = plan(x).cpu().numpy()
             assert np.array_equal(got, ref), (direction, leaf, chunk)
