@@ -39,6 +39,24 @@ __device__ double lc_Lambda(double z) {
   return f * tau / sqrt(y);
 }
 
+// The same series for the kernel samples inside A-hat (entries needed to a
+// block-relative 1e-14, not to a few ulp): one reciprocal square root gives
+// both y^(-1/2) and x = y^(-2), instead of two divisions and a square root.
+__device__ double lc_Lambda_sample(double z) {
+  double f = 1.0;
+  while (z < 20.0) {
+    f *= (z + 1.0) / (z + 0.5);
+    z += 1.0;
+  }
+  const double y = z + 0.25;
+  const double r = rsqrt(y);
+  const double r2 = r * r;
+  const double x = r2 * r2;
+  const double tau =
+      1.0 + x * (-1.0 / 64.0 + x * (21.0 / 8192.0 + x * (-671.0 / 524288.0 + x * (180323.0 / 134217728.0))));
+  return f * tau * r;
+}
+
 __global__ void k_plan_lambda(int64_t N, double* __restrict__ lam) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t i0 = 8 * t;
@@ -91,16 +109,23 @@ __global__ void k_plan_T(int s, double* __restrict__ T) {
 
 // B(0) by the exact row recurrence (one thread; M^2 work).
 __global__ void k_plan_B(double* __restrict__ B) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int i = 0; i < LC_M * LC_M; ++i) B[i] = 0.0;
-  B[0] = 1.0;          // T_0(u) = 1
-  B[LC_M + 0] = -0.5;  // T_1(u) = u = Y/2 - 1/2
-  B[LC_M + 1] = 0.5;
+  // One warp: row k+1 from rows k and k-1, entry i per lane (rows are
+  // independent across i, sequential in k).
+  const int i = threadIdx.x;
+  if (blockIdx.x != 0 || i >= 32) return;
+  for (int t = i; t < LC_M * LC_M; t += 32) B[t] = 0.0;
+  __syncwarp();
+  if (i == 0) {
+    B[0] = 1.0;          // T_0(u) = 1
+    B[LC_M + 0] = -0.5;  // T_1(u) = u = Y/2 - 1/2
+    B[LC_M + 1] = 0.5;
+  }
+  __syncwarp();
   for (int k = 1; k + 1 < LC_M; ++k) {
     const double* bk = B + k * LC_M;
     const double* bm = B + (k - 1) * LC_M;
     double* bn = B + (k + 1) * LC_M;
-    for (int i = 0; i <= k + 1; ++i) {
+    if (i <= k + 1) {
       // Y * T_k(u) expanded in T_j(Y): T_0 -> T_1, T_j -> (T_{j+1} + T_{j-1})/2.
       double y = 0.0;
       if (i == 1) y += bk[0];
@@ -111,6 +136,7 @@ __global__ void k_plan_B(double* __restrict__ B) {
       const double prev = (i <= k - 1) ? bm[i] : 0.0;
       bn[i] = y - own - prev;
     }
+    __syncwarp();
   }
 }
 
@@ -169,7 +195,7 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
     const double* lm = lminus + (size_t(gamma) * 2 + (r == 1 ? 1 : 0)) * (LC_M * LC_M);
     __syncthreads();
     if (r0 <= c0) {  // Lambda((x_m + y_n)/2), symmetric in (m, n)
-      const double lp = lc_Lambda(0.5 * (i0 + j0 + h * (cs[1][r0] + cs[1][c0] + 2.0)));
+      const double lp = lc_Lambda_sample(0.5 * (i0 + j0 + h * (cs[1][r0] + cs[1][c0] + 2.0)));
       S[r0][c0] = lp;
       S[c0][r0] = lp;
     }
@@ -181,9 +207,8 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
       double val;
       if (dir == LC_L2C) {
         val = lmi * S[r0][c0];  // A(x, y) = Lambda((y-x)/2) Lambda((y+x)/2)
-      } else {                  // L(x, y) of eq:Lxymod
-        const double pre = 2.0 * (x + 0.5) * y / ((x + y) * (x + y + 1.0) * (x - y + 1.0));
-        val = pre * lmi / S[r0][c0];
+      } else {                  // L(x, y) of eq:Lxymod (one division)
+        val = 2.0 * (x + 0.5) * y * lmi / ((x + y) * (x + y + 1.0) * (x - y + 1.0) * S[r0][c0]);
       }
       __syncthreads();
       S[r0][c0] = val;
