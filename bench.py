@@ -345,10 +345,18 @@ def batched_leg(lc, dev, flush, args):
     plan = lc.Plan(direction="l2c", dtype="f64_split", device=dev, lengths=lengths)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
+    # leaf tile s picked by the autotuner (plan-time, untimed like the plan itself)
+    tplan, tile_s, tile_ms = lc.autotune_tile(x, "l2c", "f64_split", dev, lengths=lengths)
+    if tile_ms[tile_s] < tile_ms.get(32, float("inf")):
+        plan = tplan
+    else:
+        tile_s = 32
     step = graph_step(lambda: plan(x, out=z))
     ms = time_fn(step, flush, steps, 2)
     out["ragged_4096_l2c"] = {"coefficients_per_s": float(lengths.sum()) / (ms / 1e3), "ms": ms,
-                              "coefficients": int(lengths.sum()), "plan_s": plan_s, "launches": plan.launches()}
+                              "coefficients": int(lengths.sum()), "plan_s": plan_s, "launches": plan.launches(),
+                              "leaf_tile_s": tile_s, "autotune_ms_per_s": tile_ms}
+    del tplan
     del plan, x, z
     # (b') the plain per-vector FP64 and double-float paths on a sample of 128 members
     sample = np.random.default_rng(6).choice(len(lengths), 128, replace=False)

@@ -9,7 +9,7 @@ from .binding import (  # noqa: F401
     lc_plan_workspace_size, lc_plan_create, lc_plan_workspace_size_ragged, lc_plan_create_ragged,
     lc_execute, lc_adjoint, lc_destroy, lc_status_string, lc_plan_info, lc_plan_table, lc_plan_launches,
 )
-from .api import Plan, get_plan  # noqa: F401
+from .api import Plan, get_plan, autotune_tile  # noqa: F401
 from .autograd import leg2cheb, cheb2leg  # noqa: F401
 
 binding.load()

@@ -178,3 +178,48 @@ def cheb2leg(x: torch.Tensor, dtype: str | None = None, **options) -> torch.Tens
     dtype = dtype or ("f32" if x.dtype == torch.float32 else "f64")
     batch = 1 if x.dim() == 1 else x.shape[0]
     return get_plan(x.shape[-1], "c2l", batch, dtype, x.device, **options)(x)
+
+
+# -------------------------------------------------- leaf tile size autotuner
+_TILE_CACHE: dict = {}
+
+
+def autotune_tile(x: torch.Tensor, direction: str = "l2c", dtype: str = "f64_split", device=None, lengths=None,
+                  n: int | None = None, batch: int = 1, candidates=(16, 20, 24, 28, 32), reps: int = 3,
+                  **options):
+    """Pick the leaf segment size s -- the tile every level inherits (level gamma
+    works on blocks of h = s 2^(L-gamma-1) coefficients) -- for a plan shape by
+    timing: one plan per candidate s (option fixed_s), `reps` executions on x
+    each after a warm-up, the fastest kept.  Every s gives the same linear map;
+    s changes the padding to N = s 2^(L+2), the number of levels and the block
+    shapes.  Returns (plan, s, {s: ms per execution}).  The choice is cached
+    per (lengths or (n, batch), direction, dtype) for later calls."""
+    key = (tuple(int(v) for v in lengths) if lengths is not None else (int(n), int(batch)), direction, dtype)
+    dev = torch.device(device) if device is not None else x.device
+    if key in _TILE_CACHE:
+        s = _TILE_CACHE[key][0]
+        plan = Plan(n, direction, batch, dtype, dev, lengths=lengths, fixed_s=s, **options)
+        return plan, s, dict(_TILE_CACHE[key][1])
+    times = {}
+    best = None
+    for s in candidates:
+        plan = Plan(n, direction, batch, dtype, dev, lengths=lengths, fixed_s=int(s), **options)
+        out = torch.empty_like(x)
+        plan(x, out=out)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            plan(x, out=out)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        times[int(s)] = e0.elapsed_time(e1) / reps
+        if best is None or times[int(s)] < times[best[0]]:
+            if best is not None:
+                best[1].close()
+            best = (int(s), plan)
+        else:
+            plan.close()
+    _TILE_CACHE[key] = (best[0], dict(times))
+    return best[1], best[0], times

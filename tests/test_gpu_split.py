@@ -181,3 +181,22 @@ def test_split_adjoint_dot_test_and_strides(lc):
         plan.execute_strided(yt, out, (1, batch), (n, 1), adjoint=True)
         e = ((out - aty).norm() / aty.norm()).item()
         assert e <= 1e-15, (direction, e)
+
+
+def test_leaf_tile_autotuner(lc):
+    # Every leaf tile s gives the same transform: the tuned plan matches the oracle.
+    lengths = [1, 64, 129, 700, 1000, 2500, 4096, 5000]
+    x = workloads.ragged_batch(lengths, seed=12)
+    offs = workloads.ragged_offsets(lengths)
+    dev = torch.device("cuda", 0)
+    xt = torch.as_tensor(x, device=dev)
+    plan, s, times = lc.autotune_tile(xt, "c2l", "f64_split", dev, lengths=lengths, candidates=(16, 24, 32), reps=1)
+    assert s in (16, 24, 32) and set(times) == {16, 24, 32}
+    assert plan.info["s"] == s
+    z = plan(xt).cpu().numpy()
+    for i in range(len(lengths)):
+        a, b = offs[i], offs[i + 1]
+        e2, _ = rel_errors(z[a:b], oracle.apply(oracle.C2L, x[a:b]))
+        assert e2 <= 1e-12, (i, s, e2)
+    again, s2, _ = lc.autotune_tile(xt, "c2l", "f64_split", dev, lengths=lengths, candidates=(16, 24, 32))
+    assert s2 == s and again.info["s"] == s
