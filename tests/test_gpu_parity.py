@@ -108,6 +108,26 @@ def test_batched_strided_fibres(lc, direction, code, tier):
 
 
 @pytest.mark.parametrize("tier", ["f64", "f64_df"])
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_single_vector_element_strides(lc, direction, code, tier, adjoint):
+    # one vector (the band runs as its own kernel) read with element stride 3
+    # and written with element stride 2
+    n = 20011
+    x = _input(n, seed=55)
+    dev = torch.device("cuda", 0)
+    xs = torch.zeros(3 * n, dtype=torch.float64, device=dev)
+    xs[::3] = torch.as_tensor(x, device=dev)
+    out = torch.full((2 * n,), 7.0, dtype=torch.float64, device=dev)
+    plan = lc.Plan(n, direction, 1, tier, dev)
+    plan.execute_strided(xs, out, (0, 3), (0, 2), adjoint=adjoint)
+    z = out.cpu().numpy()
+    assert np.all(z[1::2] == 7.0)  # untouched between the strided outputs
+    e2, _ = rel_errors(z[::2], oracle.apply(code, x, adjoint=adjoint))
+    assert e2 <= 1e-13, e2
+
+
+@pytest.mark.parametrize("tier", ["f64", "f64_df"])
 @pytest.mark.parametrize("n", [1, 2, 100, 129, 1024, 5000])
 @pytest.mark.parametrize("direction,code", DIRS)
 def test_adjoint_matches_oracle_transpose(lc, n, direction, code, tier):
