@@ -78,14 +78,32 @@ template <>
 struct eo_pairs<double> { static constexpr bool value = true; };
 
 // Dot-product accumulation.  Generic: fused multiply-add in R.  The
-// double-float tier specialises these to keep an unnormalised error word and
-// normalise once at the end (see lc_df.cu).
+// double-float tier specialises these to keep an unnormalised error word,
+// which finish() folds back into the leading word (see lc_df.cu).  Sums of
+// more than a few terms call finish() every few terms as well: the error
+// word's own FP32 rounding grows with its size, and an error word left to
+// collect 60 terms (a long band row) costs about 2e-13 relative.
 template <typename R>
 __device__ __forceinline__ R acc2(const R& acc, const R& a, const R& b) { return fma(a, b, acc); }
 template <typename R>
 __device__ __forceinline__ R acc3(const R& acc, const R& a, const R& b, const R& c) { return fma(a * b, c, acc); }
 template <typename R>
 __device__ __forceinline__ R finish(const R& acc) { return acc; }
+// sum_{k < cnt} of the terms that step(acc, k) accumulates, renormalised
+// every 4 terms.
+template <typename R, typename F>
+__device__ __forceinline__ R band_sum(int cnt, F&& step) {
+  R acc = R(0);
+  int k = 0;
+#pragma unroll 1
+  for (; k + 4 <= cnt; k += 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc = step(acc, k + q);
+    acc = finish(acc);
+  }
+  for (; k < cnt; ++k) acc = step(acc, k);
+  return finish(acc);
+}
 // A-hat(m)[k][l]: the FP64 table keeps row-major [k][l]; the FP32 and
 // double-float copies are stored transposed, [l][k], so that threads that
 // own consecutive k read consecutive addresses.
@@ -377,7 +395,8 @@ __device__ __forceinline__ int pad_index(int64_t x, int64_t two_s, int pad) {
 // Forward rows i and i + 2 of one parity: row i + 2r takes, at step k, the
 // entry factors lamk[k] and lm[2r + k] (lambda_k, lambda_(i+2r+k), or u, v
 // for C2L) and the operand fo[2(r + k)].  Row i has cnt >= 1 terms, row i + 2
-// one fewer.  fwd_steps runs steps [k, kend) two at a time with the operand
+// one fewer.  fwd_steps runs steps [k, kend) two at a time (renormalising
+// the sums after every second pair of steps) with the operand
 // and lambda tiles fp, lp; the values of row i + 2 at step k are those of row
 // i at steps k + 1 and k + 2, kept in registers (f0, l0, l1) from step to step.
 template <typename R>
@@ -389,8 +408,9 @@ __device__ __forceinline__ void fwd_steps(const R* __restrict__ lamk, const R* _
   const R* pk = lamk + kk;
   const R* pf = fp + 2 * kk;
   const R* pl = lp + kk;
-#pragma unroll 1
-  for (; kk + 2 <= kend; kk += 2, pk += 2, pf += 4, pl += 2) {
+  int it = 0;
+#pragma unroll 2
+  for (; kk + 2 <= kend; kk += 2, pk += 2, pf += 4, pl += 2, ++it) {
     const R k0 = pk[0], k1 = pk[1];
     const R F1 = pf[2], F2 = pf[4];
     const R L2 = pl[2], L3 = pl[3];
@@ -398,6 +418,10 @@ __device__ __forceinline__ void fwd_steps(const R* __restrict__ lamk, const R* _
     A1 = acc3(A1, k0, L2, F1);
     A0 = acc3(A0, k1, L1, F1);
     A1 = acc3(A1, k1, L3, F2);
+    if (it & 1) {
+      A0 = finish(A0);
+      A1 = finish(A1);
+    }
     F0 = F2;
     L0 = L2;
     L1 = L3;
@@ -453,8 +477,9 @@ __device__ __forceinline__ void adj_steps(const R* __restrict__ lamk, const R* _
   const R* pk = lamk + kk;
   const R* pg = rp - 2 * kk;
   const R* pl = lp - kk;
-#pragma unroll 1
-  for (; kk + 2 <= kend; kk += 2, pk += 2, pg -= 4, pl -= 2) {
+  int it = 0;
+#pragma unroll 2
+  for (; kk + 2 <= kend; kk += 2, pk += 2, pg -= 4, pl -= 2, ++it) {
     const R k0 = pk[0], k1 = pk[1];
     const R G0 = pg[0], Gm = pg[-2];
     const R L0 = pl[0], Lm = pl[-1];
@@ -462,6 +487,10 @@ __device__ __forceinline__ void adj_steps(const R* __restrict__ lamk, const R* _
     A1 = acc3(A1, k0, L2, G1);
     A0 = acc3(A0, k1, Lm, Gm);
     A1 = acc3(A1, k1, L1, G0);
+    if (it & 1) {
+      A0 = finish(A0);
+      A1 = finish(A1);
+    }
     G1 = Gm;
     L2 = L0;
     L1 = Lm;
@@ -589,8 +618,7 @@ __device__ __forceinline__ void near_tile(const Args<R>& a, int64_t b, int64_t l
         const int cnt = int((a.n - i + 1) >> 1);
         const R* fo = opnd + (i - olo);
         const R* lm = lamm + (i - mlo);
-        for (int kk = 0; kk < cnt; ++kk) near = acc3(near, lamk[kk], lm[kk], fo[2 * kk]);
-        near = finish(near);
+        near = band_sum<R>(cnt, [&](const R& c, int kk) { return acc3(c, lamk[kk], lm[kk], fo[2 * kk]); });
         if (l2c) {
           near = cinv<R>(i) * near;
         } else {
@@ -601,8 +629,7 @@ __device__ __forceinline__ void near_tile(const Args<R>& a, int64_t b, int64_t l
         const int cnt = int(i / 2 + 1);
         const R* ro = opnd + (i - olo);
         const R* lm = lamm + (i - mlo);
-        for (int k = 0; k < cnt; ++k) near = acc3(near, lamk[k], lm[-k], ro[-2 * k]);
-        near = finish(near);
+        near = band_sum<R>(cnt, [&](const R& c, int k) { return acc3(c, lamk[k], lm[-k], ro[-2 * k]); });
         if (!l2c) {
           near = R(i) * near;
           if (i == 0) near += lc_ld<R>(f);
@@ -912,9 +939,7 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
             const int cnt = int((end - i + 1) >> 1);
             const R* fo = opnd + (i - olo);
             const R* lm = lamm + (i - mlo);
-#pragma unroll 4
-            for (int kk = 0; kk < cnt; ++kk) near = acc3(near, lamk[kk], lm[kk], fo[2 * kk]);
-            near = finish(near);
+            near = band_sum<R>(cnt, [&](const R& c, int kk) { return acc3(c, lamk[kk], lm[kk], fo[2 * kk]); });
             if (l2c) {
               res = cinv<R>(i) * (far + near);
             } else {
@@ -929,9 +954,7 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
             const int cnt = int((i - st) / 2 + 1);
             const R* ro = opnd + (i - olo);  // ro[-2k] = row i - 2k
             const R* lm = lamm + (i - mlo);  // lm[-k]  = (r + i)/2 = i - k
-#pragma unroll 4
-            for (int k = 0; k < cnt; ++k) near = acc3(near, lamk[k], lm[-k], ro[-2 * k]);
-            near = finish(near);
+            near = band_sum<R>(cnt, [&](const R& c, int k) { return acc3(c, lamk[k], lm[-k], ro[-2 * k]); });
             if (!l2c) {
               near = R(i) * near;
               if (i == 0) near += lc_ld<R>(f);

@@ -58,6 +58,36 @@ def test_f64_matches_oracle(lc, n, direction, code, tier):
     assert einf <= (1e-13 if code == oracle.L2C else 3e-13), (n, direction, e2, einf)
 
 
+_R1_MEMBERS = (25, 65)
+_R1_REFS = {}
+
+
+def _r1_case(code):
+    """Members 25 and 65 of the n = 65536, r = 1, seed 5 batch, with oracle results."""
+    X = workloads.decaying_vector(65536, seed=5, r=1.0, batch=max(_R1_MEMBERS) + 1)[list(_R1_MEMBERS)]
+    if code not in _R1_REFS:
+        _R1_REFS[code] = np.stack([oracle.apply(code, x) for x in X])
+    return X, _R1_REFS[code]
+
+
+@pytest.mark.parametrize("batched", [False, True])
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_df_long_band_rows_r1_input(lc, direction, code, batched):
+    """Double-float band rows of about 2s = 62 terms on an r = 1 input, whose
+    first rows take the largest coefficients: within 1e-13 of the oracle.  Of
+    the 256 vectors of this batch these two drew the largest errors (1.4e-13
+    and 9.7e-14) with band sums whose error words collect all 62 terms before
+    being folded back; folding every 4 terms keeps them near 3e-14."""
+    X, refs = _r1_case(code)
+    if batched:
+        Z, _ = _run(lc, X, direction, dtype="f64_df", batch=len(X))
+    else:
+        Z = np.stack([_run(lc, x, direction, dtype="f64_df")[0] for x in X])
+    for m, z, ref in zip(_R1_MEMBERS, Z, refs):
+        e2, einf = rel_errors(z, ref)
+        assert e2 <= 1e-13 and einf <= 1e-13, (m, direction, batched, e2, einf)
+
+
 @pytest.mark.parametrize("tier", ["f64", "f64_df"])
 @pytest.mark.parametrize("direction,code", DIRS)
 def test_config_n1024_uniform(lc, direction, code, tier):
