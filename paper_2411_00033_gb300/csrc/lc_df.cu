@@ -1,7 +1,8 @@
 // lc_df.cu -- LC_F64_DF: FP64 input and output, Algorithm 4 in double-float
 // arithmetic on the FP32 pipe (the kernels of lc_exec_kernels.cuh with
 // R = lc_df).  The plan tables are rounded once from the FP64 plan to
-// double-float pairs.
+// double-float pairs; A-hat keeps the trailing FP32 word only where the
+// entry needs it (the compact layout of lc_internal.cuh).
 #include "lc_df.cuh"
 #include "lc_exec_kernels.cuh"
 
@@ -53,6 +54,8 @@ template <>
 __device__ __forceinline__ lc_df finish<lc_df>(const lc_df& acc) {
   return lc_df_fast2(acc.hi, acc.lo);
 }
+template <>
+struct compact_ahat<lc_df> { static constexpr bool value = true; };
 }  // namespace lc_exec
 
 using namespace lc_exec;
@@ -65,8 +68,12 @@ __global__ void k_d2df(int64_t n, const double* __restrict__ a, lc_df* __restric
     b[i] = lc_df(h, float(x - double(h)));
   }
 }
-// A-hat copies for the double-float tier are stored transposed, [m][l][k].
-__global__ void k_d2df_T(int64_t nm, const double* __restrict__ a, lc_df* __restrict__ b) {
+// A-hat for the double-float tier in the compact layout of lc_internal.cuh:
+// one thread per entry of the FP64 table (row-major [m][k][l]); the spare
+// words at the end of each matrix are zeroed.
+__global__ void k_d2df_compact(int64_t nm, int head, int words, const double* __restrict__ a,
+                               float* __restrict__ b) {
+  const int used = LC_M * LC_M + lc_dfa_rowstart(head + 1, head);
   const int64_t total = nm * LC_M * LC_M;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t m = i / (LC_M * LC_M);
@@ -74,7 +81,10 @@ __global__ void k_d2df_T(int64_t nm, const double* __restrict__ a, lc_df* __rest
     const int k = r / LC_M, l = r % LC_M;
     const double x = a[i];
     const float h = float(x);
-    b[m * (LC_M * LC_M) + l * LC_M + k] = lc_df(h, float(x - double(h)));
+    float* d = b + m * words;
+    d[r] = h;
+    if (k + l <= head) d[LC_M * LC_M + lc_dfa_rowstart(k, head) + l] = float(x - double(h));
+    if (r < words - used) d[used + r] = 0.0f;
   }
 }
 unsigned blocks_for(int64_t n) {
@@ -93,8 +103,9 @@ lc_status lc_df_prepare(lc_plan p, cudaStream_t st) {
   if (p->dir == LC_C2L) k_d2df<<<blocks_for(g.N), 256, 0, st>>>(g.N, p->lam2, static_cast<lc_df*>(p->df_lam2));
   k_d2df<<<1, 256, 0, st>>>(int64_t(2) * g.s * LC_M, p->T, static_cast<lc_df*>(p->df_T));
   k_d2df<<<1, 256, 0, st>>>(LC_M * LC_M, p->B, static_cast<lc_df*>(p->df_B));
-  if (g.nc > 0) k_d2df_T<<<blocks_for(g.nc * LC_M * LC_M), 256, 0, st>>>(g.nc, p->Ahat,
-                                                                        static_cast<lc_df*>(p->df_Ahat));
+  if (g.nc > 0)
+    k_d2df_compact<<<blocks_for(g.nc * LC_M * LC_M), 256, 0, st>>>(
+        g.nc, lc_dfa_head(p->dir), lc_dfa_words(p->dir), p->Ahat, static_cast<float*>(p->df_Ahat));
   LC_LAUNCH_CHECK();
   return LC_OK;
 }

@@ -76,6 +76,10 @@ template <typename R>
 struct eo_pairs { static constexpr bool value = false; };
 template <>
 struct eo_pairs<double> { static constexpr bool value = true; };
+// A-hat in the compact double-float layout of lc_internal.cuh (leading words
+// of all entries, trailing words of the k + l <= head triangle only).
+template <typename R>
+struct compact_ahat { static constexpr bool value = false; };
 
 // Dot-product accumulation.  Generic: fused multiply-add in R.  The
 // double-float tier specialises these to keep an unnormalised error word,
@@ -104,9 +108,10 @@ __device__ __forceinline__ R band_sum(int cnt, F&& step) {
   for (; k < cnt; ++k) acc = step(acc, k);
   return finish(acc);
 }
-// A-hat(m)[k][l]: the FP64 table keeps row-major [k][l]; the FP32 and
-// double-float copies are stored transposed, [l][k], so that threads that
-// own consecutive k read consecutive addresses.
+// A-hat(m)[k][l]: the FP64 table keeps row-major [k][l]; the FP32 copy is
+// stored transposed, [l][k], so that threads that own consecutive k read
+// consecutive addresses.  (The double-float copy is compact, read by the
+// coupling kernel directly.)
 template <typename R>
 __device__ __forceinline__ const R& ahat_at(const R* Ah, int64_t m, int k, int l) {
   return Ah[m * (LC_M * LC_M) + l * LC_M + k];
@@ -266,12 +271,90 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
 //     c(2b+2) = A(b,0)^T w(2b),  c(2b+3) = A(b,1)^T w(2b) + A(b,2)^T w(2b+1).
 constexpr int kCBlocks = 7;
 
+// Step 3 products of one CTA's group of nb blocks from the compact
+// double-float A-hat (layout in lc_internal.cuh) staged at Af.  Thread item
+// (q, jb, sigma): q is the row k of A-hat (forward) or its column l
+// (transposed), consecutive threads take consecutive (block jb, parity
+// sigma) with the same q, so that a warp shares the split point: the terms
+// with k + l <= head in double-float, the rest as FP32 products of the
+// leading words, gathered in an FP32 sum that joins the error word.
+template <typename R>
+__device__ __forceinline__ void couple_compact(const Args<R>& a, int adj, int nb, int64_t b0, const float* Af,
+                                               const R* Ws, R* Cl) {
+  const int head = lc_dfa_head(a.dir);
+  const int mw = lc_dfa_words(a.dir);
+  const int pairs = 2 * nb;
+  for (int t = threadIdx.x; t < nb * kSeg; t += blockDim.x) {
+    const int q = t / pairs;
+    const int jb = (t % pairs) >> 1, sigma = t & 1;
+    const float* A0 = Af + 3 * jb * mw;   // A(b,0); A(b,1), A(b,2) follow at mw, 2 mw
+    const float* L0 = A0 + LC_M * LC_M;   // trailing words
+    const R* w0 = Ws + (2 * jb) * kSeg + sigma * LC_M;
+    const R* w1 = w0 + kSeg;
+    const int nd = head + 1 - q > 0 ? head + 1 - q : 0;  // double-float terms of row/column q
+    R c0 = R(0), c0b = R(0), c1 = R(0);
+    float e0 = 0.0f, e0b = 0.0f, e1 = 0.0f;
+    if (!adj) {
+      // c(2b) = A(b,0) w(2b+2) + A(b,1) w(2b+3);  c(2b+1) = A(b,2) w(2b+3)
+      const float* h = A0 + q * LC_M;
+      const float* lo = L0 + lc_dfa_rowstart(q, head);
+      int l = 0;
+      for (; l < nd; ++l) {
+        const R wa = w0[l], wb = w1[l];
+        c0 = acc2(c0, R(h[l], lo[l]), wa);
+        c0b = acc2(c0b, R(h[mw + l], lo[mw + l]), wb);
+        c1 = acc2(c1, R(h[2 * mw + l], lo[2 * mw + l]), wb);
+      }
+      for (; l < LC_M; ++l) {
+        const float wa = w0[l].hi, wb = w1[l].hi;
+        e0 = fmaf(h[l], wa, e0);
+        e0b = fmaf(h[mw + l], wb, e0b);
+        e1 = fmaf(h[2 * mw + l], wb, e1);
+      }
+      R* out = Cl + (2 * (b0 + jb)) * kSeg + sigma * LC_M + q;
+      out[0] = finish(R(c0.hi, c0.lo + e0)) + finish(R(c0b.hi, c0b.lo + e0b));
+      out[kSeg] = finish(R(c1.hi, c1.lo + e1));
+    } else {
+      // c(2b+2) = A(b,0)^T w(2b);  c(2b+3) = A(b,1)^T w(2b) + A(b,2)^T w(2b+1)
+      const float* h = A0 + q;
+      int k = 0, rs = q;  // rs: trailing-word index of entry (k, q)
+      for (; k < nd; ++k) {
+        const R wa = w0[k], wb = w1[k];
+        c0 = acc2(c0, R(h[k * LC_M], L0[rs]), wa);
+        c1 = acc2(c1, R(h[mw + k * LC_M], L0[mw + rs]), wa);
+        c0b = acc2(c0b, R(h[2 * mw + k * LC_M], L0[2 * mw + rs]), wb);
+        rs += head + 1 - k;
+      }
+      for (; k < LC_M; ++k) {
+        const float wa = w0[k].hi, wb = w1[k].hi;
+        e0 = fmaf(h[k * LC_M], wa, e0);
+        e1 = fmaf(h[mw + k * LC_M], wa, e1);
+        e0b = fmaf(h[2 * mw + k * LC_M], wb, e0b);
+      }
+      R* out = Cl + (2 * (b0 + jb) + 2) * kSeg + sigma * LC_M + q;
+      out[0] = finish(R(c0.hi, c0.lo + e0));
+      out[kSeg] = finish(R(c1.hi, c1.lo + e1)) + finish(R(c0b.hi, c0b.lo + e0b));
+    }
+  }
+}
+
+// Bytes of one A-hat matrix as the coupling kernel stages it.
+template <typename R>
+__host__ __device__ inline size_t ahat_matrix_bytes(int dir) {
+  return compact_ahat<R>::value ? size_t(lc_dfa_words(dir)) * sizeof(float) : size_t(LC_M) * LC_M * sizeof(R);
+}
+template <typename R>
+inline size_t couple_smem(int dir) {
+  return 3 * kCBlocks * ahat_matrix_bytes<R>(dir) + size_t(2) * kCBlocks * kSeg * sizeof(R) + 16;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, int g_lo, int g_hi) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
-  R* As = reinterpret_cast<R*>(smem_raw);          // [3 kCBlocks][M][M]
-  R* Ws = As + 3 * kCBlocks * LC_M * LC_M;          // [2 kCBlocks][2][M]
+  const size_t mat = ahat_matrix_bytes<R>(a.dir);
+  R* As = reinterpret_cast<R*>(smem_raw);                                // [3 kCBlocks] matrices
+  R* Ws = reinterpret_cast<R*>(smem_raw + 3 * kCBlocks * mat);           // [2 kCBlocks][2][M]
   // locate (level, first block) of this CTA among levels [g_lo, g_hi)
   int gamma = g_lo;
   int64_t first = blockIdx.x, per;
@@ -286,7 +369,7 @@ __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, 
   const int nb = int(nblk - b0 < kCBlocks ? nblk - b0 : kCBlocks);
   if (nb <= 0) return;
   const int64_t m0 = lc_ahat_offset(gamma) + 3 * b0;
-  const uint32_t bytesA = uint32_t(3 * nb * LC_M * LC_M * sizeof(R));
+  const uint32_t bytesA = uint32_t(3 * nb * mat);
   const uint32_t bytesW = uint32_t(2 * nb * kSeg * sizeof(R));
   const uint32_t mb = uint32_t(__cvta_generic_to_shared(&mbar));
   if (threadIdx.x == 0) {
@@ -304,7 +387,8 @@ __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, 
       lc_fence_proxy_async();
       const uint32_t bytes = bytesW + (loadA ? bytesA : 0u);
       lc_mbar_expect(mb, bytes);
-      if (loadA && !(a.t.debug & 1)) lc_bulk_g2s(As, a.t.Ahat + m0 * (LC_M * LC_M), bytesA, mb);
+      if (loadA && !(a.t.debug & 1))
+        lc_bulk_g2s(As, reinterpret_cast<const unsigned char*>(a.t.Ahat) + m0 * mat, bytesA, mb);
       lc_bulk_g2s(Ws, Wl + s0 * kSeg, bytesW, mb);
     }
     bool ok = lc_mbar_wait_bounded(mb, phase);
@@ -316,6 +400,9 @@ __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, 
       return;
     }
     phase ^= 1u;
+    if constexpr (compact_ahat<R>::value) {
+      couple_compact(a, adj, nb, b0, reinterpret_cast<const float*>(As), Ws, Cl);
+    } else {
     for (int t = threadIdx.x; t < nb * kSeg; t += blockDim.x) {
       const int jb = t / kSeg;                  // block within the group
       const int sigma = (t % kSeg) / LC_M, k = t % LC_M;
@@ -346,6 +433,7 @@ __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, 
         out[0] = finish(c0);
         out[kSeg] = finish(c1) + finish(c0b);
       }
+    }
     }
   }
 }
@@ -1016,7 +1104,7 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
   }
   int roots[64], nr;
   chunk_roots<R>(L, p->leaf_depth, p->chunk_depth, roots, &nr);
-  const size_t smc = (size_t(3) * kCBlocks * LC_M * LC_M + size_t(2) * kCBlocks * kSeg) * sizeof(R) + 16;
+  const size_t smc = couple_smem<R>(a.dir);
   {
     lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_couple_blocks<R>), smc);
     if (e != LC_OK) return e;

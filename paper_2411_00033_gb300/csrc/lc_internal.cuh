@@ -41,6 +41,22 @@ __host__ __device__ inline int64_t lc_ahat_offset(int gamma) {
   return 3 * ((int64_t(1) << (gamma + 1)) - 2 - gamma);
 }
 
+// Compact double-float A-hat.  Each M x M matrix keeps the FP32 leading
+// words of all entries, row-major [k][l], followed by the FP32 trailing
+// words of the entries with k + l <= head, row by row (row k holds
+// l = 0 .. head - k).  The entries of A-hat are the 2-D Chebyshev
+// coefficients of a kernel that is smooth across the well-separated blocks,
+// so they fall off geometrically in k + l (by about 4x per step for L2C,
+// 3x for C2L); beyond the head every entry is below 2e-9 of the matrix's
+// largest for every block size and level, and its leading word alone is
+// accurate to 1e-16 of that.  Words per matrix: a multiple of 4 (16-byte
+// bulk copies) with the 3 matrices of a block 28 (L2C) or 12 (C2L) words
+// mod 32 apart, so that the blocks staged by one CTA start in distinct
+// shared-memory banks.
+__host__ __device__ constexpr int lc_dfa_head(int dir) { return dir == LC_L2C ? 13 : 16; }
+__host__ __device__ constexpr int lc_dfa_words(int dir) { return dir == LC_L2C ? 436 : 484; }
+__host__ __device__ constexpr int lc_dfa_rowstart(int k, int head) { return k * (head + 1) - k * (k - 1) / 2; }
+
 // Device views of a plan's tables, by element type.
 template <typename R>
 struct lc_tables {

@@ -336,7 +336,7 @@ size_t layout(lc_plan_s* p, char* base) {
     p->df_lam2 = (p->dir == LC_C2L) ? c.take<char>(N * f2) : p->df_lam;
     p->df_T = c.take<char>(size_t(2) * g.s * LC_M * f2);
     p->df_B = c.take<char>(LC_M * LC_M * f2);
-    p->df_Ahat = c.take<char>(size_t(g.nc) * LC_M * LC_M * f2);
+    p->df_Ahat = c.take<char>(size_t(g.nc) * lc_dfa_words(p->dir) * sizeof(float));  // compact layout
     p->df_W = c.take<char>(nw * f2);
     p->df_Cc = c.take<char>(nw * f2);
   } else if (p->dtype == LC_F64_SPLIT) {
