@@ -131,3 +131,23 @@ def test_ahat_block_approximation(lc, direction, code, tol):
                     exact = _exact_block(code, lam, i0, j0, h, sigma)
                     worst = max(worst, np.abs(approx - exact).max() / np.abs(exact).max())
     assert worst <= tol, worst
+
+
+@pytest.mark.parametrize("direction,head", [("l2c", 13), ("c2l", 16)])
+@pytest.mark.parametrize("n", [200, 3000, 16385, 65536, 300000])
+def test_ahat_tail_below_compact_head(lc, n, direction, head):
+    """The double-float tier keeps trailing words only for the entries of
+    A-hat with k + l <= head.  That rests on the entries, the 2-D Chebyshev
+    coefficients of a kernel smooth across well-separated blocks, falling
+    off geometrically in k + l: past the head every entry of every matrix is
+    below 2e-9 of the matrix's largest, so its FP32 leading word alone
+    carries it to 1e-16 of the matrix.  These n give leaf sizes s from 17 to 32."""
+    plan = lc.Plan(n, direction, 1, "f64", torch.device("cuda", 0))
+    nc = plan.info["n_c"]
+    assert nc > 0
+    Ah = np.abs(plan.table(3).reshape(nc, M, M))
+    tail = np.add.outer(np.arange(M), np.arange(M)) > head
+    peak = Ah.reshape(nc, -1).max(axis=1)
+    assert (peak > 0).all()
+    worst = (Ah[:, tail].max(axis=1) / peak).max()
+    assert worst <= 2e-9, (plan.info["s"], worst)
