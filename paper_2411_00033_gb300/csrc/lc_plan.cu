@@ -177,6 +177,7 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
   __shared__ double S[LC_M][LC_M];
   __shared__ double F[2][H][LC_M];  // folded rows: sums (even k) and differences (odd k)
   __shared__ double Tm[LC_M][LC_M];
+  __shared__ double G[2][LC_M][H];  // Tm folded along the column variable
   __shared__ double cs[LC_M][LC_M];
   const int tid = threadIdx.x;
   const int r0 = tid / LC_M, c0 = tid % LC_M;
@@ -227,13 +228,16 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
       Tm[r0][c0] = acc;
     }
     __syncthreads();
-    {  // along the column variable (folded the same way), then 4/(c_k c_l M^2)
+    {  // fold the column variable once per (row, nn) instead of once per output
+      const int e = tid / (LC_M * H), r = (tid / H) % LC_M, nn = tid % H;
+      const double u = Tm[r][nn], v = Tm[r][LC_M - 1 - nn];
+      G[e][r][nn] = e ? u - v : u + v;
+    }
+    __syncthreads();
+    {  // DCT along the column variable, then 4/(c_k c_l M^2)
       const int e = c0 & 1;
       double acc = 0.0;
-      for (int nn = 0; nn < H; ++nn) {
-        const double u = Tm[r0][nn], v = Tm[r0][LC_M - 1 - nn];
-        acc = fma(e ? u - v : u + v, cs[c0][nn], acc);
-      }
+      for (int nn = 0; nn < H; ++nn) acc = fma(G[e][r0][nn], cs[c0][nn], acc);
       const double w = 4.0 / (double(LC_M) * double(LC_M)) * (r0 == 0 ? 0.5 : 1.0) * (c0 == 0 ? 0.5 : 1.0);
       Ahat[a * (LC_M * LC_M) + tid] = acc * w;
     }
