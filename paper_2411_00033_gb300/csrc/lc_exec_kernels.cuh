@@ -403,37 +403,37 @@ __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, 
     if constexpr (compact_ahat<R>::value) {
       couple_compact(a, adj, nb, b0, reinterpret_cast<const float*>(As), Ws, Cl);
     } else {
-    for (int t = threadIdx.x; t < nb * kSeg; t += blockDim.x) {
-      const int jb = t / kSeg;                  // block within the group
-      const int sigma = (t % kSeg) / LC_M, k = t % LC_M;
-      const R* A0 = As + (3 * jb) * (LC_M * LC_M);
-      const R* w0 = Ws + (2 * jb) * kSeg + sigma * LC_M;
-      const R* w1 = w0 + kSeg;
-      R c0 = R(0), c0b = R(0), c1 = R(0);
-      if (!adj) {
-        // c(2b) = A(b,0) w(2b+2) + A(b,1) w(2b+3);  c(2b+1) = A(b,2) w(2b+3)
-        for (int l = 0; l < LC_M; ++l) {
-          const R wa = w0[l], wb = w1[l];
-          c0 = acc2(c0, ahat_at(A0, 0, k, l), wa);
-          c0b = acc2(c0b, ahat_at(A0, 1, k, l), wb);
-          c1 = acc2(c1, ahat_at(A0, 2, k, l), wb);
+      for (int t = threadIdx.x; t < nb * kSeg; t += blockDim.x) {
+        const int jb = t / kSeg;                  // block within the group
+        const int sigma = (t % kSeg) / LC_M, k = t % LC_M;
+        const R* A0 = As + (3 * jb) * (LC_M * LC_M);
+        const R* w0 = Ws + (2 * jb) * kSeg + sigma * LC_M;
+        const R* w1 = w0 + kSeg;
+        R c0 = R(0), c0b = R(0), c1 = R(0);
+        if (!adj) {
+          // c(2b) = A(b,0) w(2b+2) + A(b,1) w(2b+3);  c(2b+1) = A(b,2) w(2b+3)
+          for (int l = 0; l < LC_M; ++l) {
+            const R wa = w0[l], wb = w1[l];
+            c0 = acc2(c0, ahat_at(A0, 0, k, l), wa);
+            c0b = acc2(c0b, ahat_at(A0, 1, k, l), wb);
+            c1 = acc2(c1, ahat_at(A0, 2, k, l), wb);
+          }
+          R* out = Cl + (2 * (b0 + jb)) * kSeg + sigma * LC_M + k;
+          out[0] = finish(c0) + finish(c0b);
+          out[kSeg] = finish(c1);
+        } else {
+          // c(2b+2) = A(b,0)^T w(2b);  c(2b+3) = A(b,1)^T w(2b) + A(b,2)^T w(2b+1)
+          for (int l = 0; l < LC_M; ++l) {
+            const R wa = w0[l], wb = w1[l];
+            c0 = acc2(c0, ahat_at(A0, 0, l, k), wa);
+            c1 = acc2(c1, ahat_at(A0, 1, l, k), wa);
+            c0b = acc2(c0b, ahat_at(A0, 2, l, k), wb);
+          }
+          R* out = Cl + (2 * (b0 + jb) + 2) * kSeg + sigma * LC_M + k;
+          out[0] = finish(c0);
+          out[kSeg] = finish(c1) + finish(c0b);
         }
-        R* out = Cl + (2 * (b0 + jb)) * kSeg + sigma * LC_M + k;
-        out[0] = finish(c0) + finish(c0b);
-        out[kSeg] = finish(c1);
-      } else {
-        // c(2b+2) = A(b,0)^T w(2b);  c(2b+3) = A(b,1)^T w(2b) + A(b,2)^T w(2b+1)
-        for (int l = 0; l < LC_M; ++l) {
-          const R wa = w0[l], wb = w1[l];
-          c0 = acc2(c0, ahat_at(A0, 0, l, k), wa);
-          c1 = acc2(c1, ahat_at(A0, 1, l, k), wa);
-          c0b = acc2(c0b, ahat_at(A0, 2, l, k), wb);
-        }
-        R* out = Cl + (2 * (b0 + jb) + 2) * kSeg + sigma * LC_M + k;
-        out[0] = finish(c0);
-        out[kSeg] = finish(c1) + finish(c0b);
       }
-    }
     }
   }
 }
