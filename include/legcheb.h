@@ -90,7 +90,9 @@ typedef struct lc_plan_s* lc_plan;
 typedef struct {
   int32_t s_hat;   /* target leaf half-size (eq:numlevels); 4 <= s_hat <= 64 */
   int32_t fixed_s; /* > 0: use this s for every length (4 <= fixed_s <= 64); 0: paper rule */
-  int32_t slices;  /* LC_F64_SPLIT: 8-bit slices per operand, 3..7 (default 6) */
+  int32_t slices;  /* LC_F64_SPLIT: 8-bit slices per operand, 3..7, or 0 (default):
+                    * 7 for n <= 1e5 (normwise relative error <= 1e-13),
+                    * 6 above (<= 1e-12); for ragged plans n is the longest member */
   /* Testing only (0 in normal use).  Bit 0: the coupling kernel withholds
    * one of its bulk copies, so its bounded wait runs out and the execution
    * reports LC_ERR_DEVICE_TIMEOUT through lc_plan_check. */
@@ -162,6 +164,27 @@ lc_status lc_execute(lc_plan plan, const void* in, void* out, int64_t in_batch_s
 lc_status lc_adjoint(lc_plan plan, const void* in, void* out, int64_t in_batch_stride,
                      int64_t in_elem_stride, int64_t out_batch_stride,
                      int64_t out_elem_stride, lc_stream stream);
+
+/* Two-level batches: vector b (0 <= b < the plan's batch) and its element j
+ * are read from and written to
+ *   in [(b / batch_inner) * in_outer_stride  + (b % batch_inner) * in_batch_stride  + j * in_elem_stride]
+ *   out[(b / batch_inner) * out_outer_stride + (b % batch_inner) * out_batch_stride + j * out_elem_stride]
+ * (strides in elements, all >= 0, 1 <= batch_inner <= batch; batch_inner
+ * equal to the batch is lc_execute / lc_adjoint).  This reaches, in one call,
+ * the fibres of a 3-D array along its middle axis (C order, shape (P, n, Q):
+ * batch P*Q, batch_inner Q, batch stride 1, element stride Q, outer stride
+ * n*Q), which no single batch stride can.  Ragged plans accept only
+ * batch_inner = count with their packed layout.  Output strides that would
+ * put two outputs on one address (a zero stride that is used) return
+ * LC_ERR_INVALID_ARG. */
+lc_status lc_execute_ex(lc_plan plan, const void* in, void* out, int64_t in_batch_stride,
+                        int64_t in_elem_stride, int64_t out_batch_stride, int64_t out_elem_stride,
+                        int64_t batch_inner, int64_t in_outer_stride, int64_t out_outer_stride,
+                        lc_stream stream);
+lc_status lc_adjoint_ex(lc_plan plan, const void* in, void* out, int64_t in_batch_stride,
+                        int64_t in_elem_stride, int64_t out_batch_stride, int64_t out_elem_stride,
+                        int64_t batch_inner, int64_t in_outer_stride, int64_t out_outer_stride,
+                        lc_stream stream);
 
 /* Device-side status of the plan's earlier executions.  Kernels that wait on
  * an asynchronous copy (mbarrier) give up after about one second, record the
@@ -245,7 +268,9 @@ lc_status lc_plan_get_timing(lc_plan plan, int32_t slot, float* ms, int32_t* kin
  * loading the library holds until the process exits; it calls no cudaMalloc
  * or cudaFree.
  *  - n > LC_STATIC_MAX_N (or n < 1, batch < 1, NULL or aliased pointers,
- *    negative strides) returns LC_ERR_INVALID_ARG and launches nothing.
+ *    negative strides, a zero output element stride with n > 1 or a zero
+ *    output batch stride with batch > 1) returns LC_ERR_INVALID_ARG and
+ *    launches nothing.
  *  - Pointers, strides and batch follow lc_execute; x and out are device
  *    memory of the caller.
  *  - The first call on a device looks up the array's device address with

@@ -113,6 +113,39 @@ class Plan:
                out_strides[1], _stream_ptr(self.device))
         return out
 
+    def execute_strided2(self, x: torch.Tensor, out: torch.Tensor, in_strides, out_strides, batch_inner: int,
+                         adjoint: bool = False):
+        """Two-level strided call (lc_execute_ex): vector b, element j at
+        x.data_ptr() + ((b // batch_inner) * so + (b % batch_inner) * sb + j * se)
+        elements, with in_strides = (sb, se, so) and out_strides likewise."""
+        self._check_in(x)
+        self._check_in(out)
+        fn = B.lc_adjoint_ex if adjoint else B.lc_execute_ex
+        with torch.cuda.device(self.device):
+            fn(self._handle, x.data_ptr(), out.data_ptr(), in_strides[0], in_strides[1], out_strides[0],
+               out_strides[1], batch_inner, in_strides[2], out_strides[2], _stream_ptr(self.device))
+        return out
+
+    def along_axis(self, x: torch.Tensor, axis: int, out: torch.Tensor | None = None, adjoint: bool = False):
+        """Transform every fibre of a contiguous 3-D array along `axis` (0, 1 or 2)
+        in one call, writing the result in the same layout (a new array unless
+        `out` is given).  The plan's n must equal x.shape[axis] and its batch the
+        product of the other two extents."""
+        if x.dim() != 3 or not x.is_contiguous():
+            raise ValueError("expected a contiguous 3-D tensor")
+        P, Nn, Q = x.shape
+        if out is None:
+            out = torch.empty_like(x)
+        if axis == 0:    # fibre (j, k): batch index j*Q + k (stride 1), element stride Nn*Q
+            self.execute_strided(x, out, (1, Nn * Q), (1, Nn * Q), adjoint=adjoint)
+        elif axis == 2:  # fibre (i, j): batch stride Q, element stride 1
+            self.execute_strided(x, out, (Q, 1), (Q, 1), adjoint=adjoint)
+        elif axis == 1:  # fibre (i, k): inner index k (stride 1), outer index i (stride Nn*Q), element stride Q
+            self.execute_strided2(x, out, (1, Q, Nn * Q), (1, Q, Nn * Q), batch_inner=Q, adjoint=adjoint)
+        else:
+            raise ValueError("axis must be 0, 1 or 2")
+        return out
+
     def table(self, which: int):
         sizes = {0: self.info["N"], 1: 2 * self.info["s"] * self.info["M"], 2: self.info["M"] ** 2,
                  3: self.info["n_c"] * self.info["M"] ** 2, 4: self.info["N"], 5: self.info["N"]}

@@ -12,6 +12,8 @@ from pathlib import Path
 _LIB_PATH = Path(__file__).resolve().parent / "_build" / "liblegcheb.so"
 
 LC_L2C, LC_C2L = 0, 1
+#: largest n that lc_direct_static accepts (LC_STATIC_MAX_N in include/legcheb.h)
+LC_STATIC_MAX_N = 16384
 LC_F64, LC_F64_SPLIT, LC_F32, LC_F64_DF = 0, 1, 2, 3
 STATUS_NAMES = {
     0: "LC_OK", 1: "LC_ERR_INVALID_ARG", 2: "LC_ERR_WORKSPACE_TOO_SMALL", 3: "LC_ERR_CUDA",
@@ -24,7 +26,7 @@ EXPORTED = (
     "lc_plan_create", "lc_plan_create_ex", "lc_plan_workspace_size_ragged", "lc_plan_create_ragged",
     "lc_execute", "lc_adjoint", "lc_destroy", "lc_status_string", "lc_plan_info", "lc_plan_table",
     "lc_plan_launches", "lc_plan_set_timing", "lc_plan_get_timing", "lc_plan_check", "lc_direct_static",
-    "lc_plan_set_config", "lc_plan_autotune",
+    "lc_plan_set_config", "lc_plan_autotune", "lc_execute_ex", "lc_adjoint_ex",
 )
 
 
@@ -69,6 +71,8 @@ def load(path: Path | None = None):
         "lc_plan_create_ragged": [ctypes.POINTER(vp), p64, i64, ctypes.c_int, ctypes.c_int, popt, vp, sz, vp],
         "lc_execute": [vp, vp, vp, i64, i64, i64, i64, vp],
         "lc_adjoint": [vp, vp, vp, i64, i64, i64, i64, vp],
+        "lc_execute_ex": [vp, vp, vp, i64, i64, i64, i64, i64, i64, i64, vp],
+        "lc_adjoint_ex": [vp, vp, vp, i64, i64, i64, i64, i64, i64, i64, vp],
         "lc_destroy": [vp],
         "lc_plan_info": [vp, p64, p64, pi32, pi32, pi32, p64, p64],
         "lc_plan_table": [vp, i32, ctypes.POINTER(ctypes.c_double), i64, p64, vp],
@@ -155,6 +159,16 @@ def lc_execute(plan, in_ptr, out_ptr, ib, ie, ob, oe, stream_ptr):
 def lc_adjoint(plan, in_ptr, out_ptr, ib, ie, ob, oe, stream_ptr):
     _check(load().lc_adjoint(ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
                              ib, ie, ob, oe, ctypes.c_void_p(stream_ptr)), "lc_adjoint")
+
+
+def lc_execute_ex(plan, in_ptr, out_ptr, ib, ie, ob, oe, inner, iob, oob, stream_ptr):
+    _check(load().lc_execute_ex(ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+                                ib, ie, ob, oe, inner, iob, oob, ctypes.c_void_p(stream_ptr)), "lc_execute_ex")
+
+
+def lc_adjoint_ex(plan, in_ptr, out_ptr, ib, ie, ob, oe, inner, iob, oob, stream_ptr):
+    _check(load().lc_adjoint_ex(ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+                                ib, ie, ob, oe, inner, iob, oob, ctypes.c_void_p(stream_ptr)), "lc_adjoint_ex")
 
 
 def lc_destroy(plan):

@@ -1,6 +1,8 @@
 // lc_df.cu -- LC_F64_DF: FP64 input and output, Algorithm 4 in double-float
 // arithmetic on the FP32 pipe (the kernels of lc_exec_kernels.cuh with
-// R = lc_df).  The plan tables are rounded once from the FP64 plan to
+// R = lc_df).  Each vector is scaled by a power of two that brings its
+// largest entry into [1, 2) before the double-float arithmetic (exponents
+// from k_vec_exponent) and scaled back exactly in the FP64 Step 7.  The plan tables are rounded once from the FP64 plan to
 // double-float pairs; A-hat keeps the trailing FP32 word only where the
 // entry needs it (the compact layout of lc_internal.cuh).
 #include "lc_df.cuh"
@@ -12,13 +14,29 @@ struct lc_io<lc_df> {
   typedef double type;
 };
 template <>
-__device__ __forceinline__ lc_df lc_ld<lc_df, double>(const double* p) {
-  return lc_df_from_double(*p);
+__device__ __forceinline__ lc_df lc_ld_in<lc_df, double>(const double* p, int e) {
+  return lc_df_from_double_s(*p, e);
+}
+// Step 7 in FP64: each double-float word is brought back to FP64 exactly
+// (times 2^e, undoing the scaling), and the near- and far-field parts are
+// summed in FP64: their leading words in FP64, their trailing words (each
+// below 2^-24 of its leading word) summed in FP32 first -- an error below
+// 2^-48 of those small words -- then added in FP64.
+template <>
+__device__ __forceinline__ double lc_out1<lc_df, double>(const lc_df& v, int e) {
+  return lc_f2d_s(v.hi, e) + lc_f2d_s(v.lo, e);
 }
 template <>
-__device__ __forceinline__ void lc_st<lc_df, double>(double* p, const lc_df& v) {
-  *p = lc_df_to_double(v);
+__device__ __forceinline__ double lc_out2<lc_df, double>(const lc_df& far, const lc_df& near, int e) {
+  return (lc_f2d_s(far.hi, e) + lc_f2d_s(near.hi, e)) + lc_f2d_s(far.lo + near.lo, e);
 }
+template <>
+__device__ __forceinline__ double lc_out_acc<lc_df, double>(double acc, const lc_df& v, int e) {
+  return (acc + lc_f2d_s(v.hi, e)) + lc_f2d_s(v.lo, e);
+}
+// The band kernel scales its operand tile by the tile's own exponent.
+template <>
+struct local_scale<lc_df, double> { static constexpr bool value = true; };
 template <>
 __device__ __forceinline__ lc_df cinv<lc_df>(int64_t i) {
   // 1/pi and 2/pi as double-floats
@@ -110,18 +128,21 @@ lc_status lc_df_prepare(lc_plan p, cudaStream_t st) {
   return LC_OK;
 }
 
-lc_status lc_exec_df(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob, int64_t oe,
-                     cudaStream_t st, int adjoint) {
+lc_status lc_exec_df(lc_plan p, const void* in, void* out, const lc_layout& lay, cudaStream_t st, int adjoint) {
   if (p->ragged) return LC_ERR_UNSUPPORTED;
   Args<lc_df> a;
   a.in = static_cast<const double*>(in);
   a.out = static_cast<double*>(out);
-  a.ib = ib; a.ie = ie; a.ob = ob; a.oe = oe;
+  a.ib = lay.ib; a.ie = lay.ie; a.ob = lay.ob; a.oe = lay.oe;
+  a.inner = lay.inner; a.iob = lay.iob; a.oob = lay.oob;
   a.n = p->g.n; a.N = p->g.N; a.L = p->g.L; a.s = p->g.s; a.nseg = p->g.nseg;
   a.batch = p->batch; a.dir = int(p->dir);
   a.t = lc_tables<lc_df>{static_cast<const lc_df*>(p->df_lam), static_cast<const lc_df*>(p->df_lam2),
                          static_cast<const lc_df*>(p->df_T), static_cast<const lc_df*>(p->df_B),
                          static_cast<const lc_df*>(p->df_Ahat), static_cast<lc_df*>(p->df_W),
                          static_cast<lc_df*>(p->df_Cc), p->err, p->opt.debug_flags};
+  a.xe = p->xexp;
+  a.xe_part = p->xexp_part;
+  a.xe_cnt = p->xexp_cnt;
   return run<lc_df>(p, a, st, adjoint);
 }

@@ -52,16 +52,31 @@ __device__ __forceinline__ lc_df fma(const lc_df& a, const lc_df& b, const lc_df
   return lc_df_fast2(s.hi, s.lo + (e + c.lo));
 }
 
-// double -> double-float from the bit pattern (no FP64 instruction); FP64
-// values below the FP32 normal range flush to zero, above it saturate.
-__device__ __forceinline__ lc_df lc_df_from_double(double x) {
+// x * 2^-e as a double-float, from the bit pattern (no FP64 instruction on
+// the common path).  The caller picks e per vector (the exponent of its
+// largest entry), so the scaled values lie below 2 and everything FP32's
+// range cannot hold is below 2^-126 of the vector's largest entry: those
+// values flush to zero, which changes a normwise result by less than 1e-38.
+// Subnormal FP64 inputs are normalised first; infinities and NaNs pass
+// through unscaled.
+__device__ __forceinline__ lc_df lc_df_from_double_s(double x, int e) {
   const uint64_t u = __double_as_longlong(x);
-  const int E = int((u >> 52) & 0x7ff);
+  int E = int((u >> 52) & 0x7ff);
+  uint64_t m = u & ((uint64_t(1) << 52) - 1);
+  if (E == 2047) return lc_df(float(x), 0.0f);
+  if (E == 0) {  // zero or subnormal: m * 2^-1074
+    if (m == 0) return lc_df(0.0f, 0.0f);
+    const int sh = __clzll(m) - 11;  // bring the leading bit to position 52
+    m <<= sh;
+    E = 1 - sh;
+  } else {
+    m |= uint64_t(1) << 52;
+  }
+  E -= e;
   const int eh = E - 1023 + 127;
-  if (E == 0 || eh < 1) return lc_df(0.0f, 0.0f);
+  if (eh < 1) return lc_df(0.0f, 0.0f);
   const uint32_t sgn = uint32_t(u >> 63) << 31;
   if (eh > 254) return lc_df(__uint_as_float(sgn | 0x7f800000u), 0.0f);
-  const uint64_t m = (u & ((uint64_t(1) << 52) - 1)) | (uint64_t(1) << 52);
   const float hi = __uint_as_float(sgn | (uint32_t(eh) << 23) | (uint32_t(m >> 29) & 0x7fffffu));
   // remaining 29 bits: value (m & (2^29-1)) * 2^(E-1075)
   const int k = E - 1075;
@@ -69,13 +84,21 @@ __device__ __forceinline__ lc_df lc_df_from_double(double x) {
   lo = (k + 127 >= 1) ? lo * __uint_as_float(uint32_t(k + 127) << 23) : ldexpf(lo, k);
   return lc_df(hi, sgn ? -lo : lo);
 }
-// float -> double, exact, from the bit pattern
-__device__ __forceinline__ double lc_f2d(float f) {
+__device__ __forceinline__ lc_df lc_df_from_double(double x) { return lc_df_from_double_s(x, 0); }
+// f * 2^e as a double: exact (from the bit pattern) when the result is a
+// normal FP64 number, else by a correctly rounded FP64 scaling.
+__device__ __forceinline__ double lc_f2d_s(float f, int e) {
   const uint32_t u = __float_as_uint(f);
   const int ef = int((u >> 23) & 0xff);
   const uint64_t sgn = uint64_t(u >> 31) << 63;
-  if (ef == 0) return __longlong_as_double(sgn);
+  if (ef == 0) return __longlong_as_double(sgn);  // FP32 subnormals are not produced by the kernels
   if (ef == 255) return __longlong_as_double(sgn | (uint64_t(2047) << 52) | (uint64_t(u & 0x7fffffu) << 29));
-  return __longlong_as_double(sgn | (uint64_t(ef - 127 + 1023) << 52) | (uint64_t(u & 0x7fffffu) << 29));
+  const int ed = ef - 127 + 1023 + e;
+  if (ed >= 1 && ed <= 2046)
+    return __longlong_as_double(sgn | (uint64_t(ed) << 52) | (uint64_t(u & 0x7fffffu) << 29));
+  return ldexp(double(f), e);
 }
-__device__ __forceinline__ double lc_df_to_double(const lc_df& v) { return lc_f2d(v.hi) + lc_f2d(v.lo); }
+__device__ __forceinline__ double lc_f2d(float f) { return lc_f2d_s(f, 0); }
+// (hi + lo) * 2^e in FP64 (one FP64 add; exact when no scaled word leaves FP64's normal range).
+__device__ __forceinline__ double lc_df_to_double_s(const lc_df& v, int e) { return lc_f2d_s(v.hi, e) + lc_f2d_s(v.lo, e); }
+__device__ __forceinline__ double lc_df_to_double(const lc_df& v) { return lc_df_to_double_s(v, 0); }

@@ -42,12 +42,6 @@
 
 namespace lc_exec {
 
-// Element conversions between the I/O type and the arithmetic type R.
-template <typename R, typename IO>
-__device__ __forceinline__ R lc_ld(const IO* p) { return R(*p); }
-template <typename R, typename IO>
-__device__ __forceinline__ void lc_st(IO* p, const R& v) { *p = IO(v); }
-
 template <typename R>
 struct lc_io { typedef R type; };
 
@@ -56,18 +50,62 @@ struct Args {
   const typename lc_io<R>::type* in;
   typename lc_io<R>::type* out;
   int64_t ib, ie, ob, oe;
+  int64_t inner, iob, oob;  // two-level batches (lc_layout)
   int64_t n, N;
   int L, s;
   int64_t nseg;
   int64_t batch;
   int dir;
   lc_tables<R> t;
+  // Per-vector power-of-two exponents (double-float tier; NULL elsewhere):
+  // vector b is computed as x_b 2^-xe[b] and its output scaled back by
+  // 2^xe[b], both exact, so that FP32's exponent range never clips FP64
+  // data.  xe_part / xe_cnt: partial maxima and arrival counters of the
+  // pre-pass that finds them (k_vec_exponent).
+  int* xe;
+  int* xe_part;
+  unsigned* xe_cnt;
 };
 
 template <typename R>
 __device__ __forceinline__ R cinv(int64_t i) {
   return i == 0 ? R(0.31830988618379067154) : R(0.63661977236758134308);  // 1/pi, 2/pi
 }
+
+// Input element x as R, times 2^-e (e: the vector's exponent, 0 unless the
+// tier scales; see Args::xe).
+template <typename R, typename IO>
+__device__ __forceinline__ R lc_ld_in(const IO* p, int) { return R(*p); }
+// Output values in the output precision IO from results v in R that carry
+// the factor 2^-e (the caller has applied C^{-1} or the C2L row factor in R):
+// v (out1), far + near (out2), acc + v (out_acc).  These are the sums of
+// Step 7 of Algorithm 4 -- the near- and far-field parts of an output
+// coefficient -- and they run in IO arithmetic: FP64 for every FP64-output
+// tier.
+template <typename R, typename IO>
+__device__ __forceinline__ IO lc_out1(const R& v, int) { return IO(v); }
+template <typename R, typename IO>
+__device__ __forceinline__ IO lc_out2(const R& far, const R& near, int) { return IO(far) + IO(near); }
+template <typename R, typename IO>
+__device__ __forceinline__ IO lc_out_acc(IO acc, const R& v, int) { return acc + IO(v); }
+// A tile's own exponent (double-float tier): kernels whose results go
+// straight to the FP64 output may scale their input tile by the exponent of
+// its own largest entry instead of the vector's, which needs no pre-pass.
+template <typename R, typename IO>
+struct local_scale { static constexpr bool value = false; };
+__device__ __forceinline__ int vec_exp(const int* xe, int64_t b) { return xe ? xe[b] : 0; }
+// Unbiased binary exponent of |x| (|x| in [2^e, 2^(e+1)), subnormals
+// normalised), or kNoTileExp for zero, infinity and NaN.
+constexpr int kNoTileExp = -(1 << 20);
+__device__ __forceinline__ int tile_exp_of(double x) {
+  const uint64_t u = __double_as_longlong(x);
+  const int E = int((u >> 52) & 0x7ff);
+  const uint64_t m = u & ((uint64_t(1) << 52) - 1);
+  if (E == 2047) return kNoTileExp;
+  if (E == 0) return m ? 1 - (__clzll(m) - 11) - 1023 : kNoTileExp;
+  return E - 1023;
+}
+__device__ __forceinline__ int tile_exp_of(float x) { return tile_exp_of(double(x)); }
 template <typename R>
 __device__ __forceinline__ R negate(const R& v) { return -v; }
 // Step 4 with one pass per parent for both children (halves the multiplies,
@@ -185,13 +223,14 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
     __syncthreads();
     if (leaf) {
       const int64_t p0 = (x0 << depth) * 2 * s;
-      const typename lc_io<R>::type* f = a.in + b * a.ib;
+      const typename lc_io<R>::type* f = a.in + lc_boff(b, a.ib, a.inner, a.iob);
       const bool scale = adj && a.dir == LC_L2C;  // transposed L2C starts with C^{-1}
+      const int e = vec_exp(a.xe, b);
       for (int i = threadIdx.x; i < nb * 2 * s; i += blockDim.x) {
         const int64_t j = p0 + i;
         R v = R(0);
         if (j < a.n) {
-          v = lc_ld<R>(f + j * a.ie);
+          v = lc_ld_in<R>(f + j * a.ie, e);
           if (scale) v *= cinv<R>(j);
         }
         fs[i] = v;
@@ -637,15 +676,14 @@ __device__ __forceinline__ void near_adj2(const R* __restrict__ lamk, const R* _
 // band's part is added.
 template <typename R>
 __device__ __forceinline__ void near_tile(const Args<R>& a, int64_t b, int64_t lo, int64_t hi, int adj,
-                                          unsigned char* tile, int add) {
+                                          unsigned char* tile) {
+  typedef typename lc_io<R>::type IO;
   const int s = a.s, L = a.L;
   const int64_t two_s = 2 * int64_t(s);
   const bool l2c = (a.dir == LC_L2C);
-  auto put = [&](int64_t i, const R& v) {
-    typename lc_io<R>::type* o = a.out + b * a.ob + i * a.oe;
-    lc_st<R>(o, add ? lc_ld<R>(o) + v : v);
-  };
-  const typename lc_io<R>::type* f = a.in + b * a.ib;
+  const IO* f = a.in + lc_boff(b, a.ib, a.inner, a.iob);
+  IO* const ob = a.out + lc_boff(b, a.ob, a.inner, a.oob);
+  __shared__ int tile_exp;
   R* opnd = reinterpret_cast<R*>(tile);  // operand tile (input values, pre-scaled)
   int64_t olo, ohi;             // operand index range
   if (!adj) {
@@ -676,19 +714,51 @@ __device__ __forceinline__ void near_tile(const Args<R>& a, int64_t b, int64_t l
   R* lamm1 = lamm + mlen + (pad ? pad * (mlen / two_s + 2) : 0) + 8;  // parity-1 copy (pad != 0)
   const int moff0 = pad_index(mlo - lbase, two_s, pad);
   const int moff1 = pad ? pad_index(mlo - lbase - 1, two_s, pad) : 0;
-  typedef typename lc_io<R>::type IO;
-  stage<4>(
-      int(olen), [&](int i) { return f[(olo + i) * a.ie]; },
-      [&](int i, IO x) {
-        const int64_t q = olo + i;
-        R v = lc_ld<R>(&x);
-        if (!adj) {
-          if (a.dir == LC_C2L) v = R(q) * v;  // L(i, j) = (2i+1) j u v: scale column j
-        } else {
-          v = (a.dir == LC_L2C) ? cinv<R>(q) * v : R(2 * q + 1) * v;  // C^{-1} r or (2i+1) r
-        }
-        opnd[pad_index(q - pbase, two_s, pad) - ooff] = v;
-      });
+  // the operand tile, scaled by 2^-e: e is the vector's exponent, or, where
+  // the tier allows, this tile's own (the band's outputs need no other)
+  auto scale_put = [&](int64_t q, R v) {
+    if (!adj) {
+      if (a.dir == LC_C2L) v = R(q) * v;  // L(i, j) = (2i+1) j u v: scale column j
+    } else {
+      v = (a.dir == LC_L2C) ? cinv<R>(q) * v : R(2 * q + 1) * v;  // C^{-1} r or (2i+1) r
+    }
+    opnd[pad_index(q - pbase, two_s, pad) - ooff] = v;
+  };
+  int e;
+  if constexpr (local_scale<R, IO>::value) {
+    // raw FP64 values first (same 8 bytes per slot), the tile's largest
+    // exponent, then the scaled conversion in place
+    static_assert(sizeof(R) == sizeof(IO), "in-place conversion needs equal sizes");
+    if (threadIdx.x == 0) tile_exp = kNoTileExp;
+    __syncthreads();
+    int m = kNoTileExp;
+    stage<4>(
+        int(olen), [&](int i) { return f[(olo + i) * a.ie]; },
+        [&](int i, IO x) {
+          m = max(m, tile_exp_of(x));
+          reinterpret_cast<IO*>(opnd)[pad_index(olo + i - pbase, two_s, pad) - ooff] = x;
+        });
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m > kNoTileExp) atomicMax(&tile_exp, m);
+    __syncthreads();
+    e = tile_exp == kNoTileExp ? 0 : tile_exp;
+    for (int i = threadIdx.x; i < int(olen); i += blockDim.x) {  // the slots this thread staged
+      const int64_t q = olo + i;
+      const int slot = pad_index(q - pbase, two_s, pad) - ooff;
+      scale_put(q, lc_ld_in<R>(reinterpret_cast<const IO*>(opnd) + slot, e));
+    }
+  } else {
+    e = vec_exp(a.xe, b);
+    stage<4>(int(olen), [&](int i) { return f[(olo + i) * a.ie]; },
+             [&](int i, IO x) { scale_put(olo + i, lc_ld_in<R>(&x, e)); });
+  }
+  // output i receives v (scaled back by 2^e, in IO arithmetic); C2L row
+  // (column) 0 also takes the entry L(0,0) = 1 times f_0 (eq:Lxymod)
+  auto put = [&](int64_t i, const R& v) {
+    IO r = lc_out1<R, IO>(v, e);
+    if (!l2c && i == 0) r += f[0];
+    ob[i * a.oe] = r;
+  };
   stage<4>(int(kmax + 2), [&](int k) { return k < a.N ? a.t.lam[k] : R(0); }, [&](int k, R v) { lamk[k] = v; });
   stage<4>(
       int(mlen), [&](int j) { return mlo + j < mcap ? a.t.lam2[mlo + j] : R(0); },
@@ -707,23 +777,14 @@ __device__ __forceinline__ void near_tile(const Args<R>& a, int64_t b, int64_t l
         const R* fo = opnd + (i - olo);
         const R* lm = lamm + (i - mlo);
         near = band_sum<R>(cnt, [&](const R& c, int kk) { return acc3(c, lamk[kk], lm[kk], fo[2 * kk]); });
-        if (l2c) {
-          near = cinv<R>(i) * near;
-        } else {
-          near = R(2 * i + 1) * near;
-          if (i == 0) near += lc_ld<R>(f);
-        }
+        put(i, l2c ? cinv<R>(i) * near : R(2 * i + 1) * near);
       } else {
         const int cnt = int(i / 2 + 1);
         const R* ro = opnd + (i - olo);
         const R* lm = lamm + (i - mlo);
         near = band_sum<R>(cnt, [&](const R& c, int k) { return acc3(c, lamk[k], lm[-k], ro[-2 * k]); });
-        if (!l2c) {
-          near = R(i) * near;
-          if (i == 0) near += lc_ld<R>(f);
-        }
+        put(i, l2c ? near : R(i) * near);
       }
-      put(i, near);
     }
     return;
   }
@@ -760,26 +821,20 @@ __device__ __forceinline__ void near_tile(const Args<R>& a, int64_t b, int64_t l
         const int64_t end = e2 < a.n ? e2 : a.n;
         near_fwd2(lamk, lm, op, int((end - i + 1) >> 1), s - m0 - 1, 2 * s - 2 * m0 - 2, pad, n0, n1);
         if (l2c) {
-          n0 = cinv<R>(i) * n0;
-          n1 = cinv<R>(i + 2) * n1;
+          put(i, cinv<R>(i) * n0);
+          if (has1) put(i + 2, cinv<R>(i + 2) * n1);
         } else {
-          // (2i+1) u_k v_(i+k) (j f_j) summed; entry (0,0) = 1 adds f_0 (eq:Lxymod)
-          n0 = R(2 * i + 1) * n0;
-          n1 = R(2 * i + 5) * n1;
-          if (i == 0) n0 += lc_ld<R>(f);
+          // (2i+1) u_k v_(i+k) (j f_j) summed
+          put(i, R(2 * i + 1) * n0);
+          if (has1) put(i + 2, R(2 * i + 5) * n1);
         }
       } else {
         int64_t st = two_s * (v - 1) > 0 ? two_s * (v - 1) : 0;
         if ((st & 1) != (i & 1)) ++st;
         near_adj2(lamk, lm, op, int((i - st) / 2 + 1), has1, m0 + 1, 2 * m0 + 1, pad, n0, n1);
-        if (!l2c) {
-          n0 = R(i) * n0;
-          n1 = R(i + 2) * n1;
-          if (i == 0) n0 += lc_ld<R>(f);
-        }
+        put(i, l2c ? n0 : R(i) * n0);
+        if (has1) put(i + 2, l2c ? n1 : R(i + 2) * n1);
       }
-      put(i, n0);
-      if (has1) put(i + 2, n1);
     }
   }
 }
@@ -794,7 +849,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_near(Args<R> a, int adj) {
     const int64_t hi = hi_raw < a.n ? hi_raw : a.n;
     if (lo >= hi) continue;
     __syncthreads();  // shared tiles of the previous batch member are free
-    near_tile(a, b, lo, hi, adj, smem_raw, 0);
+    near_tile(a, b, lo, hi, adj, smem_raw);
   }
 }
 
@@ -956,15 +1011,20 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
           far0 = cinv<R>(i) * far0;
           far1 = cinv<R>(i + 2) * far1;
         }
-        auto* o = a.out + b * a.ob + i * a.oe;
-        lc_st<R>(o, far0 + lc_ld<R>(o));
-        if (has1) lc_st<R>(o + 2 * a.oe, far1 + lc_ld<R>(o + 2 * a.oe));
+        // Step 7: the band's part (already in the output) + far, summed in the
+        // output precision
+        typedef typename lc_io<R>::type IO;
+        const int e = vec_exp(a.xe, b);
+        IO* o = a.out + lc_boff(b, a.ob, a.inner, a.oob) + i * a.oe;
+        *o = lc_out_acc<R, IO>(*o, far0, e);
+        if (has1) o[2 * a.oe] = lc_out_acc<R, IO>(o[2 * a.oe], far1, e);
       }
     } else {
       // Batched plans: Steps 5-7 here, one row (column) per step of a thread,
       // which keeps register use low enough for many CTAs per SM.
       typedef typename lc_io<R>::type IO;
-      const IO* f = a.in + b * a.ib;
+      const IO* f = a.in + lc_boff(b, a.ib, a.inner, a.iob);
+      const int e = vec_exp(a.xe, b);
       R* opnd = Ts + 2 * s * LC_M;  // operand tile (input values, pre-scaled)
       int64_t olo, ohi;             // operand index range
       if (!adj) {
@@ -985,7 +1045,7 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
           int(olen), [&](int i) { return f[(olo + i) * a.ie]; },
           [&](int i, IO x) {
             const int64_t q = olo + i;
-            R v = lc_ld<R>(&x);
+            R v = lc_ld_in<R>(&x, e);
             if (!adj) {
               if (!l2c) v = R(q) * v;  // L(i, j) = (2i+1) j u v: scale column j
             } else {
@@ -1020,7 +1080,10 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
             for (int k = 0; k < LC_M; ++k) far = acc2(far, c[k], Trow[k]);
             far = finish(far);
           }
-          R near = R(0), res;
+          R near = R(0);
+          IO res;
+          // Step 7 in the output precision: near + far (times C^{-1} for
+          // forward L2C); C2L row/column 0 adds L(0,0) f_0 = f_0 (eq:Lxymod)
           if (!adj) {
             // row i: sum over j = i + 2k in the band  (eq:hik, eq:Lxymod)
             const int64_t end = two_s * (v + 2) < a.n ? two_s * (v + 2) : a.n;
@@ -1029,11 +1092,12 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
             const R* lm = lamm + (i - mlo);
             near = band_sum<R>(cnt, [&](const R& c, int kk) { return acc3(c, lamk[kk], lm[kk], fo[2 * kk]); });
             if (l2c) {
-              res = cinv<R>(i) * (far + near);
+              const R c = cinv<R>(i);
+              res = lc_out2<R, IO>(c * far, c * near, e);
             } else {
-              // (2i+1) u_k v_(i+k) (j f_j) summed; entry (0,0) = 1 adds f_0 (eq:Lxymod)
-              res = far + R(2 * i + 1) * near;
-              if (i == 0) res += lc_ld<R>(f);
+              // (2i+1) u_k v_(i+k) (j f_j) summed
+              res = lc_out2<R, IO>(far, R(2 * i + 1) * near, e);
+              if (i == 0) res += f[0];
             }
           } else {
             // column j = i: sum over rows r <= j in the band
@@ -1043,17 +1107,114 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
             const R* ro = opnd + (i - olo);  // ro[-2k] = row i - 2k
             const R* lm = lamm + (i - mlo);  // lm[-k]  = (r + i)/2 = i - k
             near = band_sum<R>(cnt, [&](const R& c, int k) { return acc3(c, lamk[k], lm[-k], ro[-2 * k]); });
-            if (!l2c) {
-              near = R(i) * near;
-              if (i == 0) near += lc_ld<R>(f);
-            }
-            res = far + near;
+            res = lc_out2<R, IO>(far, l2c ? near : R(i) * near, e);
+            if (!l2c && i == 0) res += f[0];
           }
-          lc_st<R>(a.out + b * a.ob + i * a.oe, res);
+          a.out[lc_boff(b, a.ob, a.inner, a.oob) + i * a.oe] = res;
         }
       }
     }
   }
+}
+
+// ------------------------------------------------- per-vector exponents
+// Pre-pass of the double-float tier: xe[b] = the binary exponent of vector
+// b's largest finite entry (|x| in [2^xe, 2^(xe+1))), 0 for a vector without
+// nonzero finite entries.  The kernels then work on x 2^-xe.
+constexpr int kExpChunk = LC_EXP_CHUNK;  // elements per CTA
+constexpr int kNoExp = -(1 << 20);      // "no nonzero finite entry"
+// Biased exponent of |x| as if normalised (below 1 for subnormals), or
+// kNoExp for zero, infinity and NaN.
+__device__ __forceinline__ int exp_field(double x) {
+  const uint64_t u = __double_as_longlong(x);
+  const int E = int((u >> 52) & 0x7ff);
+  const uint64_t m = u & ((uint64_t(1) << 52) - 1);
+  if (E == 2047) return kNoExp;
+  if (E == 0) return m ? 1 - (__clzll(m) - 11) : kNoExp;
+  return E;
+}
+__device__ __forceinline__ int block_max_256(int v, int* red) {
+  v = __reduce_max_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int r = (threadIdx.x & 31) < 8 ? red[threadIdx.x & 31] : kNoExp;
+  r = __reduce_max_sync(0xffffffffu, r);
+  __syncthreads();
+  return r;
+}
+// CTA (x, y) reduces elements [x kExpChunk, (x+1) kExpChunk) of vectors
+// y, y + gridDim.y, ...; with several chunks per vector the last CTA to
+// arrive (counter cnt[b], reset by that CTA) combines the partial maxima.
+template <typename IO>
+__global__ void __launch_bounds__(256) k_vec_exponent(const IO* __restrict__ in, int64_t n, int64_t batch, int64_t ib,
+                                                      int64_t ie, int64_t inner, int64_t iob, int chunks,
+                                                      int* __restrict__ xe, int* part, unsigned* cnt) {
+  __shared__ int red[8];
+  __shared__ int last;
+  const int64_t j0 = int64_t(blockIdx.x) * kExpChunk;
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+    const IO* f = in + lc_boff(b, ib, inner, iob);
+    int m = kNoExp;
+#pragma unroll
+    for (int u = 0; u < kExpChunk / 256; ++u) {
+      const int64_t j = j0 + u * 256 + threadIdx.x;
+      if (j < n) m = max(m, exp_field(double(f[j * ie])));
+    }
+    m = block_max_256(m, red);
+    if (threadIdx.x == 0) {
+      last = 0;
+      if (chunks == 1) {
+        xe[b] = m == kNoExp ? 0 : m - 1023;
+      } else {
+        part[b * chunks + blockIdx.x] = m;
+        __threadfence();
+        last = atomicAdd(&cnt[b], 1u) == unsigned(chunks - 1);
+      }
+    }
+    __syncthreads();
+    if (last) {  // every other CTA of vector b fenced its partial before arriving
+      __threadfence();
+      int v = kNoExp;
+      for (int c = threadIdx.x; c < chunks; c += 256) v = max(v, *reinterpret_cast<volatile int*>(part + b * chunks + c));
+      v = block_max_256(v, red);
+      if (threadIdx.x == 0) {
+        xe[b] = v == kNoExp ? 0 : v - 1023;
+        cnt[b] = 0u;
+      }
+    }
+    __syncthreads();
+  }
+}
+// Many short strided fibres (element stride != 1): one thread per vector,
+// so that a warp reads 32 neighbouring vectors' entries j together.
+template <typename IO>
+__global__ void __launch_bounds__(256) k_vec_exponent_rows(const IO* __restrict__ in, int64_t n, int64_t batch,
+                                                           int64_t ib, int64_t ie, int64_t inner, int64_t iob,
+                                                           int* __restrict__ xe) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const IO* f = in + lc_boff(b, ib, inner, iob);
+  int m = kNoExp;
+#pragma unroll 8
+  for (int64_t j = 0; j < n; ++j) m = max(m, exp_field(double(f[j * ie])));
+  xe[b] = m == kNoExp ? 0 : m - 1023;
+}
+inline int64_t vec_exponent_chunks(int64_t n) { return (n + kExpChunk - 1) / kExpChunk; }
+
+template <typename R>
+lc_status launch_vec_exponent(const Args<R>& a, cudaStream_t st) {
+  typedef typename lc_io<R>::type IO;
+  if (a.ie != 1 && a.n <= kExpChunk && a.batch >= 1024) {
+    k_vec_exponent_rows<IO><<<unsigned((a.batch + 255) / 256), 256, 0, st>>>(a.in, a.n, a.batch, a.ib, a.ie, a.inner,
+                                                                             a.iob, a.xe);
+  } else {
+    const int64_t chunks = vec_exponent_chunks(a.n);
+    const dim3 grid(unsigned(chunks), unsigned(a.batch < 65535 ? a.batch : 65535));
+    k_vec_exponent<IO><<<grid, 256, 0, st>>>(a.in, a.n, a.batch, a.ib, a.ie, a.inner, a.iob, int(chunks), a.xe,
+                                             a.xe_part, a.xe_cnt);
+  }
+  LC_LAUNCH_CHECK();
+  return LC_OK;
 }
 
 // ------------------------------------------------------------------ driver
@@ -1092,7 +1253,7 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
   const int L = a.L, s = a.s;
   const unsigned gy = unsigned(a.batch < 65535 ? a.batch : 65535);
   lc_timer_begin(p);
-  if (L <= 0) {
+  if (L <= 0) {  // the band kernel alone (it scales its tile by its own exponent)
     const size_t sm = near_smem<R>(s, a.n, 1);
     lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_near<R>), sm);
     if (e != LC_OK) return e;
@@ -1134,6 +1295,11 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
     LC_CUDA_TRY(cudaEventRecord(p->ev_start, st));
     LC_CUDA_TRY(cudaStreamWaitEvent(sf, p->ev_start, 0));
     LC_CUDA_TRY(cudaStreamWaitEvent(sn, p->ev_start, 0));
+  }
+  if (a.xe) {  // per-vector exponents, read by the far-field chain (not by the band)
+    lc_timer_mark(p, st, LC_K_PREP);
+    lc_status e = launch_vec_exponent(a, sf);
+    if (e != LC_OK) return e;
   }
   {  // first up chunk: leaf restriction and the fine levels
     const int rho = roots[0];

@@ -26,6 +26,7 @@
 
 #define LC_M 18
 #define LC_MAX_S 64
+#define LC_EXP_CHUNK 2048  // elements per CTA of the double-float tier's exponent pre-pass
 
 struct lc_geom {
   int64_t n;      // logical length (longest member for ragged plans)
@@ -47,15 +48,29 @@ __host__ __device__ inline int64_t lc_ahat_offset(int gamma) {
 // l = 0 .. head - k).  The entries of A-hat are the 2-D Chebyshev
 // coefficients of a kernel that is smooth across the well-separated blocks,
 // so they fall off geometrically in k + l (by about 4x per step for L2C,
-// 3x for C2L); beyond the head every entry is below 2e-9 of the matrix's
-// largest for every block size and level, and its leading word alone is
-// accurate to 1e-16 of that.  Words per matrix: a multiple of 4 (16-byte
+// 3x for C2L); beyond the head every entry is below 4e-9 of the matrix's
+// largest for every leaf size s = 4..64 and level (2e-9 for s >= 5; tested),
+// and its leading word alone is accurate to 2.4e-16 of that.  Words per matrix: a multiple of 4 (16-byte
 // bulk copies) with the 3 matrices of a block 28 (L2C) or 12 (C2L) words
 // mod 32 apart, so that the blocks staged by one CTA start in distinct
 // shared-memory banks.
 __host__ __device__ constexpr int lc_dfa_head(int dir) { return dir == LC_L2C ? 13 : 16; }
 __host__ __device__ constexpr int lc_dfa_words(int dir) { return dir == LC_L2C ? 436 : 484; }
 __host__ __device__ constexpr int lc_dfa_rowstart(int k, int head) { return k * (head + 1) - k * (k - 1) / 2; }
+
+// Memory layout of a batch (strides in elements).  Vector b, element j:
+//   input  in[boff(b, ib, inner, iob) + j ie],
+//   output out[boff(b, ob, inner, oob) + j oe],
+// boff(b, stride, inner, outer) = (b / inner) outer + (b % inner) stride, or
+// b stride when inner = 0 (one batch stride).  Two levels reach the fibres of
+// a 3-D array along its middle axis in one call.
+struct lc_layout {
+  int64_t ib, ie, ob, oe;
+  int64_t inner, iob, oob;
+};
+__host__ __device__ __forceinline__ int64_t lc_boff(int64_t b, int64_t stride, int64_t inner, int64_t outer) {
+  return inner > 0 ? (b / inner) * outer + (b % inner) * stride : b * stride;
+}
 
 // Device views of a plan's tables, by element type.
 template <typename R>
@@ -102,6 +117,11 @@ struct lc_plan_s {
   void* df_Ahat;
   void* df_W;
   void* df_Cc;
+  // Per-vector exponents of the double-float tier and the pre-pass's
+  // partial maxima / arrival counters (counters zeroed at plan time).
+  int* xexp;
+  int* xexp_part;
+  unsigned* xexp_cnt;
   // Split tier data (see lc_split.cu).
   void* split;
   // Ragged members (host copies and device tables).
@@ -166,21 +186,20 @@ inline void lc_timer_end(lc_plan_s* p, cudaStream_t st) {
 lc_status lc_compute_geometry(int64_t n, const lc_plan_options* opt, int fixed_default, lc_geom* g);
 
 // ---- execution entry points (lc_exec.cu) ------------------------------------
-lc_status lc_exec_cuda_cores(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie,
-                             int64_t ob, int64_t oe, cudaStream_t st, int adjoint);
+lc_status lc_exec_cuda_cores(lc_plan p, const void* in, void* out, const lc_layout& lay, cudaStream_t st,
+                             int adjoint);
 int lc_exec_cuda_cores_launches(const lc_plan_s* p);
 
 // ---- double-float tier (lc_df.cu) -------------------------------------------
 lc_status lc_df_prepare(lc_plan p, cudaStream_t st);
-lc_status lc_exec_df(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob,
-                     int64_t oe, cudaStream_t st, int adjoint);
+lc_status lc_exec_df(lc_plan p, const void* in, void* out, const lc_layout& lay, cudaStream_t st, int adjoint);
 size_t lc_df_bytes(const lc_geom& g, int64_t batch);
 
 // ---- split tier (lc_split.cu) ------------------------------------------------
 size_t lc_split_bytes(const lc_plan_s* p);
 lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st);
-lc_status lc_exec_split(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob,
-                        int64_t oe, cudaStream_t st, int adjoint);
+lc_status lc_exec_split(lc_plan p, const void* in, void* out, const lc_layout& lay, cudaStream_t st,
+                        int adjoint);
 int lc_exec_split_launches(const lc_plan_s* p);
 void lc_split_release(lc_plan p);
 

@@ -80,6 +80,9 @@ extern "C" lc_status lc_direct_static(lc_direction direction, int64_t n, int64_t
   if (!in || !out || in == static_cast<const double*>(out)) return LC_ERR_INVALID_ARG;
   if (in_batch_stride < 0 || in_elem_stride < 0 || out_batch_stride < 0 || out_elem_stride < 0)
     return LC_ERR_INVALID_ARG;
+  // as lc_execute: a zero output stride would make several rows (or vectors)
+  // write one address
+  if ((out_elem_stride == 0 && n > 1) || (out_batch_stride == 0 && batch > 1)) return LC_ERR_INVALID_ARG;
   double* scratch = nullptr;
   lc_status st = scratch_address(&scratch);
   if (st != LC_OK) return st;

@@ -343,12 +343,22 @@ size_t layout(lc_plan_s* p, char* base) {
     p->df_Ahat = c.take<char>(size_t(g.nc) * lc_dfa_words(p->dir) * sizeof(float));  // compact layout
     p->df_W = c.take<char>(nw * f2);
     p->df_Cc = c.take<char>(nw * f2);
+    const size_t nb = size_t(p->batch);
+    p->xexp = c.take<int>(nb);
+    p->xexp_cnt = c.take<unsigned>(nb);
+    p->xexp_part = c.take<int>(nb * size_t((g.n + LC_EXP_CHUNK - 1) / LC_EXP_CHUNK));
   } else if (p->dtype == LC_F64_SPLIT) {
     const size_t sb = lc_split_bytes(p);
     p->split = c.take<char>(sb);
   }
   return c.off + 256;
 }
+
+// Slices per operand of the split tier when the options leave it to the
+// library: 7 (about 56 bits per operand row) up to n = 1e5, where FP64-accurate
+// output is held to a normwise relative error of 1e-13; 6 beyond, where the
+// bound is 1e-12.
+int auto_slices(int64_t n) { return n <= 100000 ? 7 : 6; }
 
 bool valid_enum(lc_direction d, lc_dtype t) {
   return (d == LC_L2C || d == LC_C2L) &&
@@ -361,9 +371,10 @@ lc_status fill_plan(lc_plan_s* p, int64_t n, lc_direction dir, int64_t batch, lc
   memset(p, 0, sizeof(*p));
   lc_plan_options_default(&p->opt);
   if (opt) p->opt = *opt;
-  if (p->opt.slices < 3 || p->opt.slices > 7) return LC_ERR_INVALID_ARG;
+  if (p->opt.slices != 0 && (p->opt.slices < 3 || p->opt.slices > 7)) return LC_ERR_INVALID_ARG;
   lc_status st = lc_compute_geometry(n, &p->opt, 0, &p->g);
   if (st != LC_OK) return st;
+  if (p->opt.slices == 0) p->opt.slices = auto_slices(n);
   p->dir = dir;
   p->dtype = dtype;
   p->batch = batch;
@@ -382,12 +393,13 @@ lc_status fill_ragged(lc_plan_s* p, const int64_t* n, int64_t count, lc_directio
   lc_plan_options_default(&p->opt);
   if (opt) p->opt = *opt;
   if (p->opt.fixed_s == 0) p->opt.fixed_s = 32;  // one s shared by every member
-  if (p->opt.slices < 3 || p->opt.slices > 7) return LC_ERR_INVALID_ARG;
+  if (p->opt.slices != 0 && (p->opt.slices < 3 || p->opt.slices > 7)) return LC_ERR_INVALID_ARG;
   int64_t nmax = 0;
   for (int64_t i = 0; i < count; ++i) {
     if (n[i] < 1) return LC_ERR_INVALID_ARG;
     if (n[i] > nmax) nmax = n[i];
   }
+  if (p->opt.slices == 0) p->opt.slices = auto_slices(nmax);
   lc_status st = lc_compute_geometry(nmax, &p->opt, 1, &p->g);
   if (st != LC_OK) return st;
   p->dir = dir;
@@ -478,6 +490,7 @@ lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
       k_d2f_T<<<grid_for(g.nc * LC_M * LC_M, 256), 256, 0, st>>>(g.nc, p->Ahat, p->Ahatf);
     LC_LAUNCH_CHECK();
   } else if (p->dtype == LC_F64_DF) {
+    LC_CUDA_TRY(cudaMemsetAsync(p->xexp_cnt, 0, size_t(p->batch) * sizeof(unsigned), st));
     lc_status s2 = lc_df_prepare(p, st);
     if (s2 != LC_OK) return s2;
   }
@@ -493,7 +506,7 @@ lc_status lc_plan_options_default(lc_plan_options* opt) {
   memset(opt, 0, sizeof(*opt));
   opt->s_hat = 32;
   opt->fixed_s = 0;
-  opt->slices = 6;
+  opt->slices = 0;  // automatic (auto_slices)
   return LC_OK;
 }
 
@@ -718,35 +731,59 @@ lc_status lc_plan_launches(lc_plan plan, int32_t* launches) {
   return LC_OK;
 }
 
-static lc_status dispatch(lc_plan plan, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob,
-                          int64_t oe, lc_stream stream, int adjoint) {
+static lc_status dispatch(lc_plan plan, const void* in, void* out, lc_layout lay, lc_stream stream, int adjoint) {
   if (!plan || !in || !out) return LC_ERR_INVALID_ARG;
-  if (ib < 0 || ie < 0 || ob < 0 || oe < 0) return LC_ERR_INVALID_ARG;
+  if (lay.ib < 0 || lay.ie < 0 || lay.ob < 0 || lay.oe < 0 || lay.iob < 0 || lay.oob < 0) return LC_ERR_INVALID_ARG;
+  if (lay.inner < 1 || lay.inner > plan->batch) return LC_ERR_INVALID_ARG;
+  if (lay.inner == plan->batch) lay.inner = 0;  // one batch stride
   if (plan->ragged) {
-    if (ib != 0 || ob != 0 || ie != 1 || oe != 1) return LC_ERR_INVALID_ARG;
+    if (lay.ib != 0 || lay.ob != 0 || lay.ie != 1 || lay.oe != 1 || lay.inner != 0) return LC_ERR_INVALID_ARG;
   } else {
-    if (oe == 0 && plan->g.n > 1) return LC_ERR_INVALID_ARG;
-    if (ob == 0 && plan->batch > 1) return LC_ERR_INVALID_ARG;
+    // no two outputs on one address: within a vector, within an inner group, across groups
+    if (lay.oe == 0 && plan->g.n > 1) return LC_ERR_INVALID_ARG;
+    if (lay.inner == 0 && lay.ob == 0 && plan->batch > 1) return LC_ERR_INVALID_ARG;
+    if (lay.inner > 1 && lay.ob == 0) return LC_ERR_INVALID_ARG;
+    if (lay.inner > 0 && lay.oob == 0) return LC_ERR_INVALID_ARG;
   }
   if (in == out) return LC_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   switch (plan->dtype) {
     case LC_F64:
-    case LC_F32: return lc_exec_cuda_cores(plan, in, out, ib, ie, ob, oe, s, adjoint);
-    case LC_F64_DF: return lc_exec_df(plan, in, out, ib, ie, ob, oe, s, adjoint);
-    case LC_F64_SPLIT: return lc_exec_split(plan, in, out, ib, ie, ob, oe, s, adjoint);
+    case LC_F32: return lc_exec_cuda_cores(plan, in, out, lay, s, adjoint);
+    case LC_F64_DF: return lc_exec_df(plan, in, out, lay, s, adjoint);
+    case LC_F64_SPLIT: return lc_exec_split(plan, in, out, lay, s, adjoint);
   }
   return LC_ERR_INVALID_ARG;
 }
 
 lc_status lc_execute(lc_plan plan, const void* in, void* out, int64_t in_batch_stride, int64_t in_elem_stride,
                      int64_t out_batch_stride, int64_t out_elem_stride, lc_stream stream) {
-  return dispatch(plan, in, out, in_batch_stride, in_elem_stride, out_batch_stride, out_elem_stride, stream, 0);
+  if (!plan) return LC_ERR_INVALID_ARG;
+  const lc_layout lay{in_batch_stride, in_elem_stride, out_batch_stride, out_elem_stride, plan->batch, 0, 0};
+  return dispatch(plan, in, out, lay, stream, 0);
 }
 
 lc_status lc_adjoint(lc_plan plan, const void* in, void* out, int64_t in_batch_stride, int64_t in_elem_stride,
                      int64_t out_batch_stride, int64_t out_elem_stride, lc_stream stream) {
-  return dispatch(plan, in, out, in_batch_stride, in_elem_stride, out_batch_stride, out_elem_stride, stream, 1);
+  if (!plan) return LC_ERR_INVALID_ARG;
+  const lc_layout lay{in_batch_stride, in_elem_stride, out_batch_stride, out_elem_stride, plan->batch, 0, 0};
+  return dispatch(plan, in, out, lay, stream, 1);
+}
+
+lc_status lc_execute_ex(lc_plan plan, const void* in, void* out, int64_t in_batch_stride, int64_t in_elem_stride,
+                        int64_t out_batch_stride, int64_t out_elem_stride, int64_t batch_inner,
+                        int64_t in_outer_stride, int64_t out_outer_stride, lc_stream stream) {
+  const lc_layout lay{in_batch_stride, in_elem_stride, out_batch_stride, out_elem_stride, batch_inner,
+                      in_outer_stride, out_outer_stride};
+  return dispatch(plan, in, out, lay, stream, 0);
+}
+
+lc_status lc_adjoint_ex(lc_plan plan, const void* in, void* out, int64_t in_batch_stride, int64_t in_elem_stride,
+                        int64_t out_batch_stride, int64_t out_elem_stride, int64_t batch_inner,
+                        int64_t in_outer_stride, int64_t out_outer_stride, lc_stream stream) {
+  const lc_layout lay{in_batch_stride, in_elem_stride, out_batch_stride, out_elem_stride, batch_inner,
+                      in_outer_stride, out_outer_stride};
+  return dispatch(plan, in, out, lay, stream, 1);
 }
 
 }  // extern "C"

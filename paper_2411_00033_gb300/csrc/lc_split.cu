@@ -19,8 +19,8 @@
 //
 // Per-vector intermediates are stored as "block floating" double-float rows:
 // 18 (hi, lo) pairs scaled into [-1/2, 1/2] plus one power-of-two exponent
-// per row, so the next product slices them without another scan.  Only the
-// final output conversion touches the FP64 pipe (one add per coefficient).
+// per row, so the next product slices them without another scan.  Step 7
+// (near + far, times C^{-1} for L2C) runs in FP64 on each output.
 //
 // Transposed pass (lc_adjoint): the same products in reverse roles --
 //   leaf    W'(0, v)  = R(v) T(sigma)                  (row strip v: spread^T)
@@ -284,16 +284,36 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
 // Exponent k of a positive normal float v with v in [2^(k-1), 2^k).
 __device__ __forceinline__ int exp_of(float v) { return int((__float_as_uint(v) >> 23) & 0xff) - 126; }
 
-// x * 2^-e_row as a double-float, built from the bit pattern (no FP64 op).
-// Subnormal doubles and results below 2^-126 are flushed to zero.
-__device__ __forceinline__ void d2df_scaled(double x, int e_row, float& hi, float& lo) {
+// Biased exponent of |x| as if normalised (below 1 for subnormals); kNoExp
+// for zero, infinity and NaN.
+constexpr int kNoExp = -(1 << 20);
+__device__ __forceinline__ int exp_field(double x) {
   const uint64_t u = __double_as_longlong(x);
   const int E = int((u >> 52) & 0x7ff);
+  const uint64_t m = u & ((uint64_t(1) << 52) - 1);
+  if (E == 2047) return kNoExp;
+  if (E == 0) return m ? 1 - (__clzll(m) - 11) : kNoExp;
+  return E;
+}
+
+// x * 2^-e_row as a double-float, built from the bit pattern (no FP64 op).
+// Subnormal doubles are normalised first; results below 2^-126 (far below
+// the row's largest entry, whose exponent e_row is) are flushed to zero.
+__device__ __forceinline__ void d2df_scaled(double x, int e_row, float& hi, float& lo) {
+  const uint64_t u = __double_as_longlong(x);
+  int E = int((u >> 52) & 0x7ff);
+  uint64_t m = u & ((uint64_t(1) << 52) - 1);
   if (E == 0) {
-    hi = lo = 0.0f;
-    return;
+    if (m == 0) {
+      hi = lo = 0.0f;
+      return;
+    }
+    const int sh = __clzll(m) - 11;
+    m <<= sh;
+    E = 1 - sh;
+  } else {
+    m |= uint64_t(1) << 52;
   }
-  const uint64_t m = (u & ((uint64_t(1) << 52) - 1)) | (uint64_t(1) << 52);
   const int k = E - 1075 - e_row;  // value = m * 2^k
   const uint32_t mh = uint32_t(m >> 29);
   const uint32_t ml = uint32_t(m & 0x1fffffffu);
@@ -305,16 +325,17 @@ __device__ __forceinline__ void d2df_scaled(double x, int e_row, float& hi, floa
   if (eh < 1) lo = 0.0f;
 }
 
-// f * 2^E as a double (exact for normal f), from the bit pattern.
+// f * 2^E as a double: from the bit pattern (exact) when the result is a
+// normal FP64 number, else by a correctly rounded FP64 scaling.
 __device__ __forceinline__ double f2d_scaled(float f, int E) {
   const uint32_t u = __float_as_uint(f);
   const int ef = int((u >> 23) & 0xff);
   if (ef == 0) return 0.0;
   const int64_t ed = int64_t(ef) - 127 + 1023 + E;
-  if (ed <= 0) return 0.0;
   const uint64_t sgn = uint64_t(u >> 31) << 63;
-  if (ed >= 2047) return __longlong_as_double(sgn | (uint64_t(2047) << 52));
-  return __longlong_as_double(sgn | (uint64_t(ed) << 52) | (uint64_t(u & 0x7fffffu) << 29));
+  if (ed >= 1 && ed <= 2046) return __longlong_as_double(sgn | (uint64_t(ed) << 52) | (uint64_t(u & 0x7fffffu) << 29));
+  if (E < -2200) return 0.0;
+  return ldexp(double(f), E > 2200 ? 2200 : E);
 }
 
 __device__ __forceinline__ uint16_t bf16_of_int(float q) { return uint16_t(__float_as_uint(q) >> 16); }
@@ -434,22 +455,29 @@ __device__ __forceinline__ void warp_ozaki(const uint16_t* Xs, int xs, const uin
 
 // Bring the Y slices of one table item ([S][NP][KP+8] bf16, padded like the
 // shared-memory layout) and its NP exponents into shared memory with two bulk
-// copies.  Must be called by all threads; returns false if the bounded wait
-// ran out (the caller records the failure and exits).
+// copies.  Must be called by all threads.  use = 0 for the CTA's first load
+// (initialises the mbarrier, waits for phase 0), use = 1 for its second
+// (phase 1).  Returns false if the bounded wait ran out; thread 0 then waits
+// once more (bounded) so that a late copy lands before the CTA exits, and the
+// caller records the failure and exits.
 __device__ __forceinline__ bool load_y(const uint16_t* __restrict__ q, const int* __restrict__ e, int S, int NP,
-                                       int KP, uint16_t* Ys, int* Ye, uint64_t* mbar) {
+                                       int KP, uint16_t* Ys, int* Ye, uint64_t* mbar, int use = 0) {
   const uint32_t mb = uint32_t(__cvta_generic_to_shared(mbar));
   const uint32_t bq = uint32_t(S) * NP * (KP + 8) * 2, be = uint32_t(NP) * 4;
   if (threadIdx.x == 0) {
-    lc_mbar_init(mb);
+    if (use == 0) lc_mbar_init(mb);
     lc_fence_proxy_async();
     lc_mbar_expect(mb, bq + be);
     lc_bulk_g2s(Ys, q, bq, mb);
     lc_bulk_g2s(Ye, e, be, mb);
   }
   __syncthreads();
-  const bool ok = lc_mbar_wait_bounded(mb, 0);
-  return !__syncthreads_or(!ok);
+  const bool ok = lc_mbar_wait_bounded(mb, uint32_t(use & 1));
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) lc_mbar_wait_bounded(mb, uint32_t(use & 1));
+    return false;
+  }
+  return true;
 }
 
 struct Dev {
@@ -477,6 +505,7 @@ struct Dev {
   const double* in;
   double* out;
   int64_t ib, ie, ob, oe;
+  int64_t inner, iob, oob;  // two-level batches (lc_layout)
 };
 
 __device__ __forceinline__ int64_t dcnt(const Dev& D, int d, int64_t g) {
@@ -567,7 +596,7 @@ __device__ __forceinline__ double in_value(const Dev& D, int64_t rb, int64_t j, 
 __device__ __forceinline__ void stage_input(const Dev& D, int64_t tile0, int64_t valid, int64_t j0, int ncols,
                                             int KP, Smem& m, const int64_t* rbase, const int64_t* rlen,
                                             int cinv = 0) {
-  for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) m.Xe[rr] = 0;
+  for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) m.Xe[rr] = -4000;  // an all-zero row stays zero
   __syncthreads();
   const int n = kRows * KP;
 #pragma unroll 4
@@ -578,8 +607,8 @@ __device__ __forceinline__ void stage_input(const Dev& D, int64_t tile0, int64_t
     if (c < ncols && tile0 + rr < valid) x = in_value(D, rbase[rr], j, rlen[rr], cinv);
     // max over the lanes of this warp that hold the same row, one atomic per row
     const unsigned grp = __match_any_sync(0xffffffffu, rr);
-    const unsigned E = __reduce_max_sync(grp, unsigned((__double_as_longlong(x) >> 52) & 0x7ff));
-    if ((threadIdx.x & 31) == __ffs(grp) - 1 && E > 0) atomicMax(&m.Xe[rr], int(E));
+    const int E = __reduce_max_sync(grp, exp_field(x));
+    if ((threadIdx.x & 31) == __ffs(grp) - 1 && E > kNoExp) atomicMax(&m.Xe[rr], E);
   }
   __syncthreads();
 #pragma unroll 4
@@ -603,8 +632,8 @@ __device__ __forceinline__ void row_info(const Dev& D, int64_t tile0, int64_t va
   for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) {
     const int64_t r = tile0 + rr;
     const bool ok = r < valid;
-    rbase[rr] = ok ? (D.ragged ? D.off[r] : D.orig[r] * D.ib) : 0;
-    if (obase) obase[rr] = ok ? (D.ragged ? D.off[r] : D.orig[r] * D.ob) : 0;
+    rbase[rr] = ok ? (D.ragged ? D.off[r] : lc_boff(D.orig[r], D.ib, D.inner, D.iob)) : 0;
+    if (obase) obase[rr] = ok ? (D.ragged ? D.off[r] : lc_boff(D.orig[r], D.ob, D.inner, D.oob)) : 0;
     rlen[rr] = ok ? D.len[r] : 0;
   }
   __syncthreads();
@@ -845,7 +874,7 @@ __device__ __forceinline__ void final_body(const Dev& D, unsigned char* sm_raw, 
     const int KPs = D.yKP[Y_SPREAD], NPs = D.yNP[Y_SPREAD];
     Smem m2 = carve(sm_raw, D.S, KPs, NPs);
     if (!load_y(D.yq[Y_SPREAD] + size_t(sigma) * D.S * NPs * (KPs + 8), D.ye[Y_SPREAD] + sigma * NPs, D.S, NPs, KPs,
-                m2.Ys, m2.Ye, mbar)) {
+                m2.Ys, m2.Ye, mbar, 1)) {
       if (threadIdx.x == 0) atomicOr(D.err, 1);
       return;
     }
@@ -882,21 +911,12 @@ __device__ __forceinline__ void final_body(const Dev& D, unsigned char* sm_raw, 
       const bool far = r < validF;
       const int E1 = ((i < 2) ? enx0 : enx1) + eny[nt][i & 1] - 16;
       const int E2 = ((i < 2) ? efx0 : efx1) + efy[nt][i & 1] - 16;
-      const int F = far ? max(E1, E2) : E1;
-      const float s1 = pow2f(E1 - F), s2 = far ? pow2f(E2 - F) : 0.0f;
-      float zh, ze;
-      two_sum(nh[nt][i] * s1, fh[nt][i] * s2, zh, ze);
-      float zl = ze + nl[nt][i] * s1 + fl[nt][i] * s2;
-      fast_two_sum(zh, zl, zh, zl);
-      if (l2c) {  // Step 7: times 2/pi (1/pi for row 0) in double-float
-        const float ch = (row_i == 0) ? 0.31830987334251404f : 0.6366197466850281f;
-        const float cl = (row_i == 0) ? 1.2841276486597053e-08f : 2.5682552973194106e-08f;
-        const float ph = zh * ch;
-        float pe = fmaf(zh, ch, -ph);
-        pe = fmaf(zh, cl, fmaf(zl, ch, pe));
-        fast_two_sum(ph, pe, zh, zl);
-      }
-      D.out[obase[rr] + row_i * D.oe] = f2d_scaled(zh, F) + f2d_scaled(zl, F);
+      // Step 7 in FP64: near (nh + nl) 2^E1 and far (fh + fl) 2^E2, each word
+      // brought to FP64 exactly, summed and scaled by C^{-1} (L2C) in FP64.
+      const double c = l2c ? ((row_i == 0) ? 0.31830988618379067154 : 0.63661977236758134308) : 1.0;
+      const double lo_sum = f2d_scaled(nl[nt][i], E1) + (far ? f2d_scaled(fl[nt][i], E2) : 0.0);
+      const double hi_far = far ? f2d_scaled(fh[nt][i], E2) : 0.0;
+      D.out[obase[rr] + row_i * D.oe] = fma(c, f2d_scaled(nh[nt][i], E1), fma(c, hi_far, c * lo_sum));
     }
 }
 
@@ -1121,8 +1141,8 @@ int lc_exec_split_launches(const lc_plan_s* p) {
   return h ? int(h->launch_kind.size()) : 0;
 }
 
-lc_status lc_exec_split(lc_plan p, const void* in, void* out, int64_t ib, int64_t ie, int64_t ob, int64_t oe,
-                        cudaStream_t st, int adjoint) {
+lc_status lc_exec_split(lc_plan p, const void* in, void* out, const lc_layout& lay, cudaStream_t st,
+                        int adjoint) {
   const SplitHost* h = static_cast<const SplitHost*>(p->ragged_dev);
   if (!h) return LC_ERR_INVALID_ARG;
   Dev D = make_dev(p, *h);
@@ -1134,10 +1154,13 @@ lc_status lc_exec_split(lc_plan p, const void* in, void* out, int64_t ib, int64_
   const std::vector<int>& lkind = adjoint ? h->alaunch_kind : h->launch_kind;
   D.in = static_cast<const double*>(in);
   D.out = static_cast<double*>(out);
-  D.ib = ib;
-  D.ie = ie;
-  D.ob = ob;
-  D.oe = oe;
+  D.ib = lay.ib;
+  D.ie = lay.ie;
+  D.ob = lay.ob;
+  D.oe = lay.oe;
+  D.inner = lay.inner;
+  D.iob = lay.iob;
+  D.oob = lay.oob;
   lc_timer_begin(p);
   for (size_t l = 0; l < lkind.size(); ++l) {
     const int64_t w0 = loff[l], nitems = loff[l + 1] - w0;

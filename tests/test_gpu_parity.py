@@ -193,15 +193,85 @@ def test_round_trip_l2c_c2l(lc):
     assert np.abs(back - x).max() <= 1e-13 * np.abs(x).max()
 
 
-def test_fixed_s_option_same_map(lc):
+@pytest.mark.parametrize("tier", ["f64", "f64_df"])
+def test_fixed_s_option_same_map(lc, tier):
     n = 10000
     x = _input(n, seed=2)
     for code, direction in ((oracle.L2C, "l2c"), (oracle.C2L, "c2l")):
         ref = oracle.apply(code, x)
-        for opts in ({"fixed_s": 32}, {"fixed_s": 20}, {"s_hat": 24}, {"fixed_s": 16}):
-            z, plan = _run(lc, x, direction, **opts)
+        for opts in ({"fixed_s": 32}, {"fixed_s": 20}, {"s_hat": 24}, {"fixed_s": 16}, {"fixed_s": 4},
+                     {"fixed_s": 7}, {"fixed_s": 48}, {"fixed_s": 64}):
+            z, plan = _run(lc, x, direction, dtype=tier, **opts)
             e2, _ = rel_errors(z, ref)
             assert e2 <= 1e-13, (opts, plan.info, e2)
+
+
+# ---- FP64 inputs outside FP32's exponent range (double-float tier)
+# The double-float tier computes in pairs of FP32 numbers.  Each vector is
+# first scaled by the power of two that brings its largest entry into [1, 2)
+# and the result scaled back (both exact), so its accuracy must not depend on
+# where the vector sits in FP64's range.  The oracle runs on the unscaled
+# vector; the GPU result times 2^-k (exact) is compared with it (so that the
+# norms in the comparison cannot overflow).
+@pytest.mark.parametrize("k", [-1000, -160, -110, 0, 120, 900])
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_df_exponent_range(lc, direction, code, adjoint, k):
+    n = 5000
+    x = workloads.decaying_vector(n, seed=71, r=1.0)
+    ref = oracle.apply(code, x, adjoint=adjoint)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, direction, 1, "f64_df", dev)
+    z = plan.execute(torch.as_tensor(x * 2.0 ** k, device=dev), adjoint=adjoint).cpu().numpy()
+    e2, einf = rel_errors(z * 2.0 ** -k, ref)
+    assert e2 <= 1e-13 and einf <= (1e-13 if code == oracle.L2C else 3e-13), (k, e2, einf)
+
+
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_df_exponent_range_batched_mixed(lc, direction, code):
+    # one batch, one vector per scale: each gets its own exponent
+    n, ks = 3000, [-1000, -160, -110, 0, 60, 120, 900]
+    X = np.stack([workloads.decaying_vector(n, seed=80 + i, r=0.5) for i in range(len(ks))])
+    scale = np.array([2.0 ** k for k in ks])[:, None]
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, direction, len(ks), "f64_df", dev)
+    Z = plan(torch.as_tensor(X * scale, device=dev)).cpu().numpy()
+    for i, k in enumerate(ks):
+        e2, _ = rel_errors(Z[i] * 2.0 ** -k, oracle.apply(code, X[i]))
+        assert e2 <= 1e-13, (k, e2)
+
+
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_df_tail_below_fp32_range(lc, direction, code):
+    # a converged spectrum: the second half of the coefficients near 1e-45,
+    # below FP32's normal range relative to nothing -- only relative to the head
+    n = 20000
+    x = workloads.decaying_vector(n, seed=72, r=1.0)
+    x[n // 2:] *= 1e-40
+    dev = torch.device("cuda", 0)
+    z = lc.Plan(n, direction, 1, "f64_df", dev)(torch.as_tensor(x, device=dev)).cpu().numpy()
+    ref = oracle.apply(code, x)
+    e2, einf = rel_errors(z, ref)
+    assert e2 <= 1e-13, (e2, einf)
+    # the tail rows themselves, from a vector that is tail only: still exact to 1e-13
+    t = np.zeros(n)
+    t[n // 2:] = x[n // 2:]
+    zt = lc.Plan(n, direction, 1, "f64_df", dev)(torch.as_tensor(t, device=dev)).cpu().numpy()
+    e2, _ = rel_errors(zt, oracle.apply(code, t))
+    assert e2 <= 1e-13, e2
+
+
+def test_df_zero_and_tiny_vectors(lc):
+    dev = torch.device("cuda", 0)
+    for n in (1, 100, 5000):
+        plan = lc.Plan(n, "l2c", 2, "f64_df", dev)
+        x = np.zeros((2, n))
+        x[1, n // 2] = 5e-324  # the smallest subnormal, alone
+        z = plan(torch.as_tensor(x, device=dev)).cpu().numpy()
+        assert np.all(z[0] == 0.0)
+        ref = oracle.apply(oracle.L2C, x[1])
+        assert np.all(np.isfinite(z[1]))
+        assert np.abs(z[1] - ref).max() <= 1e-320 + 1e-13 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("tier", ["f64", "f64_df", "f32"])
@@ -265,3 +335,20 @@ def test_autotune_picks_and_caches_a_geometry(lc):
     z = plan(x).cpu().numpy()
     e2, _ = rel_errors(z[:2000], oracle.apply(oracle.L2C, x.cpu().numpy(), rows=np.arange(2000)))
     assert e2 <= 1e-13
+
+
+def test_df_exponent_strided_fibres(lc):
+    # many short fibres along axis 0 (the pre-pass then takes one thread per
+    # fibre), each at its own scale across FP64's range
+    n, batch = 512, 1536
+    X = workloads.decaying_vector(n, seed=73, r=1.0, batch=batch)
+    k = np.random.default_rng(74).integers(-900, 900, batch)
+    A = (X * np.exp2(k.astype(np.float64))[:, None]).T.copy()  # (n, batch)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, "l2c", batch, "f64_df", dev)
+    out = torch.empty((batch, n), dtype=torch.float64, device=dev)
+    plan.execute_strided(torch.as_tensor(A, device=dev), out, (1, batch), (n, 1))
+    Z = out.cpu().numpy()
+    for b in np.random.default_rng(75).choice(batch, 16, replace=False):
+        e2, _ = rel_errors(Z[b] * 2.0 ** -int(k[b]), oracle.apply(oracle.L2C, X[b]))
+        assert e2 <= 1e-13, (b, int(k[b]), e2)

@@ -151,3 +151,22 @@ def test_ahat_tail_below_compact_head(lc, n, direction, head):
     assert (peak > 0).all()
     worst = (Ah[:, tail].max(axis=1) / peak).max()
     assert worst <= 2e-9, (plan.info["s"], worst)
+
+
+@pytest.mark.parametrize("direction,head", [("l2c", 13), ("c2l", 16)])
+@pytest.mark.parametrize("s", [4, 5, 6, 8, 11, 12, 16, 24, 40, 48, 63, 64])
+def test_ahat_tail_below_compact_head_every_leaf_size(lc, s, direction, head):
+    """The same property for leaf sizes s across the whole range the plan
+    options accept (4..64), each with six levels, so that the double-float
+    tier's compact A-hat is covered for every s it can be asked to use.  The
+    smallest blocks (s = 4, C2L) reach 2.35e-9; the bound here, 4e-9, still
+    keeps each tail entry's FP32 leading word within 2.4e-16 of its matrix."""
+    plan = lc.Plan(s * 2 ** 8 - 1, direction, 1, "f64", torch.device("cuda", 0), fixed_s=s)
+    assert plan.info["s"] == s and plan.info["L"] == 6
+    nc = plan.info["n_c"]
+    Ah = np.abs(plan.table(3).reshape(nc, M, M))
+    tail = np.add.outer(np.arange(M), np.arange(M)) > head
+    peak = Ah.reshape(nc, -1).max(axis=1)
+    assert (peak > 0).all()
+    worst = (Ah[:, tail].max(axis=1) / peak).max()
+    assert worst <= (4e-9 if s == 4 else 2e-9), (s, worst)

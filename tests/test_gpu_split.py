@@ -1,8 +1,9 @@
 """Split-precision tensor-core tier (LC_F64_SPLIT): parity with the oracle.
 
-Tolerance: the tier is FP64-accurate through exact 8-bit slice products;
-with S = 6 slices the normwise relative error stays <= 1e-12 (the gate for
-this tier), with S = 7 <= 1e-13 (the FP64 gate for n <= 1e5).
+Tolerance: FP64-accurate output is held to a normwise relative error (E_2)
+of 1e-13 for n <= 1e5 and 1e-12 above.  The tier is FP64-accurate through
+exact 8-bit slice products; by default it takes S = 7 slices per operand for
+n <= 1e5 and S = 6 above, which meet those two gates.
 """
 import numpy as np
 import pytest
@@ -40,19 +41,20 @@ def test_split_uniform_batch(lc, n, batch, direction, code):
     for b in range(batch):
         e2, _ = rel_errors(Z[b], oracle.apply(code, X[b]))
         worst = max(worst, e2)
-    assert worst <= 1e-12, (n, batch, worst)
+    assert worst <= 1e-13, (n, batch, worst)
 
 
 @pytest.mark.parametrize("direction,code", DIRS)
-def test_split_seven_slices_fp64_gate(lc, direction, code):
+def test_split_six_slices_meet_the_large_n_gate(lc, direction, code):
+    # the slice count the tier takes above n = 1e5, tried where the oracle is cheap
     n, batch = 5000, 4
     X = _batch(n, batch, seed=77)
     dev = torch.device("cuda", 0)
-    plan = lc.Plan(n, direction, batch, "f64_split", dev, slices=7)
+    plan = lc.Plan(n, direction, batch, "f64_split", dev, slices=6)
     Z = plan(torch.as_tensor(X, device=dev)).cpu().numpy()
     for b in range(batch):
         e2, einf = rel_errors(Z[b], oracle.apply(code, X[b]))
-        assert e2 <= 1e-13, (b, e2, einf)
+        assert e2 <= 1e-12, (b, e2, einf)
 
 
 @pytest.mark.parametrize("direction,code", DIRS)
@@ -71,7 +73,30 @@ def test_split_ragged(lc, direction, code):
         a, b = offs[i], offs[i + 1]
         e2, _ = rel_errors(z[a:b], oracle.apply(code, x[a:b]))
         worst = max(worst, e2)
-    assert worst <= 1e-12, worst
+    assert worst <= 1e-13, worst
+
+
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_split_ragged_full_size_batch(lc, direction, code):
+    """The ragged benchmark batch itself: 4096 members, lengths log-uniform in
+    [64, 65536] (seed 2), N(0,1)(j+1)^-1/2 entries (seed 3), one plan.  The
+    oracle checks 48 members -- the 16 longest and 32 drawn at random -- on up
+    to 512 sampled rows each (all rows of short members)."""
+    lengths = workloads.ragged_lengths(4096, 64, 65536, seed=2)
+    x = workloads.ragged_batch(lengths, seed=3)
+    offs = workloads.ragged_offsets(lengths)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(direction=direction, dtype="f64_split", device=dev, lengths=list(lengths))
+    z = plan(torch.as_tensor(x, device=dev)).cpu().numpy()
+    rng = np.random.default_rng(20)
+    pick = np.concatenate([np.argsort(lengths)[-16:], rng.choice(len(lengths), 32, replace=False)])
+    worst = 0.0
+    for i in pick:
+        a, b = offs[i], offs[i + 1]
+        rows = workloads.sample_rows(int(lengths[i]), 512, seed=int(i))
+        e2, _ = rel_errors(z[a:b][rows], oracle.apply(code, x[a:b], rows=rows))
+        worst = max(worst, e2)
+    assert worst <= 1e-13, worst
 
 
 def test_split_strided_fibres(lc):
@@ -85,20 +110,22 @@ def test_split_strided_fibres(lc):
     Z = out.cpu().numpy()
     for b in range(0, batch, 7):
         e2, _ = rel_errors(Z[b], oracle.apply(oracle.L2C, X[:, b]))
-        assert e2 <= 1e-12, (b, e2)
+        assert e2 <= 1e-13, (b, e2)
 
 
-def test_split_matches_f64_tier_large(lc):
+@pytest.mark.parametrize("r", [0.5, 1.0])
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_split_large_n_sampled_rows(lc, direction, code, r):
+    # n = 65536 (the fit and batched workloads' length): 4096 sampled rows
+    # per member against the oracle's row sums
     n, batch = 65536, 3
-    X = _batch(n, batch, seed=31)
+    X = _batch(n, batch, seed=31, r=r)
     dev = torch.device("cuda", 0)
-    xt = torch.as_tensor(X, device=dev)
-    for direction in ("l2c", "c2l"):
-        zs = lc.Plan(n, direction, batch, "f64_split", dev)(xt).cpu().numpy()
-        zf = lc.Plan(n, direction, batch, "f64", dev)(xt).cpu().numpy()
-        for b in range(batch):
-            e2, _ = rel_errors(zs[b], zf[b])
-            assert e2 <= 1e-12, (direction, b, e2)
+    Z = lc.Plan(n, direction, batch, "f64_split", dev)(torch.as_tensor(X, device=dev)).cpu().numpy()
+    rows = workloads.sample_rows(n, 4096)
+    for b in range(batch):
+        e2, einf = rel_errors(Z[b][rows], oracle.apply(code, X[b], rows=rows))
+        assert e2 <= 1e-13, (direction, r, b, e2, einf)
 
 
 def test_split_graph_capture_replay(lc):
@@ -121,7 +148,7 @@ def test_split_graph_capture_replay(lc):
     Zd = plan(torch.as_tensor(X2, device=dev)).cpu().numpy()
     assert np.array_equal(Z.cpu().numpy(), Zd)
     e2, _ = rel_errors(Zd[0], oracle.apply(oracle.C2L, X2[0]))
-    assert e2 <= 1e-12
+    assert e2 <= 1e-13
 
 
 # ---- transposed pass (lc_adjoint) on the split tier
@@ -137,7 +164,7 @@ def test_split_adjoint_uniform_batch(lc, n, batch, direction, code):
     for b in range(batch):
         e2, _ = rel_errors(Z[b], oracle.apply(code, X[b], adjoint=True))
         worst = max(worst, e2)
-    assert worst <= 1e-12, (n, batch, worst)
+    assert worst <= 1e-13, (n, batch, worst)
 
 
 @pytest.mark.parametrize("direction,code", DIRS)
@@ -156,7 +183,7 @@ def test_split_adjoint_ragged(lc, direction, code):
         a, b = offs[i], offs[i + 1]
         e2, _ = rel_errors(z[a:b], oracle.apply(code, x[a:b], adjoint=True))
         worst = max(worst, e2)
-    assert worst <= 1e-12, worst
+    assert worst <= 1e-13, worst
 
 
 def test_split_adjoint_dot_test_and_strides(lc):
@@ -197,6 +224,6 @@ def test_leaf_tile_autotuner(lc):
     for i in range(len(lengths)):
         a, b = offs[i], offs[i + 1]
         e2, _ = rel_errors(z[a:b], oracle.apply(oracle.C2L, x[a:b]))
-        assert e2 <= 1e-12, (i, s, e2)
+        assert e2 <= 1e-13, (i, s, e2)
     again, s2, _ = lc.autotune_tile(xt, "c2l", "f64_split", dev, lengths=lengths, candidates=(16, 24, 32))
     assert s2 == s and again.info["s"] == s
