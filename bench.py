@@ -153,21 +153,74 @@ def run_reference(args):
 
 # ------------------------------------------------------------- clock sampler
 class ClockSampler:
+    """SM clock and throttle reasons of one GPU, sampled while the timed
+    region runs.  NVML (read-only queries through ctypes) in a background
+    thread every ~1 ms, so that even a region of a few milliseconds is
+    sampled; nvidia-smi at 100 ms as the fallback.  Nothing is changed on the
+    GPU."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clocks-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
     def __init__(self, gpu_index: int):
+        import ctypes
+        import threading
         self.proc = None
         self.gpu = gpu_index
+        self.samples = []
+        self.max_mhz = None
+        self.thread = None
+        self.stop_flag = threading.Event()
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle")
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+                self.max_mhz = float(mx.value)
+            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+
+            def run():
+                clk = ctypes.c_uint()
+                rs = ctypes.c_ulonglong()
+                while not self.stop_flag.is_set():
+                    if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0:
+                        r = rs.value if get_reasons(h, ctypes.byref(rs)) == 0 else 0
+                        self.samples.append((float(clk.value), int(r)))
+                    time.sleep(0.001)
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            time.sleep(0.005)
         except Exception:
-            self.proc = None
+            self.thread = None
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                     "--format=csv,noheader,nounits", "-lms", "100"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except Exception:
+                self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=2)
+            if not self.samples:
+                return None
+            reasons = set()
+            for _, r in self.samples:
+                for bit, nm in self.REASONS.items():
+                    if r & bit:
+                        reasons.add(nm)
+            sm = [c for c, _ in self.samples]
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz or max(sm),
+                    "reasons": sorted(reasons), "samples": len(sm), "source": "nvml"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -193,7 +246,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi"}
 
 
 # ------------------------------------------------------------------ our leg

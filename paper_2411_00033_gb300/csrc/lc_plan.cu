@@ -41,7 +41,15 @@ __device__ double lc_Lambda(double z) {
 
 // The same series for the kernel samples inside A-hat (entries needed to a
 // block-relative 1e-14, not to a few ulp): one reciprocal square root gives
-// both y^(-1/2) and x = y^(-2), instead of two divisions and a square root.
+// both y^(-1/2) and x = y^(-2), instead of two divisions and a square root,
+// and the series keeps only the terms it needs at z: the paper notes that 4,
+// 3 or 2 terms reach machine precision above z = 40, 134 or 1844 (Sec. 4.3).
+__device__ __forceinline__ double tau_terms(double z, double x) {
+  if (z > 1844.0) return 1.0 + x * (-1.0 / 64.0);
+  if (z > 134.0) return 1.0 + x * (-1.0 / 64.0 + x * (21.0 / 8192.0));
+  if (z > 40.0) return 1.0 + x * (-1.0 / 64.0 + x * (21.0 / 8192.0 + x * (-671.0 / 524288.0)));
+  return 1.0 + x * (-1.0 / 64.0 + x * (21.0 / 8192.0 + x * (-671.0 / 524288.0 + x * (180323.0 / 134217728.0))));
+}
 __device__ double lc_Lambda_sample(double z) {
   double f = 1.0;
   while (z < 20.0) {
@@ -51,10 +59,31 @@ __device__ double lc_Lambda_sample(double z) {
   const double y = z + 0.25;
   const double r = rsqrt(y);
   const double r2 = r * r;
+  return f * tau_terms(z, r2 * r2) * r;
+}
+
+// 1 / (w (w + 1) Lambda(w/2)), the factor of L(x, y) (eq:Lxymod) that depends
+// on w = x + y, without a division.  With z = w/2 and y = z + 1/4:
+// w (w + 1) = 4 (y^2 - 1/16), and 1/Lambda(z) = y^(1/2) / tau(y^(-2)); so the
+// factor is y^(-3/2) / 4 times Q(x) = (1/tau(x)) (1/(1 - x/16)), x = y^(-2),
+// whose power series (the reciprocal of eq:tau's series times a geometric
+// series, truncated at x^4 like eq:tau) has the dyadic coefficients below and
+// the same accuracy as eq:tau: 2e-16 relative at z = 19.88, with 4, 3 or 2
+// terms enough above z = 40, 134 or 1844 (checked at 40 digits).  Below
+// z = 20 the argument is shifted up as in lc_Lambda, with one division.
+__device__ double lc_c2l_wfactor(double w) {
+  double z = 0.5 * w;
+  if (z < 20.0) return 1.0 / (w * (w + 1.0) * lc_Lambda_sample(z));
+  const double y = z + 0.25;
+  const double r = rsqrt(y);
+  const double r2 = r * r;
   const double x = r2 * r2;
-  const double tau =
-      1.0 + x * (-1.0 / 64.0 + x * (21.0 / 8192.0 + x * (-671.0 / 524288.0 + x * (180323.0 / 134217728.0))));
-  return f * tau * r;
+  double q;
+  if (z > 1844.0) q = 1.0 + x * (5.0 / 64.0);
+  else if (z > 134.0) q = 1.0 + x * (5.0 / 64.0 + x * (21.0 / 8192.0));
+  else if (z > 40.0) q = 1.0 + x * (5.0 / 64.0 + x * (21.0 / 8192.0 + x * (715.0 / 524288.0)));
+  else q = 1.0 + x * (5.0 / 64.0 + x * (21.0 / 8192.0 + x * (715.0 / 524288.0 + x * (-162877.0 / 134217728.0))));
+  return 0.25 * r2 * r * q;
 }
 
 __global__ void k_plan_lambda(int64_t N, double* __restrict__ lam) {
@@ -82,12 +111,22 @@ __global__ void k_plan_lambda(int64_t N, double* __restrict__ lam) {
 // u_k = Lambda(k)/(1-2k) and v_m = 1/(2m(2m+1) Lambda(m)) -- a factorisation
 // of eq:Lxymod at x = i, y = i + 2k.  v_0 = 0; entry (0,0) = 1 is added
 // separately.  Input: lambda in v (overwritten in place).
+// One division per m: with d = 2m(2m+1) lambda_m and q = 1 / ((1-2m) d),
+// u_m = lambda_m d q and v_m = (1-2m) q (a few ulp).
 __global__ void k_plan_c2l_tables(int64_t N, double* __restrict__ u, double* __restrict__ v) {
   const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (m >= N) return;
   const double l = v[m];
-  u[m] = l / double(1 - 2 * m);
-  v[m] = (m == 0) ? 0.0 : 1.0 / (double(2 * m) * double(2 * m + 1) * l);
+  if (m == 0) {
+    u[0] = l;
+    v[0] = 0.0;
+    return;
+  }
+  const double one_m = double(1 - 2 * m);
+  const double d = double(2 * m) * double(2 * m + 1) * l;
+  const double q = 1.0 / (one_m * d);
+  u[m] = l * d * q;
+  v[m] = one_m * q;
 }
 
 __global__ void k_plan_T(int s, double* __restrict__ T) {
@@ -154,7 +193,9 @@ __global__ void k_plan_cos(double* __restrict__ cosm) {
 // (p,q) = (0,0), (1,1) and 6h for (0,1) (eq:globalij): 2 M x M tables per
 // level, shared by every block of the level (Sec. 4.3 reuses Lambda^- the
 // same way).  Table [L][2][M][M].
-__global__ void k_plan_lminus(int L, int s, const double* __restrict__ cosm, double* __restrict__ tab) {
+// For C2L the table holds Lambda((y-x)/2) / (x - y + 1), the other factor of
+// L(x, y) that depends only on y - x (eq:Lxymod).
+__global__ void k_plan_lminus(int L, int s, int dir, const double* __restrict__ cosm, double* __restrict__ tab) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= int64_t(L) * 2 * LC_M * LC_M) return;
   const int gamma = int(t / (2 * LC_M * LC_M));
@@ -163,7 +204,9 @@ __global__ void k_plan_lminus(int L, int s, const double* __restrict__ cosm, dou
   const double h = double(int64_t(s) << (L - gamma - 1));
   const double off = (c == 0 ? 4.0 : 6.0) * h;  // j0 - i0
   // (y_n - x_m)/2 with x_m = i0 + h (X_m + 1), y_n = j0 + h (Y_n + 1)   (eq:Xfromx)
-  tab[t] = lc_Lambda(0.5 * (off + h * (cosm[LC_M + n] - cosm[LC_M + m])));
+  const double ymx = off + h * (cosm[LC_M + n] - cosm[LC_M + m]);
+  const double l = lc_Lambda(0.5 * ymx);
+  tab[t] = dir == LC_L2C ? l : l / (1.0 - ymx);
 }
 
 // One CTA (M*M threads) per submatrix: sample the kernel, then the 2-D DCT-II
@@ -182,6 +225,19 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
   const int tid = threadIdx.x;
   const int r0 = tid / LC_M, c0 = tid % LC_M;
   cs[r0][c0] = cosm[tid];
+  // The symmetric factor is evaluated once per pair m <= n: 171 pairs on
+  // threads 0..170 (6 warps, full) rather than on the threads whose (r0, c0)
+  // happen to satisfy r0 <= c0 (every warp, half of each).
+  constexpr int kPairs = LC_M * (LC_M + 1) / 2;
+  int pm = 0, pn = 0;
+  if (tid < kPairs) {
+    int rest = tid;
+    while (rest >= LC_M - pm) {
+      rest -= LC_M - pm;
+      ++pm;
+    }
+    pn = pm + rest;
+  }
   for (int64_t a = blockIdx.x; a < nc; a += gridDim.x) {
     int gamma = 0;
     while (gamma + 1 < L && a >= lc_ahat_offset(gamma + 1)) ++gamma;
@@ -195,10 +251,12 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
     const double j0 = 2.0 * h * double(2 * b + q + 2);
     const double* lm = lminus + (size_t(gamma) * 2 + (r == 1 ? 1 : 0)) * (LC_M * LC_M);
     __syncthreads();
-    if (r0 <= c0) {  // Lambda((x_m + y_n)/2), symmetric in (m, n)
-      const double lp = lc_Lambda_sample(0.5 * (i0 + j0 + h * (cs[1][r0] + cs[1][c0] + 2.0)));
-      S[r0][c0] = lp;
-      S[c0][r0] = lp;
+    if (tid < kPairs) {  // the factor that depends on x_m + y_n: symmetric in (m, n)
+      const double w = i0 + j0 + h * (cs[1][pm] + cs[1][pn] + 2.0);
+      // L2C: Lambda((x+y)/2); C2L: 1 / ((x+y)(x+y+1) Lambda((x+y)/2))
+      const double lp = dir == LC_L2C ? lc_Lambda_sample(0.5 * w) : lc_c2l_wfactor(w);
+      S[pm][pn] = lp;
+      S[pn][pm] = lp;
     }
     __syncthreads();
     {
@@ -208,8 +266,8 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
       double val;
       if (dir == LC_L2C) {
         val = lmi * S[r0][c0];  // A(x, y) = Lambda((y-x)/2) Lambda((y+x)/2)
-      } else {                  // L(x, y) of eq:Lxymod (one division)
-        val = 2.0 * (x + 0.5) * y * lmi / ((x + y) * (x + y + 1.0) * (x - y + 1.0) * S[r0][c0]);
+      } else {                  // L(x, y) of eq:Lxymod, no division
+        val = 2.0 * (x + 0.5) * y * lmi * S[r0][c0];
       }
       __syncthreads();
       S[r0][c0] = val;
@@ -475,7 +533,8 @@ lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
     double* lminus = cosm + LC_M * LC_M;
     k_plan_cos<<<2, 256, 0, st>>>(cosm);
     LC_LAUNCH_CHECK();
-    k_plan_lminus<<<unsigned((int64_t(g.L) * 2 * LC_M * LC_M + 255) / 256), 256, 0, st>>>(g.L, g.s, cosm, lminus);
+    k_plan_lminus<<<unsigned((int64_t(g.L) * 2 * LC_M * LC_M + 255) / 256), 256, 0, st>>>(g.L, g.s, int(p->dir),
+                                                                                          cosm, lminus);
     LC_LAUNCH_CHECK();
     const int64_t blocks = g.nc < 1048576 ? g.nc : 1048576;
     k_plan_ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat);

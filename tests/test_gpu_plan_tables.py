@@ -87,6 +87,27 @@ def test_lambda_accuracy(lc):
     assert ulp.max() <= 5
 
 
+def test_c2l_near_field_tables(lc):
+    # u_k = Lambda(k)/(1 - 2k) and v_m = 1/(2m(2m+1) Lambda(m)), the factors of
+    # L(i, i+2k) = (2i+1)(i+2k) u_k v_(i+k) (eq:Lxymod), against the oracle's
+    # double-double lambda: lambda's own error (up to 5 ulp, test above) and
+    # the four roundings of the table kernel, below 2e-15 relative
+    n = 1 << 20
+    plan = lc.Plan(n, "c2l", 1, "f64", torch.device("cuda", 0))
+    N = plan.info["N"]
+    u, v = plan.table(4), plan.table(5)
+    hi, lo = oracle.lambda_table(N)
+    k = np.arange(N, dtype=np.float64)
+    lam = hi + lo
+    u_ref = lam / (1.0 - 2.0 * k)
+    ru = np.abs(u - u_ref) / np.abs(u_ref)
+    assert ru.max() < 2e-15, ru.max()
+    assert v[0] == 0.0
+    v_ref = 1.0 / (2.0 * k[1:] * (2.0 * k[1:] + 1.0) * lam[1:])
+    rv = np.abs(v[1:] - v_ref) / v_ref
+    assert rv.max() < 2e-15, rv.max()
+
+
 def test_T_matrix(lc):
     plan = lc.Plan(1000, "l2c", 1, "f64", torch.device("cuda", 0))
     s = plan.info["s"]
