@@ -309,27 +309,28 @@ def time_fn(fn, flush, steps, warmup):
 
 
 def split_tensor_fractions(lc, dev, X, Z, n, B):
-    """Executed bf16 tensor work of each split-tier kernel kind (mma.m16n8k16 counts
-    from the plan geometry, padding included) over its CUDA-event duration."""
+    """Executed bf16 tensor work of each split-tier kernel kind over its
+    CUDA-event duration.  Every CTA takes 128 members and issues one
+    tcgen05.mma (M = 128, N = 32, K = 16) per slice pair (S (S+1)/2 of them)
+    and K slice of its product; counts come from the plan geometry, padding
+    included."""
     plan = lc.Plan(n, "l2c", B, "f64_split", dev)
     info = plan.info
     L, s = info["L"], info["s"]
     S = 7 if n <= 100000 else 6  # the library's default slice count for this n
     pairs = S * (S + 1) // 2
-    tiles = -(-B // 64)
-    mma = 16 * 8 * 16 * 2
-    per_cta = lambda kt, nt: 4 * pairs * kt * nt  # 4 warps of 16 rows, every slice pair
-    ktiles = lambda K: max(32, -(-K // 16) * 16) // 16  # K padded to 16, at least 32
+    tiles = -(-B // 128)
+    mma = 128 * 32 * 16 * 2
+    kslices = lambda K: max(32, -(-K // 16) * 16) // 16  # K padded to 16, at least 32
     M = info["M"]
-    ctas = {  # tiles of 64 rows x 2 directions sigma, per work item of each launch kind
+    ctas = {  # CTAs (tiles x 2 parities) per work item kind
         0: ((2 << L) - 2) * tiles * 2,
         1: sum((1 << (L - d)) - 2 for d in range(L - 1)) * tiles * 2,
         2: sum((2 << (L - d)) - 2 for d in range(L)) * tiles * 2,
         3: sum((2 << (L - d)) - 4 for d in range(L - 1)) * tiles * 2,
         4: (2 << L) * tiles * 2,  # strips of width 2s
     }
-    kt_nt = {0: per_cta(ktiles(s), 3), 1: per_cta(ktiles(2 * M), 3), 2: per_cta(ktiles(2 * M), 3),
-             3: per_cta(ktiles(M), 3), 4: per_cta(ktiles(2 * s), 4) + per_cta(ktiles(M), 4)}
+    per_cta = {0: kslices(s), 1: kslices(2 * M), 2: kslices(2 * M), 3: kslices(M), 4: kslices(2 * s) + kslices(M)}
     lc.binding.lc_plan_set_timing(plan._handle, 3)
     for _ in range(3):
         plan(X, out=Z)
@@ -347,10 +348,11 @@ def split_tensor_fractions(lc, dev, X, Z, n, B):
     out = {}
     for kind, c in ctas.items():
         if kind in tot and tot[kind] > 0:
-            fl = c * kt_nt[kind] * mma
+            fl = c * pairs * per_cta[kind] * mma
             ach = fl / (tot[kind] / 1e3) / 1e12
-            out["spread_near_scale" if kind == 4 else KIND_NAMES[kind]] = {"bound": "tensor", "executed_tflop": fl / 1e12, "ms": tot[kind],
-                                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak}
+            out["spread_near_scale" if kind == 4 else KIND_NAMES[kind]] = {
+                "bound": "tensor", "executed_tflop": fl / 1e12, "ms": tot[kind], "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak}
     del plan
     return out
 

@@ -47,12 +47,16 @@
 
 #include "lc_internal.cuh"
 #include "lc_tma.cuh"
+#include "lc_umma.cuh"
 
 namespace {
 
-constexpr int kRows = 64;       // members per CTA tile (4 warps x 16 rows)
-constexpr int kThreads = 128;
-constexpr int kNP18 = 24;       // 18 outputs padded to 3 n8 tiles
+constexpr int kRows = 128;      // members per CTA tile: the MMA's M (one TMEM lane per member)
+constexpr int kThreads = 256;   // 8 warps; warp w reads TMEM lanes 32 (w % 4) .. + 31
+constexpr int kNP = 32;         // outputs per product (18, or s <= 32) padded to the MMA's N
+constexpr int kCols = kNP / 2;  // accumulator columns per thread (two threads per member row)
+constexpr int kTmemCols = 256;  // S <= 7 diagonals x kNP columns, rounded up to a power of two
+constexpr int kXCols = 32;      // per-vector operand columns staged at a time
 
 enum YKind {
   Y_LEAF = 0, Y_SPREAD = 1, Y_UP = 2, Y_DOWN = 3, Y_COUPLE = 4, Y_NEAR = 5,
@@ -62,8 +66,8 @@ enum YKind {
 };
 
 struct YTable {
-  int items, K, KP, NP;  // KP: K rounded up to 16; NP: padded outputs
-  size_t off_q, off_e;   // byte offsets in the split region: bf16 [items][S][NP][KP], int32 [items][NP]
+  int items, K, KP;     // KP: K rounded up to 16 (at least 32)
+  size_t off_q, off_e;  // byte offsets in the split region: bf16 [items][S][kNP x KP canonical], int32 [items][kNP]
 };
 
 struct Work {
@@ -222,22 +226,21 @@ void build_host(const lc_plan_s* p, SplitHost& h) {
 
   // Y tables
   const int s = h.s;
-  auto ktab = [&](YKind k, int items, int K, int NP) {
+  auto ktab = [&](YKind k, int items, int K) {
     h.y[k].items = items;
     h.y[k].K = K;
     h.y[k].KP = std::max(32, (K + 15) / 16 * 16);
-    h.y[k].NP = NP;
   };
   int64_t nrowseg = 0;
   for (int G = 0; G < h.Lmax; ++G) nrowseg += (int64_t(4) << G) - 2;
-  ktab(Y_LEAF, 2, s, kNP18);
-  ktab(Y_SPREAD, 2, LC_M, 32);
-  ktab(Y_UP, 1, 2 * LC_M, kNP18);
-  ktab(Y_DOWN, 2, LC_M, kNP18);
-  ktab(Y_COUPLE, int(nrowseg), 2 * LC_M, kNP18);
-  ktab(Y_NEAR, int(2 * h.nstrips), 2 * s, 32);
-  ktab(Y_COUPLE_T, int(nrowseg), 2 * LC_M, kNP18);
-  ktab(Y_NEAR_T, int(2 * h.nstrips), 2 * s, 32);
+  ktab(Y_LEAF, 2, s);
+  ktab(Y_SPREAD, 2, LC_M);
+  ktab(Y_UP, 1, 2 * LC_M);
+  ktab(Y_DOWN, 2, LC_M);
+  ktab(Y_COUPLE, int(nrowseg), 2 * LC_M);
+  ktab(Y_NEAR, int(2 * h.nstrips), 2 * s);
+  ktab(Y_COUPLE_T, int(nrowseg), 2 * LC_M);
+  ktab(Y_NEAR_T, int(2 * h.nstrips), 2 * s);
 
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -248,8 +251,8 @@ void build_host(const lc_plan_s* p, SplitHost& h) {
   };
   for (int k = 0; k < Y_KINDS; ++k) {
     YTable& y = h.y[k];
-    y.off_q = take(size_t(y.items) * h.S * y.NP * (y.KP + 8) * 2);  // rows padded as in shared memory
-    y.off_e = take(size_t(y.items) * y.NP * 4);
+    y.off_q = take(size_t(y.items) * h.S * kNP * y.KP * 2);  // laid out as in shared memory
+    y.off_e = take(size_t(y.items) * kNP * 4);
   }
   h.off_len = take(size_t(h.count) * 8);
   h.off_orig = take(size_t(h.count) * 8);
@@ -342,128 +345,71 @@ __device__ __forceinline__ uint16_t bf16_of_int(float q) { return uint16_t(__flo
 
 // Cut a normalised double-float x = hi + lo (|x| <= 1/2, |lo| <= ulp(hi)) into
 // S base-2^8 digits q_1..q_S (rounded to nearest at each step):
-// x = sum_s q_s 2^(-8 s) + r, |r| <= 2^(-8S-1); dst[s * stride] = bf16(q_s).
+// x = sum_s q_s 2^(-8 s) + r, |r| <= 2^(-8S-1); q[s] = bf16(q_(s+1)).
 // The first two digits come from hi alone (its 24 bits are exact under the
 // 8-bit shifts), lo joins once through TwoSum, and after the third digit the
 // residual fits one float.  Digits stay within [-129, 129].
-__device__ __forceinline__ void slice_df_fast(float hi, float lo, int S, uint16_t* dst, int stride) {
+__device__ __forceinline__ void slice_digits(float hi, float lo, int S, uint16_t (&q)[7]) {
   float r = hi;
-  int sl = 0;
-  for (; sl < 2 && sl < S; ++sl) {
+#pragma unroll
+  for (int sl = 0; sl < 2; ++sl) {
     const float t = r * 256.0f;
-    const float q = rintf(t);
-    r = t - q;
-    dst[sl * stride] = bf16_of_int(q);
+    const float d = rintf(t);
+    r = t - d;
+    q[sl] = bf16_of_int(d);
   }
-  if (sl >= S) return;
   float rh, rl;
   two_sum(r, lo * 65536.0f, rh, rl);  // residual after two digits, lo brought to the same scale
   {
     const float th = rh * 256.0f, tl = rl * 256.0f;
-    const float q = rintf(th);
-    r = (th - q) + tl;  // the rest fits one float
-    dst[sl * stride] = bf16_of_int(q);
-    ++sl;
+    const float d = rintf(th);
+    r = (th - d) + tl;  // the rest fits one float
+    q[2] = bf16_of_int(d);
   }
-  for (; sl < S; ++sl) {
+#pragma unroll
+  for (int sl = 3; sl < 7; ++sl) {
     const float t = r * 256.0f;
-    const float q = rintf(t);
-    r = t - q;
-    dst[sl * stride] = bf16_of_int(q);
+    const float d = rintf(t);
+    r = t - d;
+    q[sl] = sl < S ? bf16_of_int(d) : uint16_t(0);
   }
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-  asm(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// Sliced product of this warp's 16 rows of X (smem [S][kRows][xs]) with Y
-// (smem [S][NT*8][ys]) over KT k16 tiles.  Result per fragment element:
-// hi + lo = sum_u P_u 2^(-8(u-2)), i.e. the product times 2^16 in units of
-// 2^(e_x + e_y).
-__device__ __forceinline__ void ldsm_x4(const uint16_t* p, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  const uint32_t a = uint32_t(__cvta_generic_to_shared(p));
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x2(const uint16_t* p, uint32_t& r0, uint32_t& r1) {
-  const uint32_t a = uint32_t(__cvta_generic_to_shared(p));
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
-}
-
-// Sliced product of this warp's 16 rows of X (smem [S][kRows][xs]) with Y
-// (smem [S][NT*8][ys]) over KT k16 tiles.  Result per fragment element:
-// hi + lo = sum_u P_u 2^(-8(u-2)), i.e. the product times 2^16 in units of
-// 2^(e_x + e_y).  Fragments are loaded with ldmatrix (rows 16-byte aligned).
-template <int KT, int NT>
-__device__ __forceinline__ void warp_ozaki(const uint16_t* Xs, int xs, const uint16_t* Ys, int ys, int S,
-                                           float (&hi)[NT][4], float (&lo)[NT][4]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int xslice = kRows * xs, yslice = NT * 8 * ys;
-  // ldmatrix row addresses of this lane
-  const uint16_t* xw = Xs + (warp * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * xs + (lane >> 4) * 8;
-  const int yrow = (lane & 7) + (lane >> 4) * 8, ycol = ((lane >> 3) & 1) * 8;
-  for (int u = S + 1; u >= 2; --u) {
-    float p[NT][4];
+// Slice the 8 double-floats hi[j] + lo[j], columns 8 ch .. 8 ch + 7 of tile
+// row rr, into the S planes of an operand in the canonical K-major layout of
+// lc_umma.cuh (Kp columns per row, plane_bytes apart): one 16-byte store per
+// plane.  Threads that take consecutive rows at the same ch write one
+// contiguous 128-byte core-matrix row group, free of bank conflicts.
+__device__ __forceinline__ void put_chunk(unsigned char* X, int plane_bytes, int Kp, int rr, int ch, int S,
+                                          const float (&hi)[8], const float (&lo)[8]) {
+  uint32_t w[7][4];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
+  for (int j = 0; j < 8; ++j) {
+    uint16_t q[7];
+    slice_digits(hi[j], lo[j], S, q);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) p[nt][i] = 0.0f;
-    const int s0 = (u - S > 1) ? u - S : 1;
-    const int s1 = (u - 1 < S) ? u - 1 : S;
-    for (int sx = s0; sx <= s1; ++sx) {
-      const uint16_t* xa = xw + (sx - 1) * xslice;
-      const uint16_t* yb = Ys + (u - sx - 1) * yslice + yrow * ys + ycol;
-#pragma unroll
-      for (int kt = 0; kt < KT; ++kt) {
-        uint32_t a0, a1, a2, a3;
-        ldsm_x4(xa + kt * 16, a0, a1, a2, a3);
-#pragma unroll
-        for (int nt = 0; nt + 1 < NT; nt += 2) {
-          uint32_t b0, b1, b2, b3;
-          ldsm_x4(yb + nt * 8 * ys + kt * 16, b0, b1, b2, b3);
-          mma_bf16(p[nt], a0, a1, a2, a3, b0, b1);
-          mma_bf16(p[nt + 1], a0, a1, a2, a3, b2, b3);
-        }
-        if (NT & 1) {
-          uint32_t b0, b1;
-          ldsm_x2(yb + (NT - 1) * 8 * ys + kt * 16, b0, b1);
-          mma_bf16(p[NT - 1], a0, a1, a2, a3, b0, b1);
-        }
-      }
+    for (int sl = 0; sl < 7; ++sl) {
+      if (j & 1) w[sl][j >> 1] |= uint32_t(q[sl]) << 16;
+      else w[sl][j >> 1] = q[sl];
     }
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (u == S + 1) {
-          hi[nt][i] = p[nt][i];
-          lo[nt][i] = 0.0f;
-        } else {
-          float sh, se;
-          two_sum(hi[nt][i] * (1.0f / 256.0f), p[nt][i], sh, se);
-          fast_two_sum(sh, lo[nt][i] * (1.0f / 256.0f) + se, hi[nt][i], lo[nt][i]);
-        }
-      }
   }
+  const uint32_t off = umma_offset(rr, 8 * ch, Kp);
+#pragma unroll
+  for (int sl = 0; sl < 7; ++sl)
+    if (sl < S) *reinterpret_cast<uint4*>(X + sl * plane_bytes + off) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
 }
 
-// Bring the Y slices of one table item ([S][NP][KP+8] bf16, padded like the
-// shared-memory layout) and its NP exponents into shared memory with two bulk
+// Bring the Y slices of one table item (S planes of kNP x KP bf16 in the
+// canonical layout) and its kNP exponents into shared memory with two bulk
 // copies.  Must be called by all threads.  use = 0 for the CTA's first load
 // (initialises the mbarrier, waits for phase 0), use = 1 for its second
 // (phase 1).  Returns false if the bounded wait ran out; thread 0 then waits
 // once more (bounded) so that a late copy lands before the CTA exits, and the
-// caller records the failure and exits.
-__device__ __forceinline__ bool load_y(const uint16_t* __restrict__ q, const int* __restrict__ e, int S, int NP,
-                                       int KP, uint16_t* Ys, int* Ye, uint64_t* mbar, int use = 0) {
-  const uint32_t mb = uint32_t(__cvta_generic_to_shared(mbar));
-  const uint32_t bq = uint32_t(S) * NP * (KP + 8) * 2, be = uint32_t(NP) * 4;
+// caller records the failure.
+__device__ __forceinline__ bool load_y(const uint16_t* __restrict__ q, const int* __restrict__ e, int S, int KP,
+                                       unsigned char* Ys, int* Ye, uint64_t* mbar, int use = 0) {
+  const uint32_t mb = lc_smem_u32(mbar);
+  const uint32_t bq = uint32_t(S) * kNP * KP * 2, be = uint32_t(kNP) * 4;
   if (threadIdx.x == 0) {
     if (use == 0) lc_mbar_init(mb);
     lc_fence_proxy_async();
@@ -496,7 +442,7 @@ struct Dev {
   int* Ce;
   const uint16_t* yq[Y_KINDS];
   const int* ye[Y_KINDS];
-  int yKP[Y_KINDS], yNP[Y_KINDS];
+  int yKP[Y_KINDS];
   int dir;
   int ragged;
   int adj;  // transposed pass
@@ -523,39 +469,51 @@ __device__ __forceinline__ int64_t drow(const Dev& D, int d, int64_t g, int sigm
   return D.rowbase[db + g] + sigma * dcnt(D, d, g) + r;
 }
 
-// smem layout shared by the stage kernels
+// Shared memory of the stage kernels: the per-vector operand X (S planes of
+// kRows x KPx, staged kXCols columns at a time at most), the shared operand
+// Y (S planes of kNP x KP), and small per-row / per-column arrays.
 struct Smem {
-  uint16_t* Xs;
-  int xs;
-  uint16_t* Ys;
-  int ys;
-  int* Xe;
-  int* Ye;
-  int* re;  // [2][kRows] exponents of the staged rows
+  unsigned char* X;
+  unsigned char* Y;
+  int xplane, yplane;  // bytes per slice plane
+  int KPx, KP;         // columns of the staged X chunk and of the Y item
+  int* Xe;             // [kRows] exponent of each staged row
+  int* Ye;             // [kNP]   exponent of each Y row (output column)
+  int* re;             // [2 kRows] stored exponents of the source rows
+  float* rmax;         // [2 kRows] row maxima of the two column halves
 };
-__device__ __forceinline__ Smem carve(unsigned char* base, int S, int KP, int NP) {
+__device__ __forceinline__ Smem carve(unsigned char* base, int S, int KPx, int KP) {
   Smem m;
-  m.xs = KP + 8;
-  m.ys = KP + 8;
-  m.Xs = reinterpret_cast<uint16_t*>(base);
-  m.Ys = m.Xs + S * kRows * m.xs;
-  m.Xe = reinterpret_cast<int*>(m.Ys + S * NP * m.ys);
+  m.KPx = KPx;
+  m.KP = KP;
+  m.xplane = kRows * KPx * 2;
+  m.yplane = kNP * KP * 2;
+  m.X = base;
+  m.Y = base + S * m.xplane;
+  m.Xe = reinterpret_cast<int*>(m.Y + S * m.yplane);
   m.Ye = m.Xe + kRows;
-  m.re = m.Ye + NP;
+  m.re = m.Ye + kNP;
+  m.rmax = reinterpret_cast<float*>(m.re + 2 * kRows);
   return m;
 }
-size_t smem_bytes(int S, int KP, int NP) {
-  return size_t(S) * kRows * (KP + 8) * 2 + size_t(S) * NP * (KP + 8) * 2 + (3 * kRows + NP) * 4 + 16;
+size_t smem_bytes(int S, int KPx, int KP) {
+  return size_t(S) * kRows * KPx * 2 + size_t(S) * kNP * KP * 2 + size_t(kRows + kNP + 4 * kRows) * 4 + 16;
+}
+
+// Make this thread's shared-memory operand writes visible to the tensor
+// cores and order its earlier TMEM reads, then synchronise the CTA.
+__device__ __forceinline__ void sync_for_mma() {
+  lc_fence_proxy_async();
+  umma_fence_before();
+  __syncthreads();
 }
 
 // Stage up to two 18-wide double-float row blocks (rows A0 and, if two, A1
 // for the same members) side by side as one operand row of 18 or 36 columns,
-// in a common exponent frame, sliced into Xs.  The frame comes from the
-// stored row exponents, so every element is then loaded, rescaled and sliced
-// independently (all loads in flight at once).  Rows beyond `valid` are zero.
+// in a common exponent frame (from the stored row exponents), sliced into X.
+// Rows beyond `valid` are zero.
 __device__ __forceinline__ void stage_rows_df(const Dev& D, const float2* A, const int* Ae, int64_t rowA0,
-                                              int64_t rowA1, int two, int64_t tile0, int64_t valid, int KP,
-                                              Smem& m) {
+                                              int64_t rowA1, int two, int64_t tile0, int64_t valid, Smem& m) {
   const int parts = two ? 2 : 1;
   for (int i = threadIdx.x; i < kRows * parts; i += blockDim.x) {
     const int part = i / kRows, rr = i % kRows;
@@ -566,64 +524,78 @@ __device__ __forceinline__ void stage_rows_df(const Dev& D, const float2* A, con
   for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x)
     m.Xe[rr] = two ? max(m.re[rr], m.re[kRows + rr]) : m.re[rr];
   __syncthreads();
-#pragma unroll 4
-  for (int i = threadIdx.x; i < kRows * KP; i += blockDim.x) {
-    const int rr = i / KP, c = i % KP;
-    float hi = 0.0f, lo = 0.0f;
-    if (c < LC_M * parts && tile0 + rr < valid) {
-      const int part = c / LC_M;
-      const float2 v = A[((part ? rowA1 : rowA0) + tile0 + rr) * LC_M + (c - part * LC_M)];
-      const float sc = pow2f(m.re[part * kRows + rr] - m.Xe[rr]);
-      hi = v.x * sc;
-      lo = v.y * sc;
+  const int nch = m.KPx / 8;
+  for (int i = threadIdx.x; i < kRows * nch; i += blockDim.x) {
+    const int rr = i % kRows, ch = i / kRows;
+    const bool ok = tile0 + rr < valid;
+    const float sc0 = ok ? pow2f(m.re[rr] - m.Xe[rr]) : 0.0f;
+    const float sc1 = (ok && two) ? pow2f(m.re[kRows + rr] - m.Xe[rr]) : 0.0f;
+    float hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = 8 * ch + j;
+      hi[j] = lo[j] = 0.0f;
+      if (ok && c < LC_M * parts) {
+        const int part = c >= LC_M;
+        const float2 v = A[((part ? rowA1 : rowA0) + tile0 + rr) * LC_M + (c - part * LC_M)];
+        const float sc = part ? sc1 : sc0;
+        hi[j] = v.x * sc;
+        lo[j] = v.y * sc;
+      }
     }
-    slice_df_fast(hi, lo, D.S, m.Xs + rr * m.xs + c, kRows * m.xs);
+    put_chunk(m.X, m.xplane, m.KPx, rr, ch, D.S, hi, lo);
   }
-  __syncthreads();
+  sync_for_mma();
 }
 
-// Stage the strip/segment of FP64 input: column c < ncols of member row rr
-// is f_r[j0 + 2c] (zero beyond the member's length).  Pass 1 finds each row's
-// exponent (max over the warp's lanes of the same row, then one shared atomic
-// per row); pass 2 reloads the values (L1 hits), frames and slices them.
-// cinv != 0 multiplies each input value by C^{-1} (2/pi, 1/pi at index 0)
-// first (transposed L2C pass); indices below 0 read as zero.
+// FP64 input value j of a member (zero outside [0, len)); cinv != 0
+// multiplies it by C^{-1} (2/pi, 1/pi at index 0) first (transposed L2C pass).
 __device__ __forceinline__ double in_value(const Dev& D, int64_t rb, int64_t j, int64_t len, int cinv) {
   if (j < 0 || j >= len) return 0.0;
   const double x = D.in[rb + j * D.ie];
   return cinv ? x * (j == 0 ? 0.31830988618379067154 : 0.63661977236758134308) : x;
 }
-__device__ __forceinline__ void stage_input(const Dev& D, int64_t tile0, int64_t valid, int64_t j0, int ncols,
-                                            int KP, Smem& m, const int64_t* rbase, const int64_t* rlen,
-                                            int cinv = 0) {
-  for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) m.Xe[rr] = -4000;  // an all-zero row stays zero
+// Exponent of each tile row's largest input value among columns c < ncols
+// (column c of member row rr is x_r[j0 + 2c]); m.Xe receives the row frame
+// exponent (largest entry brought into [1/4, 1/2)).
+__device__ __forceinline__ void input_frames(const Dev& D, int64_t tile0, int64_t valid, int64_t j0, int ncols, Smem& m,
+                                             const int64_t* rbase, const int64_t* rlen, int cinv) {
+  for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) m.Xe[rr] = kNoExp;
   __syncthreads();
-  const int n = kRows * KP;
-#pragma unroll 4
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int rr = i / KP, c = i - rr * KP;
-    double x = 0.0;
-    const int64_t j = j0 + 2 * c;
-    if (c < ncols && tile0 + rr < valid) x = in_value(D, rbase[rr], j, rlen[rr], cinv);
-    // max over the lanes of this warp that hold the same row, one atomic per row
-    const unsigned grp = __match_any_sync(0xffffffffu, rr);
-    const int E = __reduce_max_sync(grp, exp_field(x));
-    if ((threadIdx.x & 31) == __ffs(grp) - 1 && E > kNoExp) atomicMax(&m.Xe[rr], E);
+  const int nch = (ncols + 7) / 8;
+  for (int i = threadIdx.x; i < kRows * nch; i += blockDim.x) {
+    const int rr = i % kRows, ch = i / kRows;
+    if (tile0 + rr >= valid) continue;
+    int E = kNoExp;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = 8 * ch + j;
+      if (c < ncols) E = max(E, exp_field(in_value(D, rbase[rr], j0 + 2 * c, rlen[rr], cinv)));
+    }
+    if (E > kNoExp) atomicMax(&m.Xe[rr], E);
   }
   __syncthreads();
-#pragma unroll 4
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int rr = i / KP, c = i - rr * KP;
-    double x = 0.0;
-    const int64_t j = j0 + 2 * c;
-    if (c < ncols && tile0 + rr < valid) x = in_value(D, rbase[rr], j, rlen[rr], cinv);
-    float hi, lo;
-    d2df_scaled(x, m.Xe[rr] - 1021, hi, lo);
-    slice_df_fast(hi, lo, D.S, m.Xs + rr * m.xs + c, kRows * m.xs);
+  for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) m.Xe[rr] = (m.Xe[rr] > kNoExp ? m.Xe[rr] : -4000) - 1021;
+  __syncthreads();
+}
+// Slice columns [c0, c0 + KPx) of the input operand (zero at c >= ncols) into X
+// in the frame of m.Xe.
+__device__ __forceinline__ void stage_input(const Dev& D, int64_t tile0, int64_t valid, int64_t j0, int ncols, int c0,
+                                            Smem& m, const int64_t* rbase, const int64_t* rlen, int cinv) {
+  const int nch = m.KPx / 8;
+  for (int i = threadIdx.x; i < kRows * nch; i += blockDim.x) {
+    const int rr = i % kRows, ch = i / kRows;
+    const bool ok = tile0 + rr < valid;
+    float hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = c0 + 8 * ch + j;
+      const double x = (ok && c < ncols) ? in_value(D, rbase[rr], j0 + 2 * c, rlen[rr], cinv) : 0.0;
+      d2df_scaled(x, m.Xe[rr], hi[j], lo[j]);
+    }
+    put_chunk(m.X, m.xplane, m.KPx, rr, ch, D.S, hi, lo);
   }
-  __syncthreads();
-  for (int rr = threadIdx.x; rr < kRows; rr += blockDim.x) m.Xe[rr] -= 1021;
-  __syncthreads();
+  sync_for_mma();
 }
 
 // Per-row input/output bases and lengths of a member tile.
@@ -639,125 +611,209 @@ __device__ __forceinline__ void row_info(const Dev& D, int64_t tile0, int64_t va
   __syncthreads();
 }
 
-// Value frame of a fragment row: scale so the row max lies in [1/4, 1/2).
-// hi/lo hold P * 2^16 in units of 2^(e_x + e_y(col)); returns e_row and
-// rescales hi/lo in place to value * 2^-e_row for the 18 real columns.
-template <int NT>
-__device__ __forceinline__ void frame_rows(float (&hi)[NT][4], float (&lo)[NT][4], const int* Ye, int ex0, int ex1,
-                                           int& er0, int& er1) {
-  const int t = threadIdx.x & 3;
-  float m0 = 0.0f, m1 = 0.0f;
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int col = nt * 8 + 2 * t + (i & 1);
-      if (col >= LC_M) continue;
-      const float a = fabsf(hi[nt][i]) * pow2f(Ye[col]);
-      if (i < 2) m0 = fmaxf(m0, a); else m1 = fmaxf(m1, a);
-    }
-  m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 1));
-  m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 2));
-  m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 1));
-  m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 2));
-  const int k0 = (m0 > 0.0f) ? exp_of(m0) : 0;
-  const int k1 = (m1 > 0.0f) ? exp_of(m1) : 0;
-  er0 = ex0 - 16 + k0 + 1;
-  er1 = ex1 - 16 + k1 + 1;
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int col = nt * 8 + 2 * t + (i & 1);
-      const float sc = (col < LC_M) ? pow2f(Ye[col] - ((i < 2) ? k0 : k1) - 1) : 0.0f;
-      hi[nt][i] *= sc;
-      lo[nt][i] *= sc;
-    }
+// ---- tensor-core stage: TMEM holds one kNP-column accumulator per slice
+// diagonal u = s + t (u = 2 .. S + 1), at columns (u - 2) kNP.
+__device__ __forceinline__ void tc_begin(uint32_t* tslot, uint64_t* mbar_mma) {
+  if (threadIdx.x < 32) {
+    umma_alloc(tslot, kTmemCols);
+    umma_relinquish();
+  }
+  if (threadIdx.x == 32) lc_mbar_init(lc_smem_u32(mbar_mma));
+  umma_fence_before();
+  __syncthreads();
+  umma_fence_after();
+}
+__device__ __forceinline__ void tc_end(uint32_t tmem) {
+  umma_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) umma_dealloc(tmem, kTmemCols);
 }
 
-// Store a framed fragment row pair to a double-float row array.
-template <int NT>
-__device__ __forceinline__ void store_rows(float2* Out, int* OutE, int64_t row_base, int64_t tile0, int64_t valid,
-                                           float (&hi)[NT][4], float (&lo)[NT][4], int er0, int er1) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int64_t r0 = tile0 + warp * 16 + g, r1 = r0 + 8;
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int col = nt * 8 + 2 * t + (i & 1);
-      const int64_t r = (i < 2) ? r0 : r1;
-      if (col < LC_M && r < valid) Out[(row_base + r) * LC_M + col] = make_float2(hi[nt][i], lo[nt][i]);
+// Slice products of the staged X (its K slices [xkt0, xkt0 + KPx/16) of the
+// full operand) with the Y item over the K slices [kt0, kt1): thread 0 issues
+// one tcgen05.mma (M = kRows, N = kNP, K = 16) per slice pair and K slice into
+// the diagonal's accumulator -- acc_first: add to what it holds -- and
+// commits them to the mbarrier; every thread waits for that phase (bounded).
+// A timeout returns false after a second bounded wait, so that no MMA is in
+// flight when the caller releases TMEM.
+__device__ __forceinline__ bool tc_products(const Smem& m, int S, int xkt0, int kt0, int kt1, uint32_t tmem,
+                                            uint64_t* mbar_mma, uint32_t& phase, bool acc_first) {
+  const uint32_t mb = lc_smem_u32(mbar_mma);
+  if (threadIdx.x == 0) {
+    umma_fence_after();
+    const uint32_t xs = lc_smem_u32(m.X), ys = lc_smem_u32(m.Y);
+    constexpr uint32_t idesc = umma_idesc_bf16(kRows, kNP);
+    for (int u = 2; u <= S + 1; ++u) {
+      uint32_t acc = acc_first ? 1u : 0u;
+      const int s0 = u - S > 1 ? u - S : 1, s1 = u - 1 < S ? u - 1 : S;
+      for (int sx = s0; sx <= s1; ++sx) {
+        const uint32_t xa = xs + uint32_t(sx - 1) * m.xplane, ya = ys + uint32_t(u - sx - 1) * m.yplane;
+        for (int kt = kt0; kt < kt1; ++kt) {
+          umma_bf16(tmem + uint32_t(u - 2) * kNP, umma_desc_kslice(xa, m.KPx, kt - xkt0),
+                    umma_desc_kslice(ya, m.KP, kt), idesc, acc);
+          acc = 1u;
+        }
+      }
     }
-  if (t == 0) {
-    if (r0 < valid) OutE[row_base + r0] = er0;
-    if (r1 < valid) OutE[row_base + r1] = er1;
+    umma_commit(mb);
   }
+  const bool ok = lc_mbar_wait_bounded(mb, phase);
+  const bool bad = __syncthreads_or(!ok);
+  if (bad && threadIdx.x == 0) lc_mbar_wait_bounded(mb, phase);
+  phase ^= 1u;
+  umma_fence_after();
+  return !bad;
+}
+
+// This thread's place in the accumulators: tile row ep_row() (TMEM lane
+// 32 (warp % 4) + lane), columns ep_col0() .. + kCols - 1.
+__device__ __forceinline__ int ep_row() { return ((threadIdx.x >> 5) & 3) * 32 + (threadIdx.x & 31); }
+__device__ __forceinline__ int ep_col0() { return int(threadIdx.x >> 7) * kCols; }
+
+// Recombine the diagonals of this thread's row and columns:
+// hi + lo = sum_u P_u 2^(-8 (u - 2)), the product times 2^16 in units of
+// 2^(e_x + e_y), by a Horner sum in base 2^8 in double-float.
+__device__ __forceinline__ void tc_recombine(uint32_t tmem, int S, float (&hi)[kCols], float (&lo)[kCols]) {
+  const uint32_t base = tmem + (uint32_t(32 * ((threadIdx.x >> 5) & 3)) << 16) + uint32_t(ep_col0());
+  for (int u = S + 1; u >= 2; --u) {
+    float p[kCols];
+    umma_ld16(base + uint32_t(u - 2) * kNP, p);
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) {
+      if (u == S + 1) {
+        hi[j] = p[j];
+        lo[j] = 0.0f;
+      } else {
+        float sh, se;
+        two_sum(hi[j] * (1.0f / 256.0f), p[j], sh, se);
+        fast_two_sum(sh, lo[j] * (1.0f / 256.0f) + se, hi[j], lo[j]);
+      }
+    }
+  }
+}
+
+// Value frame of this thread's row: hi/lo hold P 2^16 in units of
+// 2^(e_x + e_y(col)); scale them to value 2^-e_row so that the row's largest
+// of its `valid_cols` columns lies in [1/4, 1/2) and return e_row.  The two
+// threads that share a row (column halves) exchange their maxima through
+// shared memory.
+__device__ __forceinline__ int tc_frame(float (&hi)[kCols], float (&lo)[kCols], const int* Ye, int ex,
+                                        int valid_cols, float* rmax) {
+  const int r = ep_row(), c0 = ep_col0();
+  float mx = 0.0f;
+#pragma unroll
+  for (int j = 0; j < kCols; ++j)
+    if (c0 + j < valid_cols) mx = fmaxf(mx, fabsf(hi[j]) * pow2f(Ye[c0 + j]));
+  rmax[(threadIdx.x >> 7) * kRows + r] = mx;
+  __syncthreads();
+  mx = fmaxf(rmax[r], rmax[kRows + r]);
+  const int k = (mx > 0.0f) ? exp_of(mx) : 0;
+#pragma unroll
+  for (int j = 0; j < kCols; ++j) {
+    const float sc = (c0 + j < valid_cols) ? pow2f(Ye[c0 + j] - k - 1) : 0.0f;
+    hi[j] *= sc;
+    lo[j] *= sc;
+  }
+  __syncthreads();  // rmax is free again
+  return ex - 16 + k + 1;
+}
+
+// Store this thread's part of a framed row to a double-float row array.
+__device__ __forceinline__ void tc_store_row(float2* Out, int* OutE, int64_t row_base, int64_t tile0, int64_t valid,
+                                             const float (&hi)[kCols], const float (&lo)[kCols], int er) {
+  const int r = ep_row(), c0 = ep_col0();
+  const int64_t row = tile0 + r;
+  if (row >= valid) return;
+#pragma unroll
+  for (int j = 0; j < kCols; ++j)
+    if (c0 + j < LC_M) Out[(row_base + row) * LC_M + c0 + j] = make_float2(hi[j], lo[j]);
+  if (c0 == 0) OutE[row_base + row] = er;
 }
 
 // ------------------------------------------------------------------ kernels
+// Every kernel: one (segment or strip, parity sigma = blockIdx.y, tile of
+// kRows members) per CTA; TMEM allocated at the start and released at the
+// end on every path; a failed bounded wait sets the plan's status word.
+
 // Step 1: W(0, g, sigma) = F(g, sigma) T(sigma).
 __global__ void __launch_bounds__(kThreads) k_s_leaf(Dev D, int64_t w0) {
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t mbar;
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
+  __shared__ uint32_t tslot;
+  __shared__ int64_t rbase[kRows], rlen[kRows];
   const Work it = D.work[w0 + blockIdx.x];
   const int sigma = blockIdx.y;
-  const int KP = D.yKP[Y_LEAF], NP = D.yNP[Y_LEAF];
-  Smem m = carve(sm_raw, D.S, KP, NP);
+  const int KP = D.yKP[Y_LEAF];
+  Smem m = carve(sm_raw, D.S, KP, KP);
+  tc_begin(&tslot, &mbar_mma);
+  const uint32_t tmem = tslot;
+  uint32_t phase = 0;
   const int64_t g = it.seg, tile0 = int64_t(it.tile) * kRows;  // column segment (transposed: row strip)
   const int64_t valid = dcnt(D, 0, D.adj ? g + 2 : g);
-  if (!load_y(D.yq[Y_LEAF] + size_t(sigma) * D.S * NP * (KP + 8), D.ye[Y_LEAF] + sigma * NP, D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
-    if (threadIdx.x == 0) atomicOr(D.err, 1);
-    return;
+  bool ok = load_y(D.yq[Y_LEAF] + size_t(sigma) * D.S * kNP * KP, D.ye[Y_LEAF] + sigma * kNP, D.S, KP, m.Y, m.Ye,
+                   &mbar_y);
+  if (ok) {
+    const int s = D.s;
+    const int cinv = D.adj && D.dir == LC_L2C;
+    row_info(D, tile0, valid, rbase, nullptr, rlen);
+    input_frames(D, tile0, valid, 2 * int64_t(s) * g + sigma, s, m, rbase, rlen, cinv);
+    stage_input(D, tile0, valid, 2 * int64_t(s) * g + sigma, s, 0, m, rbase, rlen, cinv);
+    ok = tc_products(m, D.S, 0, 0, KP / 16, tmem, &mbar_mma, phase, false);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int s = D.s;
-  __shared__ int64_t rbase[kRows], rlen[kRows];
-  row_info(D, tile0, valid, rbase, nullptr, rlen);
-  stage_input(D, tile0, valid, 2 * int64_t(s) * g + sigma, s, KP, m, rbase, rlen, D.adj && D.dir == LC_L2C);
-  float hi[3][4], lo[3][4];
-  warp_ozaki<2, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
-  const int g8 = lane >> 2;
-  int er0, er1;
-  frame_rows<3>(hi, lo, m.Ye, m.Xe[warp * 16 + g8], m.Xe[warp * 16 + g8 + 8], er0, er1);
-  store_rows<3>(D.W, D.We, drow(D, 0, g, sigma, 0), tile0, valid, hi, lo, er0, er1);
+  if (ok) {
+    float hi[kCols], lo[kCols];
+    tc_recombine(tmem, D.S, hi, lo);
+    const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
+    tc_store_row(D.W, D.We, drow(D, 0, g, sigma, 0), tile0, valid, hi, lo, er);
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
+  tc_end(tmem);
 }
 
 // Step 2: W(d+1, G) = [W(d, 2G) W(d, 2G+1)] [B(0) B(1)]^T.
 __global__ void __launch_bounds__(kThreads) k_s_up(Dev D, int64_t w0) {
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t mbar;
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
+  __shared__ uint32_t tslot;
   const Work it = D.work[w0 + blockIdx.x];
   const int sigma = blockIdx.y;
-  const int KP = D.yKP[Y_UP], NP = D.yNP[Y_UP];
-  Smem m = carve(sm_raw, D.S, KP, NP);
+  const int KP = D.yKP[Y_UP];
+  Smem m = carve(sm_raw, D.S, KP, KP);
+  tc_begin(&tslot, &mbar_mma);
+  const uint32_t tmem = tslot;
+  uint32_t phase = 0;
   const int dp = it.d;  // parent level
   const int64_t G = it.seg, tile0 = int64_t(it.tile) * kRows;
   const int64_t valid = dcnt(D, dp, D.adj ? G + 2 : G);  // transposed: row tree
-  if (!load_y(D.yq[Y_UP], D.ye[Y_UP], D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
-    if (threadIdx.x == 0) atomicOr(D.err, 1);
-    return;
+  bool ok = load_y(D.yq[Y_UP], D.ye[Y_UP], D.S, KP, m.Y, m.Ye, &mbar_y);
+  if (ok) {
+    stage_rows_df(D, D.W, D.We, drow(D, dp - 1, 2 * G, sigma, 0), drow(D, dp - 1, 2 * G + 1, sigma, 0), 1, tile0,
+                  valid, m);
+    ok = tc_products(m, D.S, 0, 0, KP / 16, tmem, &mbar_mma, phase, false);
   }
-  stage_rows_df(D, D.W, D.We, drow(D, dp - 1, 2 * G, sigma, 0), drow(D, dp - 1, 2 * G + 1, sigma, 0), 1, tile0,
-                valid, KP, m);
-  float hi[3][4], lo[3][4];
-  warp_ozaki<3, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2;
-  int er0, er1;
-  frame_rows<3>(hi, lo, m.Ye, m.Xe[warp * 16 + g8], m.Xe[warp * 16 + g8 + 8], er0, er1);
-  store_rows<3>(D.W, D.We, drow(D, dp, G, sigma, 0), tile0, valid, hi, lo, er0, er1);
+  if (ok) {
+    float hi[kCols], lo[kCols];
+    tc_recombine(tmem, D.S, hi, lo);
+    const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
+    tc_store_row(D.W, D.We, drow(D, dp, G, sigma, 0), tile0, valid, hi, lo, er);
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
+  tc_end(tmem);
 }
 
 // Step 3: C(d, v) = [W(d, v+2) W(d, v+3)] [A-hat(b,0) A-hat(b,1)]^T (v even),
 //                  W(d, v+2) A-hat(b,2)^T (v odd).
 __global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) {
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t mbar;
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
+  __shared__ uint32_t tslot;
   const Work it = D.work[w0 + blockIdx.x];
   const int sigma = blockIdx.y;
-  const int KP = D.yKP[Y_COUPLE], NP = D.yNP[Y_COUPLE];
-  Smem m = carve(sm_raw, D.S, KP, NP);
+  const int KP = D.yKP[Y_COUPLE];
+  Smem m = carve(sm_raw, D.S, KP, KP);
+  tc_begin(&tslot, &mbar_mma);
+  const uint32_t tmem = tslot;
+  uint32_t phase = 0;
   const int d = it.d;
   // forward: row segment v from column segments v+2 (and v+3);
   // transposed: column segment g = seg from row segments g-2 (and g-3)
@@ -766,163 +822,85 @@ __global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) {
   const int Gam = D.Lmax - 1 - d;  // level in the shared table
   const int64_t item = (int64_t(4) * ((int64_t(1) << Gam) - 1) - 2 * Gam) + (D.adj ? v - 2 : v);
   const YKind yk = D.adj ? Y_COUPLE_T : Y_COUPLE;
-  if (!load_y(D.yq[yk] + size_t(item) * D.S * NP * (KP + 8), D.ye[yk] + item * NP, D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
-    if (threadIdx.x == 0) atomicOr(D.err, 1);
-    return;
+  bool ok = load_y(D.yq[yk] + size_t(item) * D.S * kNP * KP, D.ye[yk] + item * kNP, D.S, KP, m.Y, m.Ye, &mbar_y);
+  if (ok) {
+    const int two = D.adj ? int(v & 1) : ((v & 1) == 0 ? 1 : 0);
+    const int64_t s0 = D.adj ? v - 2 : v + 2, s1 = D.adj ? v - 3 : v + 3;
+    stage_rows_df(D, D.W, D.We, drow(D, d, s0, sigma, 0), two ? drow(D, d, s1, sigma, 0) : 0, two, tile0, valid, m);
+    ok = tc_products(m, D.S, 0, 0, KP / 16, tmem, &mbar_mma, phase, false);
   }
-  const int two = D.adj ? int(v & 1) : ((v & 1) == 0 ? 1 : 0);
-  const int64_t s0 = D.adj ? v - 2 : v + 2, s1 = D.adj ? v - 3 : v + 3;
-  stage_rows_df(D, D.W, D.We, drow(D, d, s0, sigma, 0), two ? drow(D, d, s1, sigma, 0) : 0, two, tile0, valid, KP, m);
-  float hi[3][4], lo[3][4];
-  warp_ozaki<3, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2;
-  int er0, er1;
-  frame_rows<3>(hi, lo, m.Ye, m.Xe[warp * 16 + g8], m.Xe[warp * 16 + g8 + 8], er0, er1);
-  store_rows<3>(D.C, D.Ce, drow(D, d, v, sigma, 0), tile0, valid, hi, lo, er0, er1);
+  if (ok) {
+    float hi[kCols], lo[kCols];
+    tc_recombine(tmem, D.S, hi, lo);
+    const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
+    tc_store_row(D.C, D.Ce, drow(D, d, v, sigma, 0), tile0, valid, hi, lo, er);
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
+  tc_end(tmem);
 }
 
 // Step 4: C(d, v) += C(d+1, v/2) B(v mod 2).
 __global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) {
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t mbar;
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
+  __shared__ uint32_t tslot;
   const Work it = D.work[w0 + blockIdx.x];
   const int sigma = blockIdx.y;
-  const int KP = D.yKP[Y_DOWN], NP = D.yNP[Y_DOWN];
-  Smem m = carve(sm_raw, D.S, KP, NP);
+  const int KP = D.yKP[Y_DOWN];
+  Smem m = carve(sm_raw, D.S, KP, KP);
+  tc_begin(&tslot, &mbar_mma);
+  const uint32_t tmem = tslot;
+  uint32_t phase = 0;
   const int d = it.d;
   const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;  // child (row segment; transposed: column segment)
   const int64_t valid = dcnt(D, d, D.adj ? v : v + 4);
   const int p = int(v & 1);
-  if (!load_y(D.yq[Y_DOWN] + size_t(p) * D.S * NP * (KP + 8), D.ye[Y_DOWN] + p * NP, D.S, NP, KP, m.Ys, m.Ye, &mbar)) {
-    if (threadIdx.x == 0) atomicOr(D.err, 1);
-    return;
+  bool ok = load_y(D.yq[Y_DOWN] + size_t(p) * D.S * kNP * KP, D.ye[Y_DOWN] + p * kNP, D.S, KP, m.Y, m.Ye, &mbar_y);
+  if (ok) {
+    stage_rows_df(D, D.C, D.Ce, drow(D, d + 1, v >> 1, sigma, 0), 0, 0, tile0, valid, m);
+    ok = tc_products(m, D.S, 0, 0, KP / 16, tmem, &mbar_mma, phase, false);
   }
-  stage_rows_df(D, D.C, D.Ce, drow(D, d + 1, v >> 1, sigma, 0), 0, 0, tile0, valid, KP, m);
-  float hi[3][4], lo[3][4];
-  warp_ozaki<2, 3>(m.Xs, m.xs, m.Ys, m.ys, D.S, hi, lo);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2, t = lane & 3;
-  int er0, er1;
-  frame_rows<3>(hi, lo, m.Ye, m.Xe[warp * 16 + g8], m.Xe[warp * 16 + g8 + 8], er0, er1);
-  // add the existing row (couple result) in a common frame
-  const int64_t base = drow(D, d, v, sigma, 0);
-  const int64_t r0 = tile0 + warp * 16 + g8, r1 = r0 + 8;
-  int eo0 = 0, eo1 = 0;
-  if (r0 < valid) eo0 = D.Ce[base + r0];
-  if (r1 < valid) eo1 = D.Ce[base + r1];
-  const int F0 = max(er0, eo0) + 1, F1 = max(er1, eo1) + 1;
-  const float sa0 = pow2f(er0 - F0), sb0 = pow2f(eo0 - F0), sa1 = pow2f(er1 - F1), sb1 = pow2f(eo1 - F1);
+  if (ok) {
+    float hi[kCols], lo[kCols];
+    tc_recombine(tmem, D.S, hi, lo);
+    const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
+    // add the existing row (couple result) in a common frame
+    const int64_t base = drow(D, d, v, sigma, 0);
+    const int r = ep_row(), c0 = ep_col0();
+    const int64_t row = tile0 + r;
+    const int eo = row < valid ? D.Ce[base + row] : 0;
+    const int F = max(er, eo) + 1;
+    const float sa = pow2f(er - F), sb = pow2f(eo - F);
+    __syncthreads();  // both halves of every row have read the old exponent
+    if (row < valid) {
 #pragma unroll
-  for (int nt = 0; nt < 3; ++nt)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int col = nt * 8 + 2 * t + (i & 1);
-      const int64_t r = (i < 2) ? r0 : r1;
-      if (col >= LC_M || r >= valid) continue;
-      const float2 o = D.C[(base + r) * LC_M + col];
-      const float sa = (i < 2) ? sa0 : sa1, sb = (i < 2) ? sb0 : sb1;
-      float sh, se;
-      two_sum(hi[nt][i] * sa, o.x * sb, sh, se);
-      float nh, nl;
-      fast_two_sum(sh, se + lo[nt][i] * sa + o.y * sb, nh, nl);
-      D.C[(base + r) * LC_M + col] = make_float2(nh, nl);
+      for (int j = 0; j < kCols; ++j) {
+        const int col = c0 + j;
+        if (col >= LC_M) continue;
+        const float2 o = D.C[(base + row) * LC_M + col];
+        float sh, se, nh, nl;
+        two_sum(hi[j] * sa, o.x * sb, sh, se);
+        fast_two_sum(sh, se + lo[j] * sa + o.y * sb, nh, nl);
+        D.C[(base + row) * LC_M + col] = make_float2(nh, nl);
+      }
+      if (c0 == 0) D.Ce[base + row] = F;
     }
-  if (t == 0) {
-    if (r0 < valid) D.Ce[base + r0] = F0;
-    if (r1 < valid) D.Ce[base + r1] = F1;
   }
+  if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
+  tc_end(tmem);
 }
 
-// Steps 5-7 for strip t and parity sigma, 64 members per CTA:
-//   Z = F(strip) E^T + C(0, t) T(sigma)^T, then C^{-1}, store.
-// Two sliced products (near field, K = 2s; spread, K = 18) that reuse the
-// same shared memory; their double-float results are added in a common frame.
-template <int KTN>
-__device__ __forceinline__ void final_body(const Dev& D, unsigned char* sm_raw, uint64_t* mbar, int64_t t, int sigma,
-                                           int64_t tile0, int64_t validN, int64_t validF) {
-  const int s = D.s;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g8 = lane >> 2, tq = lane & 3;
-  __shared__ int64_t rbase[kRows], obase[kRows], rlen[kRows];
-  row_info(D, tile0, validN, rbase, obase, rlen);
-  // ---- near field
-  const int KPn = KTN * 16, NPn = D.yNP[Y_NEAR];
-  Smem m = carve(sm_raw, D.S, KPn, NPn);
-  const int64_t item = 2 * t + sigma;
-  const YKind yk = D.adj ? Y_NEAR_T : Y_NEAR;
-  if (!load_y(D.yq[yk] + size_t(item) * D.S * NPn * (KPn + 8), D.ye[yk] + item * NPn, D.S, NPn, KPn, m.Ys, m.Ye,
-              mbar)) {
-    if (threadIdx.x == 0) atomicOr(D.err, 1);
-    return;
-  }
-  // forward: columns of strips t, t+1 of the band of rows in strip t;
-  // transposed: rows of strips t-1, t (times C^{-1} for L2C) for columns in strip t
-  stage_input(D, tile0, validN, 2 * int64_t(s) * (D.adj ? t - 1 : t) + sigma, 2 * s, KPn, m, rbase, rlen,
-              D.adj && D.dir == LC_L2C);
-  float nh[4][4], nl[4][4];
-  warp_ozaki<KTN, 4>(m.Xs, m.xs, m.Ys, m.ys, D.S, nh, nl);
-  const int enx0 = m.Xe[warp * 16 + g8], enx1 = m.Xe[warp * 16 + g8 + 8];
-  int eny[4][2];
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-    eny[nt][0] = m.Ye[nt * 8 + 2 * tq];
-    eny[nt][1] = m.Ye[nt * 8 + 2 * tq + 1];
-  }
-  __syncthreads();
-  // ---- far field (spread)
-  float fh[4][4], fl[4][4];
-  int efx0 = 0, efx1 = 0, efy[4][2];
-  if (validF > tile0) {
-    const int KPs = D.yKP[Y_SPREAD], NPs = D.yNP[Y_SPREAD];
-    Smem m2 = carve(sm_raw, D.S, KPs, NPs);
-    if (!load_y(D.yq[Y_SPREAD] + size_t(sigma) * D.S * NPs * (KPs + 8), D.ye[Y_SPREAD] + sigma * NPs, D.S, NPs, KPs,
-                m2.Ys, m2.Ye, mbar, 1)) {
-      if (threadIdx.x == 0) atomicOr(D.err, 1);
-      return;
-    }
-    stage_rows_df(D, D.C, D.Ce, drow(D, 0, t, sigma, 0), 0, 0, tile0, validF, KPs, m2);
-    warp_ozaki<2, 4>(m2.Xs, m2.xs, m2.Ys, m2.ys, D.S, fh, fl);
-    efx0 = m2.Xe[warp * 16 + g8];
-    efx1 = m2.Xe[warp * 16 + g8 + 8];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      efy[nt][0] = m2.Ye[nt * 8 + 2 * tq];
-      efy[nt][1] = m2.Ye[nt * 8 + 2 * tq + 1];
-    }
-  } else {
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) fh[nt][i] = fl[nt][i] = 0.0f;
-      efy[nt][0] = efy[nt][1] = 0;
-    }
-  }
-  // ---- combine, scale, store
-  const int64_t r0 = tile0 + warp * 16 + g8, r1 = r0 + 8;
-  const bool l2c = (D.dir == LC_L2C) && !D.adj;  // Step 7 (the transposed pass applied C^{-1} first)
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int col = nt * 8 + 2 * tq + (i & 1);  // local row m of the strip
-      const int rr = warp * 16 + g8 + ((i < 2) ? 0 : 8);
-      const int64_t r = (i < 2) ? r0 : r1;
-      if (col >= s || r >= validN) continue;
-      const int64_t row_i = 2 * int64_t(s) * t + 2 * col + sigma;
-      if (row_i >= rlen[rr]) continue;
-      const bool far = r < validF;
-      const int E1 = ((i < 2) ? enx0 : enx1) + eny[nt][i & 1] - 16;
-      const int E2 = ((i < 2) ? efx0 : efx1) + efy[nt][i & 1] - 16;
-      // Step 7 in FP64: near (nh + nl) 2^E1 and far (fh + fl) 2^E2, each word
-      // brought to FP64 exactly, summed and scaled by C^{-1} (L2C) in FP64.
-      const double c = l2c ? ((row_i == 0) ? 0.31830988618379067154 : 0.63661977236758134308) : 1.0;
-      const double lo_sum = f2d_scaled(nl[nt][i], E1) + (far ? f2d_scaled(fl[nt][i], E2) : 0.0);
-      const double hi_far = far ? f2d_scaled(fh[nt][i], E2) : 0.0;
-      D.out[obase[rr] + row_i * D.oe] = fma(c, f2d_scaled(nh[nt][i], E1), fma(c, hi_far, c * lo_sum));
-    }
-}
-
+// Steps 5-7 for strip t and parity sigma, kRows members per CTA:
+//   Z = F(strip) E^T + C(0, t) T(sigma)^T, then C^{-1} (L2C), store.
+// The near-field product (K = 2s, staged kXCols columns at a time) and the
+// spread (K = 18) reuse the same shared memory and TMEM one after the other;
+// their results meet in the FP64 Step 7.
 __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t mbar;
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
+  __shared__ uint32_t tslot;
+  __shared__ int64_t rbase[kRows], obase[kRows], rlen[kRows];
+  __shared__ int ye_near[kNP];
   const Work it = D.work[w0 + blockIdx.x];
   const int sigma = blockIdx.y;
   const int64_t t = it.seg, tile0 = int64_t(it.tile) * kRows;
@@ -931,13 +909,82 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
   const int64_t validF = D.Lmax <= 0 ? 0
                          : D.adj ? ((t >= 2 && t < (int64_t(2) << D.Lmax)) ? dcnt(D, 0, t) : 0)
                                  : ((t + 2 < (int64_t(2) << D.Lmax)) ? dcnt(D, 0, t + 2) : 0);
+  const int s = D.s;
   const int KPn = D.yKP[Y_NEAR];
-  if (KPn == 64)
-    final_body<4>(D, sm_raw, &mbar, t, sigma, tile0, validN, validF);
-  else if (KPn == 48)
-    final_body<3>(D, sm_raw, &mbar, t, sigma, tile0, validN, validF);
-  else
-    final_body<2>(D, sm_raw, &mbar, t, sigma, tile0, validN, validF);
+  const int KPx = KPn < kXCols ? KPn : kXCols;
+  Smem m = carve(sm_raw, D.S, KPx, KPn);
+  tc_begin(&tslot, &mbar_mma);
+  const uint32_t tmem = tslot;
+  uint32_t phase = 0;
+  const int r = ep_row(), c0 = ep_col0();
+  float nh[kCols], nl[kCols], fh[kCols], fl[kCols];
+  int enx = 0, efx = 0;
+  // ---- near field
+  const int64_t item = 2 * t + sigma;
+  const YKind yk = D.adj ? Y_NEAR_T : Y_NEAR;
+  bool ok = load_y(D.yq[yk] + size_t(item) * D.S * kNP * KPn, D.ye[yk] + item * kNP, D.S, KPn, m.Y, m.Ye, &mbar_y);
+  if (ok) {
+    // forward: columns of strips t, t+1 of the band of rows in strip t;
+    // transposed: rows of strips t-1, t (times C^{-1} for L2C) for columns in strip t
+    const int cinv = D.adj && D.dir == LC_L2C;
+    const int64_t j0 = 2 * int64_t(s) * (D.adj ? t - 1 : t) + sigma;
+    row_info(D, tile0, validN, rbase, obase, rlen);
+    input_frames(D, tile0, validN, j0, 2 * s, m, rbase, rlen, cinv);
+    for (int cc = 0; cc < KPn && ok; cc += KPx) {
+      if (cc > 0) sync_for_mma();  // (the previous chunk's products are complete)
+      stage_input(D, tile0, validN, j0, 2 * s, cc, m, rbase, rlen, cinv);
+      const int kt1 = (cc + KPx < KPn ? cc + KPx : KPn) / 16;
+      ok = tc_products(m, D.S, cc / 16, cc / 16, kt1, tmem, &mbar_mma, phase, cc > 0);
+    }
+  }
+  if (ok) {
+    tc_recombine(tmem, D.S, nh, nl);
+    enx = m.Xe[r];
+    if (threadIdx.x < kNP) ye_near[threadIdx.x] = m.Ye[threadIdx.x];
+    sync_for_mma();  // every TMEM read of the near field is done; Y and Xe may be overwritten
+  }
+  // ---- far field (spread)
+  const bool far_tile = validF > tile0;
+  if (ok && far_tile) {
+    const int KPs = D.yKP[Y_SPREAD];
+    Smem m2 = carve(sm_raw, D.S, KPs, KPs);
+    ok = load_y(D.yq[Y_SPREAD] + size_t(sigma) * D.S * kNP * KPs, D.ye[Y_SPREAD] + sigma * kNP, D.S, KPs, m2.Y,
+                m2.Ye, &mbar_y, 1);
+    if (ok) {
+      stage_rows_df(D, D.C, D.Ce, drow(D, 0, t, sigma, 0), 0, 0, tile0, validF, m2);
+      ok = tc_products(m2, D.S, 0, 0, KPs / 16, tmem, &mbar_mma, phase, false);
+    }
+    if (ok) {
+      tc_recombine(tmem, D.S, fh, fl);
+      efx = m2.Xe[r];
+      m.Ye = m2.Ye;
+    }
+  }
+  // ---- Step 7 in FP64 and the store
+  if (ok) {
+    const int64_t row = tile0 + r;
+    const bool l2c = (D.dir == LC_L2C) && !D.adj;  // (the transposed pass applied C^{-1} first)
+    const bool far = far_tile && row < validF;
+    if (row < validN) {
+#pragma unroll
+      for (int j = 0; j < kCols; ++j) {
+        const int col = c0 + j;  // local row m of the strip
+        if (col >= s) continue;
+        const int64_t row_i = 2 * int64_t(s) * t + 2 * col + sigma;
+        if (row_i >= rlen[r]) continue;
+        const int E1 = enx + ye_near[col] - 16;
+        const int E2 = efx + (far ? m.Ye[col] : 0) - 16;
+        // near (nh + nl) 2^E1 and far (fh + fl) 2^E2, each word brought to
+        // FP64 exactly, summed and scaled by C^{-1} (L2C) in FP64
+        const double c = l2c ? ((row_i == 0) ? 0.31830988618379067154 : 0.63661977236758134308) : 1.0;
+        const double lo_sum = f2d_scaled(nl[j], E1) + (far ? f2d_scaled(fl[j], E2) : 0.0);
+        const double hi_far = far ? f2d_scaled(fh[j], E2) : 0.0;
+        D.out[obase[r] + row_i * D.oe] = fma(c, f2d_scaled(nh[j], E1), fma(c, hi_far, c * lo_sum));
+      }
+    }
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
+  tc_end(tmem);
 }
 
 // ------------------------------------------------------------ plan kernels
@@ -1017,8 +1064,12 @@ __device__ double y_value(int kind, int64_t item, int k, int n, const lc_plan_s&
   return 0.0;
 }
 
-__global__ void k_make_y(int kind, int items, int K, int KP, int NP, int S, lc_plan_s P, int s, int L, int64_t N,
+// Slice planes of the shared operands, item by item: plane sl of item it
+// holds digit sl of every entry (row n < kNP, column k < KP) in the canonical
+// K-major layout of lc_umma.cuh, scaled by the row's exponent e[it][n].
+__global__ void k_make_y(int kind, int items, int K, int KP, int S, lc_plan_s P, int s, int L, int64_t N,
                          int dir, uint16_t* __restrict__ q, int* __restrict__ e) {
+  constexpr int NP = kNP;
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (tid >= int64_t(items) * NP) return;
   const int64_t item = tid / NP;
@@ -1032,15 +1083,15 @@ __global__ void k_make_y(int kind, int items, int K, int KP, int NP, int S, lc_p
     ey = ex + 1;
   }
   e[item * NP + n] = ey;
-  const int KS = KP + 8;  // row stride of the shared-memory layout
-  uint16_t* dst = q + (size_t(item) * S * NP + n) * KS;
-  for (int k = 0; k < KS; ++k) {
+  unsigned char* dst = reinterpret_cast<unsigned char*>(q) + size_t(item) * S * NP * KP * 2;
+  for (int k = 0; k < KP; ++k) {
     double y = (k < K) ? ldexp(y_value(kind, item, k, n, P, s, L, N, dir), -ey) : 0.0;
     for (int sl = 0; sl < S; ++sl) {
       const double tt = y * 256.0;
       const double qq = rint(tt);
       y = tt - qq;
-      dst[size_t(sl) * NP * KS + k] = uint16_t(__float_as_uint(float(qq)) >> 16);
+      *reinterpret_cast<uint16_t*>(dst + size_t(sl) * NP * KP * 2 + umma_offset(n, k, KP)) =
+          uint16_t(__float_as_uint(float(qq)) >> 16);
     }
   }
 }
@@ -1070,7 +1121,6 @@ Dev make_dev(const lc_plan_s* p, const SplitHost& h) {
     D.yq[k] = reinterpret_cast<const uint16_t*>(base + h.y[k].off_q);
     D.ye[k] = reinterpret_cast<const int*>(base + h.y[k].off_e);
     D.yKP[k] = h.y[k].KP;
-    D.yNP[k] = h.y[k].NP;
   }
   D.dir = int(p->dir);
   D.ragged = p->ragged;
@@ -1114,13 +1164,13 @@ lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st)
   for (int k = 0; k < Y_KINDS; ++k) {
     const YTable& y = h->y[k];
     if (y.items == 0) continue;
-    const int64_t threads = int64_t(y.items) * y.NP;
+    const int64_t threads = int64_t(y.items) * kNP;
     k_make_y<<<unsigned((threads + 127) / 128), 128, 0, st>>>(
-        k, y.items, Ks[k], y.KP, y.NP, h->S, *p, h->s, h->Lmax, h->Nmax, int(p->dir),
+        k, y.items, Ks[k], y.KP, h->S, *p, h->s, h->Lmax, h->Nmax, int(p->dir),
         reinterpret_cast<uint16_t*>(base + y.off_q), reinterpret_cast<int*>(base + y.off_e));
     LC_LAUNCH_CHECK();
   }
-  const size_t big = smem_bytes(h->S, 64, 32);
+  const size_t big = smem_bytes(7, 64, 64);  // the largest configuration any kernel takes
   LC_CUDA_TRY(cudaFuncSetAttribute(k_s_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
   LC_CUDA_TRY(cudaFuncSetAttribute(k_s_up, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
   LC_CUDA_TRY(cudaFuncSetAttribute(k_s_couple, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
@@ -1171,27 +1221,28 @@ lc_status lc_exec_split(lc_plan p, const void* in, void* out, const lc_layout& l
     switch (kind) {
       case LC_K_LEAF: {
         const YTable& y = h->y[Y_LEAF];
-        k_s_leaf<<<grid, kThreads, smem_bytes(h->S, y.KP, y.NP), st>>>(D, w0);
+        k_s_leaf<<<grid, kThreads, smem_bytes(h->S, y.KP, y.KP), st>>>(D, w0);
         break;
       }
       case LC_K_UP: {
         const YTable& y = h->y[Y_UP];
-        k_s_up<<<grid, kThreads, smem_bytes(h->S, y.KP, y.NP), st>>>(D, w0);
+        k_s_up<<<grid, kThreads, smem_bytes(h->S, y.KP, y.KP), st>>>(D, w0);
         break;
       }
       case LC_K_COUPLE: {
         const YTable& y = h->y[Y_COUPLE];
-        k_s_couple<<<grid, kThreads, smem_bytes(h->S, y.KP, y.NP), st>>>(D, w0);
+        k_s_couple<<<grid, kThreads, smem_bytes(h->S, y.KP, y.KP), st>>>(D, w0);
         break;
       }
       case LC_K_DOWN: {
         const YTable& y = h->y[Y_DOWN];
-        k_s_down<<<grid, kThreads, smem_bytes(h->S, y.KP, y.NP), st>>>(D, w0);
+        k_s_down<<<grid, kThreads, smem_bytes(h->S, y.KP, y.KP), st>>>(D, w0);
         break;
       }
       case LC_K_FINAL: {
         const YTable& y = h->y[Y_NEAR];
-        k_s_final<<<grid, kThreads, smem_bytes(h->S, y.KP, y.NP), st>>>(D, w0);
+        const int kpx = y.KP < kXCols ? y.KP : kXCols;
+        k_s_final<<<grid, kThreads, smem_bytes(h->S, kpx, y.KP), st>>>(D, w0);
         break;
       }
     }
