@@ -401,13 +401,14 @@ __device__ __forceinline__ void put_chunk(unsigned char* X, int plane_bytes, int
 
 // Bring the Y slices of one table item (S planes of kNP x KP bf16 in the
 // canonical layout) and its kNP exponents into shared memory with two bulk
-// copies.  Must be called by all threads.  use = 0 for the CTA's first load
-// (initialises the mbarrier, waits for phase 0), use = 1 for its second
-// (phase 1).  Returns false if the bounded wait ran out; thread 0 then waits
-// once more (bounded) so that a late copy lands before the CTA exits, and the
-// caller records the failure.
-__device__ __forceinline__ bool load_y(const uint16_t* __restrict__ q, const int* __restrict__ e, int S, int KP,
-                                       unsigned char* Ys, int* Ye, uint64_t* mbar, int use = 0) {
+// copies: y_issue starts them (thread 0; use = 0 for the CTA's first load,
+// which initialises the mbarrier, use = 1 for its second), y_wait waits for
+// them (all threads, phase use & 1).  Between the two the CTA stages its own
+// operand.  y_wait returns false if the bounded wait ran out; thread 0 then
+// waits once more (bounded) so that a late copy lands before the CTA exits,
+// and the caller records the failure.
+__device__ __forceinline__ void y_issue(const uint16_t* __restrict__ q, const int* __restrict__ e, int S, int KP,
+                                        unsigned char* Ys, int* Ye, uint64_t* mbar, int use = 0) {
   const uint32_t mb = lc_smem_u32(mbar);
   const uint32_t bq = uint32_t(S) * kNP * KP * 2, be = uint32_t(kNP) * 4;
   if (threadIdx.x == 0) {
@@ -417,7 +418,9 @@ __device__ __forceinline__ bool load_y(const uint16_t* __restrict__ q, const int
     lc_bulk_g2s(Ys, q, bq, mb);
     lc_bulk_g2s(Ye, e, be, mb);
   }
-  __syncthreads();
+}
+__device__ __forceinline__ bool y_wait(uint64_t* mbar, int use = 0) {
+  const uint32_t mb = lc_smem_u32(mbar);
   const bool ok = lc_mbar_wait_bounded(mb, uint32_t(use & 1));
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) lc_mbar_wait_bounded(mb, uint32_t(use & 1));
@@ -612,21 +615,39 @@ __device__ __forceinline__ void row_info(const Dev& D, int64_t tile0, int64_t va
 }
 
 // ---- tensor-core stage: TMEM holds one kNP-column accumulator per slice
-// diagonal u = s + t (u = 2 .. S + 1), at columns (u - 2) kNP.
-__device__ __forceinline__ void tc_begin(uint32_t* tslot, uint64_t* mbar_mma) {
+// diagonal u = s + t (u = 2 .. S + 1), at columns (u - 2) kNP.  TMEM is
+// taken only once the first operand is staged (tc_acquire): a CTA resident
+// beside two others that hold TMEM stages its operands meanwhile and waits
+// in the allocation, instead of idling from its start.
+struct TcState {
+  uint32_t* tslot;  // shared: TMEM base address
+  uint64_t* mbar;   // shared: MMA completion barrier
+  uint32_t tmem;
+  uint32_t phase;
+  bool held;
+};
+__device__ __forceinline__ TcState tc_begin(uint32_t* tslot, uint64_t* mbar_mma) {
+  if (threadIdx.x == 32) lc_mbar_init(lc_smem_u32(mbar_mma));
+  __syncthreads();
+  return TcState{tslot, mbar_mma, 0u, 0u, false};
+}
+__device__ __forceinline__ void tc_acquire(TcState& tc) {
+  if (tc.held) return;
   if (threadIdx.x < 32) {
-    umma_alloc(tslot, kTmemCols);
+    umma_alloc(tc.tslot, kTmemCols);
     umma_relinquish();
   }
-  if (threadIdx.x == 32) lc_mbar_init(lc_smem_u32(mbar_mma));
   umma_fence_before();
   __syncthreads();
   umma_fence_after();
+  tc.tmem = *tc.tslot;
+  tc.held = true;
 }
-__device__ __forceinline__ void tc_end(uint32_t tmem) {
+__device__ __forceinline__ void tc_end(const TcState& tc) {
+  if (!tc.held) return;
   umma_fence_before();
   __syncthreads();
-  if (threadIdx.x < 32) umma_dealloc(tmem, kTmemCols);
+  if (threadIdx.x < 32) umma_dealloc(tc.tmem, kTmemCols);
 }
 
 // Slice products of the staged X (its K slices [xkt0, xkt0 + KPx/16) of the
@@ -636,9 +657,12 @@ __device__ __forceinline__ void tc_end(uint32_t tmem) {
 // commits them to the mbarrier; every thread waits for that phase (bounded).
 // A timeout returns false after a second bounded wait, so that no MMA is in
 // flight when the caller releases TMEM.
-__device__ __forceinline__ bool tc_products(const Smem& m, int S, int xkt0, int kt0, int kt1, uint32_t tmem,
-                                            uint64_t* mbar_mma, uint32_t& phase, bool acc_first) {
-  const uint32_t mb = lc_smem_u32(mbar_mma);
+__device__ __forceinline__ bool tc_products(const Smem& m, int S, int xkt0, int kt0, int kt1, TcState& tc,
+                                            bool acc_first) {
+  tc_acquire(tc);
+  const uint32_t tmem = tc.tmem;
+  uint32_t& phase = tc.phase;
+  const uint32_t mb = lc_smem_u32(tc.mbar);
   if (threadIdx.x == 0) {
     umma_fence_after();
     const uint32_t xs = lc_smem_u32(m.X), ys = lc_smem_u32(m.Y);
@@ -673,22 +697,37 @@ __device__ __forceinline__ int ep_col0() { return int(threadIdx.x >> 7) * kCols;
 // Recombine the diagonals of this thread's row and columns:
 // hi + lo = sum_u P_u 2^(-8 (u - 2)), the product times 2^16 in units of
 // 2^(e_x + e_y), by a Horner sum in base 2^8 in double-float.
+// The diagonals are read in groups of up to two loads in flight, one wait
+// per group (more would cost the registers of a third resident CTA).
+__device__ __forceinline__ void horner_step(float (&hi)[kCols], float (&lo)[kCols], const uint32_t (&p)[kCols],
+                                            bool first) {
+#pragma unroll
+  for (int j = 0; j < kCols; ++j) {
+    const float pj = __uint_as_float(p[j]);
+    if (first) {
+      hi[j] = pj;
+      lo[j] = 0.0f;
+    } else {
+      float sh, se;
+      two_sum(hi[j] * (1.0f / 256.0f), pj, sh, se);
+      fast_two_sum(sh, lo[j] * (1.0f / 256.0f) + se, hi[j], lo[j]);
+    }
+  }
+}
 __device__ __forceinline__ void tc_recombine(uint32_t tmem, int S, float (&hi)[kCols], float (&lo)[kCols]) {
   const uint32_t base = tmem + (uint32_t(32 * ((threadIdx.x >> 5) & 3)) << 16) + uint32_t(ep_col0());
-  for (int u = S + 1; u >= 2; --u) {
-    float p[kCols];
-    umma_ld16(base + uint32_t(u - 2) * kNP, p);
+  int u = S + 1;
+  while (u >= 2) {
+    const int g = u - 1 < 2 ? u - 1 : 2;  // diagonals u (and u - 1) in this group
+    uint32_t p[2][kCols];
 #pragma unroll
-    for (int j = 0; j < kCols; ++j) {
-      if (u == S + 1) {
-        hi[j] = p[j];
-        lo[j] = 0.0f;
-      } else {
-        float sh, se;
-        two_sum(hi[j] * (1.0f / 256.0f), p[j], sh, se);
-        fast_two_sum(sh, lo[j] * (1.0f / 256.0f) + se, hi[j], lo[j]);
-      }
-    }
+    for (int q = 0; q < 2; ++q)
+      if (q < g) umma_ld16_async(base + uint32_t(u - q - 2) * kNP, p[q]);
+    umma_wait_ld();
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (q < g) horner_step(hi, lo, p[q], u - q == S + 1);
+    u -= g;
   }
 }
 
@@ -731,7 +770,7 @@ __device__ __forceinline__ void tc_store_row(float2* Out, int* OutE, int64_t row
 }
 
 // ------------------------------------------------------------------ kernels
-// Every kernel: one (segment or strip, parity sigma = blockIdx.y, tile of
+// Every kernel: one (segment or strip, parity sigma = blockIdx.x % 2, tile of
 // kRows members) per CTA; TMEM allocated at the start and released at the
 // end on every path; a failed bounded wait sets the plan's status word.
 
@@ -741,33 +780,31 @@ __global__ void __launch_bounds__(kThreads) k_s_leaf(Dev D, int64_t w0) {
   __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
   __shared__ uint32_t tslot;
   __shared__ int64_t rbase[kRows], rlen[kRows];
-  const Work it = D.work[w0 + blockIdx.x];
-  const int sigma = blockIdx.y;
+  const Work it = D.work[w0 + (blockIdx.x >> 1)];
+  const int sigma = int(blockIdx.x & 1);
   const int KP = D.yKP[Y_LEAF];
   Smem m = carve(sm_raw, D.S, KP, KP);
-  tc_begin(&tslot, &mbar_mma);
-  const uint32_t tmem = tslot;
-  uint32_t phase = 0;
+  TcState tc = tc_begin(&tslot, &mbar_mma);
   const int64_t g = it.seg, tile0 = int64_t(it.tile) * kRows;  // column segment (transposed: row strip)
   const int64_t valid = dcnt(D, 0, D.adj ? g + 2 : g);
-  bool ok = load_y(D.yq[Y_LEAF] + size_t(sigma) * D.S * kNP * KP, D.ye[Y_LEAF] + sigma * kNP, D.S, KP, m.Y, m.Ye,
-                   &mbar_y);
-  if (ok) {
+  y_issue(D.yq[Y_LEAF] + size_t(sigma) * D.S * kNP * KP, D.ye[Y_LEAF] + sigma * kNP, D.S, KP, m.Y, m.Ye, &mbar_y);
+  {
     const int s = D.s;
     const int cinv = D.adj && D.dir == LC_L2C;
     row_info(D, tile0, valid, rbase, nullptr, rlen);
     input_frames(D, tile0, valid, 2 * int64_t(s) * g + sigma, s, m, rbase, rlen, cinv);
     stage_input(D, tile0, valid, 2 * int64_t(s) * g + sigma, s, 0, m, rbase, rlen, cinv);
-    ok = tc_products(m, D.S, 0, 0, KP / 16, tmem, &mbar_mma, phase, false);
   }
+  bool ok = y_wait(&mbar_y);
+  if (ok) ok = tc_products(m, D.S, 0, 0, KP / 16, tc, false);
   if (ok) {
     float hi[kCols], lo[kCols];
-    tc_recombine(tmem, D.S, hi, lo);
+    tc_recombine(tc.tmem, D.S, hi, lo);
     const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
     tc_store_row(D.W, D.We, drow(D, 0, g, sigma, 0), tile0, valid, hi, lo, er);
   }
   if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
-  tc_end(tmem);
+  tc_end(tc);
 }
 
 // Step 2: W(d+1, G) = [W(d, 2G) W(d, 2G+1)] [B(0) B(1)]^T.
@@ -775,30 +812,27 @@ __global__ void __launch_bounds__(kThreads) k_s_up(Dev D, int64_t w0) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
   __shared__ uint32_t tslot;
-  const Work it = D.work[w0 + blockIdx.x];
-  const int sigma = blockIdx.y;
+  const Work it = D.work[w0 + (blockIdx.x >> 1)];
+  const int sigma = int(blockIdx.x & 1);
   const int KP = D.yKP[Y_UP];
   Smem m = carve(sm_raw, D.S, KP, KP);
-  tc_begin(&tslot, &mbar_mma);
-  const uint32_t tmem = tslot;
-  uint32_t phase = 0;
+  TcState tc = tc_begin(&tslot, &mbar_mma);
   const int dp = it.d;  // parent level
   const int64_t G = it.seg, tile0 = int64_t(it.tile) * kRows;
   const int64_t valid = dcnt(D, dp, D.adj ? G + 2 : G);  // transposed: row tree
-  bool ok = load_y(D.yq[Y_UP], D.ye[Y_UP], D.S, KP, m.Y, m.Ye, &mbar_y);
-  if (ok) {
-    stage_rows_df(D, D.W, D.We, drow(D, dp - 1, 2 * G, sigma, 0), drow(D, dp - 1, 2 * G + 1, sigma, 0), 1, tile0,
-                  valid, m);
-    ok = tc_products(m, D.S, 0, 0, KP / 16, tmem, &mbar_mma, phase, false);
-  }
+  y_issue(D.yq[Y_UP], D.ye[Y_UP], D.S, KP, m.Y, m.Ye, &mbar_y);
+  stage_rows_df(D, D.W, D.We, drow(D, dp - 1, 2 * G, sigma, 0), drow(D, dp - 1, 2 * G + 1, sigma, 0), 1, tile0,
+                valid, m);
+  bool ok = y_wait(&mbar_y);
+  if (ok) ok = tc_products(m, D.S, 0, 0, KP / 16, tc, false);
   if (ok) {
     float hi[kCols], lo[kCols];
-    tc_recombine(tmem, D.S, hi, lo);
+    tc_recombine(tc.tmem, D.S, hi, lo);
     const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
     tc_store_row(D.W, D.We, drow(D, dp, G, sigma, 0), tile0, valid, hi, lo, er);
   }
   if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
-  tc_end(tmem);
+  tc_end(tc);
 }
 
 // Step 3: C(d, v) = [W(d, v+2) W(d, v+3)] [A-hat(b,0) A-hat(b,1)]^T (v even),
@@ -807,13 +841,11 @@ __global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
   __shared__ uint32_t tslot;
-  const Work it = D.work[w0 + blockIdx.x];
-  const int sigma = blockIdx.y;
+  const Work it = D.work[w0 + (blockIdx.x >> 1)];
+  const int sigma = int(blockIdx.x & 1);
   const int KP = D.yKP[Y_COUPLE];
   Smem m = carve(sm_raw, D.S, KP, KP);
-  tc_begin(&tslot, &mbar_mma);
-  const uint32_t tmem = tslot;
-  uint32_t phase = 0;
+  TcState tc = tc_begin(&tslot, &mbar_mma);
   const int d = it.d;
   // forward: row segment v from column segments v+2 (and v+3);
   // transposed: column segment g = seg from row segments g-2 (and g-3)
@@ -822,21 +854,22 @@ __global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) {
   const int Gam = D.Lmax - 1 - d;  // level in the shared table
   const int64_t item = (int64_t(4) * ((int64_t(1) << Gam) - 1) - 2 * Gam) + (D.adj ? v - 2 : v);
   const YKind yk = D.adj ? Y_COUPLE_T : Y_COUPLE;
-  bool ok = load_y(D.yq[yk] + size_t(item) * D.S * kNP * KP, D.ye[yk] + item * kNP, D.S, KP, m.Y, m.Ye, &mbar_y);
-  if (ok) {
+  y_issue(D.yq[yk] + size_t(item) * D.S * kNP * KP, D.ye[yk] + item * kNP, D.S, KP, m.Y, m.Ye, &mbar_y);
+  {
     const int two = D.adj ? int(v & 1) : ((v & 1) == 0 ? 1 : 0);
     const int64_t s0 = D.adj ? v - 2 : v + 2, s1 = D.adj ? v - 3 : v + 3;
     stage_rows_df(D, D.W, D.We, drow(D, d, s0, sigma, 0), two ? drow(D, d, s1, sigma, 0) : 0, two, tile0, valid, m);
-    ok = tc_products(m, D.S, 0, 0, KP / 16, tmem, &mbar_mma, phase, false);
   }
+  bool ok = y_wait(&mbar_y);
+  if (ok) ok = tc_products(m, D.S, 0, 0, KP / 16, tc, false);
   if (ok) {
     float hi[kCols], lo[kCols];
-    tc_recombine(tmem, D.S, hi, lo);
+    tc_recombine(tc.tmem, D.S, hi, lo);
     const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
     tc_store_row(D.C, D.Ce, drow(D, d, v, sigma, 0), tile0, valid, hi, lo, er);
   }
   if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
-  tc_end(tmem);
+  tc_end(tc);
 }
 
 // Step 4: C(d, v) += C(d+1, v/2) B(v mod 2).
@@ -844,25 +877,22 @@ __global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
   __shared__ uint32_t tslot;
-  const Work it = D.work[w0 + blockIdx.x];
-  const int sigma = blockIdx.y;
+  const Work it = D.work[w0 + (blockIdx.x >> 1)];
+  const int sigma = int(blockIdx.x & 1);
   const int KP = D.yKP[Y_DOWN];
   Smem m = carve(sm_raw, D.S, KP, KP);
-  tc_begin(&tslot, &mbar_mma);
-  const uint32_t tmem = tslot;
-  uint32_t phase = 0;
+  TcState tc = tc_begin(&tslot, &mbar_mma);
   const int d = it.d;
   const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;  // child (row segment; transposed: column segment)
   const int64_t valid = dcnt(D, d, D.adj ? v : v + 4);
   const int p = int(v & 1);
-  bool ok = load_y(D.yq[Y_DOWN] + size_t(p) * D.S * kNP * KP, D.ye[Y_DOWN] + p * kNP, D.S, KP, m.Y, m.Ye, &mbar_y);
-  if (ok) {
-    stage_rows_df(D, D.C, D.Ce, drow(D, d + 1, v >> 1, sigma, 0), 0, 0, tile0, valid, m);
-    ok = tc_products(m, D.S, 0, 0, KP / 16, tmem, &mbar_mma, phase, false);
-  }
+  y_issue(D.yq[Y_DOWN] + size_t(p) * D.S * kNP * KP, D.ye[Y_DOWN] + p * kNP, D.S, KP, m.Y, m.Ye, &mbar_y);
+  stage_rows_df(D, D.C, D.Ce, drow(D, d + 1, v >> 1, sigma, 0), 0, 0, tile0, valid, m);
+  bool ok = y_wait(&mbar_y);
+  if (ok) ok = tc_products(m, D.S, 0, 0, KP / 16, tc, false);
   if (ok) {
     float hi[kCols], lo[kCols];
-    tc_recombine(tmem, D.S, hi, lo);
+    tc_recombine(tc.tmem, D.S, hi, lo);
     const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
     // add the existing row (couple result) in a common frame
     const int64_t base = drow(D, d, v, sigma, 0);
@@ -887,7 +917,7 @@ __global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) {
     }
   }
   if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
-  tc_end(tmem);
+  tc_end(tc);
 }
 
 // Steps 5-7 for strip t and parity sigma, kRows members per CTA:
@@ -901,8 +931,8 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
   __shared__ uint32_t tslot;
   __shared__ int64_t rbase[kRows], obase[kRows], rlen[kRows];
   __shared__ int ye_near[kNP];
-  const Work it = D.work[w0 + blockIdx.x];
-  const int sigma = blockIdx.y;
+  const Work it = D.work[w0 + (blockIdx.x >> 1)];
+  const int sigma = int(blockIdx.x & 1);
   const int64_t t = it.seg, tile0 = int64_t(it.tile) * kRows;
   const int64_t validN = D.cntN[t];
   // far field of strip t: row segment t (forward), column segment t (transposed)
@@ -913,17 +943,16 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
   const int KPn = D.yKP[Y_NEAR];
   const int KPx = KPn < kXCols ? KPn : kXCols;
   Smem m = carve(sm_raw, D.S, KPx, KPn);
-  tc_begin(&tslot, &mbar_mma);
-  const uint32_t tmem = tslot;
-  uint32_t phase = 0;
+  TcState tc = tc_begin(&tslot, &mbar_mma);
   const int r = ep_row(), c0 = ep_col0();
   float nh[kCols], nl[kCols], fh[kCols], fl[kCols];
   int enx = 0, efx = 0;
   // ---- near field
   const int64_t item = 2 * t + sigma;
   const YKind yk = D.adj ? Y_NEAR_T : Y_NEAR;
-  bool ok = load_y(D.yq[yk] + size_t(item) * D.S * kNP * KPn, D.ye[yk] + item * kNP, D.S, KPn, m.Y, m.Ye, &mbar_y);
-  if (ok) {
+  y_issue(D.yq[yk] + size_t(item) * D.S * kNP * KPn, D.ye[yk] + item * kNP, D.S, KPn, m.Y, m.Ye, &mbar_y);
+  bool ok = true;
+  {
     // forward: columns of strips t, t+1 of the band of rows in strip t;
     // transposed: rows of strips t-1, t (times C^{-1} for L2C) for columns in strip t
     const int cinv = D.adj && D.dir == LC_L2C;
@@ -931,14 +960,14 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
     row_info(D, tile0, validN, rbase, obase, rlen);
     input_frames(D, tile0, validN, j0, 2 * s, m, rbase, rlen, cinv);
     for (int cc = 0; cc < KPn && ok; cc += KPx) {
-      if (cc > 0) sync_for_mma();  // (the previous chunk's products are complete)
       stage_input(D, tile0, validN, j0, 2 * s, cc, m, rbase, rlen, cinv);
+      if (cc == 0) ok = y_wait(&mbar_y);
       const int kt1 = (cc + KPx < KPn ? cc + KPx : KPn) / 16;
-      ok = tc_products(m, D.S, cc / 16, cc / 16, kt1, tmem, &mbar_mma, phase, cc > 0);
+      if (ok) ok = tc_products(m, D.S, cc / 16, cc / 16, kt1, tc, cc > 0);
     }
   }
   if (ok) {
-    tc_recombine(tmem, D.S, nh, nl);
+    tc_recombine(tc.tmem, D.S, nh, nl);
     enx = m.Xe[r];
     if (threadIdx.x < kNP) ye_near[threadIdx.x] = m.Ye[threadIdx.x];
     sync_for_mma();  // every TMEM read of the near field is done; Y and Xe may be overwritten
@@ -948,14 +977,13 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
   if (ok && far_tile) {
     const int KPs = D.yKP[Y_SPREAD];
     Smem m2 = carve(sm_raw, D.S, KPs, KPs);
-    ok = load_y(D.yq[Y_SPREAD] + size_t(sigma) * D.S * kNP * KPs, D.ye[Y_SPREAD] + sigma * kNP, D.S, KPs, m2.Y,
-                m2.Ye, &mbar_y, 1);
+    y_issue(D.yq[Y_SPREAD] + size_t(sigma) * D.S * kNP * KPs, D.ye[Y_SPREAD] + sigma * kNP, D.S, KPs, m2.Y, m2.Ye,
+            &mbar_y, 1);
+    stage_rows_df(D, D.C, D.Ce, drow(D, 0, t, sigma, 0), 0, 0, tile0, validF, m2);
+    ok = y_wait(&mbar_y, 1);
+    if (ok) ok = tc_products(m2, D.S, 0, 0, KPs / 16, tc, false);
     if (ok) {
-      stage_rows_df(D, D.C, D.Ce, drow(D, 0, t, sigma, 0), 0, 0, tile0, validF, m2);
-      ok = tc_products(m2, D.S, 0, 0, KPs / 16, tmem, &mbar_mma, phase, false);
-    }
-    if (ok) {
-      tc_recombine(tmem, D.S, fh, fl);
+      tc_recombine(tc.tmem, D.S, fh, fl);
       efx = m2.Xe[r];
       m.Ye = m2.Ye;
     }
@@ -984,7 +1012,7 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
     }
   }
   if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
-  tc_end(tmem);
+  tc_end(tc);
 }
 
 // ------------------------------------------------------------ plan kernels
@@ -1216,7 +1244,10 @@ lc_status lc_exec_split(lc_plan p, const void* in, void* out, const lc_layout& l
     const int64_t w0 = loff[l], nitems = loff[l + 1] - w0;
     if (nitems <= 0) continue;
     const int kind = lkind[l];
-    dim3 grid(unsigned(nitems), 2);
+    // the two parities of an item are neighbouring CTAs, and neighbouring
+    // items share input lines, so CTAs that read the same data run together
+    // (the second read hits L2)
+    dim3 grid(unsigned(2 * nitems), 1);
     lc_timer_mark(p, st, kind);
     switch (kind) {
       case LC_K_LEAF: {
