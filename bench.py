@@ -281,6 +281,34 @@ def kernel_work(info, kind, direction, leaf_depth=4):
     return None
 
 
+def measured_fp32_tflops(dev):
+    """FP32 FLOP/s of the CUDA cores on this GPU, measured: cuBLAS SGEMM 8192^3
+    with TF32 off (best of 5, CUDA events).  The double-float ceiling is this
+    rate / 12 (one FP64-equivalent multiply-add = 12 FP32-pipe instructions)."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        a = torch.randn(n, n, device=dev, dtype=torch.float32)
+        b = torch.randn(n, n, device=dev, dtype=torch.float32)
+        c = a @ b
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b, c
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def graph_step(fn):
     """Capture fn (library launches on the current stream) into a CUDA graph."""
     import torch
@@ -702,6 +730,11 @@ def run_ours(args):
                     "kernel": KIND_NAMES[dom], "avg_launch_ms": avg_ms, "flops_per_launch": flops,
                     "peak_kind": "derived from unit counts and the maximum SM clock (not measured)",
                     "peak_note": note}
+        if chosen == "f64_df":
+            # the same ceiling from a measured FP32 rate (SGEMM on the CUDA cores, TF32 off)
+            f32 = measured_fp32_tflops(dev)
+            roofline["measured_view"] = {"fp32_sgemm_tflops": f32, "peak": f32 / 12, "frac": achieved / (f32 / 12),
+                                         "note": "double-float ceiling = measured FP32 FLOP/s / 12"}
         if TRAFFIC.get((chosen, dom)):
             # the same launch against HBM: its DRAM bytes (ncu) over its duration
             gbs = TRAFFIC[(chosen, dom)] / (avg_ms / 1e3) / 1e9

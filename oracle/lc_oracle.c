@@ -27,8 +27,20 @@
  * is deliberately a different route from the tau series that the GPU plan
  * uses (eq:tau).
  *
+ * Values at Chebyshev points (lco_dct): the Chebyshev series with
+ * coefficients c evaluated at the n Chebyshev-Gauss points
+ * x_m = cos((m + 1/2) pi / n), v_m = sum_k c_k T_k(x_m) =
+ * sum_k c_k cos(pi k (2m + 1) / (2n)) (kind 0), and its inverse by discrete
+ * orthogonality, c_k = (2 / n) / (1 + [k = 0]) sum_m v_m cos(pi k (2m+1)/(2n))
+ * (kind 1), exact for degree < n.  Direct O(n^2) sums in double-double; each
+ * cosine's argument is reduced exactly in integers first (k (2m+1) mod 4n),
+ * so every cosine is within about one ulp.  With lco_apply these give the
+ * Legendre synthesis on Chebyshev points (L2C, then kind 0; Sec. 1 names the
+ * Chebyshev-Legendre Galerkin use) and its inverse (kind 1, then C2L).
+ *
  * Rows are independent; with OpenMP available they are spread over threads.
  */
+#define _GNU_SOURCE 1
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -195,6 +207,38 @@ int lco_apply(int direction, int adjoint, int64_t n, const double* x,
 }
 
 /* Number of threads the OpenMP runtime would use (1 without OpenMP). */
+/* cos(pi r / d) for integers 0 <= r < 2d, d >= 1: reduced to an angle in
+ * [0, pi/4] by the symmetries of cos, then one libm call. */
+static double cospi_ratio(int64_t r, int64_t d) {
+  double sign = 1.0;
+  if (r > d) r = 2 * d - r;            /* cos(2 pi - t) = cos t */
+  if (2 * r > d) {                     /* cos(pi - t) = -cos t */
+    r = d - r;
+    sign = -1.0;
+  }
+  if (4 * r <= d) return sign * cos(M_PI * (double)r / (double)d);
+  return sign * sin(M_PI * (double)(d - 2 * r) / (2.0 * (double)d)); /* cos t = sin(pi/2 - t) */
+}
+
+/* kind 0: y_m = sum_k x_k cos(pi k (2m+1) / (2n)); kind 1: y_k =
+ * (2/n)/(1 + [k = 0]) sum_m x_m cos(pi k (2m+1) / (2n)). */
+int lco_dct(int kind, int64_t n, const double* x, double* y) {
+  if (n < 1 || !x || !y || (kind != 0 && kind != 1)) return 1;
+  const int64_t d = 2 * n; /* angle pi q / d with q = k (2m+1) mod 2d */
+#pragma omp parallel for schedule(static)
+  for (int64_t o = 0; o < n; ++o) {
+    dd acc = dd_from(0.0);
+    for (int64_t t = 0; t < n; ++t) {
+      const int64_t k = kind == 0 ? t : o, m = kind == 0 ? o : t;
+      const int64_t q = (k % (2 * d)) * ((2 * m + 1) % (2 * d)) % (2 * d);
+      acc = dd_add(acc, two_prod(x[t], cospi_ratio(q, d)));
+    }
+    if (kind == 1) acc = dd_mul_d(acc, (o == 0 ? 1.0 : 2.0) / (double)n);
+    y[o] = dd_to(acc);
+  }
+  return 0;
+}
+
 int lco_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

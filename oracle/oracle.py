@@ -55,7 +55,8 @@ def _load():
         lib.lco_entry.argtypes = [ctypes.c_int, i64, i64, i64, dp]
         lib.lco_apply.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, i64, ip, dp]
         lib.lco_threads.argtypes = []
-        for f in (lib.lco_lambda, lib.lco_entry, lib.lco_apply, lib.lco_threads):
+        lib.lco_dct.argtypes = [ctypes.c_int, i64, dp, dp]
+        for f in (lib.lco_lambda, lib.lco_entry, lib.lco_apply, lib.lco_threads, lib.lco_dct):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -124,3 +125,28 @@ def dense_matrix(direction: int, n: int):
         e[j] = 1.0
         m[:, j] = apply(direction, e)
     return m
+
+
+def dct(kind: int, x):
+    """kind 0: v_m = sum_k x_k cos(pi k (2m+1)/(2n)) -- the Chebyshev series with
+    coefficients x at the Chebyshev-Gauss points x_m = cos((m+1/2) pi/n);
+    kind 1: its inverse, (2/n)/(1+[k=0]) sum_m x_m cos(pi k (2m+1)/(2n))."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    rc = _load().lco_dct(int(kind), x.size, _dptr(x), _dptr(out))
+    if rc:
+        raise RuntimeError("lco_dct failed (%d)" % rc)
+    return out
+
+
+def synthesis(f):
+    """Values p(x_m) of p = sum_j f_j P_j at the n Chebyshev-Gauss points
+    x_m = cos((m+1/2) pi/n): the L2C map, then the Chebyshev series at the
+    points (Sec. 1: Legendre coefficients to values through the Chebyshev basis)."""
+    return dct(0, apply(L2C, f))
+
+
+def analysis(v):
+    """Legendre coefficients of the degree < n polynomial through the values v
+    at the n Chebyshev-Gauss points: discrete Chebyshev transform, then C2L."""
+    return apply(C2L, dct(1, v))

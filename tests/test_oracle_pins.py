@@ -174,3 +174,81 @@ def test_planted_mistakes_fail_the_pins():
     }
     for name, bad in mistakes.items():
         assert np.abs(bad - want).max() > 1e-6 * np.abs(want).max(), name
+
+
+# ---- values at Chebyshev points (the synthesis and its inverse)
+def _mp_values(f, dps=50):
+    """p(x_m) for p = sum_j f_j P_j at the n Chebyshev-Gauss nodes, 50 digits,
+    exact nodes, Bonnet's recurrence: a route that never forms C^{-1}A or a
+    cosine sum."""
+    n = len(f)
+    with mp.workdps(dps):
+        out = []
+        for m in range(n):
+            x = mp.cos((m + mp.mpf(1) / 2) * mp.pi / n)
+            p0, p1 = mp.mpf(1), x
+            acc = mp.mpf(f[0])
+            if n > 1:
+                acc += mp.mpf(f[1]) * p1
+            for j in range(1, n - 1):
+                p0, p1 = p1, ((2 * j + 1) * x * p1 - j * p0) / (j + 1)
+                acc += mp.mpf(f[j + 1]) * p1
+            out.append(float(acc))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 16, 33, 64])
+def test_synthesis_matches_node_evaluation(n):
+    f = np.random.default_rng(300 + n).uniform(-1, 1, n)
+    want = _mp_values(f)
+    got = oracle.synthesis(f)
+    scale = max(np.abs(want).max(), 1e-300)
+    assert np.abs(got - want).max() <= 1e-15 * scale, (n, np.abs(got - want).max() / scale)
+
+
+def test_chebyshev_values_closed_forms():
+    # T_0 is 1 at every node, T_1 is the node itself, T_k(x_m) = cos(k (m+1/2) pi/n),
+    # and at k = n the nodes are the zeros of T_n (so T_n would vanish, not tested: k < n)
+    def cheb_at_nodes(k, n):
+        with mp.workdps(50):
+            return np.array([float(mp.cos(k * (m + mp.mpf(1) / 2) * mp.pi / n)) for m in range(n)])
+    for n in (1, 2, 7, 64, 1000):
+        nodes = cheb_at_nodes(1, n)
+        e = np.zeros(n)
+        e[0] = 1.0
+        assert np.abs(oracle.dct(0, e) - 1.0).max() == 0.0
+        if n > 1:
+            e[:] = 0.0
+            e[1] = 1.0
+            assert np.abs(oracle.dct(0, e) - nodes).max() <= 2.3e-16
+            k = n - 1
+            e[:] = 0.0
+            e[k] = 1.0
+            assert np.abs(oracle.dct(0, e) - cheb_at_nodes(k, n)).max() <= 2.3e-16
+
+
+@pytest.mark.parametrize("n", [1, 5, 64, 500])
+def test_values_round_trip_and_inverse(n):
+    # discrete orthogonality makes kind 1 the exact inverse of kind 0 for degree < n;
+    # analysis(synthesis(f)) returns the Legendre coefficients
+    rng = np.random.default_rng(400 + n)
+    c = rng.standard_normal(n)
+    assert np.abs(oracle.dct(1, oracle.dct(0, c)) - c).max() <= 4e-15 * max(1.0, np.abs(c).max())
+    f = rng.standard_normal(n) / np.arange(1, n + 1) ** 0.5
+    assert np.abs(oracle.analysis(oracle.synthesis(f)) - f).max() <= 4e-14 * np.abs(f).max()
+
+
+def test_values_planted_mistakes_fail():
+    # a dropped half-node offset or a missing k = 0 weight would not match the node evaluation
+    n = 16
+    f = np.random.default_rng(9).uniform(-1, 1, n)
+    want = _mp_values(f)
+    c = oracle.apply(L2C, f)
+    m = np.arange(n)[:, None]
+    k = np.arange(n)[None, :]
+    wrong_nodes = np.cos(k * m * np.pi / n) @ c
+    assert np.abs(wrong_nodes - want).max() > 1e-3
+    ca = oracle.dct(1, want)
+    ca_bad = ca.copy()
+    ca_bad[0] *= 2
+    assert np.abs(oracle.apply(C2L, ca_bad) - f).max() > 1e-3
