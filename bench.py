@@ -495,6 +495,27 @@ def batched_leg(lc, dev, flush, args):
                                     "E2_vs_oracle_max_64_fibres": worst}
         out["cube512_l2c_" + tier] = res
         del plan, outc
+    # (c') Legendre synthesis on Chebyshev points along the last axis: values
+    #      p(x_m) at x_m = cos((m+1/2) pi/512) of every fibre (L2C, then the
+    #      cosine transform of each result vector in place)
+    syn = {}
+    for tier in ("f64_split", "f64_df"):
+        plan = lc.Plan(N3, "l2c", N3 * N3, tier, dev, values=True)
+        outc = torch.empty_like(cube64)
+        step = graph_step(lambda: plan.along_axis(cube64, 2, out=outc))
+        ms = time_fn(step, flush, max(3, steps // 2), 1)
+        step()
+        torch.cuda.synchronize()
+        worst = 0.0
+        for a_, b_ in fib[:16]:
+            xin = cube64[int(a_), int(b_), :].cpu().numpy()
+            zz = outc[int(a_), int(b_), :].cpu().numpy()
+            ref = oracle.synthesis(xin)
+            worst = max(worst, float(np.linalg.norm(zz - ref) / np.linalg.norm(ref)))
+        syn[tier] = {"coefficients_per_s": N3 ** 3 / (ms / 1e3), "ms": ms, "launches": plan.launches(),
+                     "E2_vs_oracle_max_16_fibres": worst}
+        del plan, outc
+    out["cube512_synthesis_axis2"] = syn
     del cube64
     # (d) differentiable least-squares fit: loss = ||leg2cheb(x) - y||^2, n = 65536, batch 256,
     #     one step = forward transform + hand-written adjoint (autograd backward)

@@ -97,8 +97,21 @@ typedef struct {
    * one of its bulk copies, so its bounded wait runs out and the execution
    * reports LC_ERR_DEVICE_TIMEOUT through lc_plan_check. */
   int32_t debug_flags;
-  int32_t reserved[4];
+  /* 1: the Chebyshev side holds values at the n Chebyshev-Gauss points
+   * x_m = cos((m + 1/2) pi / n), m = 0 .. n-1, instead of Chebyshev
+   * coefficients (Sec. 1: the Chebyshev-Legendre Galerkin use, point values
+   * through fast cosine transforms).  LC_L2C then gives out_m = p(x_m) for
+   * p = sum_j in_j P_j (Legendre synthesis on Chebyshev points); LC_C2L takes
+   * in_m = p(x_m) and gives the Legendre coefficients of the degree < n
+   * polynomial through those values.  n must be a power of two with
+   * 2 <= n <= LC_VALUES_MAX_N, the tier LC_F64, LC_F64_DF or LC_F64_SPLIT,
+   * the plan uniform (not ragged); otherwise plan creation returns
+   * LC_ERR_UNSUPPORTED.  lc_adjoint of such a plan returns
+   * LC_ERR_UNSUPPORTED.  0 (default): coefficients. */
+  int32_t values;
+  int32_t reserved[3];
 } lc_plan_options;
+#define LC_VALUES_MAX_N 4096
 
 /* Fill *opt with the defaults above.  Returns LC_ERR_INVALID_ARG for NULL. */
 lc_status lc_plan_options_default(lc_plan_options* opt);

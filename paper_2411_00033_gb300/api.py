@@ -17,8 +17,10 @@ def _stream_ptr(device) -> int:
 
 
 def make_options(s_hat: int | None = None, fixed_s: int | None = None, slices: int | None = None,
-                 debug_flags: int | None = None):
+                 debug_flags: int | None = None, values: bool | None = None):
     o = B.lc_plan_options_default()
+    if values is not None:
+        o.values = int(bool(values))
     if debug_flags is not None:
         o.debug_flags = debug_flags
     if s_hat is not None:
@@ -36,6 +38,9 @@ class Plan:
     direction: "l2c" (f_cheb = C^{-1} A f_leg) or "c2l" (f_leg = A^{-1} C f_cheb)
     dtype:     "f64" | "f64_split" | "f32" | "f64_df"
     lengths:   for a ragged plan, the member lengths (then n and batch are ignored)
+    values:    True: the Chebyshev side holds values at the n Chebyshev-Gauss points
+               cos((m + 1/2) pi / n) instead of coefficients ("l2c": Legendre synthesis
+               on those points; "c2l": Legendre coefficients from the values)
     """
 
     def __init__(self, n: int | None = None, direction: str = "l2c", batch: int = 1, dtype: str = "f64",

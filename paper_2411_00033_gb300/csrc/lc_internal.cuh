@@ -122,6 +122,10 @@ struct lc_plan_s {
   int* xexp;
   int* xexp_part;
   unsigned* xexp_cnt;
+  // Values at Chebyshev points (lc_values.cu): twiddle tables, and for C2L
+  // plans a [batch][n] buffer for the Chebyshev coefficients of the input.
+  void* val_tables;
+  double* val_scratch;
   // Split tier data (see lc_split.cu).
   void* split;
   // Ragged members (host copies and device tables).
@@ -202,6 +206,13 @@ lc_status lc_exec_split(lc_plan p, const void* in, void* out, const lc_layout& l
                         int adjoint);
 int lc_exec_split_launches(const lc_plan_s* p);
 void lc_split_release(lc_plan p);
+
+// ---- values at Chebyshev points (lc_values.cu) -------------------------------
+bool lc_values_supported(int64_t n);
+size_t lc_values_table_bytes(int64_t n);
+lc_status lc_values_prepare(lc_plan p, cudaStream_t st);
+lc_status lc_values_synth(lc_plan p, double* out, const lc_layout& lay, cudaStream_t st);
+lc_status lc_values_analysis(lc_plan p, const double* in, const lc_layout& lay, double* scratch, cudaStream_t st);
 
 // ---- autotuning cache (lc_tune.cu) ------------------------------------------
 void lc_tune_apply_cached(lc_plan p);

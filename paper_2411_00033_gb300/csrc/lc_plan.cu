@@ -409,6 +409,12 @@ size_t layout(lc_plan_s* p, char* base) {
     const size_t sb = lc_split_bytes(p);
     p->split = c.take<char>(sb);
   }
+  p->val_tables = nullptr;
+  p->val_scratch = nullptr;
+  if (p->opt.values) {
+    p->val_tables = c.take<char>(lc_values_table_bytes(g.n));
+    if (p->dir == LC_C2L) p->val_scratch = c.take<double>(size_t(p->batch) * size_t(g.n));
+  }
   return c.off + 256;
 }
 
@@ -433,6 +439,8 @@ lc_status fill_plan(lc_plan_s* p, int64_t n, lc_direction dir, int64_t batch, lc
   lc_status st = lc_compute_geometry(n, &p->opt, 0, &p->g);
   if (st != LC_OK) return st;
   if (p->opt.slices == 0) p->opt.slices = auto_slices(n);
+  if (p->opt.values != 0 && p->opt.values != 1) return LC_ERR_INVALID_ARG;
+  if (p->opt.values && (!lc_values_supported(n) || dtype == LC_F32)) return LC_ERR_UNSUPPORTED;
   p->dir = dir;
   p->dtype = dtype;
   p->batch = batch;
@@ -452,6 +460,7 @@ lc_status fill_ragged(lc_plan_s* p, const int64_t* n, int64_t count, lc_directio
   if (opt) p->opt = *opt;
   if (p->opt.fixed_s == 0) p->opt.fixed_s = 32;  // one s shared by every member
   if (p->opt.slices != 0 && (p->opt.slices < 3 || p->opt.slices > 7)) return LC_ERR_INVALID_ARG;
+  if (p->opt.values) return LC_ERR_UNSUPPORTED;  // values at Chebyshev points: uniform plans only
   int64_t nmax = 0;
   for (int64_t i = 0; i < count; ++i) {
     if (n[i] < 1) return LC_ERR_INVALID_ARG;
@@ -552,6 +561,10 @@ lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
     LC_CUDA_TRY(cudaMemsetAsync(p->xexp_cnt, 0, size_t(p->batch) * sizeof(unsigned), st));
     lc_status s2 = lc_df_prepare(p, st);
     if (s2 != LC_OK) return s2;
+  }
+  if (p->opt.values) {
+    lc_status s3 = lc_values_prepare(p, st);
+    if (s3 != LC_OK) return s3;
   }
   return LC_OK;
 }
@@ -787,7 +800,19 @@ lc_status lc_plan_table(lc_plan plan, int32_t which, double* dst, int64_t count,
 lc_status lc_plan_launches(lc_plan plan, int32_t* launches) {
   if (!plan || !launches) return LC_ERR_INVALID_ARG;
   *launches = (plan->dtype == LC_F64_SPLIT) ? lc_exec_split_launches(plan) : lc_exec_cuda_cores_launches(plan);
+  if (plan->opt.values) *launches += 1;  // the cosine transform
   return LC_OK;
+}
+
+static lc_status transform(lc_plan plan, const void* in, void* out, const lc_layout& lay, cudaStream_t s,
+                           int adjoint) {
+  switch (plan->dtype) {
+    case LC_F64:
+    case LC_F32: return lc_exec_cuda_cores(plan, in, out, lay, s, adjoint);
+    case LC_F64_DF: return lc_exec_df(plan, in, out, lay, s, adjoint);
+    case LC_F64_SPLIT: return lc_exec_split(plan, in, out, lay, s, adjoint);
+  }
+  return LC_ERR_INVALID_ARG;
 }
 
 static lc_status dispatch(lc_plan plan, const void* in, void* out, lc_layout lay, lc_stream stream, int adjoint) {
@@ -806,13 +831,26 @@ static lc_status dispatch(lc_plan plan, const void* in, void* out, lc_layout lay
   }
   if (in == out) return LC_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  switch (plan->dtype) {
-    case LC_F64:
-    case LC_F32: return lc_exec_cuda_cores(plan, in, out, lay, s, adjoint);
-    case LC_F64_DF: return lc_exec_df(plan, in, out, lay, s, adjoint);
-    case LC_F64_SPLIT: return lc_exec_split(plan, in, out, lay, s, adjoint);
+  if (plan->opt.values) {
+    // values at Chebyshev points: L2C, then the cosine transform of its
+    // result in place; or the inverse cosine transform into the plan's
+    // buffer, then C2L from there
+    if (adjoint) return LC_ERR_UNSUPPORTED;
+    if (plan->dir == LC_L2C) {
+      lc_status e = transform(plan, in, out, lay, s, 0);
+      if (e != LC_OK) return e;
+      return lc_values_synth(plan, static_cast<double*>(out), lay, s);
+    }
+    lc_status e = lc_values_analysis(plan, static_cast<const double*>(in), lay, plan->val_scratch, s);
+    if (e != LC_OK) return e;
+    lc_layout packed = lay;
+    packed.ib = plan->g.n;
+    packed.ie = 1;
+    packed.iob = 0;
+    if (packed.inner > 0) packed.iob = packed.inner * plan->g.n;  // vector b at b n either way
+    return transform(plan, plan->val_scratch, out, packed, s, 0);
   }
-  return LC_ERR_INVALID_ARG;
+  return transform(plan, in, out, lay, s, adjoint);
 }
 
 lc_status lc_execute(lc_plan plan, const void* in, void* out, int64_t in_batch_stride, int64_t in_elem_stride,

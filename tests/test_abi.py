@@ -107,3 +107,27 @@ def test_static_entry_rejects_bad_arguments_without_gpu(lib):
     ]
     for c in cases:
         assert f(*c, None) == 1, c
+
+
+def test_values_option_validation_without_gpu():
+    # values at Chebyshev points: power-of-two n up to LC_VALUES_MAX_N, FP64 tiers, uniform plans
+    from paper_2411_00033_gb300 import binding as B
+    opts = B.lc_plan_options_default()
+    assert opts.values == 0
+    opts.values = 1
+    assert B.lc_plan_workspace_size(512, B.LC_L2C, 3, B.LC_F64_SPLIT, opts) > \
+        B.lc_plan_workspace_size(512, B.LC_L2C, 3, B.LC_F64_SPLIT)
+    for n, dt in ((1000, B.LC_F64), (B.LC_VALUES_MAX_N * 2, B.LC_F64), (1, B.LC_F64_DF), (512, B.LC_F32)):
+        with pytest.raises(B.LegChebError) as e:
+            B.lc_plan_workspace_size(n, B.LC_C2L, 1, dt, opts)
+        assert e.value.status == 5, (n, dt)
+    with pytest.raises(B.LegChebError) as e:
+        B.lc_plan_workspace_size_ragged([64, 128], B.LC_L2C, B.LC_F64_SPLIT, opts)
+    assert e.value.status == 5
+    opts.values = 2
+    with pytest.raises(B.LegChebError) as e:
+        B.lc_plan_workspace_size(512, B.LC_L2C, 1, B.LC_F64, opts)
+    assert e.value.status == 1
+    text = (ROOT / "include" / "legcheb.h").read_text()
+    m = re.search(r"#define\s+LC_VALUES_MAX_N\s+(\d+)", text)
+    assert m and int(m.group(1)) == B.LC_VALUES_MAX_N

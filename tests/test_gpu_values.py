@@ -1,0 +1,101 @@
+"""Values at Chebyshev points: Legendre synthesis on the n Chebyshev-Gauss
+points x_m = cos((m + 1/2) pi / n) (an L2C plan with values=True) and its
+inverse (a C2L plan with values=True), against the oracle's synthesis (its
+L2C, then a direct cosine sum in double-double with exact angle reduction)
+and analysis.  Tolerance: E_2 <= 1e-13, the FP64-accurate gate."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_util import rel_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TIERS = ["f64", "f64_df", "f64_split"]
+
+
+@pytest.fixture(scope="module")
+def lc():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_00033_gb300 as m
+    return m
+
+
+def _batch(n, batch, seed, r=0.5):
+    return np.stack([workloads.decaying_vector(n, seed=seed + b, r=r) for b in range(batch)])
+
+
+@pytest.mark.parametrize("tier", TIERS)
+@pytest.mark.parametrize("n,batch", [(2, 1), (8, 3), (64, 2), (256, 5), (512, 3), (1024, 2), (4096, 2)])
+def test_synthesis_matches_oracle(lc, tier, n, batch):
+    F = _batch(n, batch, seed=500 + n)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, "l2c", batch, tier, dev, values=True)
+    V = plan(torch.as_tensor(F if batch > 1 else F[0], device=dev)).cpu().numpy().reshape(batch, n)
+    for b in range(batch):
+        e2, einf = rel_errors(V[b], oracle.synthesis(F[b]))
+        assert e2 <= 1e-13, (tier, n, b, e2, einf)
+
+
+@pytest.mark.parametrize("tier", TIERS)
+@pytest.mark.parametrize("n,batch", [(2, 1), (8, 3), (64, 2), (512, 3), (4096, 2)])
+def test_analysis_matches_oracle(lc, tier, n, batch):
+    # values of a decaying Legendre series at the points (so the answer decays too)
+    V = np.stack([oracle.synthesis(f) for f in _batch(n, batch, seed=600 + n, r=1.0)])
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(n, "c2l", batch, tier, dev, values=True)
+    Fg = plan(torch.as_tensor(V if batch > 1 else V[0], device=dev)).cpu().numpy().reshape(batch, n)
+    for b in range(batch):
+        e2, einf = rel_errors(Fg[b], oracle.analysis(V[b]))
+        assert e2 <= 1e-13, (tier, n, b, e2, einf)
+
+
+def test_round_trip_and_strided_fibres(lc):
+    dev = torch.device("cuda", 0)
+    n = 512
+    F = torch.as_tensor(_batch(n, 6, seed=70), device=dev)
+    for tier in TIERS:
+        v = lc.Plan(n, "l2c", 6, tier, dev, values=True)(F)
+        back = lc.Plan(n, "c2l", 6, tier, dev, values=True)(v)
+        e = ((back - F).norm() / F.norm()).item()
+        assert e <= 1e-13, (tier, e)
+    # fibres of a (10, n, 6) array along its middle axis: two-level batch layout
+    X = np.random.default_rng(71).standard_normal((10, n, 6)) / np.arange(1, n + 1)[None, :, None]
+    xt = torch.as_tensor(X, device=dev)
+    plan = lc.Plan(n, "l2c", 60, "f64_split", dev, values=True)
+    out = plan.along_axis(xt, 1).cpu().numpy()
+    for i, k in ((0, 0), (3, 5), (9, 2)):
+        e2, _ = rel_errors(out[i, :, k], oracle.synthesis(X[i, :, k]))
+        assert e2 <= 1e-13, (i, k, e2)
+
+
+@pytest.mark.parametrize("k", [-900, -130, 140, 800])
+def test_values_over_the_exponent_range(lc, k):
+    n = 1024
+    f = workloads.decaying_vector(n, seed=72, r=1.0)
+    dev = torch.device("cuda", 0)
+    v = lc.Plan(n, "l2c", 1, "f64_df", dev, values=True)(torch.as_tensor(f * 2.0 ** k, device=dev)).cpu().numpy()
+    e2, _ = rel_errors(v * 2.0 ** -k, oracle.synthesis(f))
+    assert e2 <= 1e-13, (k, e2)
+    vals = oracle.synthesis(f)
+    g = lc.Plan(n, "c2l", 1, "f64_split", dev, values=True)(torch.as_tensor(vals * 2.0 ** k, device=dev)).cpu().numpy()
+    e2, _ = rel_errors(g * 2.0 ** -k, oracle.analysis(vals))
+    assert e2 <= 1e-13, (k, e2)
+
+
+def test_values_unsupported_requests(lc):
+    dev = torch.device("cuda", 0)
+    for n, tier in ((1000, "f64"), (8192, "f64"), (1, "f64"), (512, "f32")):
+        with pytest.raises(lc.LegChebError) as e:
+            lc.Plan(n, "l2c", 1, tier, dev, values=True)
+        assert e.value.status == 5, (n, tier)
+    with pytest.raises(lc.LegChebError) as e:
+        lc.Plan(direction="l2c", dtype="f64_split", device=dev, lengths=[64, 128], values=True)
+    assert e.value.status == 5
+    plan = lc.Plan(512, "l2c", 1, "f64", dev, values=True)
+    x = torch.zeros(512, dtype=torch.float64, device=dev)
+    with pytest.raises(lc.LegChebError) as e:
+        plan.execute(x, adjoint=True)
+    assert e.value.status == 5
