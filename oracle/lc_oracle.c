@@ -38,6 +38,22 @@
  * Legendre synthesis on Chebyshev points (L2C, then kind 0; Sec. 1 names the
  * Chebyshev-Legendre Galerkin use) and its inverse (kind 1, then C2L).
  *
+ * Gegenbauer bases (lco_apply_geg, lco_entry_geg).  The Conclusions note that
+ * the method carries over to transforms between Gegenbauer bases.  The maps
+ * here connect the Gegenbauer polynomials C_j^(a), a > -1/2, a != 0, with the
+ * Chebyshev polynomials; a = 1/2 gives the Legendre maps above.  Their plain
+ * definitions, written out without any Gamma function:
+ *   Gegenbauer -> Chebyshev.  The generating function
+ *   (1 - 2xt + t^2)^(-a) = (1 - e^{it} t)^(-a) (1 - e^{-it} t)^(-a) at x = cos t,
+ *   expanded as a product of two binomial series, gives
+ *   C_j^(a)(cos t) = sum_k g_k g_{j-k} cos((j - 2k) t), g_k = (a)_k / k!,
+ *   so entry (i, j), j - i = 2l >= 0, is (2/c_i) g_l g_m with m = (i + j)/2.
+ *   Chebyshev -> Gegenbauer.  The connection C^(mu) -> C^(a) (DLMF 18.18.16)
+ *   in the limit T_j = (j/2) lim_{mu->0} C_j^(mu)/mu gives, for j >= 1,
+ *   entry (i, j) = (2i + 2a) j K u_l w_m with K = 1/(4a(a+1)),
+ *   u_l = (-a)_l / l!, w_m = (m-1)! / (a+2)_{m-1}; entry (0,0) = 1.
+ * The three sequences come from their ratio recursions in double-double.
+ *
  * Rows are independent; with OpenMP available they are spread over threads.
  */
 #define _GNU_SOURCE 1
@@ -144,6 +160,40 @@ static dd entry(int direction, const dd* lam, int64_t i, int64_t j) {
   return direction == 0 ? l2c_entry(lam, i, j) : c2l_entry(lam, i, j);
 }
 
+/* Gegenbauer parameter a: the double-double sequences of the header,
+ * t0[k] = g_k = (a)_k/k! (direction 0), or t0[l] = u_l = (-a)_l/l! and
+ * t1[m] = w_m = (m-1)!/(a+2)_{m-1}, t1[0] = 0 (direction 1), for indices < n. */
+static void geg_tables(int direction, double a, int64_t n, dd* t0, dd* t1) {
+  if (n <= 0) return;
+  t0[0] = dd_from(1.0);
+  for (int64_t k = 1; k < n; ++k) {
+    /* g_k = g_{k-1} (k - 1 + a)/k, u_k = u_{k-1} (k - 1 - a)/k: the sums are
+     * exact as double-doubles */
+    dd f = two_sum((double)(k - 1), direction == 0 ? a : -a);
+    t0[k] = dd_div(dd_mul(t0[k - 1], f), dd_from((double)k));
+  }
+  if (direction == 0) return;
+  t1[0] = dd_from(0.0);
+  if (n > 1) t1[1] = dd_from(1.0);
+  for (int64_t m = 2; m < n; ++m)
+    t1[m] = dd_div(dd_mul_d(t1[m - 1], (double)(m - 1)), two_sum((double)m, a));
+}
+
+static dd geg_entry(int direction, double a, const dd* t0, const dd* t1, int64_t i, int64_t j) {
+  if (j < i || ((j - i) & 1)) return dd_from(0.0);
+  const int64_t l = (j - i) / 2, m = (i + j) / 2;
+  if (direction == 0) {
+    dd e = dd_mul(t0[l], t0[m]);
+    return i == 0 ? e : dd_mul_d(e, 2.0);
+  }
+  if (i == 0 && j == 0) return dd_from(1.0);
+  /* K = 1 / (4 a (a + 1)) */
+  dd den = dd_mul(dd_from(4.0 * a), two_sum(a, 1.0));
+  dd e = dd_div(dd_mul(t0[l], t1[m]), den);
+  e = dd_mul(e, two_sum((double)(2 * i), 2.0 * a));
+  return dd_mul_d(e, (double)j);
+}
+
 /* ---------------------------------------------------------------- API -- */
 
 /* Lambda(k), k < n, rounded to double (hi) plus the double-double tail. */
@@ -203,6 +253,62 @@ int lco_apply(int direction, int adjoint, int64_t n, const double* x,
     out[r] = dd_to(acc);
   }
   free(lam);
+  return 0;
+}
+
+/* The Gegenbauer maps of the header (direction 0: Gegenbauer -> Chebyshev,
+ * 1: Chebyshev -> Gegenbauer), or their transposes, for parameter a with
+ * -1/2 < a, a != 0; arguments as lco_apply. */
+int lco_apply_geg(int direction, int adjoint, double a, int64_t n, const double* x,
+                  int64_t nrows, const int64_t* rows, double* out) {
+  if (n <= 0 || !x || !out || (direction != 0 && direction != 1)) return 1;
+  if (!(a > -0.5) || a == 0.0 || !isfinite(a)) return 1;
+  int64_t count = rows ? nrows : n;
+  for (int64_t r = 0; rows && r < count; ++r)
+    if (rows[r] < 0 || rows[r] >= n) return 1;
+  dd* t0 = (dd*)malloc(sizeof(dd) * (size_t)n);
+  dd* t1 = (dd*)malloc(sizeof(dd) * (size_t)n);
+  if (!t0 || !t1) {
+    free(t0);
+    free(t1);
+    return 2;
+  }
+  geg_tables(direction, a, n, t0, t1);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t r = 0; r < count; ++r) {
+    int64_t i = rows ? rows[r] : r;
+    dd acc = dd_from(0.0);
+    if (!adjoint) {
+      for (int64_t j = i; j < n; j += 2)
+        acc = dd_add(acc, dd_mul_d(geg_entry(direction, a, t0, t1, i, j), x[j]));
+    } else {
+      int64_t j = i;
+      for (int64_t ii = (j & 1); ii <= j; ii += 2)
+        acc = dd_add(acc, dd_mul_d(geg_entry(direction, a, t0, t1, ii, j), x[ii]));
+    }
+    out[r] = dd_to(acc);
+  }
+  free(t0);
+  free(t1);
+  return 0;
+}
+
+/* One entry of a Gegenbauer map, rounded to double. */
+int lco_entry_geg(int direction, double a, int64_t n, int64_t i, int64_t j, double* out) {
+  if (n <= 0 || i < 0 || j < 0 || i >= n || j >= n || !out) return 1;
+  if (direction != 0 && direction != 1) return 1;
+  if (!(a > -0.5) || a == 0.0 || !isfinite(a)) return 1;
+  dd* t0 = (dd*)malloc(sizeof(dd) * (size_t)n);
+  dd* t1 = (dd*)malloc(sizeof(dd) * (size_t)n);
+  if (!t0 || !t1) {
+    free(t0);
+    free(t1);
+    return 2;
+  }
+  geg_tables(direction, a, n, t0, t1);
+  *out = dd_to(geg_entry(direction, a, t0, t1, i, j));
+  free(t0);
+  free(t1);
   return 0;
 }
 

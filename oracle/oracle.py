@@ -56,7 +56,10 @@ def _load():
         lib.lco_apply.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, i64, ip, dp]
         lib.lco_threads.argtypes = []
         lib.lco_dct.argtypes = [ctypes.c_int, i64, dp, dp]
-        for f in (lib.lco_lambda, lib.lco_entry, lib.lco_apply, lib.lco_threads, lib.lco_dct):
+        lib.lco_apply_geg.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, i64, dp, i64, ip, dp]
+        lib.lco_entry_geg.argtypes = [ctypes.c_int, ctypes.c_double, i64, i64, i64, dp]
+        for f in (lib.lco_lambda, lib.lco_entry, lib.lco_apply, lib.lco_threads, lib.lco_dct,
+                  lib.lco_apply_geg, lib.lco_entry_geg):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -93,37 +96,54 @@ def entry(direction: int, n: int, i: int, j: int) -> float:
     return out.value
 
 
-def apply(direction: int, x, rows=None, adjoint: bool = False):
+def apply(direction: int, x, rows=None, adjoint: bool = False, alpha=None):
     """Apply the L2C (direction 0) or C2L (direction 1) map, or its transpose.
 
     x: 1-D float64 array of length n.  rows: optional int64 output indices;
     when given only those outputs are computed (in that order).
+    alpha: None for the Legendre maps; otherwise the Gegenbauer parameter a
+    (-1/2 < a, a != 0) of the maps between C_j^(a) and Chebyshev (Conclusions;
+    the definitions are in the header of lc_oracle.c).
     """
     x = np.ascontiguousarray(x, dtype=np.float64)
     if x.ndim != 1 or x.size == 0:
         raise ValueError("x must be a non-empty 1-D array")
     n = x.size
+    lib = _load()
+    if alpha is None:
+        call = lambda nr, rp, op: lib.lco_apply(direction, int(adjoint), n, _dptr(x), nr, rp, op)
+    else:
+        a = float(alpha)
+        call = lambda nr, rp, op: lib.lco_apply_geg(direction, int(adjoint), a, n, _dptr(x), nr, rp, op)
     if rows is None:
         out = np.empty(n, np.float64)
-        rc = _load().lco_apply(direction, int(adjoint), n, _dptr(x), 0, None, _dptr(out))
+        rc = call(0, None, _dptr(out))
     else:
         rows = np.ascontiguousarray(rows, dtype=np.int64)
         out = np.empty(rows.size, np.float64)
-        rc = _load().lco_apply(direction, int(adjoint), n, _dptr(x), rows.size,
-                               rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(out))
+        rc = call(rows.size, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(out))
     if rc:
-        raise RuntimeError("lco_apply failed (%d)" % rc)
+        raise RuntimeError("oracle apply failed (%d)" % rc)
     return out
 
 
-def dense_matrix(direction: int, n: int):
+def entry_geg(direction: int, alpha: float, n: int, i: int, j: int) -> float:
+    """Entry (i, j) of the Gegenbauer map for parameter alpha and size n."""
+    out = ctypes.c_double()
+    rc = _load().lco_entry_geg(direction, float(alpha), n, i, j, ctypes.byref(out))
+    if rc:
+        raise ValueError("lco_entry_geg failed (%d)" % rc)
+    return out.value
+
+
+def dense_matrix(direction: int, n: int, alpha=None):
     """The full n x n matrix of the map, column by column (small n only)."""
     m = np.zeros((n, n), np.float64)
     e = np.zeros(n, np.float64)
     for j in range(n):
         e[:] = 0.0
         e[j] = 1.0
-        m[:, j] = apply(direction, e)
+        m[:, j] = apply(direction, e, alpha=alpha)
     return m
 
 
@@ -139,14 +159,16 @@ def dct(kind: int, x):
     return out
 
 
-def synthesis(f):
+def synthesis(f, alpha=None):
     """Values p(x_m) of p = sum_j f_j P_j at the n Chebyshev-Gauss points
     x_m = cos((m+1/2) pi/n): the L2C map, then the Chebyshev series at the
-    points (Sec. 1: Legendre coefficients to values through the Chebyshev basis)."""
-    return dct(0, apply(L2C, f))
+    points (Sec. 1: Legendre coefficients to values through the Chebyshev basis).
+    With alpha, p = sum_j f_j C_j^(alpha)."""
+    return dct(0, apply(L2C, f, alpha=alpha))
 
 
-def analysis(v):
-    """Legendre coefficients of the degree < n polynomial through the values v
-    at the n Chebyshev-Gauss points: discrete Chebyshev transform, then C2L."""
-    return apply(C2L, dct(1, v))
+def analysis(v, alpha=None):
+    """Legendre (or, with alpha, Gegenbauer) coefficients of the degree < n
+    polynomial through the values v at the n Chebyshev-Gauss points: discrete
+    Chebyshev transform, then C2L."""
+    return apply(C2L, dct(1, v), alpha=alpha)
