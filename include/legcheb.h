@@ -110,7 +110,20 @@ typedef struct {
    * LC_ERR_UNSUPPORTED.  0 (default): coefficients. */
   int32_t values;
   int32_t reserved[3];
+  /* Gegenbauer parameter a of the non-Chebyshev side (Conclusions: the
+   * method carries over to Gegenbauer bases).  0 (default) or 0.5: Legendre,
+   * P_j = C_j^(1/2).  Otherwise -1/2 < a <= LC_GEGENBAUER_MAX_ALPHA, a != 0:
+   * LC_L2C maps coefficients of C_j^(a) to Chebyshev coefficients, with
+   * entries (2/c_i) g_l g_m, g_k = (a)_k / k!, l = (j-i)/2, m = (j+i)/2 (the
+   * generating function of C^(a) at x = cos t); LC_C2L is its inverse, with
+   * entries (2i + 2a) j u_l w_m / (4a(a+1)), u_l = (-a)_l / l!,
+   * w_m = (m-1)!/(a+2)_{m-1}, entry (0,0) = 1.  The far-field kernels are
+   * the same products of Gamma ratios at real arguments, sampled through
+   * their asymptotic series; every tier, adjoints, ragged plans and the
+   * values option accept it.  Anything else returns LC_ERR_INVALID_ARG. */
+  double alpha;
 } lc_plan_options;
+#define LC_GEGENBAUER_MAX_ALPHA 2.0
 #define LC_VALUES_MAX_N 4096
 
 /* Fill *opt with the defaults above.  Returns LC_ERR_INVALID_ARG for NULL. */

@@ -293,6 +293,28 @@ int lco_apply_geg(int direction, int adjoint, double a, int64_t n, const double*
   return 0;
 }
 
+/* The sequences of geg_tables rounded to double: t0 = g (direction 0) or u
+ * (direction 1), t1 = w (direction 1; may be NULL for direction 0). */
+int lco_geg_tables(int direction, double a, int64_t n, double* t0, double* t1) {
+  if (n <= 0 || !t0 || (direction != 0 && direction != 1) || (direction == 1 && !t1)) return 1;
+  if (!(a > -0.5) || a == 0.0 || !isfinite(a)) return 1;
+  dd* d0 = (dd*)malloc(sizeof(dd) * (size_t)n);
+  dd* d1 = (dd*)malloc(sizeof(dd) * (size_t)n);
+  if (!d0 || !d1) {
+    free(d0);
+    free(d1);
+    return 2;
+  }
+  geg_tables(direction, a, n, d0, d1);
+  for (int64_t k = 0; k < n; ++k) {
+    t0[k] = dd_to(d0[k]);
+    if (direction == 1) t1[k] = dd_to(d1[k]);
+  }
+  free(d0);
+  free(d1);
+  return 0;
+}
+
 /* One entry of a Gegenbauer map, rounded to double. */
 int lco_entry_geg(int direction, double a, int64_t n, int64_t i, int64_t j, double* out) {
   if (n <= 0 || i < 0 || j < 0 || i >= n || j >= n || !out) return 1;

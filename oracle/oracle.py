@@ -58,8 +58,9 @@ def _load():
         lib.lco_dct.argtypes = [ctypes.c_int, i64, dp, dp]
         lib.lco_apply_geg.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, i64, dp, i64, ip, dp]
         lib.lco_entry_geg.argtypes = [ctypes.c_int, ctypes.c_double, i64, i64, i64, dp]
+        lib.lco_geg_tables.argtypes = [ctypes.c_int, ctypes.c_double, i64, dp, dp]
         for f in (lib.lco_lambda, lib.lco_entry, lib.lco_apply, lib.lco_threads, lib.lco_dct,
-                  lib.lco_apply_geg, lib.lco_entry_geg):
+                  lib.lco_apply_geg, lib.lco_entry_geg, lib.lco_geg_tables):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -125,6 +126,18 @@ def apply(direction: int, x, rows=None, adjoint: bool = False, alpha=None):
     if rc:
         raise RuntimeError("oracle apply failed (%d)" % rc)
     return out
+
+
+def geg_tables(direction: int, alpha: float, n: int):
+    """The sequences behind the Gegenbauer entries, indices < n: direction 0
+    returns g_k = (a)_k/k!; direction 1 returns (u, w) with u_l = (-a)_l/l!,
+    w_m = (m-1)!/(a+2)_{m-1}, w_0 = 0 (header of lc_oracle.c)."""
+    t0 = np.empty(n, np.float64)
+    t1 = np.empty(n, np.float64)
+    rc = _load().lco_geg_tables(direction, float(alpha), n, _dptr(t0), _dptr(t1))
+    if rc:
+        raise ValueError("lco_geg_tables failed (%d)" % rc)
+    return t0 if direction == 0 else (t0, t1)
 
 
 def entry_geg(direction: int, alpha: float, n: int, i: int, j: int) -> float:

@@ -17,8 +17,10 @@ def _stream_ptr(device) -> int:
 
 
 def make_options(s_hat: int | None = None, fixed_s: int | None = None, slices: int | None = None,
-                 debug_flags: int | None = None, values: bool | None = None):
+                 debug_flags: int | None = None, values: bool | None = None, alpha: float | None = None):
     o = B.lc_plan_options_default()
+    if alpha is not None:
+        o.alpha = float(alpha)
     if values is not None:
         o.values = int(bool(values))
     if debug_flags is not None:
@@ -41,6 +43,8 @@ class Plan:
     values:    True: the Chebyshev side holds values at the n Chebyshev-Gauss points
                cos((m + 1/2) pi / n) instead of coefficients ("l2c": Legendre synthesis
                on those points; "c2l": Legendre coefficients from the values)
+    alpha:     Gegenbauer parameter a (-1/2 < a <= 2, a != 0): the non-Chebyshev side
+               holds coefficients of C_j^(a) instead of P_j = C_j^(1/2) (default: Legendre)
     """
 
     def __init__(self, n: int | None = None, direction: str = "l2c", batch: int = 1, dtype: str = "f64",

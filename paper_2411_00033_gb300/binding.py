@@ -16,6 +16,8 @@ LC_L2C, LC_C2L = 0, 1
 LC_STATIC_MAX_N = 16384
 #: largest n of a plan with values at Chebyshev points (LC_VALUES_MAX_N)
 LC_VALUES_MAX_N = 4096
+#: largest Gegenbauer parameter a of a plan (LC_GEGENBAUER_MAX_ALPHA)
+LC_GEGENBAUER_MAX_ALPHA = 2.0
 LC_F64, LC_F64_SPLIT, LC_F32, LC_F64_DF = 0, 1, 2, 3
 STATUS_NAMES = {
     0: "LC_OK", 1: "LC_ERR_INVALID_ARG", 2: "LC_ERR_WORKSPACE_TOO_SMALL", 3: "LC_ERR_CUDA",
@@ -40,7 +42,8 @@ class LegChebError(RuntimeError):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("s_hat", ctypes.c_int32), ("fixed_s", ctypes.c_int32), ("slices", ctypes.c_int32),
-                ("debug_flags", ctypes.c_int32), ("values", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("debug_flags", ctypes.c_int32), ("values", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+                ("alpha", ctypes.c_double)]
 
 
 _lib = None

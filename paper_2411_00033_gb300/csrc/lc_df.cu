@@ -38,6 +38,8 @@ __device__ __forceinline__ double lc_out_acc<lc_df, double>(double acc, const lc
 template <>
 struct local_scale<lc_df, double> { static constexpr bool value = true; };
 template <>
+__device__ __forceinline__ lc_df lc_from_double<lc_df>(double x) { return lc_df_from_double(x); }
+template <>
 __device__ __forceinline__ lc_df cinv<lc_df>(int64_t i) {
   // 1/pi and 2/pi as double-floats
   return i == 0 ? lc_df(0.31830987334251404f, 1.2841276486597053e-08f)
@@ -137,6 +139,7 @@ lc_status lc_exec_df(lc_plan p, const void* in, void* out, const lc_layout& lay,
   a.inner = lay.inner; a.iob = lay.iob; a.oob = lay.oob;
   a.n = p->g.n; a.N = p->g.N; a.L = p->g.L; a.s = p->g.s; a.nseg = p->g.nseg;
   a.batch = p->batch; a.dir = int(p->dir);
+  a.two_alpha = p->geg.two_alpha;
   a.t = lc_tables<lc_df>{static_cast<const lc_df*>(p->df_lam), static_cast<const lc_df*>(p->df_lam2),
                          static_cast<const lc_df*>(p->df_T), static_cast<const lc_df*>(p->df_B),
                          static_cast<const lc_df*>(p->df_Ahat), static_cast<lc_df*>(p->df_W),

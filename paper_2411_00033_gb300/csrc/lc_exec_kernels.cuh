@@ -65,11 +65,23 @@ struct Args {
   int* xe;
   int* xe_part;
   unsigned* xe_cnt;
+  // C2L row factor 2i + two_alpha (1 for Legendre; 2a for Gegenbauer a).
+  double two_alpha;
 };
 
 template <typename R>
 __device__ __forceinline__ R cinv(int64_t i) {
   return i == 0 ? R(0.31830988618379067154) : R(0.63661977236758134308);  // 1/pi, 2/pi
+}
+
+template <typename R>
+__device__ __forceinline__ R lc_from_double(double x) { return R(x); }
+// C2L row factor 2i + 2a of the entries (2i + 2a) j u_k v_(i+k): at a = 1/2
+// (eq:Lxymod) the integer 2i + 1.
+template <typename R>
+__device__ __forceinline__ R c2l_row(const Args<R>& a, int64_t i) {
+  if (a.two_alpha == 1.0) return R(2 * i + 1);
+  return lc_from_double<R>(double(2 * i) + a.two_alpha);
 }
 
 // Input element x as R, times 2^-e (e: the vector's exponent, 0 unless the
@@ -718,9 +730,9 @@ __device__ __forceinline__ void near_tile(const Args<R>& a, int64_t b, int64_t l
   // the tier allows, this tile's own (the band's outputs need no other)
   auto scale_put = [&](int64_t q, R v) {
     if (!adj) {
-      if (a.dir == LC_C2L) v = R(q) * v;  // L(i, j) = (2i+1) j u v: scale column j
+      if (a.dir == LC_C2L) v = R(q) * v;  // L(i, j) = (2i+2a) j u v: scale column j
     } else {
-      v = (a.dir == LC_L2C) ? cinv<R>(q) * v : R(2 * q + 1) * v;  // C^{-1} r or (2i+1) r
+      v = (a.dir == LC_L2C) ? cinv<R>(q) * v : c2l_row(a, q) * v;  // C^{-1} r or (2i+2a) r
     }
     opnd[pad_index(q - pbase, two_s, pad) - ooff] = v;
   };
@@ -777,7 +789,7 @@ __device__ __forceinline__ void near_tile(const Args<R>& a, int64_t b, int64_t l
         const R* fo = opnd + (i - olo);
         const R* lm = lamm + (i - mlo);
         near = band_sum<R>(cnt, [&](const R& c, int kk) { return acc3(c, lamk[kk], lm[kk], fo[2 * kk]); });
-        put(i, l2c ? cinv<R>(i) * near : R(2 * i + 1) * near);
+        put(i, l2c ? cinv<R>(i) * near : c2l_row(a, i) * near);
       } else {
         const int cnt = int(i / 2 + 1);
         const R* ro = opnd + (i - olo);
@@ -824,9 +836,9 @@ __device__ __forceinline__ void near_tile(const Args<R>& a, int64_t b, int64_t l
           put(i, cinv<R>(i) * n0);
           if (has1) put(i + 2, cinv<R>(i + 2) * n1);
         } else {
-          // (2i+1) u_k v_(i+k) (j f_j) summed
-          put(i, R(2 * i + 1) * n0);
-          if (has1) put(i + 2, R(2 * i + 5) * n1);
+          // (2i+2a) u_k v_(i+k) (j f_j) summed
+          put(i, c2l_row(a, i) * n0);
+          if (has1) put(i + 2, c2l_row(a, i + 2) * n1);
         }
       } else {
         int64_t st = two_s * (v - 1) > 0 ? two_s * (v - 1) : 0;
@@ -1049,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
             if (!adj) {
               if (!l2c) v = R(q) * v;  // L(i, j) = (2i+1) j u v: scale column j
             } else {
-              v = l2c ? cinv<R>(q) * v : R(2 * q + 1) * v;  // C^{-1} r or (2i+1) r
+              v = l2c ? cinv<R>(q) * v : c2l_row(a, q) * v;  // C^{-1} r or (2i+2a) r
             }
             opnd[i] = v;
           });
@@ -1095,8 +1107,8 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
               const R c = cinv<R>(i);
               res = lc_out2<R, IO>(c * far, c * near, e);
             } else {
-              // (2i+1) u_k v_(i+k) (j f_j) summed
-              res = lc_out2<R, IO>(far, R(2 * i + 1) * near, e);
+              // (2i+2a) u_k v_(i+k) (j f_j) summed
+              res = lc_out2<R, IO>(far, c2l_row(a, i) * near, e);
               if (i == 0) res += f[0];
             }
           } else {

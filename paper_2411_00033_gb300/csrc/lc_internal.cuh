@@ -50,7 +50,9 @@ __host__ __device__ inline int64_t lc_ahat_offset(int gamma) {
 // so they fall off geometrically in k + l (by about 4x per step for L2C,
 // 3x for C2L); beyond the head every entry is below 4e-9 of the matrix's
 // largest for every leaf size s = 4..64 and level (2e-9 for s >= 5; tested),
-// and its leading word alone is accurate to 2.4e-16 of that.  Words per matrix: a multiple of 4 (16-byte
+// and its leading word alone is accurate to 2.4e-16 of that.  Gegenbauer
+// kernels (lc_geg) reach 2.2e-8 past the head for -1/2 < a <= 2 (tested),
+// so 2e-15 of the matrix.  Words per matrix: a multiple of 4 (16-byte
 // bulk copies) with the 3 matrices of a block 28 (L2C) or 12 (C2L) words
 // mod 32 apart, so that the blocks staged by one CTA start in distinct
 // shared-memory banks.
@@ -72,11 +74,39 @@ __host__ __device__ __forceinline__ int64_t lc_boff(int64_t b, int64_t stride, i
   return inner > 0 ? (b / inner) * outer + (b % inner) * stride : b * stride;
 }
 
+// Gegenbauer parameter a of a plan (lc_plan_options.alpha) and the constants
+// its tables use.  Legendre plans (a = 1/2) keep on = 0 and the specialised
+// Lambda routines.  Gamma(z + p)/Gamma(z + q) at real z is sampled through
+// its asymptotic series in v = z + (p + q - 1)/2: v^(p-q) times a power
+// series in 1/v^2 (even, because the Stirling expansions of the two log-Gamma
+// terms cancel in every odd power); LC_GEG_TERMS + 1 coefficients after the
+// argument is shifted to z >= 20 keep the truncation below 2e-18 for
+// -1/2 < a <= 2.
+#define LC_GEG_TERMS 8
+struct lc_geg {
+  int on;
+  double alpha;
+  double two_alpha;  // C2L row factor 2i + 2a (2i + 1 for Legendre)
+  double c_lam;      // sqrt(pi) / Gamma(a): lambda_a(z) = c_lam Gamma(z+a)/Gamma(z+1)
+  double c_u;        // Gamma(a) / (4 Gamma(-a)): u_a(z) = c_u Gamma(z-a)/Gamma(z+1)
+  double u0;         // u_a(0) = Gamma(a)/4
+  double v1;         // v_a(1) = 1/Gamma(a+2); v_a(m) = Gamma(m)/Gamma(m+a+1)
+  double p_lam[LC_GEG_TERMS + 1];  // series of Gamma(z+a)/Gamma(z+1)
+  double p_u[LC_GEG_TERMS + 1];    // series of Gamma(z-a)/Gamma(z+1)
+  double p_v[LC_GEG_TERMS + 1];    // series of Gamma(z)/Gamma(z+a+1)
+};
+
 // Device views of a plan's tables, by element type.
 template <typename R>
 struct lc_tables {
-  const R* lam;   // L2C: lambda[N]; C2L: u[N] = lambda_k / (1 - 2k)
-  const R* lam2;  // L2C: lambda[N]; C2L: v[N] = 1 / (2m (2m+1) lambda_m), v[0] = 0
+  // Legendre: L2C lambda[N]; C2L u[N] = lambda_k / (1 - 2k).  Gegenbauer a:
+  // L2C sqrt(pi) (a)_k / k! (so that the Legendre C^{-1} applies unchanged);
+  // C2L u_k = Gamma(a)/4 (-a)_k / k!.
+  const R* lam;
+  // L2C: lam again; C2L: v[N] = 1 / (2m (2m+1) lambda_m) (Legendre) or
+  // Gamma(m)/Gamma(m+a+1) (Gegenbauer), v[0] = 0.  C2L entries are
+  // (2i + 2a) j u_k v_(i+k).
+  const R* lam2;
   const R* T;     // [2][s][M]   T_k(-1 + (2m+sigma)/s)           (eq:Xs)
   const R* B;     // [M][M]      B(0), lower triangular           (eq:Tmap)
   const R* Ahat;  // [nc][M][M]
@@ -92,6 +122,7 @@ struct lc_plan_s {
   lc_dtype dtype;
   int64_t batch;
   lc_plan_options opt;
+  lc_geg geg;
   int ragged;
   // FP64 tables (always built; they are the plan).
   double* lam;

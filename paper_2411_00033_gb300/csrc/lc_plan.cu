@@ -129,6 +129,71 @@ __global__ void k_plan_c2l_tables(int64_t N, double* __restrict__ u, double* __r
   v[m] = one_m * q;
 }
 
+// ------------------------------------------------------------- Gegenbauer --
+// Gamma(z + p)/Gamma(z + q) for real z with z + min(p, q) > 0: shifted up to
+// z >= 20 by Gamma(x+1) = x Gamma(x), then v^(p-q) times the series pc in
+// x = 1/v^2, v = z + (p + q - 1)/2 (lc_geg).
+__device__ double lc_gratio(double z, double pa, double qb, const double* pc) {
+  double f = 1.0;
+  for (int it = 0; it < 64 && z < 20.0; ++it) {
+    f *= (z + qb) / (z + pa);
+    z += 1.0;
+  }
+  const double v = z + 0.5 * (pa + qb - 1.0);
+  const double x = 1.0 / (v * v);
+  double q = pc[LC_GEG_TERMS];
+  for (int j = LC_GEG_TERMS - 1; j >= 0; --j) q = fma(q, x, pc[j]);
+  return f * q * pow(v, pa - qb);
+}
+__device__ __forceinline__ double lc_geg_lam(const lc_geg& G, double z) {
+  return G.c_lam * lc_gratio(z, G.alpha, 1.0, G.p_lam);
+}
+__device__ __forceinline__ double lc_geg_u(const lc_geg& G, double z) {
+  return G.c_u * lc_gratio(z, -G.alpha, 1.0, G.p_u);
+}
+__device__ __forceinline__ double lc_geg_v(const lc_geg& G, double z) {
+  return lc_gratio(z, 0.0, G.alpha + 1.0, G.p_v);
+}
+
+// Near-field tables of a Gegenbauer plan, 8 consecutive indices per thread:
+// the first from the series (from the start value below index 24), the rest
+// by the ratio recursions g_k = g_(k-1) (k-1+a)/k, u_k = u_(k-1) (k-1-a)/k,
+// v_m = v_(m-1) (m-1)/(m+a).  L2C: lam = sqrt(pi) g; C2L: lam = u, lam2 = v.
+__global__ void k_plan_geg_tables(int64_t N, int dir, lc_geg G, double* __restrict__ lam,
+                                  double* __restrict__ lam2) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i0 = 8 * t;
+  if (i0 >= N) return;
+  const double a = G.alpha;
+  const double ua = dir == LC_L2C ? a : -a;  // g or u recursion
+  double x;
+  int64_t k = 0;
+  if (i0 < 24) {
+    x = dir == LC_L2C ? 1.7724538509055160273 : G.u0;
+    for (k = 1; k <= i0; ++k) x *= (double(k - 1) + ua) / double(k);
+  } else {
+    x = dir == LC_L2C ? lc_geg_lam(G, double(i0)) : lc_geg_u(G, double(i0));
+  }
+  lam[i0] = x;
+  for (k = i0 + 1; k < i0 + 8 && k < N; ++k) {
+    x *= (double(k - 1) + ua) / double(k);
+    lam[k] = x;
+  }
+  if (dir == LC_L2C) return;
+  double v;
+  if (i0 < 24) {
+    v = G.v1;
+    for (k = 2; k <= i0; ++k) v *= double(k - 1) / (double(k) + a);
+  } else {
+    v = lc_geg_v(G, double(i0));
+  }
+  lam2[i0] = i0 == 0 ? 0.0 : v;
+  for (k = i0 + 1; k < i0 + 8 && k < N; ++k) {
+    if (k >= 2) v *= double(k - 1) / (double(k) + a);
+    lam2[k] = v;
+  }
+}
+
 __global__ void k_plan_T(int s, double* __restrict__ T) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * s) return;
@@ -195,7 +260,8 @@ __global__ void k_plan_cos(double* __restrict__ cosm) {
 // same way).  Table [L][2][M][M].
 // For C2L the table holds Lambda((y-x)/2) / (x - y + 1), the other factor of
 // L(x, y) that depends only on y - x (eq:Lxymod).
-__global__ void k_plan_lminus(int L, int s, int dir, const double* __restrict__ cosm, double* __restrict__ tab) {
+__global__ void k_plan_lminus(int L, int s, int dir, lc_geg G, const double* __restrict__ cosm,
+                              double* __restrict__ tab) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= int64_t(L) * 2 * LC_M * LC_M) return;
   const int gamma = int(t / (2 * LC_M * LC_M));
@@ -205,6 +271,10 @@ __global__ void k_plan_lminus(int L, int s, int dir, const double* __restrict__ 
   const double off = (c == 0 ? 4.0 : 6.0) * h;  // j0 - i0
   // (y_n - x_m)/2 with x_m = i0 + h (X_m + 1), y_n = j0 + h (Y_n + 1)   (eq:Xfromx)
   const double ymx = off + h * (cosm[LC_M + n] - cosm[LC_M + m]);
+  if (G.on) {  // Gegenbauer: lambda_a((y-x)/2) or u_a((y-x)/2)
+    tab[t] = dir == LC_L2C ? lc_geg_lam(G, 0.5 * ymx) : lc_geg_u(G, 0.5 * ymx);
+    return;
+  }
   const double l = lc_Lambda(0.5 * ymx);
   tab[t] = dir == LC_L2C ? l : l / (1.0 - ymx);
 }
@@ -215,7 +285,7 @@ __global__ void k_plan_lminus(int L, int s, int dir, const double* __restrict__ 
 // cos(k(M-1-m+1/2)pi/M) = (-1)^k cos(k(m+1/2)pi/M), so each 18-term sum is
 // folded into 9 terms of sums or differences.
 __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __restrict__ cosm,
-                            const double* __restrict__ lminus, double* __restrict__ Ahat) {
+                            const double* __restrict__ lminus, double* __restrict__ Ahat, const lc_geg geg) {
   constexpr int H = LC_M / 2;
   __shared__ double S[LC_M][LC_M];
   __shared__ double F[2][H][LC_M];  // folded rows: sums (even k) and differences (odd k)
@@ -254,7 +324,11 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
     if (tid < kPairs) {  // the factor that depends on x_m + y_n: symmetric in (m, n)
       const double w = i0 + j0 + h * (cs[1][pm] + cs[1][pn] + 2.0);
       // L2C: Lambda((x+y)/2); C2L: 1 / ((x+y)(x+y+1) Lambda((x+y)/2))
-      const double lp = dir == LC_L2C ? lc_Lambda_sample(0.5 * w) : lc_c2l_wfactor(w);
+      double lp;
+      if (geg.on)  // Gegenbauer: lambda_a((x+y)/2) or v_a((x+y)/2)
+        lp = dir == LC_L2C ? lc_geg_lam(geg, 0.5 * w) : lc_geg_v(geg, 0.5 * w);
+      else
+        lp = dir == LC_L2C ? lc_Lambda_sample(0.5 * w) : lc_c2l_wfactor(w);
       S[pm][pn] = lp;
       S[pn][pm] = lp;
     }
@@ -267,7 +341,7 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
       if (dir == LC_L2C) {
         val = lmi * S[r0][c0];  // A(x, y) = Lambda((y-x)/2) Lambda((y+x)/2)
       } else {                  // L(x, y) of eq:Lxymod, no division
-        val = 2.0 * (x + 0.5) * y * lmi * S[r0][c0];
+        val = (2.0 * x + geg.two_alpha) * y * lmi * S[r0][c0];
       }
       __syncthreads();
       S[r0][c0] = val;
@@ -424,6 +498,67 @@ size_t layout(lc_plan_s* p, char* base) {
 // bound is 1e-12.
 int auto_slices(int64_t n) { return n <= 100000 ? 7 : 6; }
 
+// sin(pi a), exactly 0 at integers (the reflection formula below needs the zeros).
+double sinpi_host(double a) {
+  if (a == floor(a)) return 0.0;
+  double r = a - 2.0 * floor(0.5 * a);  // [0, 2)
+  if (r > 1.0) r -= 2.0;                // (-1, 1]
+  if (r > 0.5) r = 1.0 - r;
+  if (r < -0.5) r = -1.0 - r;
+  return sin(M_PI * r);
+}
+
+// Coefficients of exp(sum_j e_j x^j), the series of Gamma(z+p)/Gamma(z+q)
+// in x = 1/v^2 (lc_geg), with h = (p - q)/2 and
+// e_j = -2 B_{2j+1}(1/2 + h) / (2j (2j+1)): the difference of the two Stirling
+// series of log Gamma(v + 1/2 +- h), whose odd powers cancel.  The Bernoulli
+// polynomials are expanded about 1/2: B_n(1/2 + h) = sum_k C(n,k) B_k(1/2) h^(n-k),
+// B_k(1/2) = (2^(1-k) - 1) B_k (zero for odd k).
+void geg_series(double h, double* pc) {
+  static const double Bk[17] = {1.0, -0.5, 1.0 / 6, 0, -1.0 / 30, 0, 1.0 / 42, 0, -1.0 / 30, 0, 5.0 / 66, 0,
+                                -691.0 / 2730, 0, 7.0 / 6, 0, -3617.0 / 510};
+  double e[LC_GEG_TERMS + 1] = {0.0};
+  for (int j = 1; j <= LC_GEG_TERMS; ++j) {
+    const int n = 2 * j + 1;
+    double b = 0.0, binom = 1.0;  // C(n, k)
+    for (int k = 0; k <= n; ++k) {
+      if (k > 0) binom = binom * double(n - k + 1) / double(k);
+      if (k % 2 == 0 && k <= 16) b += binom * (ldexp(1.0, 1 - k) - 1.0) * Bk[k] * pow(h, double(n - k));
+    }
+    e[j] = -2.0 * b / (double(2 * j) * double(2 * j + 1));
+  }
+  pc[0] = 1.0;
+  for (int n = 1; n <= LC_GEG_TERMS; ++n) {
+    double acc = 0.0;
+    for (int k = 1; k <= n; ++k) acc += double(k) * e[k] * pc[n - k];
+    pc[n] = acc / double(n);
+  }
+}
+
+// Validates lc_plan_options.alpha and fills p->geg (Legendre: on = 0).
+lc_status geg_setup(lc_plan_s* p) {
+  const double a = p->opt.alpha;
+  memset(&p->geg, 0, sizeof(p->geg));
+  p->geg.alpha = 0.5;
+  p->geg.two_alpha = 1.0;
+  if (a == 0.0 || a == 0.5) return LC_OK;
+  if (!(a > -0.5 && a <= LC_GEGENBAUER_MAX_ALPHA)) return LC_ERR_INVALID_ARG;  // NaN fails too
+  lc_geg& G = p->geg;
+  G.on = 1;
+  G.alpha = a;
+  G.two_alpha = 2.0 * a;
+  const double ga = tgamma(a);
+  G.c_lam = sqrt(M_PI) / ga;
+  // 1/Gamma(-a) = -a / Gamma(1-a) = -a Gamma(a) sin(pi a) / pi (reflection)
+  G.c_u = 0.25 * ga * (-a * ga * sinpi_host(a) / M_PI);
+  G.u0 = 0.25 * ga;
+  G.v1 = 1.0 / (a * (a + 1.0) * ga);
+  geg_series(0.5 * (a - 1.0), G.p_lam);
+  geg_series(0.5 * (-a - 1.0), G.p_u);
+  geg_series(0.5 * (-a - 1.0), G.p_v);
+  return LC_OK;
+}
+
 bool valid_enum(lc_direction d, lc_dtype t) {
   return (d == LC_L2C || d == LC_C2L) &&
          (t == LC_F64 || t == LC_F64_SPLIT || t == LC_F32 || t == LC_F64_DF);
@@ -441,6 +576,8 @@ lc_status fill_plan(lc_plan_s* p, int64_t n, lc_direction dir, int64_t batch, lc
   if (p->opt.slices == 0) p->opt.slices = auto_slices(n);
   if (p->opt.values != 0 && p->opt.values != 1) return LC_ERR_INVALID_ARG;
   if (p->opt.values && (!lc_values_supported(n) || dtype == LC_F32)) return LC_ERR_UNSUPPORTED;
+  st = geg_setup(p);
+  if (st != LC_OK) return st;
   p->dir = dir;
   p->dtype = dtype;
   p->batch = batch;
@@ -461,6 +598,7 @@ lc_status fill_ragged(lc_plan_s* p, const int64_t* n, int64_t count, lc_directio
   if (p->opt.fixed_s == 0) p->opt.fixed_s = 32;  // one s shared by every member
   if (p->opt.slices != 0 && (p->opt.slices < 3 || p->opt.slices > 7)) return LC_ERR_INVALID_ARG;
   if (p->opt.values) return LC_ERR_UNSUPPORTED;  // values at Chebyshev points: uniform plans only
+  if (geg_setup(p) != LC_OK) return LC_ERR_INVALID_ARG;
   int64_t nmax = 0;
   for (int64_t i = 0; i < count; ++i) {
     if (n[i] < 1) return LC_ERR_INVALID_ARG;
@@ -526,12 +664,17 @@ int grid_for(int64_t work, int threads) {
 lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
   const lc_geom& g = p->g;
   LC_CUDA_TRY(cudaMemsetAsync(p->err, 0, 64 * sizeof(int), st));
-  double* lam_target = (p->dir == LC_C2L) ? p->lam2 : p->lam;
-  k_plan_lambda<<<grid_for((g.N + 7) / 8, 256), 256, 0, st>>>(g.N, lam_target);
-  LC_LAUNCH_CHECK();
-  if (p->dir == LC_C2L) {
-    k_plan_c2l_tables<<<grid_for(g.N, 256), 256, 0, st>>>(g.N, p->lam, p->lam2);
+  if (p->geg.on) {
+    k_plan_geg_tables<<<grid_for((g.N + 7) / 8, 256), 256, 0, st>>>(g.N, int(p->dir), p->geg, p->lam, p->lam2);
     LC_LAUNCH_CHECK();
+  } else {
+    double* lam_target = (p->dir == LC_C2L) ? p->lam2 : p->lam;
+    k_plan_lambda<<<grid_for((g.N + 7) / 8, 256), 256, 0, st>>>(g.N, lam_target);
+    LC_LAUNCH_CHECK();
+    if (p->dir == LC_C2L) {
+      k_plan_c2l_tables<<<grid_for(g.N, 256), 256, 0, st>>>(g.N, p->lam, p->lam2);
+      LC_LAUNCH_CHECK();
+    }
   }
   k_plan_T<<<1, 2 * LC_MAX_S, 0, st>>>(g.s, p->T);
   LC_LAUNCH_CHECK();
@@ -543,10 +686,10 @@ lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
     k_plan_cos<<<2, 256, 0, st>>>(cosm);
     LC_LAUNCH_CHECK();
     k_plan_lminus<<<unsigned((int64_t(g.L) * 2 * LC_M * LC_M + 255) / 256), 256, 0, st>>>(g.L, g.s, int(p->dir),
-                                                                                          cosm, lminus);
+                                                                                          p->geg, cosm, lminus);
     LC_LAUNCH_CHECK();
     const int64_t blocks = g.nc < 1048576 ? g.nc : 1048576;
-    k_plan_ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat);
+    k_plan_ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat, p->geg);
     LC_LAUNCH_CHECK();
   }
   if (p->dtype == LC_F32) {

@@ -1071,7 +1071,7 @@ __device__ double y_value(int kind, int64_t item, int k, int n, const lc_plan_s&
       if (i < 0 || j < i || j >= N) return 0.0;
       const int64_t kk = (j - i) / 2;
       if (dir == LC_L2C) return P.lam[kk] * P.lam2[i + kk];
-      double e = double(2 * i + 1) * double(j) * P.lam[kk] * P.lam2[i + kk];
+      double e = (double(2 * i) + P.geg.two_alpha) * double(j) * P.lam[kk] * P.lam2[i + kk];
       if (i == 0 && j == 0) e += 1.0;
       return e;
     }
@@ -1084,7 +1084,7 @@ __device__ double y_value(int kind, int64_t item, int k, int n, const lc_plan_s&
       if (j < i || j >= N || i >= N) return 0.0;
       const int64_t kk = (j - i) / 2;
       if (dir == LC_L2C) return P.lam[kk] * P.lam2[i + kk];
-      double e = double(2 * i + 1) * double(j) * P.lam[kk] * P.lam2[i + kk];
+      double e = (double(2 * i) + P.geg.two_alpha) * double(j) * P.lam[kk] * P.lam2[i + kk];
       if (i == 0 && j == 0) e += 1.0;
       return e;
     }

@@ -131,3 +131,26 @@ def test_values_option_validation_without_gpu():
     text = (ROOT / "include" / "legcheb.h").read_text()
     m = re.search(r"#define\s+LC_VALUES_MAX_N\s+(\d+)", text)
     assert m and int(m.group(1)) == B.LC_VALUES_MAX_N
+
+
+def test_alpha_option_validation_without_gpu():
+    # Gegenbauer parameter: 0 or 1/2 is Legendre; -1/2 < a <= LC_GEGENBAUER_MAX_ALPHA otherwise
+    from paper_2411_00033_gb300 import binding as B
+    opts = B.lc_plan_options_default()
+    assert opts.alpha == 0.0
+    base = B.lc_plan_workspace_size(5000, B.LC_C2L, 2, B.LC_F64_DF)
+    for a in (0.5, 0.25, -0.49, 1.0, B.LC_GEGENBAUER_MAX_ALPHA):
+        opts.alpha = a
+        assert B.lc_plan_workspace_size(5000, B.LC_C2L, 2, B.LC_F64_DF, opts) == base
+        assert B.lc_plan_workspace_size_ragged([64, 5000], B.LC_L2C, B.LC_F64_SPLIT, opts) > 0
+    for a in (-0.5, -1.0, 2.0001, float("nan"), float("inf")):
+        opts.alpha = a
+        with pytest.raises(B.LegChebError) as e:
+            B.lc_plan_workspace_size(5000, B.LC_L2C, 1, B.LC_F64, opts)
+        assert e.value.status == 1, a
+        with pytest.raises(B.LegChebError) as e:
+            B.lc_plan_workspace_size_ragged([64, 5000], B.LC_L2C, B.LC_F64_SPLIT, opts)
+        assert e.value.status == 1, a
+    text = (ROOT / "include" / "legcheb.h").read_text()
+    m = re.search(r"#define\s+LC_GEGENBAUER_MAX_ALPHA\s+([0-9.]+)", text)
+    assert m and float(m.group(1)) == B.LC_GEGENBAUER_MAX_ALPHA
