@@ -667,6 +667,29 @@ def run_ours(args):
         tier_vals[t] = {"coefficients_per_s": 2 * n / (statistics.median(m2) / 1e3),
                         "ms_per_step_median": statistics.median(m2), "launches_per_step": p2[0].launches() + p2[1].launches()}
 
+    # Gegenbauer plans (coefficients of C_j^(a) <-> Chebyshev; a = 1/2 is the
+    # Legendre case above): the same vector, tier and step, with the oracle's
+    # error on 256 of the sampled rows per direction
+    geg = {}
+    if not args.no_batched:
+        for a_ in (0.25, 1.5):
+            pg = (lc.Plan(n, "l2c", 1, chosen, dev, alpha=a_), lc.Plan(n, "c2l", 1, chosen, dev, alpha=a_))
+            m2, _, _ = time_tier(pg, max(10, min(50, args.steps)), 2)
+            rec = {"coefficients_per_s": 2 * n / (statistics.median(m2) / 1e3),
+                   "ms_per_step_median": statistics.median(m2), "tier": chosen}
+            if rank == 0 and not args.no_cpu:
+                import oracle
+                rows = workloads.sample_rows(n, 4096)[::16]
+                step(pg)
+                torch.cuda.synchronize()
+                for d_, o_ in enumerate((outs[0], outs[1])):
+                    ref = oracle.apply(d_, x_host, rows=rows, alpha=a_)
+                    dz = o_.cpu().numpy()[rows] - ref
+                    rec[("l2c", "c2l")[d_] + "_E2_vs_oracle"] = float(np.linalg.norm(dz) / np.linalg.norm(ref))
+                rec["oracle_rows"] = int(rows.size)
+            geg["alpha_%g" % a_] = rec
+            del pg
+
     # end to end through the C ABI with pinned host buffers: every step copies
     # its two inputs in from pinned host memory and its two results back.  One
     # compute stream and one copy stream with double-buffered device arrays, so
@@ -821,6 +844,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 2 * 8 * n, "matches_device_output": e2e_same, "pipelined": "copy stream + compute stream, double-buffered"},
         "gpu_launches": launches,
         "tiers": tier_vals,
+        "gegenbauer": geg,
         "plan_ms": plan_ms,
         "stage_ms_per_step": {KIND_NAMES[k]: v / args.steps for k, v in sorted(totals.items())},
         "ms_per_step_warm_l2": sum(ms_warm) / len(ms_warm),
