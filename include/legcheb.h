@@ -227,6 +227,16 @@ lc_status lc_plan_check(lc_plan plan, lc_stream stream);
  * depend on them. */
 lc_status lc_plan_set_config(lc_plan plan, int32_t leaf_depth, int32_t chunk_depth);
 
+/* Launch shape of the near-field band (Step 6) of single-vector plans on the
+ * CUDA-core tiers: ctas = number of CTAs of the band kernel, each taking
+ * groups of 16 strips of 2s rows in turn (0, the default: one CTA per
+ * group; fewer leave SM room for the far-field chain that runs beside it);
+ * after_leaf = 1 starts the band only after the leaf restriction and the
+ * fine levels of Step 2, 0 (default) with them.  Results do not depend on
+ * either.  LC_ERR_INVALID_ARG for a NULL plan, ctas < 0 or > 2^24, or
+ * after_leaf not 0 or 1. */
+lc_status lc_plan_set_band(lc_plan plan, int32_t ctas, int32_t after_leaf);
+
 /* Autotuner (not in the paper): time every candidate chunk geometry
  * (leaf_depth in {3,4,5} x chunk_depth in {3,4,6}) on the given input with
  * CUDA events on `stream` (synchronises it; `out` is overwritten, same layout

@@ -175,6 +175,11 @@ class Plan:
     def set_config(self, leaf_depth: int, chunk_depth: int):
         B.lc_plan_set_config(self._handle, leaf_depth, chunk_depth)
 
+    def set_band(self, ctas: int = 0, after_leaf: bool = False):
+        """Launch shape of the single-vector band (Step 6): CTAs (0 = one per group of
+        strips) and whether it starts after the leaf restriction; results are unchanged."""
+        B.lc_plan_set_band(self._handle, int(ctas), int(bool(after_leaf)))
+
     def check(self):
         """Raise if a bounded device-side wait of an earlier execution ran out."""
         with torch.cuda.device(self.device):

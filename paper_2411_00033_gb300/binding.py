@@ -30,7 +30,7 @@ EXPORTED = (
     "lc_plan_create", "lc_plan_create_ex", "lc_plan_workspace_size_ragged", "lc_plan_create_ragged",
     "lc_execute", "lc_adjoint", "lc_destroy", "lc_status_string", "lc_plan_info", "lc_plan_table",
     "lc_plan_launches", "lc_plan_set_timing", "lc_plan_get_timing", "lc_plan_check", "lc_direct_static",
-    "lc_plan_set_config", "lc_plan_autotune", "lc_execute_ex", "lc_adjoint_ex",
+    "lc_plan_set_config", "lc_plan_autotune", "lc_execute_ex", "lc_adjoint_ex", "lc_plan_set_band",
 )
 
 
@@ -85,6 +85,7 @@ def load(path: Path | None = None):
         "lc_plan_set_timing": [vp, i32],
         "lc_plan_check": [vp, vp],
         "lc_plan_set_config": [vp, i32, i32],
+        "lc_plan_set_band": [vp, i32, i32],
         "lc_plan_autotune": [vp, vp, vp, i64, i64, i64, i64, vp, pi32, pi32, ctypes.POINTER(ctypes.c_float)],
         "lc_plan_get_timing": [vp, i32, ctypes.POINTER(ctypes.c_float), pi32, i32, pi32],
     }
@@ -236,6 +237,10 @@ def lc_direct_static(direction, n, batch, in_ptr, out_ptr, ib, ie, ob, oe, strea
 
 def lc_plan_set_config(plan, leaf_depth: int, chunk_depth: int):
     _check(load().lc_plan_set_config(ctypes.c_void_p(plan), leaf_depth, chunk_depth), "lc_plan_set_config")
+
+
+def lc_plan_set_band(plan, ctas: int, after_leaf: int):
+    _check(load().lc_plan_set_band(ctypes.c_void_p(plan), ctas, after_leaf), "lc_plan_set_band")
 
 
 def lc_plan_autotune(plan, in_ptr, out_ptr, ib, ie, ob, oe, stream_ptr):

@@ -855,13 +855,18 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads, 4) k_near(Args<R> a, int adj) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t two_s = 2 * int64_t(a.s);
+  // groups of kNearStrips strips, grid-strided (the grid may be smaller than
+  // the number of groups, to leave SM room for the far-field chain)
+  const int64_t groups = (a.L > 0) ? (a.n + kNearStrips * two_s - 1) / (kNearStrips * two_s) : 1;
   for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
-    const int64_t lo = (a.L > 0) ? int64_t(blockIdx.x) * kNearStrips * two_s : 0;
-    const int64_t hi_raw = (a.L > 0) ? lo + kNearStrips * two_s : a.n;
-    const int64_t hi = hi_raw < a.n ? hi_raw : a.n;
-    if (lo >= hi) continue;
-    __syncthreads();  // shared tiles of the previous batch member are free
-    near_tile(a, b, lo, hi, adj, smem_raw);
+    for (int64_t gi = blockIdx.x; gi < groups; gi += gridDim.x) {
+      const int64_t lo = (a.L > 0) ? gi * kNearStrips * two_s : 0;
+      const int64_t hi_raw = (a.L > 0) ? lo + kNearStrips * two_s : a.n;
+      const int64_t hi = hi_raw < a.n ? hi_raw : a.n;
+      if (lo >= hi) continue;
+      __syncthreads();  // shared tiles of the previous group are free
+      near_tile(a, b, lo, hi, adj, smem_raw);
+    }
   }
 }
 
@@ -1313,6 +1318,20 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
     lc_status e = launch_vec_exponent(a, sf);
     if (e != LC_OK) return e;
   }
+  auto launch_band = [&]() -> lc_status {  // rows (columns) of kNearStrips strips per CTA
+    const size_t sm = near_smem<R>(s, int64_t(kNearStrips) * 2 * s, 0);
+    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_near<R>), sm);
+    if (e != LC_OK) return e;
+    const int64_t strips = (a.n + 2 * s - 1) / (2 * s);
+    int64_t ctas = (strips + kNearStrips - 1) / kNearStrips;
+    if (p->band_ctas > 0 && p->band_ctas < ctas) ctas = p->band_ctas;
+    lc_timer_mark(p, st, LC_K_NEAR);
+    k_near<R><<<dim3(unsigned(ctas), gy), kThreads, sm, sn>>>(a, adjoint);
+    LC_LAUNCH_CHECK();
+    if (overlap) LC_CUDA_TRY(cudaEventRecord(p->ev_near, sn));
+    return LC_OK;
+  };
+  const bool band_late = overlap && p->band_after_leaf;
   {  // first up chunk: leaf restriction and the fine levels
     const int rho = roots[0];
     const int depth = L - 1 - rho;
@@ -1323,15 +1342,13 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
     k_up_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sf>>>(a, rho, depth, 1, adjoint);
     LC_LAUNCH_CHECK();
   }
-  if (!fused) {  // band: rows (columns) of kNearStrips strips per CTA
-    const size_t sm = near_smem<R>(s, int64_t(kNearStrips) * 2 * s, 0);
-    lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_near<R>), sm);
+  if (!fused) {
+    if (band_late) {  // the band starts once the first up chunk is done
+      LC_CUDA_TRY(cudaEventRecord(p->ev_fork, sf));
+      LC_CUDA_TRY(cudaStreamWaitEvent(sn, p->ev_fork, 0));
+    }
+    lc_status e = launch_band();
     if (e != LC_OK) return e;
-    const int64_t strips = (a.n + 2 * s - 1) / (2 * s);
-    lc_timer_mark(p, st, LC_K_NEAR);
-    k_near<R><<<dim3(unsigned((strips + kNearStrips - 1) / kNearStrips), gy), kThreads, sm, sn>>>(a, adjoint);
-    LC_LAUNCH_CHECK();
-    if (overlap) LC_CUDA_TRY(cudaEventRecord(p->ev_near, sn));
   }
   if (roots[0] > 0) {
     if (coarse_side) {

@@ -174,6 +174,9 @@ struct lc_plan_s {
   cudaEvent_t ev_fork, ev_join, ev_start, ev_near, ev_done;
   // Chunk geometry of the CUDA-core tiers (lc_plan_autotune / lc_plan_set_config).
   int leaf_depth, chunk_depth;
+  // Single-vector band launch (lc_plan_set_band): CTAs of k_near (0: one per
+  // group of strips) and whether it starts after the first up chunk.
+  int band_ctas, band_after_leaf;
   // Optional per-kernel timing (lc_plan_set_timing).
   int timing_slots;
   int timing_stride;       // events per slot

@@ -49,6 +49,13 @@ lc_status lc_plan_set_config(lc_plan plan, int32_t leaf_depth, int32_t chunk_dep
   return LC_OK;
 }
 
+lc_status lc_plan_set_band(lc_plan plan, int32_t ctas, int32_t after_leaf) {
+  if (!plan || ctas < 0 || ctas > (1 << 24) || (after_leaf != 0 && after_leaf != 1)) return LC_ERR_INVALID_ARG;
+  plan->band_ctas = ctas;
+  plan->band_after_leaf = after_leaf;
+  return LC_OK;
+}
+
 lc_status lc_plan_autotune(lc_plan plan, const void* in, void* out, int64_t in_batch_stride, int64_t in_elem_stride,
                            int64_t out_batch_stride, int64_t out_elem_stride, lc_stream stream, int32_t* leaf_depth,
                            int32_t* chunk_depth, float* best_ms) {

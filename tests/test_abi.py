@@ -154,3 +154,13 @@ def test_alpha_option_validation_without_gpu():
     text = (ROOT / "include" / "legcheb.h").read_text()
     m = re.search(r"#define\s+LC_GEGENBAUER_MAX_ALPHA\s+([0-9.]+)", text)
     assert m and float(m.group(1)) == B.LC_GEGENBAUER_MAX_ALPHA
+
+
+def test_set_band_validation_without_gpu():
+    from paper_2411_00033_gb300 import binding as B
+    lib = B.load()
+    import ctypes
+    assert lib.lc_plan_set_band(None, 0, 0) == 1
+    # a plan handle is needed for the range checks; NULL is rejected before them
+    text = (ROOT / "include" / "legcheb.h").read_text()
+    assert "lc_status lc_plan_set_band(lc_plan plan, int32_t ctas, int32_t after_leaf);" in text

@@ -325,6 +325,22 @@ def test_chunk_geometry_does_not_change_results(lc, tier):
             assert np.array_equal(got_adj, plan(x, adjoint=True).cpu().numpy()), (direction, leaf, chunk)
 
 
+@pytest.mark.parametrize("tier", ["f64", "f64_df", "f32"])
+def test_band_launch_shape_does_not_change_results(lc, tier):
+    # the band's grid only changes which CTA takes which strips: bitwise-equal outputs
+    n = 300000
+    dev = torch.device("cuda", 0)
+    dt = torch.float32 if tier == "f32" else torch.float64
+    x = torch.as_tensor(workloads.decaying_vector(n, seed=15), device=dev, dtype=dt)
+    for direction in ("l2c", "c2l"):
+        plan = lc.Plan(n, direction, 1, tier, dev)
+        ref, ref_adj = plan(x).cpu().numpy(), plan(x, adjoint=True).cpu().numpy()
+        for ctas, late in ((1, False), (152, True), (457, False), (100000, True)):
+            plan.set_band(ctas, late)
+            assert np.array_equal(plan(x).cpu().numpy(), ref), (direction, ctas, late)
+            assert np.array_equal(plan(x, adjoint=True).cpu().numpy(), ref_adj), (direction, ctas, late)
+
+
 def test_autotune_picks_and_caches_a_geometry(lc):
     n = 500000
     dev = torch.device("cuda", 0)
