@@ -667,6 +667,22 @@ def run_ours(args):
         tier_vals[t] = {"coefficients_per_s": 2 * n / (statistics.median(m2) / 1e3),
                         "ms_per_step_median": statistics.median(m2), "launches_per_step": p2[0].launches() + p2[1].launches()}
 
+    # the nodal variant of the far field (eq:AijLag, the method the paper's
+    # modal one replaces) beside the modal one, plain FP64 tier: execution
+    # (same step) and planning
+    nodal = {}
+    if not args.no_batched:
+        for nd in (0, 1):
+            t0p = time.perf_counter()
+            pn = (lc.Plan(n, "l2c", 1, "f64", dev, nodal=bool(nd)), lc.Plan(n, "c2l", 1, "f64", dev, nodal=bool(nd)))
+            torch.cuda.synchronize()
+            plan_s = time.perf_counter() - t0p
+            m2, _, _ = time_tier(pn, max(10, min(50, args.steps)), 2)
+            nodal["nodal" if nd else "modal"] = {
+                "coefficients_per_s": 2 * n / (statistics.median(m2) / 1e3),
+                "ms_per_step_median": statistics.median(m2), "plan_ms_both_directions": plan_s * 1e3}
+            del pn
+
     # Gegenbauer plans (coefficients of C_j^(a) <-> Chebyshev; a = 1/2 is the
     # Legendre case above): the same vector, tier and step, with the oracle's
     # error on 256 of the sampled rows per direction
@@ -845,6 +861,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "tiers": tier_vals,
         "gegenbauer": geg,
+        "modal_vs_nodal_f64": nodal,
         "plan_ms": plan_ms,
         "stage_ms_per_step": {KIND_NAMES[k]: v / args.steps for k, v in sorted(totals.items())},
         "ms_per_step_warm_l2": sum(ms_warm) / len(ms_warm),

@@ -109,7 +109,19 @@ typedef struct {
    * LC_ERR_UNSUPPORTED.  lc_adjoint of such a plan returns
    * LC_ERR_UNSUPPORTED.  0 (default): coefficients. */
   int32_t values;
-  int32_t reserved[3];
+  /* 1: the nodal variant (eq:AijLag; the original method of Alpert and
+   * Rokhlin that the paper's modal method replaces): every far-field block is
+   * represented by the kernel's values at the M x M Chebyshev-Gauss node
+   * pairs of the block with Lagrange bases instead of 2-D Chebyshev
+   * coefficients, the leaf matrices hold the Lagrange basis at the leaf
+   * points, and the level-to-level maps of Steps 2 and 4 are the two dense
+   * M x M Lagrange interpolation matrices between a parent's and its
+   * children's nodes instead of the triangular B(0), B(1).  The same linear
+   * map to the same accuracy; planning skips the 2-D DCT, execution does
+   * dense level maps.  LC_F64 and LC_F32 only (otherwise plan creation
+   * returns LC_ERR_UNSUPPORTED).  0 (default): the modal method. */
+  int32_t nodal;
+  int32_t reserved[2];
   /* Gegenbauer parameter a of the non-Chebyshev side (Conclusions: the
    * method carries over to Gegenbauer bases).  0 (default) or 0.5: Legendre,
    * P_j = C_j^(1/2).  Otherwise -1/2 < a <= LC_GEGENBAUER_MAX_ALPHA, a != 0:
@@ -263,7 +275,10 @@ lc_status lc_plan_info(lc_plan plan, int64_t* n, int64_t* N, int32_t* L, int32_t
 
 /* Copy plan tables to host memory for inspection (synchronises `stream`):
  * which = 0: lambda[N]; 1: T[2][s][M]; 2: B(0)[M][M]; 3: A-hat[N_c][M][M]
- * (row k = expansion in the row variable X, column l in Y, eq:Aij).
+ * (row k = expansion in the row variable X, column l in Y, eq:Aij); C2L
+ * plans: 4: u[N], 5: v[N].  Nodal plans: 1 holds the Lagrange basis at the
+ * leaf points, 2 the level maps P(0), P(1) ([2][M][M]) and 3 the kernel at
+ * the node pairs of each block (eq:AijLag).
  * `count` is the capacity of dst in doubles; the number copied is returned
  * in *copied. */
 lc_status lc_plan_table(lc_plan plan, int32_t which, double* dst, int64_t count,

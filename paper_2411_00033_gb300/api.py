@@ -17,8 +17,11 @@ def _stream_ptr(device) -> int:
 
 
 def make_options(s_hat: int | None = None, fixed_s: int | None = None, slices: int | None = None,
-                 debug_flags: int | None = None, values: bool | None = None, alpha: float | None = None):
+                 debug_flags: int | None = None, values: bool | None = None, alpha: float | None = None,
+                 nodal: bool | None = None):
     o = B.lc_plan_options_default()
+    if nodal is not None:
+        o.nodal = int(bool(nodal))
     if alpha is not None:
         o.alpha = float(alpha)
     if values is not None:
@@ -45,6 +48,8 @@ class Plan:
                on those points; "c2l": Legendre coefficients from the values)
     alpha:     Gegenbauer parameter a (-1/2 < a <= 2, a != 0): the non-Chebyshev side
                holds coefficients of C_j^(a) instead of P_j = C_j^(1/2) (default: Legendre)
+    nodal:     True: the nodal (Lagrange) variant of the far field instead of the modal
+               one ("f64" and "f32" only); the same map
     """
 
     def __init__(self, n: int | None = None, direction: str = "l2c", batch: int = 1, dtype: str = "f64",
@@ -156,9 +161,10 @@ class Plan:
         return out
 
     def table(self, which: int):
-        sizes = {0: self.info["N"], 1: 2 * self.info["s"] * self.info["M"], 2: self.info["M"] ** 2,
+        sizes = {0: self.info["N"], 1: 2 * self.info["s"] * self.info["M"], 2: 2 * self.info["M"] ** 2,
                  3: self.info["n_c"] * self.info["M"] ** 2, 4: self.info["N"], 5: self.info["N"]}
         with torch.cuda.device(self.device):
+            # the table's own length when shorter (B(0): M^2; nodal P(0), P(1): 2 M^2)
             return B.lc_plan_table(self._handle, which, sizes[which], _stream_ptr(self.device))
 
     def autotune(self, x: torch.Tensor, out: torch.Tensor | None = None):

@@ -67,6 +67,9 @@ struct Args {
   unsigned* xe_cnt;
   // C2L row factor 2i + two_alpha (1 for Legendre; 2a for Gegenbauer a).
   double two_alpha;
+  // Nodal variant (eq:AijLag): t.B holds the dense level maps P(0), P(1)
+  // ([2][M][M]) instead of the triangular B(0).
+  int nodal;
 };
 
 template <typename R>
@@ -185,6 +188,15 @@ __device__ __forceinline__ bool node_valid(bool col, int gamma, int64_t x) {
   return col ? (x >= 2 && x < n) : (x >= 0 && x < n - 2);
 }
 
+// Elements of the up chunk's dynamic tiles: subtree nodes, the work array of
+// Algorithm a.1, and for the leaf chunk T and the input strip; a nodal plan
+// appends the transposed second level map P(1)^T.
+__host__ __device__ inline size_t up_words(int depth, int s, int leaf) {
+  size_t v = size_t((2 << depth) - 1) * kSeg + 2 * size_t(1 << (depth > 0 ? depth - 1 : 0)) * kSeg;
+  if (leaf) v += size_t(2) * s * LC_M + size_t(1 << depth) * 2 * s;
+  return v;
+}
+
 // Offsets (in R elements) of level d inside a subtree buffer.
 __device__ __forceinline__ int sub_off(int d) { return ((1 << d) - 1) * kSeg; }
 
@@ -221,13 +233,18 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
   R* zt = nodes + sub_off(depth + 1);                         // 2 x 2^(depth-1) segments
   R* Ts = zt + 2 * (1 << (depth > 0 ? depth - 1 : 0)) * kSeg;  // [2][s][M]
   R* fs = Ts + 2 * a.s * LC_M;                                // [2^depth][2s]
-  __shared__ R Bt[LC_M * LC_M];  // B(0) transposed: Bt[j][k] = b_kj
+  __shared__ R Bt[LC_M * LC_M];  // B(0) transposed: Bt[j][k] = b_kj (nodal: P(0) transposed)
+  R* Bt1 = nodes + up_words(depth, a.s, leaf);  // nodal: P(1) transposed
   const bool col = !adj;
   const int s = a.s;
   const int64_t x0 = blockIdx.x;
   const int gb = rho + depth;
   const int nb = 1 << depth;
-  for (int i = threadIdx.x; i < LC_M * LC_M; i += blockDim.x) Bt[(i % LC_M) * LC_M + i / LC_M] = a.t.B[i];
+  const int nB = a.nodal ? 2 : 1;
+  for (int i = threadIdx.x; i < nB * LC_M * LC_M; i += blockDim.x) {
+    const int r = i % (LC_M * LC_M);
+    (i < LC_M * LC_M ? Bt : Bt1)[(r % LC_M) * LC_M + r / LC_M] = a.t.B[i];
+  }
   if (leaf)
     for (int i = threadIdx.x; i < 2 * s * LC_M; i += blockDim.x) Ts[i] = a.t.T[i];
   for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
@@ -276,7 +293,7 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
       const int nd = 1 << d;
       const R* ch = nodes + sub_off(d + 1);
       // z0 = w(2x) + w(2x+1), z1 = w(2x) - w(2x+1)   (Algorithm a.1)
-      for (int t = threadIdx.x; t < nd * kSeg; t += blockDim.x) {
+      for (int t = threadIdx.x; t < (a.nodal ? 0 : nd * kSeg); t += blockDim.x) {
         const int j = t / kSeg, e = t % kSeg;
         const R l = ch[(2 * j) * kSeg + e], r = ch[(2 * j + 1) * kSeg + e];
         zt[t] = l + r;
@@ -292,7 +309,15 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
           // Algorithm a.1: b_kj times z0 on even k-j, z1 on odd k-j (two chains)
           const R* z0 = zt + j * kSeg + sigma * LC_M;
           const R* z1 = z0 + nd * kSeg;
-          if constexpr (eo_pairs<R>::value) {  // FP64 pipe: only the nonzero b_kj (j <= k)
+          if (a.nodal) {  // dense P(0) w(2x) + P(1) w(2x+1)
+            const R* wl = ch + (2 * j) * kSeg + sigma * LC_M;
+            const R* wr = wl + kSeg;
+#pragma unroll 6
+            for (int jj = 0; jj < LC_M; ++jj) {
+              acc = acc2(acc, Bt[jj * LC_M + k], wl[jj]);
+              acc = acc2(acc, Bt1[jj * LC_M + k], wr[jj]);
+            }
+          } else if constexpr (eo_pairs<R>::value) {  // FP64 pipe: only the nonzero b_kj (j <= k)
             for (int jj = 0; jj <= k; ++jj) acc = acc2(acc, Bt[jj * LC_M + k], ((k - jj) & 1) ? z1[jj] : z0[jj]);
           } else {
             // b_kj = 0 exactly for j > k, so all M terms, unrolled: the lanes of a
@@ -498,10 +523,8 @@ inline int64_t couple_ctas(int g_lo, int g_hi) {
 
 // Shared-memory sizes (bytes) of the chunk kernels.
 template <typename R>
-inline size_t up_smem(int depth, int s, int leaf) {
-  size_t v = size_t((2 << depth) - 1) * kSeg + 2 * size_t(1 << (depth > 0 ? depth - 1 : 0)) * kSeg;
-  if (leaf) v += size_t(2) * s * LC_M + size_t(1 << depth) * 2 * s;
-  return v * sizeof(R) + 16;
+inline size_t up_smem(int depth, int s, int leaf, int nodal) {
+  return (up_words(depth, s, leaf) + (nodal ? size_t(LC_M) * LC_M : 0)) * sizeof(R) + 16;
 }
 template <typename R>
 inline size_t down_smem(int depth, int s, int fin) {
@@ -888,12 +911,14 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
   R* nodes = reinterpret_cast<R*>(smem_raw);
   R* Ts = nodes + sub_off(depth + 1);
   __shared__ R par[kSeg];  // c of the root's parent
-  __shared__ R Bs1[eo_pairs<R>::value ? 1 : LC_M * LC_M];  // B(1): B(0) with odd diagonals negated
+  // B(1): B(0) with odd diagonals negated; nodal: the second level map P(1)
+  __shared__ R Bs1[LC_M * LC_M];
   constexpr int U = fuse ? 1 : 4;
   stage<U>(LC_M * LC_M, [&](int i) { return a.t.B[i]; }, [&](int i, R v) {
     Bs[i] = v;
-    if constexpr (!eo_pairs<R>::value) Bs1[i] = ((i / LC_M - i % LC_M) & 1) ? negate(v) : v;
+    if (!a.nodal) Bs1[i] = ((i / LC_M - i % LC_M) & 1) ? negate(v) : v;
   });
+  if (a.nodal) stage<U>(LC_M * LC_M, [&](int i) { return a.t.B[LC_M * LC_M + i]; }, [&](int i, R v) { Bs1[i] = v; });
   if (fin) stage<U>(2 * s * LC_M, [&](int i) { return a.t.T[i]; }, [&](int i, R v) { Ts[i] = v; });
   for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
     R* Cb = a.t.Cc + b * a.nseg * kSeg;
@@ -927,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
       // diagonals of B(0)^T c) and O (odd diagonals); child 2x receives E + O,
       // child 2x + 1 receives E - O -- half the multiplies.  Other types
       // (latency-bound): one thread per child entry, twice the parallelism.
-      if constexpr (eo_pairs<R>::value) {
+      if (eo_pairs<R>::value && !a.nodal) {
         for (int d = 0; d <= depth; ++d) {
           __syncthreads();
           const int gamma = rho + d;
@@ -967,7 +992,8 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
             if (gamma > 0 && node_valid(col, gamma, x) && node_valid(col, gamma - 1, x >> 1)) {
               const R* pv = (d == 0) ? (fuse ? Cb + (lc_seg_offset(gamma - 1) + (x >> 1)) * kSeg : par) + sigma * LC_M
                                      : nodes + sub_off(d - 1) + (j >> 1) * kSeg + sigma * LC_M;
-              // B(x mod 2); b_jk = 0 exactly for j < k, so all M terms, unrolled
+              // B(x mod 2) (nodal: P(x mod 2)); for B, b_jk = 0 exactly for j < k:
+              // all M terms, unrolled
               const R* Bp = (x & 1) ? Bs1 : Bs;
 #pragma unroll
               for (int jj = 0; jj < LC_M; ++jj) c = acc2(c, Bp[jj * LC_M + k], pv[jj]);
@@ -1335,7 +1361,7 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
   {  // first up chunk: leaf restriction and the fine levels
     const int rho = roots[0];
     const int depth = L - 1 - rho;
-    const size_t sm = up_smem<R>(depth, s, 1);
+    const size_t sm = up_smem<R>(depth, s, 1, a.nodal);
     lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_up_chunk<R>), sm);
     if (e != LC_OK) return e;
     lc_timer_mark(p, st, LC_K_LEAF);
@@ -1358,7 +1384,7 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
     for (int c = 1; c < nr; ++c) {  // coarse up chunks
       const int rho = roots[c];
       const int depth = roots[c - 1] - rho;
-      const size_t sm = up_smem<R>(depth, s, 0);
+      const size_t sm = up_smem<R>(depth, s, 0, a.nodal);
       lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_up_chunk<R>), sm);
       if (e != LC_OK) return e;
       lc_timer_mark(p, st, LC_K_UP);

@@ -244,6 +244,40 @@ __global__ void k_plan_B(double* __restrict__ B) {
   }
 }
 
+// Nodal variant (eq:AijLag): Lagrange basis l_k(X) of the M Chebyshev-Gauss
+// nodes X_k = cos((k+1/2) pi/M), in the second (true) barycentric form with
+// the weights of first-kind Chebyshev points, w_k = (-1)^k sin((k+1/2) pi/M);
+// a point on a node gives the Kronecker delta.
+__device__ double lc_lagrange(int k, double X) {
+  double num = 0.0, den = 0.0;
+  for (int j = 0; j < LC_M; ++j) {
+    const double d = X - cospi((j + 0.5) / LC_M);
+    const double w = ((j & 1) ? -1.0 : 1.0) * sinpi((j + 0.5) / LC_M);
+    if (d == 0.0) return j == k ? 1.0 : 0.0;
+    const double t = w / d;
+    den += t;
+    if (j == k) num = t;
+  }
+  return num / den;
+}
+// Leaf matrices of the nodal variant, T(sigma)_{mk} = l_k(-1 + (2m+sigma)/s):
+// Step 1 gives the leaf's expansion on its own Lagrange basis (the nodal w).
+__global__ void k_plan_nodal_T(int s, double* __restrict__ T) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * s * LC_M) return;
+  const int sigma = t / (s * LC_M), m = (t / LC_M) % s, k = t % LC_M;
+  T[t] = lc_lagrange(k, -1.0 + double(2 * m + sigma) / double(s));
+}
+// Level maps of the nodal variant, P(l)_{kj} = l_k((X_j + 2l - 1)/2): a
+// parent's Lagrange basis at the nodes of child l (the nodal counterpart of
+// B(l), eq:Tmap; dense).  Table [2][M][M].
+__global__ void k_plan_nodal_P(double* __restrict__ B) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * LC_M * LC_M) return;
+  const int l = t / (LC_M * LC_M), k = (t / LC_M) % LC_M, j = t % LC_M;
+  B[t] = lc_lagrange(k, 0.5 * (cospi((j + 0.5) / LC_M) + double(2 * l - 1)));
+}
+
 // cosm[k][m] = cos(k (m + 1/2) pi / M): the DCT-II matrix of eq:aklmore.
 // Row 1 holds the Chebyshev-Gauss points X_m.
 __global__ void k_plan_cos(double* __restrict__ cosm) {
@@ -285,7 +319,8 @@ __global__ void k_plan_lminus(int L, int s, int dir, lc_geg G, const double* __r
 // cos(k(M-1-m+1/2)pi/M) = (-1)^k cos(k(m+1/2)pi/M), so each 18-term sum is
 // folded into 9 terms of sums or differences.
 __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __restrict__ cosm,
-                            const double* __restrict__ lminus, double* __restrict__ Ahat, const lc_geg geg) {
+                            const double* __restrict__ lminus, double* __restrict__ Ahat, const lc_geg geg,
+                            int nodal) {
   constexpr int H = LC_M / 2;
   __shared__ double S[LC_M][LC_M];
   __shared__ double F[2][H][LC_M];  // folded rows: sums (even k) and differences (odd k)
@@ -342,6 +377,10 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
         val = lmi * S[r0][c0];  // A(x, y) = Lambda((y-x)/2) Lambda((y+x)/2)
       } else {                  // L(x, y) of eq:Lxymod, no division
         val = (2.0 * x + geg.two_alpha) * y * lmi * S[r0][c0];
+      }
+      if (nodal) {  // eq:AijLag: the samples themselves are the block's representation
+        Ahat[a * (LC_M * LC_M) + tid] = val;
+        continue;
       }
       __syncthreads();
       S[r0][c0] = val;
@@ -450,7 +489,7 @@ size_t layout(lc_plan_s* p, char* base) {
   p->lam2 = (p->dir == LC_C2L) ? c.take<double>(N) : p->lam;
   p->err = c.take<int>(64);
   p->T = c.take<double>(size_t(2) * g.s * LC_M);
-  p->B = c.take<double>(LC_M * LC_M);
+  p->B = c.take<double>(2 * LC_M * LC_M);  // B(0) (modal) or P(0), P(1) (nodal)
   // + plan scratch: the DCT matrix and the per-level Lambda((y-x)/2) tables
   p->Ahat = c.take<double>(size_t(g.nc) * LC_M * LC_M + LC_M * LC_M + size_t(2 * (g.L > 0 ? g.L : 1)) * LC_M * LC_M);
   p->W = p->Cc = nullptr;
@@ -462,7 +501,7 @@ size_t layout(lc_plan_s* p, char* base) {
     p->lamf = c.take<float>(N);
     p->lam2f = (p->dir == LC_C2L) ? c.take<float>(N) : p->lamf;
     p->Tf = c.take<float>(size_t(2) * g.s * LC_M);
-    p->Bf = c.take<float>(LC_M * LC_M);
+    p->Bf = c.take<float>(2 * LC_M * LC_M);
     p->Ahatf = c.take<float>(size_t(g.nc) * LC_M * LC_M);
     p->Wf = c.take<float>(nw);
     p->Ccf = c.take<float>(nw);
@@ -576,6 +615,8 @@ lc_status fill_plan(lc_plan_s* p, int64_t n, lc_direction dir, int64_t batch, lc
   if (p->opt.slices == 0) p->opt.slices = auto_slices(n);
   if (p->opt.values != 0 && p->opt.values != 1) return LC_ERR_INVALID_ARG;
   if (p->opt.values && (!lc_values_supported(n) || dtype == LC_F32)) return LC_ERR_UNSUPPORTED;
+  if (p->opt.nodal != 0 && p->opt.nodal != 1) return LC_ERR_INVALID_ARG;
+  if (p->opt.nodal && dtype != LC_F64 && dtype != LC_F32) return LC_ERR_UNSUPPORTED;
   st = geg_setup(p);
   if (st != LC_OK) return st;
   p->dir = dir;
@@ -598,6 +639,8 @@ lc_status fill_ragged(lc_plan_s* p, const int64_t* n, int64_t count, lc_directio
   if (p->opt.fixed_s == 0) p->opt.fixed_s = 32;  // one s shared by every member
   if (p->opt.slices != 0 && (p->opt.slices < 3 || p->opt.slices > 7)) return LC_ERR_INVALID_ARG;
   if (p->opt.values) return LC_ERR_UNSUPPORTED;  // values at Chebyshev points: uniform plans only
+  if (p->opt.nodal != 0 && p->opt.nodal != 1) return LC_ERR_INVALID_ARG;
+  if (p->opt.nodal) return LC_ERR_UNSUPPORTED;  // the nodal variant: CUDA-core tiers
   if (geg_setup(p) != LC_OK) return LC_ERR_INVALID_ARG;
   int64_t nmax = 0;
   for (int64_t i = 0; i < count; ++i) {
@@ -676,10 +719,17 @@ lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
       LC_LAUNCH_CHECK();
     }
   }
-  k_plan_T<<<1, 2 * LC_MAX_S, 0, st>>>(g.s, p->T);
-  LC_LAUNCH_CHECK();
-  k_plan_B<<<1, 32, 0, st>>>(p->B);
-  LC_LAUNCH_CHECK();
+  if (p->opt.nodal) {
+    k_plan_nodal_T<<<(2 * g.s * LC_M + 255) / 256, 256, 0, st>>>(g.s, p->T);
+    LC_LAUNCH_CHECK();
+    k_plan_nodal_P<<<(2 * LC_M * LC_M + 255) / 256, 256, 0, st>>>(p->B);
+    LC_LAUNCH_CHECK();
+  } else {
+    k_plan_T<<<1, 2 * LC_MAX_S, 0, st>>>(g.s, p->T);
+    LC_LAUNCH_CHECK();
+    k_plan_B<<<1, 32, 0, st>>>(p->B);
+    LC_LAUNCH_CHECK();
+  }
   if (g.L > 0) {
     double* cosm = p->Ahat + size_t(g.nc) * LC_M * LC_M;
     double* lminus = cosm + LC_M * LC_M;
@@ -689,14 +739,15 @@ lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
                                                                                           p->geg, cosm, lminus);
     LC_LAUNCH_CHECK();
     const int64_t blocks = g.nc < 1048576 ? g.nc : 1048576;
-    k_plan_ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat, p->geg);
+    k_plan_ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat, p->geg,
+                                                                p->opt.nodal);
     LC_LAUNCH_CHECK();
   }
   if (p->dtype == LC_F32) {
     k_d2f<<<grid_for(g.N, 256), 256, 0, st>>>(g.N, p->lam, p->lamf);
     if (p->dir == LC_C2L) k_d2f<<<grid_for(g.N, 256), 256, 0, st>>>(g.N, p->lam2, p->lam2f);
     k_d2f<<<1, 256, 0, st>>>(int64_t(2) * g.s * LC_M, p->T, p->Tf);
-    k_d2f<<<1, 256, 0, st>>>(LC_M * LC_M, p->B, p->Bf);
+    k_d2f<<<1, 256, 0, st>>>(2 * LC_M * LC_M, p->B, p->Bf);
     if (g.nc > 0)
       k_d2f_T<<<grid_for(g.nc * LC_M * LC_M, 256), 256, 0, st>>>(g.nc, p->Ahat, p->Ahatf);
     LC_LAUNCH_CHECK();
@@ -925,7 +976,7 @@ lc_status lc_plan_table(lc_plan plan, int32_t which, double* dst, int64_t count,
   switch (which) {
     case 0: src = (plan->dir == LC_C2L) ? nullptr : plan->lam; len = plan->g.N; break;
     case 1: src = plan->T; len = int64_t(2) * plan->g.s * LC_M; break;
-    case 2: src = plan->B; len = LC_M * LC_M; break;
+    case 2: src = plan->B; len = (plan->opt.nodal ? 2 : 1) * LC_M * LC_M; break;
     case 3: src = plan->Ahat; len = plan->g.nc * LC_M * LC_M; break;
     case 4: src = plan->lam; len = plan->g.N; break;   // C2L: u table
     case 5: src = plan->lam2; len = plan->g.N; break;  // C2L: v table

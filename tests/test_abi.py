@@ -164,3 +164,24 @@ def test_set_band_validation_without_gpu():
     # a plan handle is needed for the range checks; NULL is rejected before them
     text = (ROOT / "include" / "legcheb.h").read_text()
     assert "lc_status lc_plan_set_band(lc_plan plan, int32_t ctas, int32_t after_leaf);" in text
+
+
+def test_nodal_option_validation_without_gpu():
+    # the nodal variant: LC_F64 and LC_F32, uniform plans
+    from paper_2411_00033_gb300 import binding as B
+    opts = B.lc_plan_options_default()
+    assert opts.nodal == 0
+    opts.nodal = 1
+    for dt in (B.LC_F64, B.LC_F32):
+        assert B.lc_plan_workspace_size(5000, B.LC_L2C, 2, dt, opts) > 0
+    for dt in (B.LC_F64_DF, B.LC_F64_SPLIT):
+        with pytest.raises(B.LegChebError) as e:
+            B.lc_plan_workspace_size(5000, B.LC_L2C, 2, dt, opts)
+        assert e.value.status == 5
+    with pytest.raises(B.LegChebError) as e:
+        B.lc_plan_workspace_size_ragged([64, 5000], B.LC_L2C, B.LC_F64_SPLIT, opts)
+    assert e.value.status == 5
+    opts.nodal = 2
+    with pytest.raises(B.LegChebError) as e:
+        B.lc_plan_workspace_size(5000, B.LC_L2C, 1, B.LC_F64, opts)
+    assert e.value.status == 1
