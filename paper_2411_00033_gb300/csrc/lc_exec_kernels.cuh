@@ -571,7 +571,7 @@ __device__ __forceinline__ void fwd_steps(const R* __restrict__ lamk, const R* _
   const R* pf = fp + 2 * kk;
   const R* pl = lp + kk;
   int it = 0;
-#pragma unroll 2
+#pragma unroll 4
   for (; kk + 2 <= kend; kk += 2, pk += 2, pf += 4, pl += 2, ++it) {
     const R k0 = pk[0], k1 = pk[1];
     const R F1 = pf[2], F2 = pf[4];
@@ -640,7 +640,7 @@ __device__ __forceinline__ void adj_steps(const R* __restrict__ lamk, const R* _
   const R* pg = rp - 2 * kk;
   const R* pl = lp - kk;
   int it = 0;
-#pragma unroll 2
+#pragma unroll 4
   for (; kk + 2 <= kend; kk += 2, pk += 2, pg -= 4, pl -= 2, ++it) {
     const R k0 = pk[0], k1 = pk[1];
     const R G0 = pg[0], Gm = pg[-2];
