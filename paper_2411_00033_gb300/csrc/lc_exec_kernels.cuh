@@ -1198,10 +1198,20 @@ __global__ void __launch_bounds__(256) k_vec_exponent(const IO* __restrict__ in,
   for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
     const IO* f = in + lc_boff(b, ib, inner, iob);
     int m = kNoExp;
+    if (ie == 1 && j0 + kExpChunk <= n && (reinterpret_cast<uintptr_t>(f + j0) & 15) == 0 && sizeof(IO) == 8) {
+      // whole chunk, contiguous and 16-byte aligned: all loads issued first, 16 bytes each
+      const double2* p = reinterpret_cast<const double2*>(f + j0);
+      double2 v[kExpChunk / 512];
 #pragma unroll
-    for (int u = 0; u < kExpChunk / 256; ++u) {
-      const int64_t j = j0 + u * 256 + threadIdx.x;
-      if (j < n) m = max(m, exp_field(double(f[j * ie])));
+      for (int u = 0; u < kExpChunk / 512; ++u) v[u] = __ldg(p + u * 256 + threadIdx.x);
+#pragma unroll
+      for (int u = 0; u < kExpChunk / 512; ++u) m = max(m, max(exp_field(v[u].x), exp_field(v[u].y)));
+    } else {
+#pragma unroll
+      for (int u = 0; u < kExpChunk / 256; ++u) {
+        const int64_t j = j0 + u * 256 + threadIdx.x;
+        if (j < n) m = max(m, exp_field(double(f[j * ie])));
+      }
     }
     m = block_max_256(m, red);
     if (threadIdx.x == 0) {
