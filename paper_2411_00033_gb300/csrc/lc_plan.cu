@@ -318,9 +318,12 @@ __global__ void k_plan_lminus(int L, int s, int dir, lc_geg G, const double* __r
 // the same nodes, so only m <= n is evaluated; the DCT matrix satisfies
 // cos(k(M-1-m+1/2)pi/M) = (-1)^k cos(k(m+1/2)pi/M), so each 18-term sum is
 // folded into 9 terms of sums or differences.
+// GEG: Gegenbauer kernel samples (lc_geg); NODAL: keep the samples (eq:AijLag)
+// instead of their DCT.  Template flags, so that the Legendre modal
+// instantiation carries no code of the other variants.
+template <bool GEG, bool NODAL>
 __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __restrict__ cosm,
-                            const double* __restrict__ lminus, double* __restrict__ Ahat, const lc_geg geg,
-                            int nodal) {
+                            const double* __restrict__ lminus, double* __restrict__ Ahat, const lc_geg geg) {
   constexpr int H = LC_M / 2;
   __shared__ double S[LC_M][LC_M];
   __shared__ double F[2][H][LC_M];  // folded rows: sums (even k) and differences (odd k)
@@ -360,7 +363,7 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
       const double w = i0 + j0 + h * (cs[1][pm] + cs[1][pn] + 2.0);
       // L2C: Lambda((x+y)/2); C2L: 1 / ((x+y)(x+y+1) Lambda((x+y)/2))
       double lp;
-      if (geg.on)  // Gegenbauer: lambda_a((x+y)/2) or v_a((x+y)/2)
+      if constexpr (GEG)  // Gegenbauer: lambda_a((x+y)/2) or v_a((x+y)/2)
         lp = dir == LC_L2C ? lc_geg_lam(geg, 0.5 * w) : lc_geg_v(geg, 0.5 * w);
       else
         lp = dir == LC_L2C ? lc_Lambda_sample(0.5 * w) : lc_c2l_wfactor(w);
@@ -376,9 +379,9 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
       if (dir == LC_L2C) {
         val = lmi * S[r0][c0];  // A(x, y) = Lambda((y-x)/2) Lambda((y+x)/2)
       } else {                  // L(x, y) of eq:Lxymod, no division
-        val = (2.0 * x + geg.two_alpha) * y * lmi * S[r0][c0];
+        val = 2.0 * (x + (GEG ? 0.5 * geg.two_alpha : 0.5)) * y * lmi * S[r0][c0];
       }
-      if (nodal) {  // eq:AijLag: the samples themselves are the block's representation
+      if constexpr (NODAL) {  // eq:AijLag: the samples themselves are the block's representation
         Ahat[a * (LC_M * LC_M) + tid] = val;
         continue;
       }
@@ -739,8 +742,9 @@ lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
                                                                                           p->geg, cosm, lminus);
     LC_LAUNCH_CHECK();
     const int64_t blocks = g.nc < 1048576 ? g.nc : 1048576;
-    k_plan_ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat, p->geg,
-                                                                p->opt.nodal);
+    auto ahat = p->geg.on ? (p->opt.nodal ? k_plan_ahat<true, true> : k_plan_ahat<true, false>)
+                          : (p->opt.nodal ? k_plan_ahat<false, true> : k_plan_ahat<false, false>);
+    ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat, p->geg);
     LC_LAUNCH_CHECK();
   }
   if (p->dtype == LC_F32) {
