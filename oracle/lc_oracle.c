@@ -349,12 +349,17 @@ static double cospi_ratio(int64_t r, int64_t d) {
 }
 
 /* kind 0: y_m = sum_k x_k cos(pi k (2m+1) / (2n)); kind 1: y_k =
- * (2/n)/(1 + [k = 0]) sum_m x_m cos(pi k (2m+1) / (2n)). */
-int lco_dct(int kind, int64_t n, const double* x, double* y) {
+ * (2/n)/(1 + [k = 0]) sum_m x_m cos(pi k (2m+1) / (2n)).  rows == NULL: all
+ * n outputs; otherwise outputs rows[0:nrows] into y[0:nrows]. */
+int lco_dct_rows(int kind, int64_t n, const double* x, int64_t nrows, const int64_t* rows, double* y) {
   if (n < 1 || !x || !y || (kind != 0 && kind != 1)) return 1;
+  const int64_t count = rows ? nrows : n;
+  for (int64_t r = 0; rows && r < count; ++r)
+    if (rows[r] < 0 || rows[r] >= n) return 1;
   const int64_t d = 2 * n; /* angle pi q / d with q = k (2m+1) mod 2d */
 #pragma omp parallel for schedule(static)
-  for (int64_t o = 0; o < n; ++o) {
+  for (int64_t r = 0; r < count; ++r) {
+    const int64_t o = rows ? rows[r] : r;
     dd acc = dd_from(0.0);
     for (int64_t t = 0; t < n; ++t) {
       const int64_t k = kind == 0 ? t : o, m = kind == 0 ? o : t;
@@ -362,10 +367,12 @@ int lco_dct(int kind, int64_t n, const double* x, double* y) {
       acc = dd_add(acc, two_prod(x[t], cospi_ratio(q, d)));
     }
     if (kind == 1) acc = dd_mul_d(acc, (o == 0 ? 1.0 : 2.0) / (double)n);
-    y[o] = dd_to(acc);
+    y[r] = dd_to(acc);
   }
   return 0;
 }
+
+int lco_dct(int kind, int64_t n, const double* x, double* y) { return lco_dct_rows(kind, n, x, 0, NULL, y); }
 
 int lco_threads(void) {
 #ifdef _OPENMP

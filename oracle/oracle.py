@@ -56,6 +56,8 @@ def _load():
         lib.lco_apply.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, i64, ip, dp]
         lib.lco_threads.argtypes = []
         lib.lco_dct.argtypes = [ctypes.c_int, i64, dp, dp]
+        lib.lco_dct_rows.argtypes = [ctypes.c_int, i64, dp, i64, ip, dp]
+        lib.lco_dct_rows.restype = ctypes.c_int
         lib.lco_apply_geg.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, i64, dp, i64, ip, dp]
         lib.lco_entry_geg.argtypes = [ctypes.c_int, ctypes.c_double, i64, i64, i64, dp]
         lib.lco_geg_tables.argtypes = [ctypes.c_int, ctypes.c_double, i64, dp, dp]
@@ -160,13 +162,20 @@ def dense_matrix(direction: int, n: int, alpha=None):
     return m
 
 
-def dct(kind: int, x):
+def dct(kind: int, x, rows=None):
     """kind 0: v_m = sum_k x_k cos(pi k (2m+1)/(2n)) -- the Chebyshev series with
     coefficients x at the Chebyshev-Gauss points x_m = cos((m+1/2) pi/n);
-    kind 1: its inverse, (2/n)/(1+[k=0]) sum_m x_m cos(pi k (2m+1)/(2n))."""
+    kind 1: its inverse, (2/n)/(1+[k=0]) sum_m x_m cos(pi k (2m+1)/(2n)).
+    rows: optional output indices (then only those outputs, in that order)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
-    out = np.empty_like(x)
-    rc = _load().lco_dct(int(kind), x.size, _dptr(x), _dptr(out))
+    if rows is None:
+        out = np.empty_like(x)
+        rc = _load().lco_dct(int(kind), x.size, _dptr(x), _dptr(out))
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        out = np.empty(rows.size, np.float64)
+        rc = _load().lco_dct_rows(int(kind), x.size, _dptr(x), rows.size,
+                                  rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(out))
     if rc:
         raise RuntimeError("lco_dct failed (%d)" % rc)
     return out

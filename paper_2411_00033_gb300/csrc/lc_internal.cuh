@@ -157,6 +157,7 @@ struct lc_plan_s {
   // plans a [batch][n] buffer for the Chebyshev coefficients of the input.
   void* val_tables;
   double* val_scratch;
+  void* val_work;  // large n: the [batch][n] complex work array of the two FFT passes, exponents
   // Split tier data (see lc_split.cu).
   void* split;
   // Ragged members (host copies and device tables).
@@ -244,6 +245,8 @@ void lc_split_release(lc_plan p);
 // ---- values at Chebyshev points (lc_values.cu) -------------------------------
 bool lc_values_supported(int64_t n);
 size_t lc_values_table_bytes(int64_t n);
+size_t lc_values_work_bytes(int64_t n, int64_t batch);
+int lc_values_launches(const lc_plan_s* p);
 lc_status lc_values_prepare(lc_plan p, cudaStream_t st);
 lc_status lc_values_synth(lc_plan p, double* out, const lc_layout& lay, cudaStream_t st);
 lc_status lc_values_analysis(lc_plan p, const double* in, const lc_layout& lay, double* scratch, cudaStream_t st);

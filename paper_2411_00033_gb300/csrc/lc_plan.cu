@@ -527,9 +527,12 @@ size_t layout(lc_plan_s* p, char* base) {
   }
   p->val_tables = nullptr;
   p->val_scratch = nullptr;
+  p->val_work = nullptr;
   if (p->opt.values) {
     p->val_tables = c.take<char>(lc_values_table_bytes(g.n));
     if (p->dir == LC_C2L) p->val_scratch = c.take<double>(size_t(p->batch) * size_t(g.n));
+    const size_t wb = lc_values_work_bytes(g.n, p->batch);
+    if (wb) p->val_work = c.take<char>(wb);
   }
   return c.off + 256;
 }
@@ -998,7 +1001,7 @@ lc_status lc_plan_table(lc_plan plan, int32_t which, double* dst, int64_t count,
 lc_status lc_plan_launches(lc_plan plan, int32_t* launches) {
   if (!plan || !launches) return LC_ERR_INVALID_ARG;
   *launches = (plan->dtype == LC_F64_SPLIT) ? lc_exec_split_launches(plan) : lc_exec_cuda_cores_launches(plan);
-  if (plan->opt.values) *launches += 1;  // the cosine transform
+  if (plan->opt.values) *launches += lc_values_launches(plan);  // the cosine transform
   return LC_OK;
 }
 

@@ -252,3 +252,10 @@ def test_values_planted_mistakes_fail():
     ca_bad = ca.copy()
     ca_bad[0] *= 2
     assert np.abs(oracle.apply(C2L, ca_bad) - f).max() > 1e-3
+
+
+def test_dct_sampled_rows_equal_full_rows():
+    x = np.random.default_rng(410).standard_normal(700)
+    rows = np.array([0, 1, 5, 349, 698, 699], np.int64)
+    for kind in (0, 1):
+        assert np.array_equal(oracle.dct(kind, x)[rows], oracle.dct(kind, x, rows=rows))
