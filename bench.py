@@ -575,16 +575,31 @@ def run_ours(args):
             if e.status != 5:  # LC_ERR_UNSUPPORTED: tier not built for this request
                 raise
             continue
-        # plan build time (FP64 on the GPU, off the timed path; reported separately)
-        tp = []
+        # plan build time (tables on the GPU, off the timed path; reported
+        # separately): host clock around lc_plan_create on a workspace the caller
+        # has already allocated (the C ABI never allocates), plan kernels included
+        tp, tpa = [], []
         for d in ("l2c", "c2l"):
+            code = lc.LC_L2C if d == "l2c" else lc.LC_C2L
+            tcode = {"f64": lc.LC_F64, "f64_df": lc.LC_F64_DF}[t]
+            nbytes = lc.binding.lc_plan_workspace_size(n, code, 1, tcode)
+            ws_t = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            sp = torch.cuda.current_stream(dev).cuda_stream
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = lc.binding.lc_plan_create(n, code, 1, tcode, ws_t.data_ptr(), nbytes, sp)
+            torch.cuda.synchronize()
+            tp.append((time.perf_counter() - t0) * 1e3)
+            lc.binding.lc_destroy(h)
+            del ws_t
+            # the same through the Python Plan, workspace allocation included
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             tmp = lc.Plan(n, d, 1, t, dev)
             torch.cuda.synchronize()
-            tp.append((time.perf_counter() - t0) * 1e3)
+            tpa.append((time.perf_counter() - t0) * 1e3)
             del tmp
-        plan_ms[t] = {"l2c": tp[0], "c2l": tp[1]}
+        plan_ms[t] = {"l2c": tp[0], "c2l": tp[1], "with_workspace_allocation": {"l2c": tpa[0], "c2l": tpa[1]}}
         # plan setup includes the autotuner's choice of chunk geometry (untimed, like planning)
         tuned[t] = [list(p.autotune(x, out=outs[0])[:2]) for p in tiers[t]]
 

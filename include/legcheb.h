@@ -123,7 +123,13 @@ typedef struct {
    * dense level maps.  LC_F64 and LC_F32 only (otherwise plan creation
    * returns LC_ERR_UNSUPPORTED).  0 (default): the modal method. */
   int32_t nodal;
-  int32_t reserved[2];
+  /* LC_F64_DF: 1 builds the tier's double-float A-hat by converting the FP64
+   * plan's (eq:aklmore on the FP64 pipe); 0 (default) computes it in
+   * double-float arithmetic on the FP32 pipe, about 10x faster on GB300,
+   * for Legendre plans with s >= 10 (others always take the FP64 route).
+   * The entries agree to a few units of 2^-48 of their matrix. */
+  int32_t fp64_plan;
+  int32_t reserved[1];
   /* Gegenbauer parameter a of the non-Chebyshev side (Conclusions: the
    * method carries over to Gegenbauer bases).  0 (default) or 0.5: Legendre,
    * P_j = C_j^(1/2).  Otherwise -1/2 < a <= LC_GEGENBAUER_MAX_ALPHA, a != 0:
@@ -280,7 +286,12 @@ lc_status lc_plan_info(lc_plan plan, int64_t* n, int64_t* N, int32_t* L, int32_t
  * (row k = expansion in the row variable X, column l in Y, eq:Aij); C2L
  * plans: 4: u[N], 5: v[N].  Nodal plans: 1 holds the Lagrange basis at the
  * leaf points, 2 the level maps P(0), P(1) ([2][M][M]) and 3 the kernel at
- * the node pairs of each block (eq:AijLag).
+ * the node pairs of each block (eq:AijLag).  LC_F64_DF plans: 6 copies the
+ * compact double-float A-hat as raw FP32 words, two per double of dst
+ * (N_c matrices of 436 (L2C) or 484 (C2L) words: the leading words of all
+ * entries row-major, then the trailing words of the entries with
+ * k + l <= 13 (L2C) or 16 (C2L), row by row); 3 returns LC_ERR_UNSUPPORTED
+ * when that copy was built without the FP64 table (lc_plan_options.fp64_plan).
  * `count` is the capacity of dst in doubles; the number copied is returned
  * in *copied. */
 lc_status lc_plan_table(lc_plan plan, int32_t which, double* dst, int64_t count,

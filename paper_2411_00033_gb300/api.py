@@ -18,8 +18,10 @@ def _stream_ptr(device) -> int:
 
 def make_options(s_hat: int | None = None, fixed_s: int | None = None, slices: int | None = None,
                  debug_flags: int | None = None, values: bool | None = None, alpha: float | None = None,
-                 nodal: bool | None = None):
+                 nodal: bool | None = None, fp64_plan: bool | None = None):
     o = B.lc_plan_options_default()
+    if fp64_plan is not None:
+        o.fp64_plan = int(bool(fp64_plan))
     if nodal is not None:
         o.nodal = int(bool(nodal))
     if alpha is not None:
@@ -162,7 +164,8 @@ class Plan:
 
     def table(self, which: int):
         sizes = {0: self.info["N"], 1: 2 * self.info["s"] * self.info["M"], 2: 2 * self.info["M"] ** 2,
-                 3: self.info["n_c"] * self.info["M"] ** 2, 4: self.info["N"], 5: self.info["N"]}
+                 3: self.info["n_c"] * self.info["M"] ** 2, 4: self.info["N"], 5: self.info["N"],
+                 6: self.info["n_c"] * 484 // 2}
         with torch.cuda.device(self.device):
             # the table's own length when shorter (B(0): M^2; nodal P(0), P(1): 2 M^2)
             return B.lc_plan_table(self._handle, which, sizes[which], _stream_ptr(self.device))

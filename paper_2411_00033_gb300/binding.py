@@ -42,7 +42,7 @@ class LegChebError(RuntimeError):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("s_hat", ctypes.c_int32), ("fixed_s", ctypes.c_int32), ("slices", ctypes.c_int32),
-                ("debug_flags", ctypes.c_int32), ("values", ctypes.c_int32), ("nodal", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+                ("debug_flags", ctypes.c_int32), ("values", ctypes.c_int32), ("nodal", ctypes.c_int32), ("fp64_plan", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
                 ("alpha", ctypes.c_double)]
 
 

@@ -146,6 +146,7 @@ struct lc_plan_s {
   void* df_T;
   void* df_B;
   void* df_Ahat;
+  int df_ahat_direct;  // df_Ahat built by the double-float plan kernel (no FP64 A-hat)
   void* df_W;
   void* df_Cc;
   // Per-vector exponents of the double-float tier and the pre-pass's

@@ -19,6 +19,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include "lc_df.cuh"
 #include "lc_internal.cuh"
 
 // ------------------------------------------------------------------ Lambda --
@@ -418,6 +419,169 @@ __global__ void k_plan_ahat(int L, int s, int dir, int64_t nc, const double* __r
   }
 }
 
+// ------------------------------------------------- double-float A-hat --
+// A-hat for the double-float tier, computed in double-float on the FP32 pipe
+// (GB300's FP64 pipe runs at about 1/64 of its FP32 rate) and written straight
+// into the compact layout of lc_internal.cuh: the samples and the folded 2-D
+// DCT of k_plan_ahat, each operation a double-float one.  Legendre modal
+// plans with s >= 10, where every sample has z = (x+y)/2 >= 2s >= 20 (the tau
+// series needs no argument shift).  The entries agree with the FP64 plan's to
+// a few units of 2^-48 of their matrix (tested).
+__device__ __forceinline__ lc_df df_c(double x) { return lc_df_from_double(x); }
+// 1/sqrt(y): FP32 estimate and two Newton steps r += r (1 - y r^2) / 2 in
+// double-float (the relative error e goes to 1.5 e^2 per step: 2^-22 ->
+// 2^-43 -> below the double-float rounding level; one step from an FP32-exact
+// start would stop at 2e-14).
+__device__ __forceinline__ lc_df df_rsqrt(const lc_df& y) {
+  lc_df r(rsqrtf(y.hi), 0.0f);
+  for (int it = 0; it < 2; ++it) {
+    const lc_df e = lc_df(1.0f, 0.0f) - y * (r * r);
+    r = r + lc_df(0.5f * r.hi, 0.5f * r.lo) * e;
+  }
+  return r;
+}
+// Lambda(z) (L2C) or 1/(w(w+1) Lambda(w/2)) with w = 2z (C2L), z >= 20: the
+// series of lc_Lambda_sample / lc_c2l_wfactor in double-float.
+__device__ __forceinline__ lc_df df_sample(int dir, const lc_df& z) {
+  const lc_df y = z + lc_df(0.25f, 0.0f);
+  const lc_df r = df_rsqrt(y);
+  const lc_df r2 = r * r;
+  const lc_df x = r2 * r2;
+  const float zf = z.hi;
+  lc_df q;
+  if (dir == LC_L2C) {  // tau coefficients 1, -1/64, 21/8192, -671/524288, 180323/134217728 (exact in FP32)
+    if (zf > 1844.0f) q = lc_df(-1.0f / 64.0f, 0.0f);
+    else if (zf > 134.0f) q = lc_df(-1.0f / 64.0f, 0.0f) + x * lc_df(21.0f / 8192.0f, 0.0f);
+    else if (zf > 40.0f)
+      q = lc_df(-1.0f / 64.0f, 0.0f) + x * (lc_df(21.0f / 8192.0f, 0.0f) + x * lc_df(-671.0f / 524288.0f, 0.0f));
+    else
+      q = lc_df(-1.0f / 64.0f, 0.0f) +
+          x * (lc_df(21.0f / 8192.0f, 0.0f) +
+               x * (lc_df(-671.0f / 524288.0f, 0.0f) + x * lc_df(180323.0f / 134217728.0f, 0.0f)));
+    return (lc_df(1.0f, 0.0f) + x * q) * r;
+  }
+  // Q(x) coefficients 1, 5/64, 21/8192, 715/524288, -162877/134217728 (exact in FP32)
+  if (zf > 1844.0f) q = lc_df(5.0f / 64.0f, 0.0f);
+  else if (zf > 134.0f) q = lc_df(5.0f / 64.0f, 0.0f) + x * lc_df(21.0f / 8192.0f, 0.0f);
+  else if (zf > 40.0f)
+    q = lc_df(5.0f / 64.0f, 0.0f) + x * (lc_df(21.0f / 8192.0f, 0.0f) + x * lc_df(715.0f / 524288.0f, 0.0f));
+  else
+    q = lc_df(5.0f / 64.0f, 0.0f) +
+        x * (lc_df(21.0f / 8192.0f, 0.0f) +
+             x * (lc_df(715.0f / 524288.0f, 0.0f) + x * lc_df(-162877.0f / 134217728.0f, 0.0f)));
+  return lc_df(0.25f, 0.0f) * r2 * r * (lc_df(1.0f, 0.0f) + x * q);
+}
+
+// The per-level Lambda^- tables (k_plan_lminus) as double-float.
+__global__ void k_plan_lminus_df(int count, const double* __restrict__ lminus, lc_df* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) out[t] = df_c(lminus[t]);
+}
+
+__global__ void k_plan_ahat_df(int L, int s, int dir, int64_t nc, const double* __restrict__ cosm,
+                               const lc_df* __restrict__ lminus, float* __restrict__ Af) {
+  constexpr int H = LC_M / 2;
+  __shared__ lc_df S[LC_M][LC_M];
+  __shared__ lc_df F[2][H][LC_M];
+  __shared__ lc_df Tm[LC_M][LC_M];
+  __shared__ lc_df G[2][LC_M][H];
+  __shared__ lc_df cs[LC_M][LC_M];
+  __shared__ lc_df blk[3];  // h, i0, j0 of the current submatrix
+  __shared__ int blk_lm;    // its Lambda^- table
+  const int tid = threadIdx.x;
+  const int r0 = tid / LC_M, c0 = tid % LC_M;
+  cs[r0][c0] = df_c(cosm[tid]);
+  int gamma = 0;  // thread 0: the level of submatrix a (a only grows)
+  const int head = lc_dfa_head(dir), words = lc_dfa_words(dir);
+  const int used = LC_M * LC_M + lc_dfa_rowstart(head + 1, head);
+  constexpr int kPairs = LC_M * (LC_M + 1) / 2;
+  int pm = 0, pn = 0;
+  if (tid < kPairs) {
+    int rest = tid;
+    while (rest >= LC_M - pm) {
+      rest -= LC_M - pm;
+      ++pm;
+    }
+    pn = pm + rest;
+  }
+  // the scale 4/(c_k c_l M^2) of eq:aklmore
+  const lc_df wkl = df_c(4.0 / (double(LC_M) * double(LC_M)) * (r0 == 0 ? 0.5 : 1.0) * (c0 == 0 ? 0.5 : 1.0));
+  for (int64_t a = blockIdx.x; a < nc; a += gridDim.x) {
+    __syncthreads();  // the previous submatrix is done with the shared tiles
+    if (tid == 0) {   // the submatrix's position, once per CTA (64-bit work, conversions)
+      while (gamma + 1 < L && a >= lc_ahat_offset(gamma + 1)) ++gamma;
+      const int64_t rem = a - lc_ahat_offset(gamma);
+      const int64_t b = rem / 3;
+      const int r = int(rem % 3);
+      const int p = (r == 2) ? 1 : 0;
+      const int q = (r == 0) ? 0 : 1;
+      const int64_t hi = int64_t(s) << (L - gamma - 1);
+      blk[0] = lc_df(hi);
+      blk[1] = lc_df(2 * hi * (2 * b + p));
+      blk[2] = lc_df(2 * hi * (2 * b + q + 2));
+      blk_lm = (gamma * 2 + (r == 1 ? 1 : 0)) * (LC_M * LC_M);
+    }
+    __syncthreads();
+    const lc_df h = blk[0], i0 = blk[1], j0 = blk[2];
+    const lc_df* lm = lminus + blk_lm;
+    if (tid < kPairs) {  // symmetric in (m, n): w = x_m + y_n
+      const lc_df w = i0 + j0 + h * (cs[1][pm] + cs[1][pn] + lc_df(2.0f, 0.0f));
+      const lc_df z = lc_df(0.5f * w.hi, 0.5f * w.lo);
+      const lc_df v = df_sample(dir, z);
+      S[pm][pn] = v;
+      S[pn][pm] = v;
+    }
+    __syncthreads();
+    {
+      const lc_df lmi = lm[tid];
+      lc_df val;
+      if (dir == LC_L2C) {
+        val = lmi * S[r0][c0];
+      } else {
+        const lc_df x = i0 + h * (cs[1][r0] + lc_df(1.0f, 0.0f));
+        const lc_df y = j0 + h * (cs[1][c0] + lc_df(1.0f, 0.0f));
+        const lc_df x2 = x + x + lc_df(1.0f, 0.0f);  // 2 (x + 1/2)
+        val = x2 * y * lmi * S[r0][c0];
+      }
+      __syncthreads();
+      S[r0][c0] = val;
+    }
+    __syncthreads();
+    if (tid < 2 * H * LC_M) {  // fold the row variable
+      const int e = tid / (H * LC_M), mm = (tid / LC_M) % H, n = tid % LC_M;
+      const lc_df u = S[mm][n], v = S[LC_M - 1 - mm][n];
+      F[e][mm][n] = e ? u - v : u + v;
+    }
+    __syncthreads();
+    {
+      lc_df acc(0.0f, 0.0f);
+      const int e = r0 & 1;
+#pragma unroll
+      for (int mm = 0; mm < H; ++mm) acc = fma(cs[r0][mm], F[e][mm][c0], acc);
+      Tm[r0][c0] = acc;
+    }
+    __syncthreads();
+    {
+      const int e = tid / (LC_M * H), rr = (tid / H) % LC_M, nn = tid % H;
+      const lc_df u = Tm[rr][nn], v = Tm[rr][LC_M - 1 - nn];
+      G[e][rr][nn] = e ? u - v : u + v;
+    }
+    __syncthreads();
+    {
+      const int e = c0 & 1;
+      lc_df acc(0.0f, 0.0f);
+#pragma unroll
+      for (int nn = 0; nn < H; ++nn) acc = fma(G[e][r0][nn], cs[c0][nn], acc);
+      acc = acc * wkl;
+      const lc_df v = lc_df_two_sum(acc.hi, acc.lo);  // normalised: |lo| <= ulp(hi)/2
+      float* d = Af + a * words;
+      d[tid] = v.hi;
+      if (r0 + c0 <= head) d[LC_M * LC_M + lc_dfa_rowstart(r0, head) + c0] = v.lo;
+      if (tid < words - used) d[used + tid] = 0.0f;
+    }
+  }
+}
+
 // FP32 copy of A-hat, stored transposed per matrix: [m][l][k].
 __global__ void k_d2f_T(int64_t nm, const double* __restrict__ a, float* __restrict__ b) {
   const int64_t total = nm * LC_M * LC_M;
@@ -623,6 +787,7 @@ lc_status fill_plan(lc_plan_s* p, int64_t n, lc_direction dir, int64_t batch, lc
   if (p->opt.values && (!lc_values_supported(n) || dtype == LC_F32)) return LC_ERR_UNSUPPORTED;
   if (p->opt.nodal != 0 && p->opt.nodal != 1) return LC_ERR_INVALID_ARG;
   if (p->opt.nodal && dtype != LC_F64 && dtype != LC_F32) return LC_ERR_UNSUPPORTED;
+  if (p->opt.fp64_plan != 0 && p->opt.fp64_plan != 1) return LC_ERR_INVALID_ARG;
   st = geg_setup(p);
   if (st != LC_OK) return st;
   p->dir = dir;
@@ -710,6 +875,14 @@ int grid_for(int64_t work, int threads) {
   return int(b);
 }
 
+// The double-float tier builds its compact A-hat in double-float arithmetic
+// (k_plan_ahat_df) unless the plan asks for the FP64 plan or needs what only
+// the FP64 kernel has (Gegenbauer samples; leaf sizes below 10, whose finest
+// samples need the argument shift).
+bool df_plan(const lc_plan_s* p) {
+  return p->dtype == LC_F64_DF && !p->opt.fp64_plan && !p->geg.on && !p->opt.nodal && p->g.s >= 10;
+}
+
 lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
   const lc_geom& g = p->g;
   LC_CUDA_TRY(cudaMemsetAsync(p->err, 0, 64 * sizeof(int), st));
@@ -745,9 +918,20 @@ lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
                                                                                           p->geg, cosm, lminus);
     LC_LAUNCH_CHECK();
     const int64_t blocks = g.nc < 1048576 ? g.nc : 1048576;
-    auto ahat = p->geg.on ? (p->opt.nodal ? k_plan_ahat<true, true> : k_plan_ahat<true, false>)
-                          : (p->opt.nodal ? k_plan_ahat<false, true> : k_plan_ahat<false, false>);
-    ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat, p->geg);
+    if (df_plan(p)) {  // the double-float tier's compact A-hat, built on the FP32 pipe
+      p->df_ahat_direct = 1;
+      // the double-float Lambda^- tables go where the FP64 A-hat would be
+      lc_df* lm_df = reinterpret_cast<lc_df*>(p->Ahat);
+      const int cnt = g.L * 2 * LC_M * LC_M;
+      k_plan_lminus_df<<<(cnt + 255) / 256, 256, 0, st>>>(cnt, lminus, lm_df);
+      LC_LAUNCH_CHECK();
+      k_plan_ahat_df<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lm_df,
+                                                          static_cast<float*>(p->df_Ahat));
+    } else {
+      auto ahat = p->geg.on ? (p->opt.nodal ? k_plan_ahat<true, true> : k_plan_ahat<true, false>)
+                            : (p->opt.nodal ? k_plan_ahat<false, true> : k_plan_ahat<false, false>);
+      ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat, p->geg);
+    }
     LC_LAUNCH_CHECK();
   }
   if (p->dtype == LC_F32) {
@@ -984,9 +1168,17 @@ lc_status lc_plan_table(lc_plan plan, int32_t which, double* dst, int64_t count,
     case 0: src = (plan->dir == LC_C2L) ? nullptr : plan->lam; len = plan->g.N; break;
     case 1: src = plan->T; len = int64_t(2) * plan->g.s * LC_M; break;
     case 2: src = plan->B; len = (plan->opt.nodal ? 2 : 1) * LC_M * LC_M; break;
-    case 3: src = plan->Ahat; len = plan->g.nc * LC_M * LC_M; break;
+    case 3:  // not built when the double-float tier makes its compact copy directly
+      src = df_plan(plan) ? nullptr : plan->Ahat;
+      len = plan->g.nc * LC_M * LC_M;
+      break;
     case 4: src = plan->lam; len = plan->g.N; break;   // C2L: u table
     case 5: src = plan->lam2; len = plan->g.N; break;  // C2L: v table
+    case 6:  // raw FP32 words of the compact double-float A-hat, two per double
+      if (plan->dtype != LC_F64_DF) return LC_ERR_UNSUPPORTED;
+      src = static_cast<const double*>(plan->df_Ahat);
+      len = plan->g.nc * lc_dfa_words(plan->dir) / 2;
+      break;
     default: return LC_ERR_INVALID_ARG;
   }
   if (!src) return LC_ERR_UNSUPPORTED;

@@ -191,3 +191,36 @@ def test_ahat_tail_below_compact_head_every_leaf_size(lc, s, direction, head):
     assert (peak > 0).all()
     worst = (Ah[:, tail].max(axis=1) / peak).max()
     assert worst <= (4e-9 if s == 4 else 2e-9), (s, worst)
+
+
+def _compact_values(words, nc, direction):
+    """Entries of the compact double-float A-hat (raw FP32 words): hi + lo where a
+    trailing word is kept (k + l <= head), hi alone elsewhere."""
+    head, per = (13, 436) if direction == "l2c" else (16, 484)
+    w = words.view(np.float32)[: nc * per].reshape(nc, per).astype(np.float64)
+    out = w[:, : M * M].reshape(nc, M, M).copy()
+    pos = M * M
+    for k in range(head + 1):
+        cnt = head + 1 - k
+        out[:, k, :cnt] += w[:, pos:pos + cnt]
+        pos += cnt
+    return out
+
+
+@pytest.mark.parametrize("direction", ["l2c", "c2l"])
+@pytest.mark.parametrize("n", [3000, 65536, 1000000])
+def test_double_float_plan_matches_fp64_plan(lc, n, direction):
+    # the double-float tier's compact A-hat built in double-float arithmetic
+    # (default) against the one converted from the FP64 plan (fp64_plan=1):
+    # within a few units of 2^-48 (3.6e-15) of each matrix's largest entry
+    dev = torch.device("cuda", 0)
+    fast = lc.Plan(n, direction, 1, "f64_df", dev)
+    ref = lc.Plan(n, direction, 1, "f64_df", dev, fp64_plan=True)
+    nc = fast.info["n_c"]
+    a = _compact_values(fast.table(6), nc, direction)
+    b = _compact_values(ref.table(6), nc, direction)
+    peak = np.abs(b).reshape(nc, -1).max(axis=1)
+    err = (np.abs(a - b).reshape(nc, -1).max(axis=1) / peak).max()
+    assert err <= 2e-14, (n, direction, err)
+    with pytest.raises(lc.LegChebError):
+        fast.table(3)  # no FP64 A-hat behind the fast plan
