@@ -699,12 +699,11 @@ def run_ours(args):
             del pn
 
     # values at the Chebyshev points (option values): Legendre synthesis on the
-    # n = 2^20 Chebyshev-Gauss points and its inverse, double-float tier; the
-    # same step shape (synthesis and analysis on two streams); the cosine
-    # pass checked against the oracle's direct sums on 256 sampled points
+    # n = 2^20 and n = 1e6 Chebyshev-Gauss points and its inverse, the chosen
+    # tier; the same step shape (synthesis and analysis on two streams); the
+    # cosine pass checked against the oracle's direct sums on 256 sampled points
     values_leg = {}
-    if not args.no_batched:
-        nv = 1 << 20
+    for nv in ((1 << 20, n) if not args.no_batched else ()):
         xv = torch.from_numpy(workloads.decaying_vector(nv, seed=1, r=1.0)).to(dev)
         pv = (lc.Plan(nv, "l2c", 1, chosen, dev, values=True), lc.Plan(nv, "c2l", 1, chosen, dev, values=True))
         ov = [torch.empty_like(xv), torch.empty_like(xv)]
@@ -717,15 +716,18 @@ def run_ours(args):
                 pv[1](xv, out=ov[1])
             cur.wait_stream(s2)
         mv = time_fn(vstep, flush, max(10, min(50, args.steps)), 3)
-        values_leg = {"n": nv, "coefficients_per_s": 2 * nv / (mv / 1e3), "ms_per_step": mv, "tier": chosen,
-                      "launches_per_step": pv[0].launches() + pv[1].launches()}
+        rec = {"coefficients_per_s": 2 * nv / (mv / 1e3), "ms_per_step": mv, "tier": chosen,
+               "launches_per_step": pv[0].launches() + pv[1].launches(),
+               "fft": "four-step, length n" if nv & (nv - 1) == 0 else "Bluestein, two FFTs of length 2^%d"
+               % (2 * nv - 1).bit_length()}
         if rank == 0 and not args.no_cpu:
             import oracle
             c = lc.Plan(nv, "l2c", 1, chosen, dev)(xv).cpu().numpy()
             rows = workloads.sample_rows(nv, 256)
             ref = oracle.dct(0, c, rows=rows)
             got = ov[0].cpu().numpy()[rows]
-            values_leg["cosine_pass_E2_vs_oracle_256_points"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            rec["cosine_pass_E2_vs_oracle_256_points"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        values_leg["n=%d" % nv] = rec
         del pv, ov, xv
 
     # Gegenbauer plans (coefficients of C_j^(a) <-> Chebyshev; a = 1/2 is the
@@ -924,7 +926,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "tiers": tier_vals,
         "gegenbauer": geg,
-        "values_n1048576": values_leg,
+        "values_at_chebyshev_points": values_leg,
         "modal_vs_nodal_f64": nodal,
         "plan_ms": plan_ms,
         "stage_ms_per_step": {KIND_NAMES[k]: v / args.steps for k, v in sorted(totals.items())},

@@ -104,9 +104,11 @@ typedef struct {
    * p = sum_j in_j P_j (Legendre synthesis on Chebyshev points); LC_C2L takes
    * in_m = p(x_m) and gives the Legendre coefficients of the degree < n
    * polynomial through those values.  The cosine transforms are FFTs of
-   * length n: one CTA per vector up to n = 4096, two passes through a work
-   * array in the plan's workspace above.  n must be a power of two with
-   * 2 <= n <= LC_VALUES_MAX_N, the tier LC_F64, LC_F64_DF or LC_F64_SPLIT,
+   * length n: for powers of two, one CTA per vector up to n = 4096 and two
+   * passes through a work array in the plan's workspace above; for other n,
+   * Bluestein's chirp convolution through FFTs of the next power of two
+   * m >= 2n - 1.  n must satisfy 2 <= n <= LC_VALUES_MAX_N (powers of two) or
+   * 2 <= n <= LC_VALUES_MAX_N_ANY (others), the tier LC_F64, LC_F64_DF or LC_F64_SPLIT,
    * the plan uniform (not ragged); otherwise plan creation returns
    * LC_ERR_UNSUPPORTED.  lc_adjoint of such a plan returns
    * LC_ERR_UNSUPPORTED.  0 (default): coefficients. */
@@ -145,6 +147,7 @@ typedef struct {
 } lc_plan_options;
 #define LC_GEGENBAUER_MAX_ALPHA 2.0
 #define LC_VALUES_MAX_N 4194304
+#define LC_VALUES_MAX_N_ANY 2097152
 
 /* Fill *opt with the defaults above.  Returns LC_ERR_INVALID_ARG for NULL. */
 lc_status lc_plan_options_default(lc_plan_options* opt);

@@ -16,6 +16,8 @@ LC_L2C, LC_C2L = 0, 1
 LC_STATIC_MAX_N = 16384
 #: largest n of a plan with values at Chebyshev points (LC_VALUES_MAX_N)
 LC_VALUES_MAX_N = 4194304
+#: largest n that is not a power of two of a plan with values at Chebyshev points
+LC_VALUES_MAX_N_ANY = 2097152
 #: largest Gegenbauer parameter a of a plan (LC_GEGENBAUER_MAX_ALPHA)
 LC_GEGENBAUER_MAX_ALPHA = 2.0
 LC_F64, LC_F64_SPLIT, LC_F32, LC_F64_DF = 0, 1, 2, 3

@@ -379,20 +379,220 @@ __global__ void __launch_bounds__(256) k_vana_rows(int n, int n1, int n2, int lo
   }
 }
 
+// --------------------------------------------------- other lengths n
+// For n not a power of two the FFT of length n is Bluestein's: with
+// zeta = exp(i pi / n) and jk = (j^2 + k^2 - (j-k)^2)/2,
+//   sum_k a_k exp(+-2 pi i jk/n) = zeta^(+-j^2) sum_k (a_k zeta^(+-k^2)) zeta^(-+(j-k)^2),
+// a convolution, computed as a circular one of power-of-two length m >= 2n-1
+// by two FFTs of length m (four-step, through the work arrays) and the
+// pointwise product with the FFT of the chirp sequence, made at plan time.
+// chirp[t] = zeta^(t^2), the angle reduced exactly (t^2 mod 2n) in integers.
+int64_t blu_m(int64_t n) {
+  int64_t m = 256;
+  while (m < 2 * n - 1) m <<= 1;
+  return m;
+}
+__global__ void k_blu_tables(int n, int m, cdf* __restrict__ twm, cd* __restrict__ twm64, cdf* __restrict__ sh,
+                             cd* __restrict__ sh64, cdf* __restrict__ ch, cd* __restrict__ ch64) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m / 2 || t < n; t += gridDim.x * blockDim.x) {
+    if (t < m / 2) {
+      const double c = cospi(2.0 * t / m), si = -sinpi(2.0 * t / m);
+      twm[t] = cdf{df_of(c), df_of(si)};
+      twm64[t] = cd{c, si};
+    }
+    if (t < n) {
+      const double c = cospi(0.5 * t / n), si = sinpi(0.5 * t / n);
+      sh[t] = cdf{df_of(c), df_of(si)};
+      sh64[t] = cd{c, si};
+      const int64_t q = (int64_t(t) * t) % (2 * int64_t(n));  // zeta^(t^2) = exp(i pi q / n)
+      const double cc = cospi(double(q) / n), ss = sinpi(double(q) / n);
+      ch[t] = cdf{df_of(cc), df_of(ss)};
+      ch64[t] = cd{cc, ss};
+    }
+  }
+}
+// The chirp sequence of the synthesis's convolution, b_t = zeta^(-t^2) for
+// |t| < n, placed circularly in [0, m) (FP64).
+__global__ void k_blu_bc(int n, int m, const cd* __restrict__ ch64, cd* __restrict__ bc) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+    const int u = t < n ? t : (m - t < n ? m - t : -1);
+    bc[t] = u < 0 ? cd{0.0, 0.0} : cd{ch64[u].re, -ch64[u].im};
+  }
+}
+__global__ void k_d2df_c(int count, const cd* __restrict__ a, cdf* __restrict__ b) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x)
+    b[t] = cdf{df_of(a[t].re), df_of(a[t].im)};
+}
+
+// FFT of length m (four-step) over work arrays in natural order: the column
+// pass reads src[b][m], runs the m2-point FFTs over k2, applies the
+// twiddles and writes rows j2 of T[b][m2][m1].
+template <typename C>
+__global__ void __launch_bounds__(256) k_cf_cols(int m, int m1, int m2, int logm2, int64_t batch,
+                                                const C* __restrict__ src, C* __restrict__ T,
+                                                const C* __restrict__ tw, int inverse) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* x = reinterpret_cast<C*>(smem);  // [kTW][m2]
+  const int c0 = blockIdx.x * kTW;
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+    const C* sb = src + b * int64_t(m);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kTW * m2; idx += blockDim.x) {
+      const int tc = idx & (kTW - 1), k2 = idx / kTW;
+      x[tc * m2 + bitrev(k2, logm2)] = sb[c0 + tc + int64_t(m1) * k2];
+    }
+    __syncthreads();
+    fft_multi(x, kTW, m2, logm2, tw, m / m2, inverse);
+    C* Tb = T + b * int64_t(m);
+    for (int idx = threadIdx.x; idx < kTW * m2; idx += blockDim.x) {
+      const int tc = idx & (kTW - 1), j2 = idx / kTW;
+      const int k1 = c0 + tc;
+      C w = tw_full(tw, int64_t(j2) * k1, m / 2);
+      if (inverse) conj_inplace(w);
+      Tb[int64_t(j2) * m1 + k1] = cmul(w, x[tc * m2 + j2]);
+    }
+  }
+}
+
+// Row pass: the m1-point FFT of row j2, then, for the outputs j = j2 + m2 j1,
+// mode 0: dst[b][j] = y * Bh[j] (the convolution's pointwise product; conj_b:
+// the analysis's filter conj(Bh[(m - j) mod m])); mode 1: dst[b][j] = y (the
+// plan-time FFT of the chirp sequence).
+template <typename C>
+__global__ void __launch_bounds__(256) k_cf_rows(int m, int m1, int m2, int logm1, int64_t batch,
+                                                const C* __restrict__ T, C* __restrict__ dst,
+                                                const C* __restrict__ tw, int inverse, int mode,
+                                                const C* __restrict__ Bh, int conj_b) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* x = reinterpret_cast<C*>(smem);  // [m1]
+  const int j2 = blockIdx.x;
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+    const C* row = T + b * int64_t(m) + int64_t(j2) * m1;
+    __syncthreads();
+    for (int k1 = threadIdx.x; k1 < m1; k1 += blockDim.x) x[bitrev(k1, logm1)] = row[k1];
+    __syncthreads();
+    fft_multi(x, 1, m1, logm1, tw, m / m1, inverse);
+    C* db = dst + b * int64_t(m);
+    for (int j1 = threadIdx.x; j1 < m1; j1 += blockDim.x) {
+      const int64_t j = j2 + int64_t(m2) * j1;
+      C y = x[j1];
+      if (mode == 0) {
+        C f = conj_b ? Bh[(m - j) & (m - 1)] : Bh[j];
+        if (conj_b) conj_inplace(f);
+        y = cmul(y, f);
+      }
+      db[j] = y;
+    }
+  }
+}
+
+// Synthesis, Bluestein input: a_k = Y_k chirp[k] (k < n; 0 up to m), Y_k from
+// the coefficients as in k_values_synth (scaled by the vector's 2^-e).
+__global__ void __launch_bounds__(256) k_blu_pre_syn(int n, int m, int64_t batch, const double* io, int64_t ob,
+                                                    int64_t oe, int64_t inner, int64_t oob,
+                                                    const int* __restrict__ xe, const cdf* __restrict__ sh,
+                                                    const cdf* __restrict__ ch, cdf* __restrict__ A) {
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+    const double* s = io + lc_boff(b, ob, inner, oob);
+    const int e = vec_e(xe, b);
+    cdf* Ab = A + b * int64_t(m);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+      cdf v{lc_df(0.0f, 0.0f), lc_df(0.0f, 0.0f)};
+      if (k < n) {
+        const lc_df P = lc_df_from_double_s(s[int64_t(k) * oe], e) * lc_df(k == 0 ? 1.0f : 0.5f, 0.0f);
+        const lc_df Q =
+            k == 0 ? lc_df(0.0f, 0.0f) : lc_df_from_double_s(s[int64_t(n - k) * oe], e) * lc_df(0.5f, 0.0f);
+        const cdf w = sh[k];
+        v = cmul(cdf{P * w.re + Q * w.im, P * w.im - Q * w.re}, ch[k]);
+      }
+      Ab[k] = v;
+    }
+  }
+}
+// Synthesis output: x_j = chirp[j] conv_j / m, out at Makhoul's position of j.
+__global__ void __launch_bounds__(256) k_blu_post_syn(int n, int m, int64_t batch, const cdf* __restrict__ conv,
+                                                     const cdf* __restrict__ ch, const int* __restrict__ xe,
+                                                     double* io, int64_t ob, int64_t oe, int64_t inner,
+                                                     int64_t oob) {
+  const lc_df inv_m(1.0f / float(m), 0.0f);  // m a power of two: exact
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+    double* s = io + lc_boff(b, ob, inner, oob);
+    const int e = vec_e(xe, b);
+    const cdf* cb = conv + b * int64_t(m);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+      const cdf x = cmul(ch[j], cb[j]);
+      const int64_t o = j < (n + 1) / 2 ? 2 * int64_t(j) : 2 * int64_t(n - 1 - j) + 1;
+      s[o * oe] = lc_df_to_double_s(x.re * inv_m, e);
+    }
+  }
+}
+// Analysis, Bluestein input: a_j = x_j conj(chirp[j]), x_j = v at Makhoul's
+// position of j (FP64).
+__global__ void __launch_bounds__(256) k_blu_pre_ana(int n, int m, int64_t batch, const double* src, int64_t ib,
+                                                    int64_t ie, int64_t inner, int64_t iob,
+                                                    const cd* __restrict__ ch64, cd* __restrict__ A) {
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+    const double* s = src + lc_boff(b, ib, inner, iob);
+    cd* Ab = A + b * int64_t(m);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+      cd v{0.0, 0.0};
+      if (j < n) {
+        const int64_t o = j < (n + 1) / 2 ? 2 * int64_t(j) : 2 * int64_t(n - 1 - j) + 1;
+        const double x = s[o * ie];
+        v = cd{x * ch64[j].re, -x * ch64[j].im};
+      }
+      Ab[j] = v;
+    }
+  }
+}
+// Analysis output: X_k = conj(chirp[k]) conv_k / m, then the coefficient
+// Re(exp(-i pi k/(2n)) X_k) 2/n (halved at k = 0) into dst[b n + k].
+__global__ void __launch_bounds__(256) k_blu_post_ana(int n, int m, int64_t batch, const cd* __restrict__ conv,
+                                                     const cd* __restrict__ ch64, const cd* __restrict__ sh64,
+                                                     double* __restrict__ dst) {
+  const double inv_m = 1.0 / double(m), two_n = 2.0 / double(n);
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+    const cd* cb = conv + b * int64_t(m);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+      const cd c{ch64[k].re, -ch64[k].im};
+      const cd X = cmul(c, cb[k]);
+      const cd w = sh64[k];
+      const double v = fma(X.re, w.re, X.im * w.im) * inv_m;
+      dst[b * int64_t(n) + k] = v * (k == 0 ? 0.5 * two_n : two_n);
+    }
+  }
+}
+
 unsigned batch_grid(int64_t batch) { return unsigned(batch < 65535 ? batch : 65535); }
 
 }  // namespace
 
-bool lc_values_supported(int64_t n) { return n >= 2 && n <= LC_VALUES_MAX_N && log2_exact(n) > 0; }
+namespace {
+bool pow2(int64_t n) { return log2_exact(n) > 0; }
+}  // namespace
 
-size_t lc_values_table_bytes(int64_t n) { return size_t(n) * 3 / 2 * (sizeof(cdf) + sizeof(cd)); }
+bool lc_values_supported(int64_t n) {
+  return n >= 2 && n <= LC_VALUES_MAX_N && (pow2(n) || n <= LC_VALUES_MAX_N_ANY);
+}
+
+size_t lc_values_table_bytes(int64_t n) {
+  if (pow2(n)) return size_t(n) * 3 / 2 * (sizeof(cdf) + sizeof(cd));
+  const int64_t m = blu_m(n);  // twiddles of m, shift and chirp of n, the chirp's FFT
+  return size_t(m / 2 + 2 * n + m) * (sizeof(cdf) + sizeof(cd));
+}
 
 size_t lc_values_work_bytes(int64_t n, int64_t batch) {
-  if (n <= kSmallN) return 0;
-  return size_t(batch) * size_t(n) * sizeof(cd) + size_t(batch) * sizeof(int) + 256;
+  if (pow2(n)) {
+    if (n <= kSmallN) return 0;
+    return size_t(batch) * size_t(n) * sizeof(cd) + size_t(batch) * sizeof(int) + 256;
+  }
+  const int64_t m = blu_m(n);  // two complex arrays of m per vector (at least two for the plan-time FFT)
+  const int64_t b = batch > 1 ? batch : 1;
+  return size_t(2 * b) * size_t(m) * sizeof(cd) + size_t(batch) * sizeof(int) + 256;
 }
 
 int lc_values_launches(const lc_plan_s* p) {
+  if (!pow2(p->g.n)) return p->dir == LC_L2C ? 7 : 6;
   if (p->g.n <= kSmallN) return 1;
   return p->dir == LC_L2C ? 3 : 2;
 }
@@ -401,18 +601,72 @@ namespace {
 struct Tables {
   cdf *tw, *sh;
   cd *tw64, *sh64;
+  cdf *ch, *Bh;    // Bluestein: chirp[n], FFT of the chirp sequence [m]
+  cd *ch64, *Bh64;
+  int64_t m;       // Bluestein length (0 for powers of two)
 };
 Tables tables_of(const lc_plan_s* p) {
   const int64_t n = p->g.n;
   cdf* t = static_cast<cdf*>(p->val_tables);
-  cd* t64 = reinterpret_cast<cd*>(t + n * 3 / 2);
-  return Tables{t, t + n / 2, t64, t64 + n / 2};
+  if (pow2(n)) {
+    cd* t64 = reinterpret_cast<cd*>(t + n * 3 / 2);
+    return Tables{t, t + n / 2, t64, t64 + n / 2, nullptr, nullptr, nullptr, nullptr, 0};
+  }
+  const int64_t m = blu_m(n), per = m / 2 + 2 * n + m;
+  cd* t64 = reinterpret_cast<cd*>(t + per);
+  return Tables{t,           t + m / 2,           t64,       t64 + m / 2, t + m / 2 + n, t + m / 2 + 2 * n,
+                t64 + m / 2 + n, t64 + m / 2 + 2 * n, m};
+}
+// The two-pass FFT of length m over work arrays (Bluestein's convolutions).
+template <typename C>
+lc_status cf_fft(int64_t m, int64_t batch, const C* src, C* T, C* dst, const C* tw, int inverse, int mode,
+                 const C* Bh, int conj_b, cudaStream_t st) {
+  const Split q = split_of(m);
+  const unsigned gy = batch_grid(batch);
+  k_cf_cols<C><<<dim3(unsigned(q.n1 / kTW), gy), 256, size_t(kTW) * q.n2 * sizeof(C), st>>>(
+      int(m), q.n1, q.n2, q.log2, batch, src, T, tw, inverse);
+  LC_LAUNCH_CHECK();
+  k_cf_rows<C><<<dim3(unsigned(q.n2), gy), 256, size_t(q.n1) * sizeof(C), st>>>(int(m), q.n1, q.n2, q.log1, batch, T,
+                                                                              dst, tw, inverse, mode, Bh, conj_b);
+  LC_LAUNCH_CHECK();
+  return LC_OK;
+}
+lc_status cf_smem(int64_t m) {
+  const Split q = split_of(m);
+  const int cols = int(size_t(kTW) * q.n2 * sizeof(cd)), rows = int(size_t(q.n1) * sizeof(cd));
+  const void* fc[2] = {reinterpret_cast<const void*>(k_cf_cols<cdf>), reinterpret_cast<const void*>(k_cf_cols<cd>)};
+  const void* fr[2] = {reinterpret_cast<const void*>(k_cf_rows<cdf>), reinterpret_cast<const void*>(k_cf_rows<cd>)};
+  for (int k = 0; k < 2; ++k) {
+    if (cols > 44 * 1024) LC_CUDA_TRY(cudaFuncSetAttribute(fc[k], cudaFuncAttributeMaxDynamicSharedMemorySize, cols));
+    if (rows > 44 * 1024) LC_CUDA_TRY(cudaFuncSetAttribute(fr[k], cudaFuncAttributeMaxDynamicSharedMemorySize, rows));
+  }
+  return LC_OK;
+}
+unsigned grid_1d(int64_t work) {
+  const int64_t g = (work + 255) / 256;
+  return unsigned(g < 4096 ? g : 4096);
 }
 }  // namespace
 
 lc_status lc_values_prepare(lc_plan p, cudaStream_t st) {
   const int n = int(p->g.n);
   const Tables t = tables_of(p);
+  if (t.m) {  // Bluestein: tables, then the FFT of the chirp sequence (FP64, once)
+    const int m = int(t.m);
+    k_blu_tables<<<grid_1d(m > 2 * n ? m : 2 * n), 256, 0, st>>>(n, m, t.tw, t.tw64, t.sh, t.sh64, t.ch, t.ch64);
+    LC_LAUNCH_CHECK();
+    lc_status e = cf_smem(m);
+    if (e != LC_OK) return e;
+    cd* A = static_cast<cd*>(p->val_work);
+    cd* T = A + m;
+    k_blu_bc<<<grid_1d(m), 256, 0, st>>>(n, m, t.ch64, A);
+    LC_LAUNCH_CHECK();
+    e = cf_fft<cd>(m, 1, A, T, t.Bh64, t.tw64, 0, 1, nullptr, 0, st);
+    if (e != LC_OK) return e;
+    k_d2df_c<<<grid_1d(m), 256, 0, st>>>(m, t.Bh64, t.Bh);
+    LC_LAUNCH_CHECK();
+    return LC_OK;
+  }
   k_values_tables<<<unsigned((n + 255) / 256), 256, 0, st>>>(n, t.tw, t.sh, t.tw64, t.sh64);
   LC_LAUNCH_CHECK();
   if (n > kSmallN) {
@@ -437,6 +691,28 @@ lc_status lc_values_prepare(lc_plan p, cudaStream_t st) {
 lc_status lc_values_synth(lc_plan p, double* out, const lc_layout& lay, cudaStream_t st) {
   const int n = int(p->g.n);
   const Tables t = tables_of(p);
+  if (t.m) {  // Bluestein: a = Y chirp, conv = IFFT(FFT(a) FFT(b)) / m, x = chirp conv
+    const int64_t m = t.m;
+    cdf* A = static_cast<cdf*>(p->val_work);
+    cdf* T = A + p->batch * m;
+    int* xe = reinterpret_cast<int*>(static_cast<cd*>(p->val_work) + 2 * (p->batch > 1 ? p->batch : 1) * m);
+    const unsigned gy = batch_grid(p->batch);
+    LC_CUDA_TRY(cudaMemsetAsync(xe, 0x80, size_t(p->batch) * sizeof(int), st));
+    k_vsyn_exp<<<dim3(unsigned((n + 4095) / 4096), gy), 256, 0, st>>>(n, p->batch, out, lay.ob, lay.oe, lay.inner,
+                                                                    lay.oob, xe);
+    LC_LAUNCH_CHECK();
+    k_blu_pre_syn<<<dim3(grid_1d(m), gy), 256, 0, st>>>(n, int(m), p->batch, out, lay.ob, lay.oe, lay.inner, lay.oob,
+                                                       xe, t.sh, t.ch, A);
+    LC_LAUNCH_CHECK();
+    lc_status e = cf_fft<cdf>(m, p->batch, A, T, A, t.tw, 0, 0, t.Bh, 0, st);
+    if (e != LC_OK) return e;
+    e = cf_fft<cdf>(m, p->batch, A, T, A, t.tw, 1, 1, nullptr, 0, st);
+    if (e != LC_OK) return e;
+    k_blu_post_syn<<<dim3(grid_1d(n), gy), 256, 0, st>>>(n, int(m), p->batch, A, t.ch, xe, out, lay.ob, lay.oe,
+                                                        lay.inner, lay.oob);
+    LC_LAUNCH_CHECK();
+    return LC_OK;
+  }
   if (n > kSmallN) {
     const Split q = split_of(n);
     cd* T = static_cast<cd*>(p->val_work);
@@ -464,6 +740,22 @@ lc_status lc_values_synth(lc_plan p, double* out, const lc_layout& lay, cudaStre
 lc_status lc_values_analysis(lc_plan p, const double* in, const lc_layout& lay, double* scratch, cudaStream_t st) {
   const int n = int(p->g.n);
   const Tables t = tables_of(p);
+  if (t.m) {  // Bluestein, FP64: a = x conj(chirp), conv with conj(b), X = conj(chirp) conv
+    const int64_t m = t.m;
+    cd* A = static_cast<cd*>(p->val_work);
+    cd* T = A + p->batch * m;
+    const unsigned gy = batch_grid(p->batch);
+    k_blu_pre_ana<<<dim3(grid_1d(m), gy), 256, 0, st>>>(n, int(m), p->batch, in, lay.ib, lay.ie, lay.inner, lay.iob,
+                                                       t.ch64, A);
+    LC_LAUNCH_CHECK();
+    lc_status e = cf_fft<cd>(m, p->batch, A, T, A, t.tw64, 0, 0, t.Bh64, 1, st);
+    if (e != LC_OK) return e;
+    e = cf_fft<cd>(m, p->batch, A, T, A, t.tw64, 1, 1, nullptr, 0, st);
+    if (e != LC_OK) return e;
+    k_blu_post_ana<<<dim3(grid_1d(n), gy), 256, 0, st>>>(n, int(m), p->batch, A, t.ch64, t.sh64, scratch);
+    LC_LAUNCH_CHECK();
+    return LC_OK;
+  }
   if (n > kSmallN) {
     const Split q = split_of(n);
     cd* T = static_cast<cd*>(p->val_work);

@@ -117,7 +117,9 @@ def test_values_option_validation_without_gpu():
     opts.values = 1
     assert B.lc_plan_workspace_size(512, B.LC_L2C, 3, B.LC_F64_SPLIT, opts) > \
         B.lc_plan_workspace_size(512, B.LC_L2C, 3, B.LC_F64_SPLIT)
-    for n, dt in ((1000, B.LC_F64), (B.LC_VALUES_MAX_N * 2, B.LC_F64), (1, B.LC_F64_DF), (512, B.LC_F32)):
+    assert B.lc_plan_workspace_size(1000, B.LC_C2L, 2, B.LC_F64, opts) > 0  # any n: Bluestein
+    for n, dt in ((B.LC_VALUES_MAX_N_ANY + 1, B.LC_F64), (B.LC_VALUES_MAX_N * 2, B.LC_F64), (1, B.LC_F64_DF),
+                  (512, B.LC_F32)):
         with pytest.raises(B.LegChebError) as e:
             B.lc_plan_workspace_size(n, B.LC_C2L, 1, dt, opts)
         assert e.value.status == 5, (n, dt)
@@ -131,6 +133,8 @@ def test_values_option_validation_without_gpu():
     text = (ROOT / "include" / "legcheb.h").read_text()
     m = re.search(r"#define\s+LC_VALUES_MAX_N\s+(\d+)", text)
     assert m and int(m.group(1)) == B.LC_VALUES_MAX_N
+    m = re.search(r"#define\s+LC_VALUES_MAX_N_ANY\s+(\d+)", text)
+    assert m and int(m.group(1)) == B.LC_VALUES_MAX_N_ANY
 
 
 def test_alpha_option_validation_without_gpu():

@@ -87,7 +87,7 @@ def test_values_over_the_exponent_range(lc, k):
 
 def test_values_unsupported_requests(lc):
     dev = torch.device("cuda", 0)
-    for n, tier in ((1000, "f64"), (3 * 4096, "f64"), (1, "f64"), (512, "f32"), (1 << 23, "f64")):
+    for n, tier in ((lc.binding.LC_VALUES_MAX_N_ANY + 1, "f64"), (1, "f64"), (512, "f32"), (1 << 23, "f64")):
         with pytest.raises(lc.LegChebError) as e:
             lc.Plan(n, "l2c", 1, tier, dev, values=True)
         assert e.value.status == 5, (n, tier)
@@ -160,3 +160,52 @@ def test_large_strided_fibres(lc):
     back = lc.Plan(n, "c2l", 12, "f64_split", dev, values=True).along_axis(torch.as_tensor(out, device=dev), 1)
     e2, _ = rel_errors(back.cpu().numpy().ravel(), X.ravel())
     assert e2 <= 1e-12, e2
+
+
+# ---- other lengths: Bluestein's chirp convolution through FFTs of length m >= 2n - 1
+@pytest.mark.parametrize("tier", TIERS)
+@pytest.mark.parametrize("n,batch", [(3, 1), (5, 2), (7, 1), (100, 3), (1000, 2), (1025, 1), (3000, 2), (5000, 1),
+                                     (12345, 1)])
+def test_other_lengths_match_oracle(lc, tier, n, batch):
+    dev = torch.device("cuda", 0)
+    F = _batch(n, batch, seed=1000 + n)
+    key = ("any", n, batch)
+    if key not in _LARGE_REF:
+        Vref = [oracle.synthesis(F[b]) for b in range(batch)]
+        _LARGE_REF[key] = (Vref, [oracle.analysis(v) for v in Vref])
+    Vref, Gref = _LARGE_REF[key]
+    V = lc.Plan(n, "l2c", batch, tier, dev, values=True)(torch.as_tensor(F if batch > 1 else F[0], device=dev))
+    V = V.cpu().numpy().reshape(batch, n)
+    for b in range(batch):
+        e2, einf = rel_errors(V[b], Vref[b])
+        assert e2 <= 1e-13, (tier, n, b, e2, einf)
+    Vin = torch.as_tensor(np.stack(Vref) if batch > 1 else Vref[0], device=dev)
+    G = lc.Plan(n, "c2l", batch, tier, dev, values=True)(Vin).cpu().numpy().reshape(batch, n)
+    for b in range(batch):
+        e2, einf = rel_errors(G[b], Gref[b])
+        assert e2 <= 1e-13, (tier, n, b, e2, einf)
+
+
+@pytest.mark.parametrize("n", [10 ** 5, 10 ** 6])
+def test_other_lengths_cosine_pass_against_sampled_oracle_sums(lc, n):
+    dev = torch.device("cuda", 0)
+    f = torch.as_tensor(workloads.decaying_vector(n, seed=901, r=1.0), device=dev)
+    c = lc.Plan(n, "l2c", 1, "f64_df", dev)(f).cpu().numpy()
+    v = lc.Plan(n, "l2c", 1, "f64_df", dev, values=True)(f)
+    rows = workloads.sample_rows(n, 512)
+    e2, einf = rel_errors(v.cpu().numpy()[rows], oracle.dct(0, c, rows=rows))
+    assert e2 <= 1e-13, (n, e2, einf)
+    back = lc.Plan(n, "c2l", 1, "f64", dev, values=True)(v)
+    e2, _ = rel_errors(back.cpu().numpy(), f.cpu().numpy())
+    assert e2 <= 2e-11, (n, e2)  # the round trip's C2L growth, as for powers of two
+
+
+def test_other_lengths_strided_fibres(lc):
+    dev = torch.device("cuda", 0)
+    n = 300
+    X = np.random.default_rng(74).standard_normal((4, n, 3)) / np.arange(1, n + 1)[None, :, None]
+    out = lc.Plan(n, "l2c", 12, "f64_split", dev, values=True).along_axis(torch.as_tensor(X, device=dev), 1)
+    out = out.cpu().numpy()
+    for i, k in ((0, 0), (3, 2)):
+        e2, _ = rel_errors(out[i, :, k], oracle.synthesis(X[i, :, k]))
+        assert e2 <= 1e-13, (i, k, e2)
