@@ -506,6 +506,11 @@ __global__ void k_plan_ahat_df(int L, int s, int dir, int64_t nc, const double* 
   }
   // the scale 4/(c_k c_l M^2) of eq:aklmore
   const lc_df wkl = df_c(4.0 / (double(LC_M) * double(LC_M)) * (r0 == 0 ? 0.5 : 1.0) * (c0 == 0 ? 0.5 : 1.0));
+  // this thread's places in the two folds and in the compact layout
+  const int fe = tid / (H * LC_M), fmm = (tid / LC_M) % H, fn = tid % LC_M;       // row fold
+  const int ge = tid / (LC_M * H), grr = (tid / H) % LC_M, gnn = tid % H;       // column fold
+  const bool keep_lo = r0 + c0 <= head;
+  const int lo_slot = LC_M * LC_M + lc_dfa_rowstart(r0, head) + c0;
   for (int64_t a = blockIdx.x; a < nc; a += gridDim.x) {
     __syncthreads();  // the previous submatrix is done with the shared tiles
     if (tid == 0) {   // the submatrix's position, once per CTA (64-bit work, conversions)
@@ -548,9 +553,8 @@ __global__ void k_plan_ahat_df(int L, int s, int dir, int64_t nc, const double* 
     }
     __syncthreads();
     if (tid < 2 * H * LC_M) {  // fold the row variable
-      const int e = tid / (H * LC_M), mm = (tid / LC_M) % H, n = tid % LC_M;
-      const lc_df u = S[mm][n], v = S[LC_M - 1 - mm][n];
-      F[e][mm][n] = e ? u - v : u + v;
+      const lc_df u = S[fmm][fn], v = S[LC_M - 1 - fmm][fn];
+      F[fe][fmm][fn] = u + (fe ? -v : v);
     }
     __syncthreads();
     {
@@ -562,9 +566,8 @@ __global__ void k_plan_ahat_df(int L, int s, int dir, int64_t nc, const double* 
     }
     __syncthreads();
     {
-      const int e = tid / (LC_M * H), rr = (tid / H) % LC_M, nn = tid % H;
-      const lc_df u = Tm[rr][nn], v = Tm[rr][LC_M - 1 - nn];
-      G[e][rr][nn] = e ? u - v : u + v;
+      const lc_df u = Tm[grr][gnn], v = Tm[grr][LC_M - 1 - gnn];
+      G[ge][grr][gnn] = u + (ge ? -v : v);
     }
     __syncthreads();
     {
@@ -576,7 +579,7 @@ __global__ void k_plan_ahat_df(int L, int s, int dir, int64_t nc, const double* 
       const lc_df v = lc_df_two_sum(acc.hi, acc.lo);  // normalised: |lo| <= ulp(hi)/2
       float* d = Af + a * words;
       d[tid] = v.hi;
-      if (r0 + c0 <= head) d[LC_M * LC_M + lc_dfa_rowstart(r0, head) + c0] = v.lo;
+      if (keep_lo) d[lo_slot] = v.lo;
       if (tid < words - used) d[used + tid] = 0.0f;
     }
   }
