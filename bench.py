@@ -359,6 +359,7 @@ def split_tensor_fractions(lc, dev, X, Z, n, B):
         4: (2 << L) * tiles * 2,  # strips of width 2s
     }
     per_cta = {0: kslices(s), 1: kslices(2 * M), 2: kslices(2 * M), 3: kslices(M), 4: kslices(2 * s) + kslices(M)}
+    plan.set_split_schedule(False)  # one launch per level, timed per kind
     lc.binding.lc_plan_set_timing(plan._handle, 3)
     for _ in range(3):
         plan(X, out=Z)
@@ -407,6 +408,12 @@ def batched_leg(lc, dev, flush, args):
                      "launches": plan.launches()}
         outs_b = locals().setdefault("outs_b", {})
         outs_b[tier] = Z.clone()
+        if tier == "f64_split":  # the same plan with one launch per level
+            plan.set_split_schedule(False)
+            step = graph_step(lambda: plan(X, out=Z))
+            ms2 = time_fn(step, flush, steps, 2)
+            res[tier]["level_launches"] = {"coefficients_per_s": n * B / (ms2 / 1e3), "ms": ms2,
+                                           "launches": plan.launches()}
         del plan
     # per result: every member's normwise error against the CPU oracle on
     # 128 sampled rows (the same rows for every member and tier)
@@ -445,6 +452,11 @@ def batched_leg(lc, dev, flush, args):
     out["ragged_4096_l2c"] = {"coefficients_per_s": float(lengths.sum()) / (ms / 1e3), "ms": ms,
                               "coefficients": int(lengths.sum()), "plan_s": plan_s, "launches": plan.launches(),
                               "leaf_tile_s": tile_s, "autotune_ms_per_s": tile_ms}
+    plan.set_split_schedule(False)  # the same plan with one launch per level
+    step = graph_step(lambda: plan(x, out=z))
+    ms2 = time_fn(step, flush, steps, 2)
+    out["ragged_4096_l2c"]["level_launches"] = {"coefficients_per_s": float(lengths.sum()) / (ms2 / 1e3),
+                                                "ms": ms2, "launches": plan.launches()}
     del tplan
     del plan, x, z
     # (b') the plain per-vector FP64 and double-float paths on a sample of 128 members

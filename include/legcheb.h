@@ -260,6 +260,23 @@ lc_status lc_plan_set_config(lc_plan plan, int32_t leaf_depth, int32_t chunk_dep
  * after_leaf not 0 or 1. */
 lc_status lc_plan_set_band(lc_plan plan, int32_t ctas, int32_t after_leaf);
 
+/* Schedule of the split-precision tier (LC_F64_SPLIT, uniform and ragged
+ * batches).  persistent = 1 (the default): Steps 1-4 of Algorithm 4 -- leaf,
+ * upward levels, coupling, downward levels -- run as ONE persistent kernel
+ * launch whose CTAs draw tasks (a level, a segment, a tile of members) from
+ * a device ticket counter; a task waits (bounded) only for the row blocks
+ * it reads, counted by per-block write counters, so tasks of different
+ * levels and member tiles overlap; the ticket order is a list schedule of
+ * the task graph built at plan time (longest chain of dependants first).
+ * The final stage (Steps 5-7) is the second launch.  persistent = 0 runs
+ * one kernel launch per level (what lc_plan_set_timing breaks down per
+ * kind).  Results are bitwise the same.  A failed bounded wait aborts the
+ * execution and is reported by lc_plan_check.  LC_ERR_INVALID_ARG for a
+ * NULL plan or a value other than 0 or 1; LC_ERR_UNSUPPORTED for other
+ * tiers, or for persistent = 1 when the plan's task lists could not be
+ * built (the plan then keeps the level launches). */
+lc_status lc_plan_set_split_schedule(lc_plan plan, int32_t persistent);
+
 /* Autotuner (not in the paper): time every candidate chunk geometry
  * (leaf_depth in {3,4,5} x chunk_depth in {3,4,6}) on the given input with
  * CUDA events on `stream` (synchronises it; `out` is overwritten, same layout

@@ -189,6 +189,11 @@ class Plan:
         strips) and whether it starts after the leaf restriction; results are unchanged."""
         B.lc_plan_set_band(self._handle, int(ctas), int(bool(after_leaf)))
 
+    def set_split_schedule(self, persistent: bool = True):
+        """Split tier: one persistent launch per execution (default) or one
+        launch per level (results are bitwise the same)."""
+        B.lc_plan_set_split_schedule(self._handle, int(bool(persistent)))
+
     def check(self):
         """Raise if a bounded device-side wait of an earlier execution ran out."""
         with torch.cuda.device(self.device):

@@ -33,6 +33,7 @@ EXPORTED = (
     "lc_execute", "lc_adjoint", "lc_destroy", "lc_status_string", "lc_plan_info", "lc_plan_table",
     "lc_plan_launches", "lc_plan_set_timing", "lc_plan_get_timing", "lc_plan_check", "lc_direct_static",
     "lc_plan_set_config", "lc_plan_autotune", "lc_execute_ex", "lc_adjoint_ex", "lc_plan_set_band",
+    "lc_plan_set_split_schedule",
 )
 
 
@@ -88,6 +89,7 @@ def load(path: Path | None = None):
         "lc_plan_check": [vp, vp],
         "lc_plan_set_config": [vp, i32, i32],
         "lc_plan_set_band": [vp, i32, i32],
+        "lc_plan_set_split_schedule": [vp, i32],
         "lc_plan_autotune": [vp, vp, vp, i64, i64, i64, i64, vp, pi32, pi32, ctypes.POINTER(ctypes.c_float)],
         "lc_plan_get_timing": [vp, i32, ctypes.POINTER(ctypes.c_float), pi32, i32, pi32],
     }
@@ -243,6 +245,10 @@ def lc_plan_set_config(plan, leaf_depth: int, chunk_depth: int):
 
 def lc_plan_set_band(plan, ctas: int, after_leaf: int):
     _check(load().lc_plan_set_band(ctypes.c_void_p(plan), ctas, after_leaf), "lc_plan_set_band")
+
+
+def lc_plan_set_split_schedule(plan, persistent: int):
+    _check(load().lc_plan_set_split_schedule(ctypes.c_void_p(plan), persistent), "lc_plan_set_split_schedule")
 
 
 def lc_plan_autotune(plan, in_ptr, out_ptr, ib, ie, ob, oe, stream_ptr):

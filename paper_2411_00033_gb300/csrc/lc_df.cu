@@ -119,10 +119,12 @@ size_t lc_df_bytes(const lc_geom&, int64_t) { return 0; }
 
 lc_status lc_df_prepare(lc_plan p, cudaStream_t st) {
   const lc_geom& g = p->g;
-  k_d2df<<<blocks_for(g.N), 256, 0, st>>>(g.N, p->lam, static_cast<lc_df*>(p->df_lam));
-  if (p->dir == LC_C2L) k_d2df<<<blocks_for(g.N), 256, 0, st>>>(g.N, p->lam2, static_cast<lc_df*>(p->df_lam2));
-  k_d2df<<<1, 256, 0, st>>>(int64_t(2) * g.s * LC_M, p->T, static_cast<lc_df*>(p->df_T));
-  k_d2df<<<1, 256, 0, st>>>(LC_M * LC_M, p->B, static_cast<lc_df*>(p->df_B));
+  if (!p->df_tables_direct) {  // else lambda (u, v), T and B were built in double-float
+    k_d2df<<<blocks_for(g.N), 256, 0, st>>>(g.N, p->lam, static_cast<lc_df*>(p->df_lam));
+    if (p->dir == LC_C2L) k_d2df<<<blocks_for(g.N), 256, 0, st>>>(g.N, p->lam2, static_cast<lc_df*>(p->df_lam2));
+    k_d2df<<<1, 256, 0, st>>>(int64_t(2) * g.s * LC_M, p->T, static_cast<lc_df*>(p->df_T));
+    k_d2df<<<1, 256, 0, st>>>(LC_M * LC_M, p->B, static_cast<lc_df*>(p->df_B));
+  }
   if (g.nc > 0 && !p->df_ahat_direct)
     k_d2df_compact<<<blocks_for(g.nc * LC_M * LC_M), 256, 0, st>>>(
         g.nc, lc_dfa_head(p->dir), lc_dfa_words(p->dir), p->Ahat, static_cast<float*>(p->df_Ahat));

@@ -146,7 +146,8 @@ struct lc_plan_s {
   void* df_T;
   void* df_B;
   void* df_Ahat;
-  int df_ahat_direct;  // df_Ahat built by the double-float plan kernel (no FP64 A-hat)
+  int df_ahat_direct;    // df_Ahat built by the double-float plan kernel (no FP64 A-hat)
+  int df_tables_direct;  // df_lam (df_lam2), df_T, df_B built at plan time in double-float (no FP64 lambda, u, v)
   void* df_W;
   void* df_Cc;
   // Per-vector exponents of the double-float tier and the pre-pass's
@@ -166,6 +167,10 @@ struct lc_plan_s {
   int64_t* h_len;
   int64_t* h_off;
   void* ragged_dev;
+  // Split tier schedule: 1 = one persistent launch (when its task lists
+  // could be built), 0 = level-by-level launches; CTAs of the persistent launch.
+  int split_sched;
+  int split_grid;
   size_t bytes_used;
   int* err;  // device status word in the workspace
   // Side stream and fork/join events used to overlap independent kernels of
@@ -241,6 +246,7 @@ lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st)
 lc_status lc_exec_split(lc_plan p, const void* in, void* out, const lc_layout& lay, cudaStream_t st,
                         int adjoint);
 int lc_exec_split_launches(const lc_plan_s* p);
+bool lc_split_persistent(const lc_plan_s* p);
 void lc_split_release(lc_plan p);
 
 // ---- values at Chebyshev points (lc_values.cu) -------------------------------

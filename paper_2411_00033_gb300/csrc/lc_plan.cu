@@ -195,9 +195,7 @@ __global__ void k_plan_geg_tables(int64_t N, int dir, lc_geg G, double* __restri
   }
 }
 
-__global__ void k_plan_T(int s, double* __restrict__ T) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * s) return;
+__device__ __forceinline__ void plan_T_row(int t, int s, double* __restrict__ T) {
   const int sigma = t / s, m = t % s;
   const double X = -1.0 + double(2 * m + sigma) / double(s);
   double* row = T + (size_t(sigma) * s + m) * LC_M;
@@ -212,12 +210,9 @@ __global__ void k_plan_T(int s, double* __restrict__ T) {
   }
 }
 
-// B(0) by the exact row recurrence (one thread; M^2 work).
-__global__ void k_plan_B(double* __restrict__ B) {
-  // One warp: row k+1 from rows k and k-1, entry i per lane (rows are
-  // independent across i, sequential in k).
-  const int i = threadIdx.x;
-  if (blockIdx.x != 0 || i >= 32) return;
+// B(0) by the exact row recurrence (M^2 work).  One warp: row k+1 from rows k and k-1, entry i per lane (rows are
+// independent across i, sequential in k).
+__device__ __forceinline__ void plan_B_warp(int i, double* __restrict__ B) {
   for (int t = i; t < LC_M * LC_M; t += 32) B[t] = 0.0;
   __syncwarp();
   if (i == 0) {
@@ -281,11 +276,35 @@ __global__ void k_plan_nodal_P(double* __restrict__ B) {
 
 // cosm[k][m] = cos(k (m + 1/2) pi / M): the DCT-II matrix of eq:aklmore.
 // Row 1 holds the Chebyshev-Gauss points X_m.
-__global__ void k_plan_cos(double* __restrict__ cosm) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= LC_M * LC_M) return;
+__device__ __forceinline__ void plan_cos_entry(int t, double* __restrict__ cosm) {
   const int k = t / LC_M, m = t % LC_M;
   cosm[t] = cospi(double(k * (2 * m + 1)) / double(2 * LC_M));
+}
+// X_m = cosm[1][m], by the same expression.
+__device__ __forceinline__ double lc_node(int m) { return cospi(double(1 * (2 * m + 1)) / double(2 * LC_M)); }
+// T(sigma) and B(0) in one launch of two CTAs (the tables are tiny; separate
+// launches cost more than their work).  Tdf and Bdf, if given, receive
+// double-float copies.
+__device__ __forceinline__ void plan_basis_block(int blk, int s, double* __restrict__ T, double* __restrict__ B,
+                                                 lc_df* __restrict__ Tdf, lc_df* __restrict__ Bdf) {
+  if (blk == 0) {
+    if (threadIdx.x < 2 * s) {
+      plan_T_row(threadIdx.x, s, T);
+      if (Tdf)
+        for (int k = 0; k < LC_M; ++k) {
+          const size_t e = size_t(threadIdx.x) * LC_M + k;
+          Tdf[e] = lc_df_from_double(T[e]);
+        }
+    }
+  } else if (threadIdx.x < 32) {
+    plan_B_warp(threadIdx.x, B);
+    __syncwarp();
+    if (Bdf)
+      for (int t = threadIdx.x; t < LC_M * LC_M; t += 32) Bdf[t] = lc_df_from_double(B[t]);
+  }
+}
+__global__ void k_plan_basis(int s, double* __restrict__ T, double* __restrict__ B) {
+  plan_basis_block(blockIdx.x, s, T, B, nullptr, nullptr);
 }
 
 // Lambda((y - x)/2) at the M x M Chebyshev-Gauss points of a submatrix
@@ -295,9 +314,12 @@ __global__ void k_plan_cos(double* __restrict__ cosm) {
 // same way).  Table [L][2][M][M].
 // For C2L the table holds Lambda((y-x)/2) / (x - y + 1), the other factor of
 // L(x, y) that depends only on y - x (eq:Lxymod).
-__global__ void k_plan_lminus(int L, int s, int dir, lc_geg G, const double* __restrict__ cosm,
-                              double* __restrict__ tab) {
+// The launch also writes the DCT matrix cosm (its first M^2 threads), which
+// the A-hat kernels read; the nodes here come from the same formula.
+__global__ void k_plan_lminus(int L, int s, int dir, lc_geg G, double* __restrict__ cosm,
+                              double* __restrict__ tab, lc_df* __restrict__ tab_df) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < LC_M * LC_M) plan_cos_entry(int(t), cosm);
   if (t >= int64_t(L) * 2 * LC_M * LC_M) return;
   const int gamma = int(t / (2 * LC_M * LC_M));
   const int c = int((t / (LC_M * LC_M)) % 2);
@@ -305,13 +327,15 @@ __global__ void k_plan_lminus(int L, int s, int dir, lc_geg G, const double* __r
   const double h = double(int64_t(s) << (L - gamma - 1));
   const double off = (c == 0 ? 4.0 : 6.0) * h;  // j0 - i0
   // (y_n - x_m)/2 with x_m = i0 + h (X_m + 1), y_n = j0 + h (Y_n + 1)   (eq:Xfromx)
-  const double ymx = off + h * (cosm[LC_M + n] - cosm[LC_M + m]);
+  const double ymx = off + h * (lc_node(n) - lc_node(m));
   if (G.on) {  // Gegenbauer: lambda_a((y-x)/2) or u_a((y-x)/2)
     tab[t] = dir == LC_L2C ? lc_geg_lam(G, 0.5 * ymx) : lc_geg_u(G, 0.5 * ymx);
     return;
   }
   const double l = lc_Lambda(0.5 * ymx);
-  tab[t] = dir == LC_L2C ? l : l / (1.0 - ymx);
+  const double v = dir == LC_L2C ? l : l / (1.0 - ymx);
+  tab[t] = v;
+  if (tab_df) tab_df[t] = lc_df_from_double(v);  // the double-float plan's copy
 }
 
 // One CTA (M*M threads) per submatrix: sample the kernel, then the 2-D DCT-II
@@ -446,40 +470,117 @@ __device__ __forceinline__ lc_df df_sample(int dir, const lc_df& z) {
   const lc_df y = z + lc_df(0.25f, 0.0f);
   const lc_df r = df_rsqrt(y);
   const lc_df r2 = r * r;
-  const lc_df x = r2 * r2;
-  const float zf = z.hi;
-  lc_df q;
-  if (dir == LC_L2C) {  // tau coefficients 1, -1/64, 21/8192, -671/524288, 180323/134217728 (exact in FP32)
-    if (zf > 1844.0f) q = lc_df(-1.0f / 64.0f, 0.0f);
-    else if (zf > 134.0f) q = lc_df(-1.0f / 64.0f, 0.0f) + x * lc_df(21.0f / 8192.0f, 0.0f);
-    else if (zf > 40.0f)
-      q = lc_df(-1.0f / 64.0f, 0.0f) + x * (lc_df(21.0f / 8192.0f, 0.0f) + x * lc_df(-671.0f / 524288.0f, 0.0f));
-    else
-      q = lc_df(-1.0f / 64.0f, 0.0f) +
-          x * (lc_df(21.0f / 8192.0f, 0.0f) +
-               x * (lc_df(-671.0f / 524288.0f, 0.0f) + x * lc_df(180323.0f / 134217728.0f, 0.0f)));
-    return (lc_df(1.0f, 0.0f) + x * q) * r;
+  const lc_df x = r2 * r2;  // x <= 1/400^2
+  const float zf = z.hi, xf = x.hi;
+  // Series 1 + c1 x + x^2 q2(x): the first-order term in double-float, the rest
+  // (below 1e-13 of the sum) in FP32; the terms kept above z = 40, 134, 1844
+  // as in lc_Lambda_sample.  L2C: tau, c1 = -1/64 (a power of two, exact);
+  // C2L: Q, c1 = 5/64.
+  float q2;
+  if (dir == LC_L2C) {
+    if (zf > 1844.0f) q2 = 0.0f;
+    else if (zf > 134.0f) q2 = 21.0f / 8192.0f;
+    else if (zf > 40.0f) q2 = fmaf(xf, -671.0f / 524288.0f, 21.0f / 8192.0f);
+    else q2 = fmaf(xf, fmaf(xf, 180323.0f / 134217728.0f, -671.0f / 524288.0f), 21.0f / 8192.0f);
+    const lc_df t = lc_df(1.0f, 0.0f) + lc_df(x.hi * (-1.0f / 64.0f), x.lo * (-1.0f / 64.0f)) +
+                    lc_df(xf * xf * q2, 0.0f);
+    return t * r;
   }
-  // Q(x) coefficients 1, 5/64, 21/8192, 715/524288, -162877/134217728 (exact in FP32)
-  if (zf > 1844.0f) q = lc_df(5.0f / 64.0f, 0.0f);
-  else if (zf > 134.0f) q = lc_df(5.0f / 64.0f, 0.0f) + x * lc_df(21.0f / 8192.0f, 0.0f);
-  else if (zf > 40.0f)
-    q = lc_df(5.0f / 64.0f, 0.0f) + x * (lc_df(21.0f / 8192.0f, 0.0f) + x * lc_df(715.0f / 524288.0f, 0.0f));
-  else
-    q = lc_df(5.0f / 64.0f, 0.0f) +
-        x * (lc_df(21.0f / 8192.0f, 0.0f) +
-             x * (lc_df(715.0f / 524288.0f, 0.0f) + x * lc_df(-162877.0f / 134217728.0f, 0.0f)));
-  return lc_df(0.25f, 0.0f) * r2 * r * (lc_df(1.0f, 0.0f) + x * q);
+  if (zf > 1844.0f) q2 = 0.0f;
+  else if (zf > 134.0f) q2 = 21.0f / 8192.0f;
+  else if (zf > 40.0f) q2 = fmaf(xf, 715.0f / 524288.0f, 21.0f / 8192.0f);
+  else q2 = fmaf(xf, fmaf(xf, -162877.0f / 134217728.0f, 715.0f / 524288.0f), 21.0f / 8192.0f);
+  const lc_df t = lc_df(1.0f, 0.0f) + x * lc_df(5.0f / 64.0f, 0.0f) + lc_df(xf * xf * q2, 0.0f);
+  return lc_df(0.25f, 0.0f) * r2 * r * t;
 }
 
-// The per-level Lambda^- tables (k_plan_lminus) as double-float.
-__global__ void k_plan_lminus_df(int count, const double* __restrict__ lminus, lc_df* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < count) out[t] = df_c(lminus[t]);
+// 1/x for a positive double-float x: FP32 quotient and one Newton step
+// r += r (1 - x r) in double-float (relative error 2^-24 -> 2^-48).
+__device__ __forceinline__ lc_df df_recip(const lc_df& x) {
+  const float r0 = 1.0f / x.hi;
+  const lc_df r(r0, 0.0f);
+  return r + r * (lc_df(1.0f, 0.0f) - x * r);
 }
+// The double-float tier's near-field tables, built in double-float: lambda
+// (eq:Lambdaint: every 8th from the tau series, the 7 in between by the
+// recursion, the first 24 from sqrt(pi)) and, for C2L, u and v from it with
+// one reciprocal per entry (the FP64 kernels' formulas).
+__device__ __forceinline__ lc_df df_lambda_ratio(int64_t i) {  // (2i - 1) / (2i)
+  return lc_df(2 * i - 1) * df_recip(lc_df(2 * i));
+}
+// C2L: u_m and v_m from lambda_m (one reciprocal), into u[m], v[m].
+__device__ __forceinline__ void df_c2l_entry(int64_t m, const lc_df& l, lc_df* __restrict__ u,
+                                             lc_df* __restrict__ v) {
+  if (m == 0) {
+    u[0] = l;
+    v[0] = lc_df(0.0f, 0.0f);
+    return;
+  }
+  const lc_df one_m(1 - 2 * m);
+  const lc_df d = lc_df(2 * m) * lc_df(2 * m + 1) * l;
+  const lc_df q = -df_recip(-(one_m * d));  // one_m d < 0
+  u[m] = l * d * q;
+  v[m] = one_m * q;
+}
+// Thread t: lambda_i for i in [8t, 8t + 8); L2C stores them in lam, C2L
+// stores u_i in lam and v_i in v.
+__device__ __forceinline__ void plan_lambda_df(int64_t t, int64_t N, int dir, lc_df* __restrict__ lam,
+                                               lc_df* __restrict__ v2) {
+  const int64_t i0 = 8 * t;
+  if (i0 >= N) return;
+  lc_df v;
+  if (i0 < 24) {
+    v = df_c(1.7724538509055160273);  // Lambda(0) = sqrt(pi)
+    for (int64_t i = 1; i <= i0; ++i) v = v * df_lambda_ratio(i);
+  } else {
+    v = df_sample(LC_L2C, lc_df(i0));
+  }
+  for (int64_t i = i0; i < i0 + 8 && i < N; ++i) {
+    if (i > i0) v = v * df_lambda_ratio(i);
+    if (dir == LC_L2C) lam[i] = v;
+    else df_c2l_entry(i, v, lam, v2);
+  }
+}
+// The double-float plan's small tables, as the first aux_ctas(N) CTAs (of M^2
+// threads) of the A-hat launch: lambda (u, v) by the CTAs before the last,
+// T(sigma) and B(0) with their double-float copies by the last one.
+struct DfAux {
+  int64_t N;
+  int dir, s;
+  lc_df* lam;  // L2C: lambda; C2L: u
+  lc_df* v2;   // C2L: v
+  double* T;
+  double* B;
+  lc_df* Tdf;
+  lc_df* Bdf;
+};
+inline int64_t df_aux_ctas(int64_t N) { return ((N + 7) / 8 + LC_M * LC_M - 1) / (LC_M * LC_M) + 1; }
+__device__ __forceinline__ void plan_df_aux(int64_t cta, int64_t ctas, const DfAux& x) {
+  if (cta + 1 < ctas) {
+    plan_lambda_df(cta * (LC_M * LC_M) + threadIdx.x, x.N, x.dir, x.lam, x.v2);
+    return;
+  }
+  // T rows by warps 0-3 (2s <= 128), B(0) by warp 4
+  if (threadIdx.x < 128) plan_basis_block(0, x.s, x.T, x.B, x.Tdf, x.Bdf);
+  else if (threadIdx.x < 160) {
+    // plan_basis_block's warp-level B expects lanes 0..31
+    const int lane = threadIdx.x - 128;
+    plan_B_warp(lane, x.B);
+    __syncwarp();
+    for (int t = lane; t < LC_M * LC_M; t += 32) x.Bdf[t] = lc_df_from_double(x.B[t]);
+  }
+}
+// Without submatrices (L = 0) the same CTAs run alone.
+__global__ void __launch_bounds__(LC_M * LC_M) k_plan_df_aux(DfAux x) { plan_df_aux(blockIdx.x, gridDim.x, x); }
 
-__global__ void k_plan_ahat_df(int L, int s, int dir, int64_t nc, const double* __restrict__ cosm,
-                               const lc_df* __restrict__ lminus, float* __restrict__ Af) {
+__global__ void __launch_bounds__(LC_M * LC_M, 4) k_plan_ahat_df(int L, int s, int dir, int64_t nc,
+                                                               const double* __restrict__ cosm,
+                               const lc_df* __restrict__ lminus, float* __restrict__ Af,
+                               DfAux aux, int64_t aux_ctas) {
+  if (blockIdx.x < aux_ctas) {  // the small tables, beside the first submatrices
+    plan_df_aux(blockIdx.x, aux_ctas, aux);
+    return;
+  }
   constexpr int H = LC_M / 2;
   __shared__ lc_df S[LC_M][LC_M];
   __shared__ lc_df F[2][H][LC_M];
@@ -511,7 +612,7 @@ __global__ void k_plan_ahat_df(int L, int s, int dir, int64_t nc, const double* 
   const int ge = tid / (LC_M * H), grr = (tid / H) % LC_M, gnn = tid % H;       // column fold
   const bool keep_lo = r0 + c0 <= head;
   const int lo_slot = LC_M * LC_M + lc_dfa_rowstart(r0, head) + c0;
-  for (int64_t a = blockIdx.x; a < nc; a += gridDim.x) {
+  for (int64_t a = blockIdx.x - aux_ctas; a < nc; a += gridDim.x - aux_ctas) {
     __syncthreads();  // the previous submatrix is done with the shared tiles
     if (tid == 0) {   // the submatrix's position, once per CTA (64-bit work, conversions)
       while (gamma + 1 < L && a >= lc_ahat_offset(gamma + 1)) ++gamma;
@@ -799,6 +900,7 @@ lc_status fill_plan(lc_plan_s* p, int64_t n, lc_direction dir, int64_t batch, lc
   p->count = batch;
   p->leaf_depth = 4;
   p->chunk_depth = 4;
+  p->split_sched = 1;
   return LC_OK;
 }
 
@@ -829,6 +931,7 @@ lc_status fill_ragged(lc_plan_s* p, const int64_t* n, int64_t count, lc_directio
   p->batch = count;
   p->count = count;
   p->ragged = 1;
+  p->split_sched = 1;
   p->h_len = static_cast<int64_t*>(malloc(sizeof(int64_t) * size_t(count)));
   p->h_off = static_cast<int64_t*>(malloc(sizeof(int64_t) * size_t(count + 1)));
   if (!p->h_len || !p->h_off) return LC_ERR_HOST_ALLOC;
@@ -889,53 +992,74 @@ bool df_plan(const lc_plan_s* p) {
 lc_status build_tables(lc_plan_s* p, cudaStream_t st) {
   const lc_geom& g = p->g;
   LC_CUDA_TRY(cudaMemsetAsync(p->err, 0, 64 * sizeof(int), st));
-  if (p->geg.on) {
-    k_plan_geg_tables<<<grid_for((g.N + 7) / 8, 256), 256, 0, st>>>(g.N, int(p->dir), p->geg, p->lam, p->lam2);
+  if (df_plan(p)) {
+    // The double-float tier's plan in two launches: Lambda^- (in double-float,
+    // where the FP64 A-hat would be) with the DCT matrix, then the compact
+    // A-hat built on the FP32 pipe, whose first CTAs build lambda (u, v),
+    // T and B directly in double-float.
+    p->df_tables_direct = 1;
+    DfAux x;
+    x.N = g.N;
+    x.dir = int(p->dir);
+    x.s = g.s;
+    x.lam = static_cast<lc_df*>(p->df_lam);
+    x.v2 = static_cast<lc_df*>(p->df_lam2);
+    x.T = p->T;
+    x.B = p->B;
+    x.Tdf = static_cast<lc_df*>(p->df_T);
+    x.Bdf = static_cast<lc_df*>(p->df_B);
+    static_assert(2 * LC_MAX_S <= 128, "T rows by the first four warps of the last aux CTA");
+    const int64_t aux = df_aux_ctas(g.N);
+    if (g.L > 0) {
+      double* cosm = p->Ahat + size_t(g.nc) * LC_M * LC_M;
+      double* lminus = cosm + LC_M * LC_M;
+      lc_df* lm_df = reinterpret_cast<lc_df*>(p->Ahat);
+      k_plan_lminus<<<unsigned((int64_t(g.L) * 2 * LC_M * LC_M + 255) / 256), 256, 0, st>>>(
+          g.L, g.s, int(p->dir), p->geg, cosm, lminus, lm_df);
+      LC_LAUNCH_CHECK();
+      p->df_ahat_direct = 1;
+      const int64_t blocks = (g.nc < 1048576 ? g.nc : 1048576) + aux;
+      k_plan_ahat_df<<<unsigned(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lm_df,
+                                                                static_cast<float*>(p->df_Ahat), x, aux);
+    } else {
+      k_plan_df_aux<<<unsigned(aux), LC_M * LC_M, 0, st>>>(x);
+    }
     LC_LAUNCH_CHECK();
   } else {
-    double* lam_target = (p->dir == LC_C2L) ? p->lam2 : p->lam;
-    k_plan_lambda<<<grid_for((g.N + 7) / 8, 256), 256, 0, st>>>(g.N, lam_target);
-    LC_LAUNCH_CHECK();
-    if (p->dir == LC_C2L) {
-      k_plan_c2l_tables<<<grid_for(g.N, 256), 256, 0, st>>>(g.N, p->lam, p->lam2);
+    if (p->geg.on) {
+      k_plan_geg_tables<<<grid_for((g.N + 7) / 8, 256), 256, 0, st>>>(g.N, int(p->dir), p->geg, p->lam, p->lam2);
+      LC_LAUNCH_CHECK();
+    } else {
+      double* lam_target = (p->dir == LC_C2L) ? p->lam2 : p->lam;
+      k_plan_lambda<<<grid_for((g.N + 7) / 8, 256), 256, 0, st>>>(g.N, lam_target);
+      LC_LAUNCH_CHECK();
+      if (p->dir == LC_C2L) {
+        k_plan_c2l_tables<<<grid_for(g.N, 256), 256, 0, st>>>(g.N, p->lam, p->lam2);
+        LC_LAUNCH_CHECK();
+      }
+    }
+    if (p->opt.nodal) {
+      k_plan_nodal_T<<<(2 * g.s * LC_M + 255) / 256, 256, 0, st>>>(g.s, p->T);
+      LC_LAUNCH_CHECK();
+      k_plan_nodal_P<<<(2 * LC_M * LC_M + 255) / 256, 256, 0, st>>>(p->B);
+      LC_LAUNCH_CHECK();
+    } else {
+      static_assert(2 * LC_MAX_S <= 256, "one thread per row of T");
+      k_plan_basis<<<2, 256, 0, st>>>(g.s, p->T, p->B);
       LC_LAUNCH_CHECK();
     }
-  }
-  if (p->opt.nodal) {
-    k_plan_nodal_T<<<(2 * g.s * LC_M + 255) / 256, 256, 0, st>>>(g.s, p->T);
-    LC_LAUNCH_CHECK();
-    k_plan_nodal_P<<<(2 * LC_M * LC_M + 255) / 256, 256, 0, st>>>(p->B);
-    LC_LAUNCH_CHECK();
-  } else {
-    k_plan_T<<<1, 2 * LC_MAX_S, 0, st>>>(g.s, p->T);
-    LC_LAUNCH_CHECK();
-    k_plan_B<<<1, 32, 0, st>>>(p->B);
-    LC_LAUNCH_CHECK();
-  }
-  if (g.L > 0) {
-    double* cosm = p->Ahat + size_t(g.nc) * LC_M * LC_M;
-    double* lminus = cosm + LC_M * LC_M;
-    k_plan_cos<<<2, 256, 0, st>>>(cosm);
-    LC_LAUNCH_CHECK();
-    k_plan_lminus<<<unsigned((int64_t(g.L) * 2 * LC_M * LC_M + 255) / 256), 256, 0, st>>>(g.L, g.s, int(p->dir),
-                                                                                          p->geg, cosm, lminus);
-    LC_LAUNCH_CHECK();
-    const int64_t blocks = g.nc < 1048576 ? g.nc : 1048576;
-    if (df_plan(p)) {  // the double-float tier's compact A-hat, built on the FP32 pipe
-      p->df_ahat_direct = 1;
-      // the double-float Lambda^- tables go where the FP64 A-hat would be
-      lc_df* lm_df = reinterpret_cast<lc_df*>(p->Ahat);
-      const int cnt = g.L * 2 * LC_M * LC_M;
-      k_plan_lminus_df<<<(cnt + 255) / 256, 256, 0, st>>>(cnt, lminus, lm_df);
+    if (g.L > 0) {
+      double* cosm = p->Ahat + size_t(g.nc) * LC_M * LC_M;
+      double* lminus = cosm + LC_M * LC_M;
+      k_plan_lminus<<<unsigned((int64_t(g.L) * 2 * LC_M * LC_M + 255) / 256), 256, 0, st>>>(
+          g.L, g.s, int(p->dir), p->geg, cosm, lminus, nullptr);
       LC_LAUNCH_CHECK();
-      k_plan_ahat_df<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lm_df,
-                                                          static_cast<float*>(p->df_Ahat));
-    } else {
+      const int64_t blocks = g.nc < 1048576 ? g.nc : 1048576;
       auto ahat = p->geg.on ? (p->opt.nodal ? k_plan_ahat<true, true> : k_plan_ahat<true, false>)
                             : (p->opt.nodal ? k_plan_ahat<false, true> : k_plan_ahat<false, false>);
       ahat<<<int(blocks), LC_M * LC_M, 0, st>>>(g.L, g.s, int(p->dir), g.nc, cosm, lminus, p->Ahat, p->geg);
+      LC_LAUNCH_CHECK();
     }
-    LC_LAUNCH_CHECK();
   }
   if (p->dtype == LC_F32) {
     k_d2f<<<grid_for(g.N, 256), 256, 0, st>>>(g.N, p->lam, p->lamf);
@@ -1006,8 +1130,8 @@ lc_status lc_plan_create_ex(lc_plan* out, int64_t n, lc_direction direction, int
   layout(p, static_cast<char*>(workspace));
   p->bytes_used = need;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  st = create_side(p);
-  if (st == LC_OK) st = build_tables(p, s);
+  st = build_tables(p, s);  // enqueued first: the host creates the side streams while they run
+  if (st == LC_OK) st = create_side(p);
   if (st == LC_OK && dtype == LC_F64_SPLIT) st = lc_split_prepare(p, static_cast<char*>(p->split), lc_split_bytes(p), s);
   if (st != LC_OK) {
     lc_split_release(p);
@@ -1168,15 +1292,15 @@ lc_status lc_plan_table(lc_plan plan, int32_t which, double* dst, int64_t count,
   const double* src = nullptr;
   int64_t len = 0;
   switch (which) {
-    case 0: src = (plan->dir == LC_C2L) ? nullptr : plan->lam; len = plan->g.N; break;
+    case 0: src = (plan->dir == LC_C2L || plan->df_tables_direct) ? nullptr : plan->lam; len = plan->g.N; break;
     case 1: src = plan->T; len = int64_t(2) * plan->g.s * LC_M; break;
     case 2: src = plan->B; len = (plan->opt.nodal ? 2 : 1) * LC_M * LC_M; break;
     case 3:  // not built when the double-float tier makes its compact copy directly
       src = df_plan(plan) ? nullptr : plan->Ahat;
       len = plan->g.nc * LC_M * LC_M;
       break;
-    case 4: src = plan->lam; len = plan->g.N; break;   // C2L: u table
-    case 5: src = plan->lam2; len = plan->g.N; break;  // C2L: v table
+    case 4: src = plan->df_tables_direct ? nullptr : plan->lam; len = plan->g.N; break;   // C2L: u table
+    case 5: src = plan->df_tables_direct ? nullptr : plan->lam2; len = plan->g.N; break;  // C2L: v table
     case 6:  // raw FP32 words of the compact double-float A-hat, two per double
       if (plan->dtype != LC_F64_DF) return LC_ERR_UNSUPPORTED;
       src = static_cast<const double*>(plan->df_Ahat);

@@ -7,8 +7,9 @@
 //   couple  C(v)      = [W(v+2) W(v+3)] [A-hat A-hat]^T (Step 3)
 //   down    C(v)     += C(v/2) B(v mod 2)              (Step 4)
 //   final   Z(strip)  = C(v) T(sigma)^T + F(strip) E^T (Steps 5-6), then C^{-1} (Step 7)
-// (E = the near-field block of the strip.)  Each product runs on the bf16
-// tensor cores (mma.sync m16n8k16, FP32 accumulation) as an exact
+// (E = the near-field block of the strip.)  Each product runs on the
+// tensor cores (tcgen05.mma kind::f16, M = 128 members, N = 32, K = 16,
+// bf16 operands from shared memory, FP32 accumulators in TMEM) as an exact
 // multi-word product: every operand row/column is scaled by a power of two
 // and cut into S signed 8-bit slices (|q| <= 128, exact in bf16), so each
 // slice product is an exact integer below 2^14 and every FP32 partial sum
@@ -34,15 +35,25 @@
 // row array keeps its slot numbering.
 //
 // Batches: members are sorted by length (descending).  At every level the
-// members owning a segment form a prefix of that order, so each CTA takes
-// one (segment, parity, 64-member tile).  A uniform batch is the special
+// members owning a segment form a prefix of that order, so each task takes
+// one (segment, parity, 128-member tile).  A uniform batch is the special
 // case of equal lengths; a ragged batch shares one coefficient table built
 // for its longest member with a fixed s (A-hat depends only on the position
 // of a submatrix in A, eq:globalij).
+//
+// Schedules: one kernel launch per level (a CTA per task), or Steps 1-4 in
+// one persistent launch whose CTAs draw the tasks in a list-scheduled order
+// and wait only for the row blocks each task reads (k_s_persist), followed
+// by the final launch.
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
+#include <queue>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "lc_internal.cuh"
@@ -57,6 +68,9 @@ constexpr int kNP = 32;         // outputs per product (18, or s <= 32) padded t
 constexpr int kCols = kNP / 2;  // accumulator columns per thread (two threads per member row)
 constexpr int kTmemCols = 256;  // S <= 7 diagonals x kNP columns, rounded up to a power of two
 constexpr int kXCols = 32;      // per-vector operand columns staged at a time
+// dynamic shared memory of the leaf and final stages beyond their operands:
+// per-row input/output bases and lengths ([3][kRows] int64)
+constexpr size_t kRowBytes = size_t(3) * kRows * 8;
 
 enum YKind {
   Y_LEAF = 0, Y_SPREAD = 1, Y_UP = 2, Y_DOWN = 3, Y_COUPLE = 4, Y_NEAR = 5,
@@ -74,6 +88,17 @@ struct Work {
   int32_t d, seg, tile;
 };
 
+// One task of the persistent schedule: a work item (kind, level d, segment
+// or strip, member tile) and its dependencies.  rd[i] names the row block
+// the task reads (a counter slot; 2 rd[i] + sigma is the counter of parity
+// sigma) and need[i] how many writes of that block must be complete first;
+// wr is the slot of the block it writes (-1: none).
+struct PTask {
+  int32_t kind, d, seg, tile;
+  int32_t rd[2], need[2];
+  int32_t wr;
+};
+
 struct SplitHost {
   int S, s, Lmax;
   int64_t count, Nmax, nstrips;
@@ -89,8 +114,12 @@ struct SplitHost {
   std::vector<int64_t> launch_off, alaunch_off;  // [launches + 1]
   std::vector<int> launch_kind, alaunch_kind;    // LC_K_*
   std::vector<int> launch_level;                 // d for up/down
+  // persistent schedule (one launch): task lists with their dependencies
+  std::vector<PTask> ptask, aptask;
+  bool persist;  // both lists were built and checked
   // device byte offsets
   size_t off_len, off_orig, off_off, off_Lcount, off_cntN, off_rowbase, off_work, off_awork;
+  size_t off_ptask, off_aptask, off_sched;  // off_sched: ticket counter, abort word, block counters
   size_t off_W, off_We, off_C, off_Ce;
   size_t total;
 };
@@ -113,8 +142,135 @@ int member_levels(int64_t n, int s) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The persistent schedule of one pass (Steps 1-4).  The data flow comes
+// from the level launches, whose order is the reference: every work item
+// with the row blocks (array W or C, level, segment, member tile) it reads
+// and writes, as the stage bodies do; a read needs every write of the block
+// by items before it in that order.  A block's counter slot is the index of
+// its first writer.  The ticket order is a list schedule of that graph on
+// `workers` CTAs with unit task times: round by round, the ready items with
+// the longest chain of dependants ahead of them first -- the coarse levels
+// of Steps 2 and 4 form the long chain, the wide levels fill the CTAs around
+// it.  Returns false -- the plan then keeps the level-by-level launches --
+// if a read finds no earlier writer, or if a block could be rewritten
+// before a reader that needs its earlier value has read it (only a
+// read-modify-write by the writer itself is allowed).
+bool build_ptasks(bool adj, const std::vector<Work>& work, const std::vector<int64_t>& loff,
+                  const std::vector<int>& lkind, int workers, std::vector<PTask>& out) {
+  struct Block {
+    int32_t slot = -1;
+    std::vector<int32_t> writers;                       // items in level order
+    std::vector<std::pair<int32_t, int32_t>> readers;  // (item, need)
+  };
+  std::map<std::tuple<int, int, int64_t, int32_t>, Block> blocks;  // (array, d, seg, tile)
+  std::vector<PTask> items;
+  std::vector<std::array<int32_t, 2>> pred;
+  out.clear();
+  for (size_t l = 0; l < lkind.size(); ++l) {
+    const int kind = lkind[l];
+    if (kind == LC_K_FINAL) continue;  // the final stage is a launch of its own
+    for (int64_t w = loff[l]; w < loff[l + 1]; ++w) {
+      const Work& it = work[w];
+      const int32_t me = int32_t(items.size());
+      PTask t{kind, it.d, it.seg, it.tile, {-1, -1}, {0, 0}, -1};
+      std::array<int32_t, 2> pr{-1, -1};
+      const int64_t v = it.seg;
+      std::vector<std::tuple<int, int, int64_t>> reads;  // (array: 0 W, 1 C; d; seg)
+      std::tuple<int, int, int64_t> wblk{-1, 0, 0};
+      switch (kind) {
+        case LC_K_LEAF: wblk = {0, 0, v}; break;
+        case LC_K_UP:
+          reads = {{0, it.d - 1, 2 * v}, {0, it.d - 1, 2 * v + 1}};
+          wblk = {0, it.d, v};
+          break;
+        case LC_K_COUPLE:
+          if (adj) {
+            reads.push_back({0, it.d, v - 2});
+            if (v & 1) reads.push_back({0, it.d, v - 3});
+          } else {
+            reads.push_back({0, it.d, v + 2});
+            if ((v & 1) == 0) reads.push_back({0, it.d, v + 3});
+          }
+          wblk = {1, it.d, v};
+          break;
+        case LC_K_DOWN:
+          reads = {{1, it.d + 1, v >> 1}, {1, it.d, v}};
+          wblk = {1, it.d, v};
+          break;
+        default:
+          return false;
+      }
+      for (size_t i = 0; i < reads.size(); ++i) {
+        auto f = blocks.find({std::get<0>(reads[i]), std::get<1>(reads[i]), std::get<2>(reads[i]), it.tile});
+        if (f == blocks.end() || f->second.writers.empty()) return false;
+        t.rd[i] = f->second.slot;
+        t.need[i] = int32_t(f->second.writers.size());
+        pr[i] = f->second.writers.back();
+        f->second.readers.push_back({me, t.need[i]});
+      }
+      if (std::get<0>(wblk) >= 0) {
+        Block& b = blocks[{std::get<0>(wblk), std::get<1>(wblk), std::get<2>(wblk), it.tile}];
+        if (b.writers.empty()) b.slot = me;
+        b.writers.push_back(me);
+        t.wr = b.slot;
+      }
+      items.push_back(t);
+      pred.push_back(pr);
+    }
+  }
+  for (const auto& kv : blocks) {
+    const Block& b = kv.second;
+    for (const auto& rd : b.readers)
+      if (rd.second < int32_t(b.writers.size()) && b.writers[rd.second] != rd.first) return false;
+    for (size_t j = 1; j < b.writers.size(); ++j) {  // each rewrite waits for the write before it
+      bool chained = false;
+      for (const auto& rd : b.readers) chained |= rd.first == b.writers[j] && rd.second == int32_t(j);
+      if (!chained) return false;
+    }
+  }
+  const int32_t n = int32_t(items.size());
+  if (size_t(n) >= (size_t(1) << 29)) return false;
+  // dependants, and the longest chain from each item (level order is topological)
+  std::vector<std::vector<int32_t>> succ(n);
+  std::vector<int32_t> indeg(n, 0), rank(n, 1);
+  for (int32_t i = 0; i < n; ++i)
+    for (int k = 0; k < 2; ++k) {
+      const int32_t q = pred[i][k];
+      if (q < 0 || (k == 1 && q == pred[i][0])) continue;
+      succ[q].push_back(i);
+      ++indeg[i];
+    }
+  for (int32_t i = n - 1; i >= 0; --i)
+    for (int32_t j : succ[i]) rank[i] = std::max(rank[i], rank[j] + 1);
+  // the list schedule: two tickets (parities) per item
+  const size_t cap = size_t(std::max(1, workers / 2));
+  auto later = [&](int32_t a, int32_t b) { return rank[a] != rank[b] ? rank[a] < rank[b] : a > b; };
+  std::priority_queue<int32_t, std::vector<int32_t>, decltype(later)> ready(later);
+  for (int32_t i = 0; i < n; ++i)
+    if (indeg[i] == 0) ready.push(i);
+  std::vector<int32_t> round, next;
+  out.reserve(size_t(n));
+  while (!ready.empty()) {
+    round.clear();
+    while (!ready.empty() && round.size() < cap) {
+      round.push_back(ready.top());
+      ready.pop();
+    }
+    for (int32_t i : round) {
+      out.push_back(items[i]);
+      for (int32_t j : succ[i])
+        if (--indeg[j] == 0) next.push_back(j);
+    }
+    for (int32_t j : next) ready.push(j);
+    next.clear();
+  }
+  return out.size() == size_t(n);
+}
+
 // Build all host tables and the byte layout of the split region.
-void build_host(const lc_plan_s* p, SplitHost& h) {
+// `workers`: CTAs of the persistent launch (its ticket order is scheduled
+// for them; the layout does not depend on it).
+void build_host(const lc_plan_s* p, SplitHost& h, int workers) {
   h.S = p->opt.slices;
   h.s = p->g.s;
   h.Lmax = p->g.L;
@@ -223,6 +379,8 @@ void build_host(const lc_plan_s* p, SplitHost& h) {
   }
   for (int64_t t = 0; t < h.nstrips; ++t) aadd(0, t, h.cntN[t]);
   aclose(LC_K_FINAL);
+  h.persist = build_ptasks(false, h.work, h.launch_off, h.launch_kind, workers, h.ptask) &&
+              build_ptasks(true, h.awork, h.alaunch_off, h.alaunch_kind, workers, h.aptask);
 
   // Y tables
   const int s = h.s;
@@ -262,6 +420,9 @@ void build_host(const lc_plan_s* p, SplitHost& h) {
   h.off_rowbase = take(h.rowbase.size() * 8);
   h.off_work = take(h.work.size() * sizeof(Work));
   h.off_awork = take(h.awork.size() * sizeof(Work));
+  h.off_ptask = take(h.ptask.size() * sizeof(PTask));
+  h.off_aptask = take(h.aptask.size() * sizeof(PTask));
+  h.off_sched = take((4 + 2 * std::max(h.ptask.size(), h.aptask.size())) * sizeof(int));
   h.off_W = take(size_t(h.rows) * LC_M * 8);
   h.off_We = take(size_t(h.rows) * 4);
   h.off_C = take(size_t(h.rows) * LC_M * 8);
@@ -401,29 +562,30 @@ __device__ __forceinline__ void put_chunk(unsigned char* X, int plane_bytes, int
 
 // Bring the Y slices of one table item (S planes of kNP x KP bf16 in the
 // canonical layout) and its kNP exponents into shared memory with two bulk
-// copies: y_issue starts them (thread 0; use = 0 for the CTA's first load,
-// which initialises the mbarrier, use = 1 for its second), y_wait waits for
-// them (all threads, phase use & 1).  Between the two the CTA stages its own
-// operand.  y_wait returns false if the bounded wait ran out; thread 0 then
-// waits once more (bounded) so that a late copy lands before the CTA exits,
-// and the caller records the failure.
+// copies: y_issue starts them (thread 0), y_wait waits for them (all
+// threads).  The mbarrier's phases run on across the loads of a CTA (`count`
+// loads waited for so far).  Between the two the CTA stages its own operand.
+// y_wait returns false if the bounded wait ran out; thread 0 then waits once
+// more (bounded) so that a late copy lands before the CTA moves on, and the
+// caller records the failure.
 __device__ __forceinline__ void y_issue(const uint16_t* __restrict__ q, const int* __restrict__ e, int S, int KP,
-                                        unsigned char* Ys, int* Ye, uint64_t* mbar, int use = 0) {
+                                        unsigned char* Ys, int* Ye, uint64_t* mbar) {
   const uint32_t mb = lc_smem_u32(mbar);
   const uint32_t bq = uint32_t(S) * kNP * KP * 2, be = uint32_t(kNP) * 4;
   if (threadIdx.x == 0) {
-    if (use == 0) lc_mbar_init(mb);
     lc_fence_proxy_async();
     lc_mbar_expect(mb, bq + be);
     lc_bulk_g2s(Ys, q, bq, mb);
     lc_bulk_g2s(Ye, e, be, mb);
   }
 }
-__device__ __forceinline__ bool y_wait(uint64_t* mbar, int use = 0) {
+__device__ __forceinline__ bool y_wait(uint64_t* mbar, uint32_t& count) {
   const uint32_t mb = lc_smem_u32(mbar);
-  const bool ok = lc_mbar_wait_bounded(mb, uint32_t(use & 1));
+  const uint32_t phase = count & 1u;
+  ++count;
+  const bool ok = lc_mbar_wait_bounded(mb, phase);
   if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) lc_mbar_wait_bounded(mb, uint32_t(use & 1));
+    if (threadIdx.x == 0) lc_mbar_wait_bounded(mb, phase);
     return false;
   }
   return true;
@@ -450,6 +612,11 @@ struct Dev {
   int ragged;
   int adj;  // transposed pass
   int* err;
+  // persistent schedule: per-block write counters, the ticket counter and the
+  // abort word of one execution (zeroed before the launch)
+  int* cnt;
+  unsigned* head;
+  int* abort;
   // I/O
   const double* in;
   double* out;
@@ -499,7 +666,7 @@ __device__ __forceinline__ Smem carve(unsigned char* base, int S, int KPx, int K
   m.rmax = reinterpret_cast<float*>(m.re + 2 * kRows);
   return m;
 }
-size_t smem_bytes(int S, int KPx, int KP) {
+__host__ __device__ __forceinline__ size_t smem_bytes(int S, int KPx, int KP) {
   return size_t(S) * kRows * KPx * 2 + size_t(S) * kNP * KP * 2 + size_t(kRows + kNP + 4 * kRows) * 4 + 16;
 }
 
@@ -514,7 +681,9 @@ __device__ __forceinline__ void sync_for_mma() {
 // Stage up to two 18-wide double-float row blocks (rows A0 and, if two, A1
 // for the same members) side by side as one operand row of 18 or 36 columns,
 // in a common exponent frame (from the stored row exponents), sliced into X.
-// Rows beyond `valid` are zero.
+// Rows beyond `valid` are zero.  In a persistent launch the rows were
+// written by other CTAs: dep_wait's acquire and the CTA barrier after it
+// order these loads after those writes.
 __device__ __forceinline__ void stage_rows_df(const Dev& D, const float2* A, const int* Ae, int64_t rowA0,
                                               int64_t rowA1, int two, int64_t tile0, int64_t valid, Smem& m) {
   const int parts = two ? 2 : 1;
@@ -626,10 +795,40 @@ struct TcState {
   uint32_t phase;
   bool held;
 };
-__device__ __forceinline__ TcState tc_begin(uint32_t* tslot, uint64_t* mbar_mma) {
-  if (threadIdx.x == 32) lc_mbar_init(lc_smem_u32(mbar_mma));
+// Shared state of a CTA across its tasks.
+struct CtaShared {
+  uint64_t mbar_y, mbar_mma;
+  uint32_t tslot;
+  int ticket;
+  int ye_near[kNP];
+};
+// Per-row input/output bases and lengths of the leaf and final stages, in
+// dynamic shared memory after the stage's operands (`off` bytes from its
+// start): [3][kRows] int64.
+
+struct RowArrays {
+  int64_t* rbase;
+  int64_t* obase;
+  int64_t* rlen;
+};
+__device__ __forceinline__ RowArrays row_arrays(unsigned char* base, size_t off) {
+  int64_t* p = reinterpret_cast<int64_t*>(base + ((off + 15) & ~size_t(15)));
+  return RowArrays{p, p + kRows, p + 2 * kRows};
+}
+// Per-CTA state of the stage bodies: the Y-copy mbarrier's running phase
+// count and the MMA state (mbarrier phase, TMEM).
+struct Ctx {
+  CtaShared* sh;
+  TcState tc;
+  uint32_t ycount;
+};
+__device__ __forceinline__ Ctx ctx_begin(CtaShared& sh) {
+  if (threadIdx.x == 0) {
+    lc_mbar_init(lc_smem_u32(&sh.mbar_y));
+    lc_mbar_init(lc_smem_u32(&sh.mbar_mma));
+  }
   __syncthreads();
-  return TcState{tslot, mbar_mma, 0u, 0u, false};
+  return Ctx{&sh, TcState{&sh.tslot, &sh.mbar_mma, 0u, 0u, false}, 0u};
 }
 __device__ __forceinline__ void tc_acquire(TcState& tc) {
   if (tc.held) return;
@@ -769,155 +968,152 @@ __device__ __forceinline__ void tc_store_row(float2* Out, int* OutE, int64_t row
   if (c0 == 0) OutE[row_base + row] = er;
 }
 
-// ------------------------------------------------------------------ kernels
-// Every kernel: one (segment or strip, parity sigma = blockIdx.x % 2, tile of
-// kRows members) per CTA; TMEM allocated at the start and released at the
-// end on every path; a failed bounded wait sets the plan's status word.
+// ------------------------------------------------------------ stage bodies
+// Every body: one (segment or strip, parity sigma, tile of kRows members);
+// `pt` is the persistent task (its dependencies), null for level-by-level
+// launches.  A body returns false if a bounded wait ran out (no MMA or copy
+// of its own is then in flight).
 
-// Step 1: W(0, g, sigma) = F(g, sigma) T(sigma).
-__global__ void __launch_bounds__(kThreads) k_s_leaf(Dev D, int64_t w0) {
-  extern __shared__ __align__(1024) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
-  __shared__ uint32_t tslot;
-  __shared__ int64_t rbase[kRows], rlen[kRows];
-  const Work it = D.work[w0 + (blockIdx.x >> 1)];
-  const int sigma = int(blockIdx.x & 1);
-  const int KP = D.yKP[Y_LEAF];
-  Smem m = carve(sm_raw, D.S, KP, KP);
-  TcState tc = tc_begin(&tslot, &mbar_mma);
-  const int64_t g = it.seg, tile0 = int64_t(it.tile) * kRows;  // column segment (transposed: row strip)
-  const int64_t valid = dcnt(D, 0, D.adj ? g + 2 : g);
-  y_issue(D.yq[Y_LEAF] + size_t(sigma) * D.S * kNP * KP, D.ye[Y_LEAF] + sigma * kNP, D.S, KP, m.Y, m.Ye, &mbar_y);
-  {
-    const int s = D.s;
-    const int cinv = D.adj && D.dir == LC_L2C;
-    row_info(D, tile0, valid, rbase, nullptr, rlen);
-    input_frames(D, tile0, valid, 2 * int64_t(s) * g + sigma, s, m, rbase, rlen, cinv);
-    stage_input(D, tile0, valid, 2 * int64_t(s) * g + sigma, s, 0, m, rbase, rlen, cinv);
-  }
-  bool ok = y_wait(&mbar_y);
-  if (ok) ok = tc_products(m, D.S, 0, 0, KP / 16, tc, false);
-  if (ok) {
-    float hi[kCols], lo[kCols];
-    tc_recombine(tc.tmem, D.S, hi, lo);
-    const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
-    tc_store_row(D.W, D.We, drow(D, 0, g, sigma, 0), tile0, valid, hi, lo, er);
-  }
-  if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
-  tc_end(tc);
+// Persistent schedule: wait until the blocks the task reads are complete.
+// Thread 0 polls their write counters (relaxed loads, both at once), then
+// one acquire fence; the CTA barrier passes the ordering on to every thread.
+// False if the execution was aborted or the bounded wait (about a second)
+// ran out.
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
-
-// Step 2: W(d+1, G) = [W(d, 2G) W(d, 2G+1)] [B(0) B(1)]^T.
-__global__ void __launch_bounds__(kThreads) k_s_up(Dev D, int64_t w0) {
-  extern __shared__ __align__(1024) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
-  __shared__ uint32_t tslot;
-  const Work it = D.work[w0 + (blockIdx.x >> 1)];
-  const int sigma = int(blockIdx.x & 1);
-  const int KP = D.yKP[Y_UP];
-  Smem m = carve(sm_raw, D.S, KP, KP);
-  TcState tc = tc_begin(&tslot, &mbar_mma);
-  const int dp = it.d;  // parent level
-  const int64_t G = it.seg, tile0 = int64_t(it.tile) * kRows;
-  const int64_t valid = dcnt(D, dp, D.adj ? G + 2 : G);  // transposed: row tree
-  y_issue(D.yq[Y_UP], D.ye[Y_UP], D.S, KP, m.Y, m.Ye, &mbar_y);
-  stage_rows_df(D, D.W, D.We, drow(D, dp - 1, 2 * G, sigma, 0), drow(D, dp - 1, 2 * G + 1, sigma, 0), 1, tile0,
-                valid, m);
-  bool ok = y_wait(&mbar_y);
-  if (ok) ok = tc_products(m, D.S, 0, 0, KP / 16, tc, false);
-  if (ok) {
-    float hi[kCols], lo[kCols];
-    tc_recombine(tc.tmem, D.S, hi, lo);
-    const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
-    tc_store_row(D.W, D.We, drow(D, dp, G, sigma, 0), tile0, valid, hi, lo, er);
-  }
-  if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
-  tc_end(tc);
-}
-
-// Step 3: C(d, v) = [W(d, v+2) W(d, v+3)] [A-hat(b,0) A-hat(b,1)]^T (v even),
-//                  W(d, v+2) A-hat(b,2)^T (v odd).
-__global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) {
-  extern __shared__ __align__(1024) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
-  __shared__ uint32_t tslot;
-  const Work it = D.work[w0 + (blockIdx.x >> 1)];
-  const int sigma = int(blockIdx.x & 1);
-  const int KP = D.yKP[Y_COUPLE];
-  Smem m = carve(sm_raw, D.S, KP, KP);
-  TcState tc = tc_begin(&tslot, &mbar_mma);
-  const int d = it.d;
-  // forward: row segment v from column segments v+2 (and v+3);
-  // transposed: column segment g = seg from row segments g-2 (and g-3)
-  const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;
-  const int64_t valid = dcnt(D, d, D.adj ? v : v + 2);
-  const int Gam = D.Lmax - 1 - d;  // level in the shared table
-  const int64_t item = (int64_t(4) * ((int64_t(1) << Gam) - 1) - 2 * Gam) + (D.adj ? v - 2 : v);
-  const YKind yk = D.adj ? Y_COUPLE_T : Y_COUPLE;
-  y_issue(D.yq[yk] + size_t(item) * D.S * kNP * KP, D.ye[yk] + item * kNP, D.S, KP, m.Y, m.Ye, &mbar_y);
-  {
-    const int two = D.adj ? int(v & 1) : ((v & 1) == 0 ? 1 : 0);
-    const int64_t s0 = D.adj ? v - 2 : v + 2, s1 = D.adj ? v - 3 : v + 3;
-    stage_rows_df(D, D.W, D.We, drow(D, d, s0, sigma, 0), two ? drow(D, d, s1, sigma, 0) : 0, two, tile0, valid, m);
-  }
-  bool ok = y_wait(&mbar_y);
-  if (ok) ok = tc_products(m, D.S, 0, 0, KP / 16, tc, false);
-  if (ok) {
-    float hi[kCols], lo[kCols];
-    tc_recombine(tc.tmem, D.S, hi, lo);
-    const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
-    tc_store_row(D.C, D.Ce, drow(D, d, v, sigma, 0), tile0, valid, hi, lo, er);
-  }
-  if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
-  tc_end(tc);
-}
-
-// Step 4: C(d, v) += C(d+1, v/2) B(v mod 2).
-__global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) {
-  extern __shared__ __align__(1024) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
-  __shared__ uint32_t tslot;
-  const Work it = D.work[w0 + (blockIdx.x >> 1)];
-  const int sigma = int(blockIdx.x & 1);
-  const int KP = D.yKP[Y_DOWN];
-  Smem m = carve(sm_raw, D.S, KP, KP);
-  TcState tc = tc_begin(&tslot, &mbar_mma);
-  const int d = it.d;
-  const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;  // child (row segment; transposed: column segment)
-  const int64_t valid = dcnt(D, d, D.adj ? v : v + 4);
-  const int p = int(v & 1);
-  y_issue(D.yq[Y_DOWN] + size_t(p) * D.S * kNP * KP, D.ye[Y_DOWN] + p * kNP, D.S, KP, m.Y, m.Ye, &mbar_y);
-  stage_rows_df(D, D.C, D.Ce, drow(D, d + 1, v >> 1, sigma, 0), 0, 0, tile0, valid, m);
-  bool ok = y_wait(&mbar_y);
-  if (ok) ok = tc_products(m, D.S, 0, 0, KP / 16, tc, false);
-  if (ok) {
-    float hi[kCols], lo[kCols];
-    tc_recombine(tc.tmem, D.S, hi, lo);
-    const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
-    // add the existing row (couple result) in a common frame
-    const int64_t base = drow(D, d, v, sigma, 0);
-    const int r = ep_row(), c0 = ep_col0();
-    const int64_t row = tile0 + r;
-    const int eo = row < valid ? D.Ce[base + row] : 0;
-    const int F = max(er, eo) + 1;
-    const float sa = pow2f(er - F), sb = pow2f(eo - F);
-    __syncthreads();  // both halves of every row have read the old exponent
-    if (row < valid) {
-#pragma unroll
-      for (int j = 0; j < kCols; ++j) {
-        const int col = c0 + j;
-        if (col >= LC_M) continue;
-        const float2 o = D.C[(base + row) * LC_M + col];
-        float sh, se, nh, nl;
-        two_sum(hi[j] * sa, o.x * sb, sh, se);
-        fast_two_sum(sh, se + lo[j] * sa + o.y * sb, nh, nl);
-        D.C[(base + row) * LC_M + col] = make_float2(nh, nl);
+__device__ __forceinline__ bool dep_wait(const Dev& D, const PTask* pt, int sigma) {
+  if (!pt || pt->rd[0] < 0) return true;  // (rd[1] is set only with rd[0])
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    const int* c0 = D.cnt + 2 * int64_t(pt->rd[0]) + sigma;
+    const int* c1 = pt->rd[1] >= 0 ? D.cnt + 2 * int64_t(pt->rd[1]) + sigma : c0;
+    const int n0 = pt->need[0], n1 = pt->rd[1] >= 0 ? pt->need[1] : 0;
+    const long long t0 = clock64();
+    for (;;) {
+      const int v0 = ld_relaxed(c0), v1 = ld_relaxed(c1);
+      if (v0 >= n0 && v1 >= n1) break;
+      if (*reinterpret_cast<volatile int*>(D.abort) || clock64() - t0 > (1ll << 31)) {
+        ok = false;
+        break;
       }
-      if (c0 == 0) D.Ce[base + row] = F;
+      __nanosleep(64);
+    }
+    asm volatile("fence.acq_rel.gpu;\n" ::: "memory");
+  }
+  return !__syncthreads_or(!ok);
+}
+
+// Steps 1-4, one product each (kind = LC_K_LEAF, _UP, _COUPLE or _DOWN):
+//   leaf    W(0, g)   = F(g, sigma) T(sigma)                      (Step 1)
+//   up      W(d+1, G) = [W(d, 2G) W(d, 2G+1)] [B(0) B(1)]^T       (Step 2)
+//   couple  C(d, v)   = [W(d, v+2) W(d, v+3)] [A-hat(b,0) A-hat(b,1)]^T (v even),
+//                       W(d, v+2) A-hat(b,2)^T (v odd)           (Step 3)
+//   down    C(d, v)  += C(d+1, v/2) B(v mod 2)                    (Step 4)
+// (the transposed pass: the roles of its header comment).  One code path
+// for the four, so that a persistent CTA that runs all of them needs the
+// registers of one.
+__device__ __forceinline__ bool s_stage(const Dev& D, int kind, Work it, int sigma, unsigned char* sm_raw, Ctx& c,
+                                        const PTask* pt) {
+  const int d = it.d;
+  const int64_t v = it.seg, tile0 = int64_t(it.tile) * kRows;
+  YKind yk = Y_LEAF;
+  int64_t yitem = 0, valid = 0, r0 = 0, r1 = 0, orow = 0;
+  int two = 0;
+  const float2* A = D.W;
+  const int* Ae = D.We;
+  float2* Out = D.W;
+  int* OutE = D.We;
+  switch (kind) {
+    case LC_K_LEAF:  // column segment v (transposed: row strip)
+      yitem = sigma;
+      valid = dcnt(D, 0, D.adj ? v + 2 : v);
+      orow = drow(D, 0, v, sigma, 0);
+      break;
+    case LC_K_UP:  // parent G = v at level d (transposed: row tree)
+      yk = Y_UP;
+      valid = dcnt(D, d, D.adj ? v + 2 : v);
+      r0 = drow(D, d - 1, 2 * v, sigma, 0);
+      r1 = drow(D, d - 1, 2 * v + 1, sigma, 0);
+      two = 1;
+      orow = drow(D, d, v, sigma, 0);
+      break;
+    case LC_K_COUPLE: {
+      // forward: row segment v from column segments v+2 (and v+3);
+      // transposed: column segment v from row segments v-2 (and v-3)
+      yk = D.adj ? Y_COUPLE_T : Y_COUPLE;
+      const int Gam = D.Lmax - 1 - d;  // level in the shared table
+      yitem = (int64_t(4) * ((int64_t(1) << Gam) - 1) - 2 * Gam) + (D.adj ? v - 2 : v);
+      valid = dcnt(D, d, D.adj ? v : v + 2);
+      two = D.adj ? int(v & 1) : ((v & 1) == 0 ? 1 : 0);
+      r0 = drow(D, d, D.adj ? v - 2 : v + 2, sigma, 0);
+      r1 = two ? drow(D, d, D.adj ? v - 3 : v + 3, sigma, 0) : 0;
+      Out = D.C;
+      OutE = D.Ce;
+      orow = drow(D, d, v, sigma, 0);
+      break;
+    }
+    default:  // down: child v at level d (transposed: column segment)
+      yk = Y_DOWN;
+      yitem = v & 1;
+      valid = dcnt(D, d, D.adj ? v : v + 4);
+      A = D.C;
+      Ae = D.Ce;
+      r0 = drow(D, d + 1, v >> 1, sigma, 0);
+      Out = D.C;
+      OutE = D.Ce;
+      orow = drow(D, d, v, sigma, 0);
+      break;
+  }
+  const int KP = D.yKP[yk];
+  Smem m = carve(sm_raw, D.S, KP, KP);
+  y_issue(D.yq[yk] + size_t(yitem) * D.S * kNP * KP, D.ye[yk] + yitem * kNP, D.S, KP, m.Y, m.Ye, &c.sh->mbar_y);
+  const bool ready = dep_wait(D, pt, sigma);
+  if (ready) {
+    if (kind == LC_K_LEAF) {
+      const int s = D.s;
+      const int cinv = D.adj && D.dir == LC_L2C;
+      const RowArrays ra = row_arrays(sm_raw, smem_bytes(D.S, KP, KP));
+      row_info(D, tile0, valid, ra.rbase, nullptr, ra.rlen);
+      input_frames(D, tile0, valid, 2 * int64_t(s) * v + sigma, s, m, ra.rbase, ra.rlen, cinv);
+      stage_input(D, tile0, valid, 2 * int64_t(s) * v + sigma, s, 0, m, ra.rbase, ra.rlen, cinv);
+    } else {
+      stage_rows_df(D, A, Ae, r0, r1, two, tile0, valid, m);
     }
   }
-  if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
-  tc_end(tc);
+  bool ok = y_wait(&c.sh->mbar_y, c.ycount) && ready;
+  if (ok) ok = tc_products(m, D.S, 0, 0, KP / 16, c.tc, false);
+  if (!ok) return false;
+  float hi[kCols], lo[kCols];
+  tc_recombine(c.tc.tmem, D.S, hi, lo);
+  const int er = tc_frame(hi, lo, m.Ye, m.Xe[ep_row()], LC_M, m.rmax);
+  if (kind != LC_K_DOWN) {
+    tc_store_row(Out, OutE, orow, tile0, valid, hi, lo, er);
+    return true;
+  }
+  // down: add the existing row (the coupling result) in a common frame
+  const int r = ep_row(), c0 = ep_col0();
+  const int64_t row = tile0 + r;
+  const int eo = row < valid ? OutE[orow + row] : 0;
+  const int F = max(er, eo) + 1;
+  const float sa = pow2f(er - F), sb = pow2f(eo - F);
+  __syncthreads();  // both halves of every row have read the old exponent
+  if (row < valid) {
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) {
+      const int col = c0 + j;
+      if (col >= LC_M) continue;
+      const float2 o = Out[(orow + row) * LC_M + col];
+      float sh, se, nh, nl;
+      two_sum(hi[j] * sa, o.x * sb, sh, se);
+      fast_two_sum(sh, se + lo[j] * sa + o.y * sb, nh, nl);
+      Out[(orow + row) * LC_M + col] = make_float2(nh, nl);
+    }
+    if (c0 == 0) OutE[orow + row] = F;
+  }
+  return true;
 }
 
 // Steps 5-7 for strip t and parity sigma, kRows members per CTA:
@@ -925,14 +1121,8 @@ __global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) {
 // The near-field product (K = 2s, staged kXCols columns at a time) and the
 // spread (K = 18) reuse the same shared memory and TMEM one after the other;
 // their results meet in the FP64 Step 7.
-__global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
-  extern __shared__ __align__(1024) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t mbar_y, mbar_mma;
-  __shared__ uint32_t tslot;
-  __shared__ int64_t rbase[kRows], obase[kRows], rlen[kRows];
-  __shared__ int ye_near[kNP];
-  const Work it = D.work[w0 + (blockIdx.x >> 1)];
-  const int sigma = int(blockIdx.x & 1);
+__device__ __forceinline__ bool s_final(const Dev& D, Work it, int sigma, unsigned char* sm_raw, Ctx& c) {
+  CtaShared& sh = *c.sh;
   const int64_t t = it.seg, tile0 = int64_t(it.tile) * kRows;
   const int64_t validN = D.cntN[t];
   // far field of strip t: row segment t (forward), column segment t (transposed)
@@ -942,48 +1132,49 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
   const int s = D.s;
   const int KPn = D.yKP[Y_NEAR];
   const int KPx = KPn < kXCols ? KPn : kXCols;
+  const int KPs = D.yKP[Y_SPREAD];
   Smem m = carve(sm_raw, D.S, KPx, KPn);
-  TcState tc = tc_begin(&tslot, &mbar_mma);
+  // after the larger of the near-field and spread operands
+  const RowArrays ra = row_arrays(sm_raw, max(smem_bytes(D.S, KPx, KPn), smem_bytes(D.S, KPs, KPs)));
   const int r = ep_row(), c0 = ep_col0();
   float nh[kCols], nl[kCols], fh[kCols], fl[kCols];
   int enx = 0, efx = 0;
   // ---- near field
   const int64_t item = 2 * t + sigma;
   const YKind yk = D.adj ? Y_NEAR_T : Y_NEAR;
-  y_issue(D.yq[yk] + size_t(item) * D.S * kNP * KPn, D.ye[yk] + item * kNP, D.S, KPn, m.Y, m.Ye, &mbar_y);
+  y_issue(D.yq[yk] + size_t(item) * D.S * kNP * KPn, D.ye[yk] + item * kNP, D.S, KPn, m.Y, m.Ye, &sh.mbar_y);
   bool ok = true;
   {
     // forward: columns of strips t, t+1 of the band of rows in strip t;
     // transposed: rows of strips t-1, t (times C^{-1} for L2C) for columns in strip t
     const int cinv = D.adj && D.dir == LC_L2C;
     const int64_t j0 = 2 * int64_t(s) * (D.adj ? t - 1 : t) + sigma;
-    row_info(D, tile0, validN, rbase, obase, rlen);
-    input_frames(D, tile0, validN, j0, 2 * s, m, rbase, rlen, cinv);
+    row_info(D, tile0, validN, ra.rbase, ra.obase, ra.rlen);
+    input_frames(D, tile0, validN, j0, 2 * s, m, ra.rbase, ra.rlen, cinv);
     for (int cc = 0; cc < KPn && ok; cc += KPx) {
-      stage_input(D, tile0, validN, j0, 2 * s, cc, m, rbase, rlen, cinv);
-      if (cc == 0) ok = y_wait(&mbar_y);
+      stage_input(D, tile0, validN, j0, 2 * s, cc, m, ra.rbase, ra.rlen, cinv);
+      if (cc == 0) ok = y_wait(&sh.mbar_y, c.ycount);
       const int kt1 = (cc + KPx < KPn ? cc + KPx : KPn) / 16;
-      if (ok) ok = tc_products(m, D.S, cc / 16, cc / 16, kt1, tc, cc > 0);
+      if (ok) ok = tc_products(m, D.S, cc / 16, cc / 16, kt1, c.tc, cc > 0);
     }
   }
   if (ok) {
-    tc_recombine(tc.tmem, D.S, nh, nl);
+    tc_recombine(c.tc.tmem, D.S, nh, nl);
     enx = m.Xe[r];
-    if (threadIdx.x < kNP) ye_near[threadIdx.x] = m.Ye[threadIdx.x];
+    if (threadIdx.x < kNP) sh.ye_near[threadIdx.x] = m.Ye[threadIdx.x];
     sync_for_mma();  // every TMEM read of the near field is done; Y and Xe may be overwritten
   }
   // ---- far field (spread)
   const bool far_tile = validF > tile0;
   if (ok && far_tile) {
-    const int KPs = D.yKP[Y_SPREAD];
     Smem m2 = carve(sm_raw, D.S, KPs, KPs);
     y_issue(D.yq[Y_SPREAD] + size_t(sigma) * D.S * kNP * KPs, D.ye[Y_SPREAD] + sigma * kNP, D.S, KPs, m2.Y, m2.Ye,
-            &mbar_y, 1);
+            &sh.mbar_y);
     stage_rows_df(D, D.C, D.Ce, drow(D, 0, t, sigma, 0), 0, 0, tile0, validF, m2);
-    ok = y_wait(&mbar_y, 1);
-    if (ok) ok = tc_products(m2, D.S, 0, 0, KPs / 16, tc, false);
+    ok = y_wait(&sh.mbar_y, c.ycount);
+    if (ok) ok = tc_products(m2, D.S, 0, 0, KPs / 16, c.tc, false);
     if (ok) {
-      tc_recombine(tc.tmem, D.S, fh, fl);
+      tc_recombine(c.tc.tmem, D.S, fh, fl);
       efx = m2.Xe[r];
       m.Ye = m2.Ye;
     }
@@ -999,20 +1190,85 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) {
         const int col = c0 + j;  // local row m of the strip
         if (col >= s) continue;
         const int64_t row_i = 2 * int64_t(s) * t + 2 * col + sigma;
-        if (row_i >= rlen[r]) continue;
-        const int E1 = enx + ye_near[col] - 16;
+        if (row_i >= ra.rlen[r]) continue;
+        const int E1 = enx + sh.ye_near[col] - 16;
         const int E2 = efx + (far ? m.Ye[col] : 0) - 16;
         // near (nh + nl) 2^E1 and far (fh + fl) 2^E2, each word brought to
         // FP64 exactly, summed and scaled by C^{-1} (L2C) in FP64
-        const double c = l2c ? ((row_i == 0) ? 0.31830988618379067154 : 0.63661977236758134308) : 1.0;
+        const double cf = l2c ? ((row_i == 0) ? 0.31830988618379067154 : 0.63661977236758134308) : 1.0;
         const double lo_sum = f2d_scaled(nl[j], E1) + (far ? f2d_scaled(fl[j], E2) : 0.0);
         const double hi_far = far ? f2d_scaled(fh[j], E2) : 0.0;
-        D.out[obase[r] + row_i * D.oe] = fma(c, f2d_scaled(nh[j], E1), fma(c, hi_far, c * lo_sum));
+        D.out[ra.obase[r] + row_i * D.oe] = fma(cf, f2d_scaled(nh[j], E1), fma(cf, hi_far, cf * lo_sum));
       }
     }
   }
+  return ok;
+}
+
+// ------------------------------------------------------------------ kernels
+// Level-by-level launches: one task per CTA (item w0 + blockIdx.x / 2,
+// parity blockIdx.x % 2); TMEM taken once the first operand is staged and
+// released at the end on every path; a failed bounded wait sets the plan's
+// status word.
+template <int KIND>
+__device__ __forceinline__ void level_task(const Dev& D, int64_t w0) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  __shared__ __align__(16) CtaShared sh;
+  Ctx c = ctx_begin(sh);
+  const Work it = D.work[w0 + (blockIdx.x >> 1)];
+  const int sigma = int(blockIdx.x & 1);
+  const bool ok = KIND == LC_K_FINAL ? s_final(D, it, sigma, sm_raw, c)
+                                     : s_stage(D, KIND, it, sigma, sm_raw, c, nullptr);
   if (!ok && threadIdx.x == 0) atomicOr(D.err, 1);
-  tc_end(tc);
+  tc_end(c.tc);
+}
+__global__ void __launch_bounds__(kThreads) k_s_leaf(Dev D, int64_t w0) { level_task<LC_K_LEAF>(D, w0); }
+__global__ void __launch_bounds__(kThreads) k_s_up(Dev D, int64_t w0) { level_task<LC_K_UP>(D, w0); }
+__global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) { level_task<LC_K_COUPLE>(D, w0); }
+__global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) { level_task<LC_K_DOWN>(D, w0); }
+__global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) { level_task<LC_K_FINAL>(D, w0); }
+
+// Steps 1-4 of an execution in one persistent launch.  Each CTA takes TMEM
+// once, before its first task, then draws tickets (task = ticket / 2,
+// parity = ticket % 2) from a global counter until they run out, always one
+// ticket ahead (the next one is drawn while the current task runs, so the
+// atomic's latency is hidden).  A task waits only for blocks written by
+// tasks of smaller tickets; the smallest unfinished ticket is always the
+// current task of the CTA holding it, and its inputs are complete, so the
+// launch finishes whatever the number of resident CTAs.  After the task's
+// stores, thread 32 publishes its block (a release increment of its counter)
+// while thread 0 starts the next task's copies.  A failed wait sets the abort
+// word: every CTA then stops drawing tickets and every waiter gives up, and
+// the plan's status word reports it.  (The final stage, Steps 5-7, is the
+// next launch: its register needs would spill here.)
+__device__ __forceinline__ int draw(const Dev& D, int n) {
+  return *reinterpret_cast<volatile int*>(D.abort) ? n : int(atomicAdd(D.head, 1u));
+}
+__global__ void __launch_bounds__(kThreads, 2) k_s_persist(Dev D, const PTask* __restrict__ tasks, int ntickets) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  __shared__ __align__(16) CtaShared sh;
+  __shared__ int tk[2];
+  if (threadIdx.x == 0) tk[0] = draw(D, ntickets);
+  Ctx c = ctx_begin(sh);
+  tc_acquire(c.tc);
+  for (int it = 0;; ++it) {
+    const int t = tk[it & 1];
+    if (t >= ntickets) break;
+    if (threadIdx.x == 0) tk[(it + 1) & 1] = draw(D, ntickets);  // read after the barrier below
+    const PTask pt = tasks[t >> 1];
+    const bool ok = s_stage(D, pt.kind, Work{pt.d, pt.seg, pt.tile}, t & 1, sm_raw, c, &pt);
+    __syncthreads();  // the task's stores are issued; the next ticket is visible
+    if (threadIdx.x == 32) {
+      if (!ok) {
+        atomicOr(D.abort, 1);
+        atomicOr(D.err, 1);
+      } else if (pt.wr >= 0) {  // release: the CTA's stores (ordered by the barrier) before the count
+        asm volatile("red.release.gpu.global.add.s32 [%0], 1;\n" ::"l"(D.cnt + 2 * int64_t(pt.wr) + (t & 1))
+                     : "memory");
+      }
+    }
+  }
+  tc_end(c.tc);
 }
 
 // ------------------------------------------------------------ plan kernels
@@ -1157,19 +1413,43 @@ Dev make_dev(const lc_plan_s* p, const SplitHost& h) {
   return D;
 }
 
+// Dynamic shared memory of each stage (kind) and of the persistent kernel
+// (the largest stage).
+size_t stage_smem(const SplitHost& h, int kind) {
+  auto sq = [&](YKind k) { return smem_bytes(h.S, h.y[k].KP, h.y[k].KP); };
+  switch (kind) {
+    case LC_K_LEAF: return sq(Y_LEAF) + 16 + kRowBytes;
+    case LC_K_UP: return sq(Y_UP);
+    case LC_K_COUPLE: return std::max(sq(Y_COUPLE), sq(Y_COUPLE_T));
+    case LC_K_DOWN: return sq(Y_DOWN);
+    default: {
+      const int kpn = h.y[Y_NEAR].KP, kpx = kpn < kXCols ? kpn : kXCols;
+      return std::max(smem_bytes(h.S, kpx, kpn), sq(Y_SPREAD)) + 16 + kRowBytes;
+    }
+  }
+}
+size_t persist_smem(const SplitHost& h) {
+  size_t b = 0;
+  for (int k : {LC_K_LEAF, LC_K_UP, LC_K_COUPLE, LC_K_DOWN}) b = std::max(b, stage_smem(h, k));
+  return b;
+}
+
 }  // namespace
 
 size_t lc_split_bytes(const lc_plan_s* p) {
   SplitHost h;
-  build_host(p, h);
+  build_host(p, h, 2);
   return h.total;
 }
 
 lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st) {
   if (p->g.s > 32) return LC_ERR_UNSUPPORTED;  // K tiles sized for s <= 32
+  int dev = 0, sms = 0;
+  LC_CUDA_TRY(cudaGetDevice(&dev));
+  LC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   SplitHost* h = new (std::nothrow) SplitHost;
   if (!h) return LC_ERR_HOST_ALLOC;
-  build_host(p, *h);
+  build_host(p, *h, 2 * sms);
   if (h->total > bytes) {
     delete h;
     return LC_ERR_WORKSPACE_TOO_SMALL;
@@ -1188,6 +1468,8 @@ lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st)
   if ((s2 = up(h->off_rowbase, h->rowbase.data(), h->rowbase.size() * 8)) != LC_OK) return s2;
   if ((s2 = up(h->off_work, h->work.data(), h->work.size() * sizeof(Work))) != LC_OK) return s2;
   if ((s2 = up(h->off_awork, h->awork.data(), h->awork.size() * sizeof(Work))) != LC_OK) return s2;
+  if ((s2 = up(h->off_ptask, h->ptask.data(), h->ptask.size() * sizeof(PTask))) != LC_OK) return s2;
+  if ((s2 = up(h->off_aptask, h->aptask.data(), h->aptask.size() * sizeof(PTask))) != LC_OK) return s2;
   const int Ks[Y_KINDS] = {h->s, LC_M, 2 * LC_M, LC_M, 2 * LC_M, 2 * h->s, 2 * LC_M, 2 * h->s};
   for (int k = 0; k < Y_KINDS; ++k) {
     const YTable& y = h->y[k];
@@ -1198,12 +1480,20 @@ lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st)
         reinterpret_cast<uint16_t*>(base + y.off_q), reinterpret_cast<int*>(base + y.off_e));
     LC_LAUNCH_CHECK();
   }
-  const size_t big = smem_bytes(7, 64, 64);  // the largest configuration any kernel takes
+  const size_t big = smem_bytes(7, 64, 64) + 16 + kRowBytes;  // the largest configuration any kernel takes
   LC_CUDA_TRY(cudaFuncSetAttribute(k_s_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
   LC_CUDA_TRY(cudaFuncSetAttribute(k_s_up, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
   LC_CUDA_TRY(cudaFuncSetAttribute(k_s_couple, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
   LC_CUDA_TRY(cudaFuncSetAttribute(k_s_down, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
   LC_CUDA_TRY(cudaFuncSetAttribute(k_s_final, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
+  LC_CUDA_TRY(cudaFuncSetAttribute(k_s_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, int(big)));
+  LC_CUDA_TRY(cudaFuncSetAttribute(k_s_persist, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   int(cudaSharedmemCarveoutMaxShared)));
+  // the persistent launch: shared memory of the largest stage, two CTAs per
+  // SM (their registers fill the register file, their TMEM all of TMEM).
+  // The schedule needs no co-residency: a CTA that finds no SM room starts
+  // when another exits, finds no tickets left and exits.
+  p->split_grid = h->persist ? 2 * sms : 0;
   return LC_OK;
 }
 
@@ -1216,7 +1506,13 @@ void lc_split_release(lc_plan p) {
 
 int lc_exec_split_launches(const lc_plan_s* p) {
   const SplitHost* h = static_cast<const SplitHost*>(p->ragged_dev);
-  return h ? int(h->launch_kind.size()) : 0;
+  if (!h) return 0;
+  return lc_split_persistent(p) ? 2 : int(h->launch_kind.size());
+}
+
+bool lc_split_persistent(const lc_plan_s* p) {
+  const SplitHost* h = static_cast<const SplitHost*>(p->ragged_dev);
+  return h && h->persist && p->split_grid > 0 && p->split_sched == 1;
 }
 
 lc_status lc_exec_split(lc_plan p, const void* in, void* out, const lc_layout& lay, cudaStream_t st,
@@ -1240,7 +1536,26 @@ lc_status lc_exec_split(lc_plan p, const void* in, void* out, const lc_layout& l
   D.iob = lay.iob;
   D.oob = lay.oob;
   lc_timer_begin(p);
-  for (size_t l = 0; l < lkind.size(); ++l) {
+  size_t first = 0;  // first launch of the level schedule still to run
+  if (lc_split_persistent(p)) {  // Steps 1-4 in one persistent launch, then the final launch
+    const std::vector<PTask>& tl = adjoint ? h->aptask : h->ptask;
+    char* base = static_cast<char*>(p->split);
+    int* sched = reinterpret_cast<int*>(base + h->off_sched);
+    D.head = reinterpret_cast<unsigned*>(sched);
+    D.abort = sched + 1;
+    D.cnt = sched + 4;
+    const int ntickets = int(2 * tl.size());
+    lc_timer_mark(p, st, LC_K_OTHER);
+    LC_CUDA_TRY(cudaMemsetAsync(sched, 0, (4 + 2 * tl.size()) * sizeof(int), st));
+    if (ntickets > 0) {
+      const int grid = std::min(p->split_grid, ntickets);
+      k_s_persist<<<grid, kThreads, persist_smem(*h), st>>>(
+          D, reinterpret_cast<const PTask*>(base + (adjoint ? h->off_aptask : h->off_ptask)), ntickets);
+      LC_LAUNCH_CHECK();
+    }
+    first = lkind.size() - 1;  // the final launch
+  }
+  for (size_t l = first; l < lkind.size(); ++l) {
     const int64_t w0 = loff[l], nitems = loff[l + 1] - w0;
     if (nitems <= 0) continue;
     const int kind = lkind[l];
@@ -1250,32 +1565,11 @@ lc_status lc_exec_split(lc_plan p, const void* in, void* out, const lc_layout& l
     dim3 grid(unsigned(2 * nitems), 1);
     lc_timer_mark(p, st, kind);
     switch (kind) {
-      case LC_K_LEAF: {
-        const YTable& y = h->y[Y_LEAF];
-        k_s_leaf<<<grid, kThreads, smem_bytes(h->S, y.KP, y.KP), st>>>(D, w0);
-        break;
-      }
-      case LC_K_UP: {
-        const YTable& y = h->y[Y_UP];
-        k_s_up<<<grid, kThreads, smem_bytes(h->S, y.KP, y.KP), st>>>(D, w0);
-        break;
-      }
-      case LC_K_COUPLE: {
-        const YTable& y = h->y[Y_COUPLE];
-        k_s_couple<<<grid, kThreads, smem_bytes(h->S, y.KP, y.KP), st>>>(D, w0);
-        break;
-      }
-      case LC_K_DOWN: {
-        const YTable& y = h->y[Y_DOWN];
-        k_s_down<<<grid, kThreads, smem_bytes(h->S, y.KP, y.KP), st>>>(D, w0);
-        break;
-      }
-      case LC_K_FINAL: {
-        const YTable& y = h->y[Y_NEAR];
-        const int kpx = y.KP < kXCols ? y.KP : kXCols;
-        k_s_final<<<grid, kThreads, smem_bytes(h->S, kpx, y.KP), st>>>(D, w0);
-        break;
-      }
+      case LC_K_LEAF: k_s_leaf<<<grid, kThreads, stage_smem(*h, kind), st>>>(D, w0); break;
+      case LC_K_UP: k_s_up<<<grid, kThreads, stage_smem(*h, kind), st>>>(D, w0); break;
+      case LC_K_COUPLE: k_s_couple<<<grid, kThreads, stage_smem(*h, kind), st>>>(D, w0); break;
+      case LC_K_DOWN: k_s_down<<<grid, kThreads, stage_smem(*h, kind), st>>>(D, w0); break;
+      case LC_K_FINAL: k_s_final<<<grid, kThreads, stage_smem(*h, kind), st>>>(D, w0); break;
     }
     LC_LAUNCH_CHECK();
   }

@@ -56,6 +56,18 @@ lc_status lc_plan_set_band(lc_plan plan, int32_t ctas, int32_t after_leaf) {
   return LC_OK;
 }
 
+lc_status lc_plan_set_split_schedule(lc_plan plan, int32_t persistent) {
+  if (!plan || (persistent != 0 && persistent != 1)) return LC_ERR_INVALID_ARG;
+  if (plan->dtype != LC_F64_SPLIT) return LC_ERR_UNSUPPORTED;
+  const int old = plan->split_sched;
+  plan->split_sched = persistent;
+  if (persistent && !lc_split_persistent(plan)) {
+    plan->split_sched = old;
+    return LC_ERR_UNSUPPORTED;
+  }
+  return LC_OK;
+}
+
 lc_status lc_plan_autotune(lc_plan plan, const void* in, void* out, int64_t in_batch_stride, int64_t in_elem_stride,
                            int64_t out_batch_stride, int64_t out_elem_stride, lc_stream stream, int32_t* leaf_depth,
                            int32_t* chunk_depth, float* best_ms) {

@@ -170,6 +170,15 @@ def test_set_band_validation_without_gpu():
     assert "lc_status lc_plan_set_band(lc_plan plan, int32_t ctas, int32_t after_leaf);" in text
 
 
+def test_split_schedule_validation_without_gpu():
+    from paper_2411_00033_gb300 import binding as B
+    lib = B.load()
+    assert lib.lc_plan_set_split_schedule(None, 1) == 1
+    assert lib.lc_plan_set_split_schedule(None, 0) == 1
+    text = (ROOT / "include" / "legcheb.h").read_text()
+    assert "lc_status lc_plan_set_split_schedule(lc_plan plan, int32_t persistent);" in text
+
+
 def test_nodal_option_validation_without_gpu():
     # the nodal variant: LC_F64 and LC_F32, uniform plans
     from paper_2411_00033_gb300 import binding as B

@@ -227,3 +227,70 @@ def test_leaf_tile_autotuner(lc):
         assert e2 <= 1e-13, (i, s, e2)
     again, s2, _ = lc.autotune_tile(xt, "c2l", "f64_split", dev, lengths=lengths, candidates=(16, 24, 32))
     assert s2 == s and again.info["s"] == s
+
+
+# ---- schedules: one persistent launch (default) against one launch per level
+def _both_schedules(plan, x, adjoint):
+    a = plan.execute(x, adjoint=adjoint)
+    plan.set_split_schedule(False)
+    levels = plan.launches()
+    b = plan.execute(x, adjoint=adjoint)
+    plan.set_split_schedule(True)
+    c = plan.execute(x, adjoint=adjoint)
+    plan.check()
+    return a.cpu().numpy(), b.cpu().numpy(), c.cpu().numpy(), levels
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("direction", ["l2c", "c2l"])
+def test_persistent_schedule_is_two_launches_and_bitwise_the_levels(lc, direction, adjoint):
+    # every task computes what its CTA of the level launch computes, from the
+    # same inputs: the results agree bit for bit, whatever order the
+    # persistent CTAs draw their tasks in
+    dev = torch.device("cuda", 0)
+    cases = [dict(n=20000, batch=130), dict(n=300, batch=3), dict(n=1, batch=2)]
+    lengths = [1, 2, 64, 129, 500, 1025, 3000] + list(workloads.ragged_lengths(300, 64, 16384, seed=21))
+    for cs in cases + [None]:
+        if cs is None:
+            plan = lc.Plan(direction=direction, dtype="f64_split", device=dev, lengths=lengths)
+            x = torch.as_tensor(workloads.ragged_batch(lengths, seed=22), device=dev)
+        else:
+            plan = lc.Plan(cs["n"], direction, cs["batch"], "f64_split", dev)
+            x = torch.as_tensor(_batch(cs["n"], cs["batch"], seed=23), device=dev)
+        assert plan.launches() == 2  # Steps 1-4 persistent, then the final stage
+        a, b, c, levels = _both_schedules(plan, x, adjoint)
+        if plan.info["L"] > 0:
+            assert levels > 1
+        assert np.array_equal(a, b) and np.array_equal(a, c), cs
+
+
+@pytest.mark.parametrize("direction,code", DIRS)
+def test_persistent_ragged_members_to_65536_sampled(lc, direction, code):
+    """Ragged batch with members up to n = 65536 (L = 9 for the longest) in
+    the persistent schedule, against the oracle on sampled rows of the 8
+    longest members and 24 random ones."""
+    lengths = workloads.ragged_lengths(600, 64, 65536, seed=31)
+    lengths[:2] = 65536
+    x = workloads.ragged_batch(lengths, seed=32)
+    offs = workloads.ragged_offsets(lengths)
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(direction=direction, dtype="f64_split", device=dev, lengths=list(lengths))
+    assert plan.launches() == 2
+    z = plan(torch.as_tensor(x, device=dev)).cpu().numpy()
+    plan.check()
+    rng = np.random.default_rng(33)
+    pick = np.concatenate([np.argsort(lengths)[-8:], rng.choice(len(lengths), 24, replace=False)])
+    worst = 0.0
+    for i in pick:
+        a, b = offs[i], offs[i + 1]
+        rows = workloads.sample_rows(int(lengths[i]), 256, seed=int(i))
+        e2, _ = rel_errors(z[a:b][rows], oracle.apply(code, x[a:b], rows=rows))
+        worst = max(worst, e2)
+    assert worst <= 1e-13, worst
+
+
+def test_split_schedule_other_tiers_unsupported(lc):
+    dev = torch.device("cuda", 0)
+    plan = lc.Plan(1000, "l2c", 2, "f64_df", dev)
+    with pytest.raises(lc.LegChebError):
+        plan.set_split_schedule(True)
