@@ -589,7 +589,8 @@ def run_ours(args):
             continue
         # plan build time (tables on the GPU, off the timed path; reported
         # separately): host clock around lc_plan_create on a workspace the caller
-        # has already allocated (the C ABI never allocates), plan kernels included
+        # has already allocated (the C ABI never allocates), plan kernels
+        # included; the median of 5 creations
         tp, tpa = [], []
         for d in ("l2c", "c2l"):
             code = lc.LC_L2C if d == "l2c" else lc.LC_C2L
@@ -597,12 +598,15 @@ def run_ours(args):
             nbytes = lc.binding.lc_plan_workspace_size(n, code, 1, tcode)
             ws_t = torch.empty(nbytes, dtype=torch.uint8, device=dev)
             sp = torch.cuda.current_stream(dev).cuda_stream
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            h = lc.binding.lc_plan_create(n, code, 1, tcode, ws_t.data_ptr(), nbytes, sp)
-            torch.cuda.synchronize()
-            tp.append((time.perf_counter() - t0) * 1e3)
-            lc.binding.lc_destroy(h)
+            reps = []
+            for _ in range(5):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h = lc.binding.lc_plan_create(n, code, 1, tcode, ws_t.data_ptr(), nbytes, sp)
+                torch.cuda.synchronize()
+                reps.append((time.perf_counter() - t0) * 1e3)
+                lc.binding.lc_destroy(h)
+            tp.append(statistics.median(reps))
             del ws_t
             # the same through the Python Plan, workspace allocation included
             torch.cuda.synchronize()
