@@ -72,7 +72,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (profiling runs)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workloads")
     ap.add_argument("--profile", default=None,
-                    help="TIER:DIRECTION:N:BATCH -- build one plan, run it twice, exit (a short target for ncu)")
+                    help="TIER:DIRECTION:N:BATCH[:levels] -- build one plan, run it twice, exit (a short target for ncu); "
+                         "':levels' gives a split plan its per-level launches")
     return ap.parse_args()
 
 
@@ -989,13 +990,16 @@ def profile_run(spec):
     __graft_entry__.build()
     import paper_2411_00033_gb300 as lc
     import workloads
-    tier, direction, n, batch = spec.split(":")
+    parts = spec.split(":")
+    tier, direction, n, batch = parts[:4]
     n, batch = int(n), int(batch)
     dev = torch.device("cuda", 0)
     dt = torch.float32 if tier == "f32" else torch.float64
     x = workloads.decaying_vector(n, seed=1, r=1.0, batch=None if batch == 1 else batch)
     xt = torch.as_tensor(x, device=dev, dtype=dt)
     plan = lc.Plan(n, direction, batch, tier, dev)
+    if len(parts) > 4 and parts[4] == "levels":  # split tier: one launch per level
+        plan.set_split_schedule(False)
     out = torch.empty_like(xt)
     for _ in range(2):
         plan(xt, out=out)

@@ -318,6 +318,9 @@ __global__ void k_plan_basis(int s, double* __restrict__ T, double* __restrict__
 // the A-hat kernels read; the nodes here come from the same formula.
 __global__ void k_plan_lminus(int L, int s, int dir, lc_geg G, double* __restrict__ cosm,
                               double* __restrict__ tab, lc_df* __restrict__ tab_df) {
+  __shared__ double X[LC_M];  // the nodes, once per CTA
+  if (threadIdx.x < LC_M) X[threadIdx.x] = lc_node(threadIdx.x);
+  __syncthreads();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < LC_M * LC_M) plan_cos_entry(int(t), cosm);
   if (t >= int64_t(L) * 2 * LC_M * LC_M) return;
@@ -327,7 +330,7 @@ __global__ void k_plan_lminus(int L, int s, int dir, lc_geg G, double* __restric
   const double h = double(int64_t(s) << (L - gamma - 1));
   const double off = (c == 0 ? 4.0 : 6.0) * h;  // j0 - i0
   // (y_n - x_m)/2 with x_m = i0 + h (X_m + 1), y_n = j0 + h (Y_n + 1)   (eq:Xfromx)
-  const double ymx = off + h * (lc_node(n) - lc_node(m));
+  const double ymx = off + h * (X[n] - X[m]);
   if (G.on) {  // Gegenbauer: lambda_a((y-x)/2) or u_a((y-x)/2)
     tab[t] = dir == LC_L2C ? lc_geg_lam(G, 0.5 * ymx) : lc_geg_u(G, 0.5 * ymx);
     return;
