@@ -95,7 +95,10 @@ typedef struct {
                     * 6 above (<= 1e-12); for ragged plans n is the longest member */
   /* Testing only (0 in normal use).  Bit 0: the coupling kernel withholds
    * one of its bulk copies, so its bounded wait runs out and the execution
-   * reports LC_ERR_DEVICE_TIMEOUT through lc_plan_check. */
+   * reports LC_ERR_DEVICE_TIMEOUT through lc_plan_check.  Bit 1 (split tier,
+   * persistent schedule): one task waits for a write its row block never
+   * receives; its bounded wait runs out, the launch aborts, and
+   * lc_plan_check reports LC_ERR_DEVICE_TIMEOUT. */
   int32_t debug_flags;
   /* 1: the Chebyshev side holds values at the n Chebyshev-Gauss points
    * x_m = cos((m + 1/2) pi / n), m = 0 .. n-1, instead of Chebyshev

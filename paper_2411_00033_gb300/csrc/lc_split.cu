@@ -1468,6 +1468,16 @@ lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st)
   if ((s2 = up(h->off_rowbase, h->rowbase.data(), h->rowbase.size() * 8)) != LC_OK) return s2;
   if ((s2 = up(h->off_work, h->work.data(), h->work.size() * sizeof(Work))) != LC_OK) return s2;
   if ((s2 = up(h->off_awork, h->awork.data(), h->awork.size() * sizeof(Work))) != LC_OK) return s2;
+  if (h->persist && (p->opt.debug_flags & 2)) {
+    // testing only: one task in the second half of each list waits for one
+    // write more than its block ever receives, so its bounded wait runs out
+    for (std::vector<PTask>* tl : {&h->ptask, &h->aptask})
+      for (size_t i = tl->size() / 2; i < tl->size(); ++i)
+        if ((*tl)[i].rd[0] >= 0) {
+          (*tl)[i].need[0] += 1;
+          break;
+        }
+  }
   if ((s2 = up(h->off_ptask, h->ptask.data(), h->ptask.size() * sizeof(PTask))) != LC_OK) return s2;
   if ((s2 = up(h->off_aptask, h->aptask.data(), h->aptask.size() * sizeof(PTask))) != LC_OK) return s2;
   const int Ks[Y_KINDS] = {h->s, LC_M, 2 * LC_M, LC_M, 2 * LC_M, 2 * h->s, 2 * LC_M, 2 * h->s};

@@ -2,9 +2,10 @@
 
 Kernels that wait on an asynchronous bulk copy (mbarrier) give up after about
 a second, record the failure in the plan's device status word and exit; the
-host reads it with lc_plan_check.  Here a test-only plan flag makes the
-coupling kernel withhold one of its copies, so the wait runs out; the call
-must report LC_ERR_DEVICE_TIMEOUT and the device must stay usable.
+host reads it with lc_plan_check.  Here test-only plan flags make the
+coupling kernel withhold one of its copies, or one task of the persistent
+split schedule wait for a write that never comes, so the wait runs out; the
+call must report LC_ERR_DEVICE_TIMEOUT and the device must stay usable.
 """
 import numpy as np
 import pytest
@@ -40,6 +41,29 @@ def test_withheld_copy_reports_timeout_and_device_survives(lc, tier):
     z = good(x).cpu().numpy()
     good.check()
     e2, _ = rel_errors(z, oracle.apply(oracle.L2C, x.cpu().numpy()))
+    assert e2 <= 1e-13
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_persistent_split_dependency_timeout_aborts(lc, adjoint):
+    # test-only flag bit 1: one task of the persistent schedule waits for a
+    # write that never comes; its bounded wait runs out, every CTA stops, and
+    # the plan reports LC_ERR_DEVICE_TIMEOUT; the device stays usable
+    n, batch = 3000, 130
+    dev = torch.device("cuda", 0)
+    X = np.stack([workloads.decaying_vector(n, seed=60 + b) for b in range(batch)])
+    x = torch.as_tensor(X, device=dev)
+    bad = lc.Plan(n, "c2l", batch, "f64_split", dev, debug_flags=2)
+    assert bad.launches() == 2
+    bad.execute(x, adjoint=adjoint)
+    with pytest.raises(lc.LegChebError) as e:
+        bad.check()
+    assert e.value.status == 4  # LC_ERR_DEVICE_TIMEOUT
+    bad.check()  # the status word was cleared
+    good = lc.Plan(n, "c2l", batch, "f64_split", dev)
+    z = good.execute(x, adjoint=adjoint).cpu().numpy()
+    good.check()
+    e2, _ = rel_errors(z[0], oracle.apply(oracle.C2L, X[0], adjoint=adjoint))
     assert e2 <= 1e-13
 
 
