@@ -50,9 +50,6 @@
 
 #include <algorithm>
 #include <array>
-#include <map>
-#include <queue>
-#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -155,17 +152,30 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // if a read finds no earlier writer, or if a block could be rewritten
 // before a reader that needs its earlier value has read it (only a
 // read-modify-write by the writer itself is allowed).
-bool build_ptasks(bool adj, const std::vector<Work>& work, const std::vector<int64_t>& loff,
+bool build_ptasks(bool adj, int Lmax, const std::vector<Work>& work, const std::vector<int64_t>& loff,
                   const std::vector<int>& lkind, int workers, std::vector<PTask>& out) {
-  struct Block {
-    int32_t slot = -1;
-    std::vector<int32_t> writers;                       // items in level order
-    std::vector<std::pair<int32_t, int32_t>> readers;  // (item, need)
+  out.clear();
+  if (Lmax <= 0) return true;  // no levels: only the final stage
+  // row blocks in flat arrays: (array W or C, level d, segment g, member tile)
+  int32_t ntiles = 1;
+  for (const Work& w : work) ntiles = std::max(ntiles, w.tile + 1);
+  const int64_t nsegtot = (int64_t(4) << Lmax) - 4;  // sum over d < Lmax of 2^(Lmax+1-d)
+  const int64_t nblk = 2 * nsegtot * ntiles;
+  if (nblk >= (int64_t(1) << 31)) return false;
+  auto block = [&](int arr, int d, int64_t g, int32_t tile) -> int64_t {
+    if (d < 0 || d >= Lmax || g < 0 || g >= (int64_t(2) << (Lmax - d))) return -1;
+    const int64_t seg = (int64_t(4) << Lmax) - (int64_t(4) << (Lmax - d)) + g;
+    return (int64_t(arr) * nsegtot + seg) * ntiles + tile;
   };
-  std::map<std::tuple<int, int, int64_t, int32_t>, Block> blocks;  // (array, d, seg, tile)
+  std::vector<int32_t> slot(size_t(nblk), -1), nw(size_t(nblk), 0), last(size_t(nblk), -1);
   std::vector<PTask> items;
   std::vector<std::array<int32_t, 2>> pred;
-  out.clear();
+  std::vector<int64_t> wblk_of;                               // block each item writes
+  std::vector<std::array<int64_t, 3>> reads_all;              // (item, block, need)
+  items.reserve(work.size());
+  pred.reserve(work.size());
+  wblk_of.reserve(work.size());
+  reads_all.reserve(2 * work.size());
   for (size_t l = 0; l < lkind.size(); ++l) {
     const int kind = lkind[l];
     if (kind == LC_K_FINAL) continue;  // the final stage is a launch of its own
@@ -175,93 +185,112 @@ bool build_ptasks(bool adj, const std::vector<Work>& work, const std::vector<int
       PTask t{kind, it.d, it.seg, it.tile, {-1, -1}, {0, 0}, -1};
       std::array<int32_t, 2> pr{-1, -1};
       const int64_t v = it.seg;
-      std::vector<std::tuple<int, int, int64_t>> reads;  // (array: 0 W, 1 C; d; seg)
-      std::tuple<int, int, int64_t> wblk{-1, 0, 0};
+      int64_t rb[2] = {-2, -2};  // -2: no read
+      int64_t wb = -1;
       switch (kind) {
-        case LC_K_LEAF: wblk = {0, 0, v}; break;
+        case LC_K_LEAF: wb = block(0, 0, v, it.tile); break;
         case LC_K_UP:
-          reads = {{0, it.d - 1, 2 * v}, {0, it.d - 1, 2 * v + 1}};
-          wblk = {0, it.d, v};
+          rb[0] = block(0, it.d - 1, 2 * v, it.tile);
+          rb[1] = block(0, it.d - 1, 2 * v + 1, it.tile);
+          wb = block(0, it.d, v, it.tile);
           break;
         case LC_K_COUPLE:
           if (adj) {
-            reads.push_back({0, it.d, v - 2});
-            if (v & 1) reads.push_back({0, it.d, v - 3});
+            rb[0] = block(0, it.d, v - 2, it.tile);
+            if (v & 1) rb[1] = block(0, it.d, v - 3, it.tile);
           } else {
-            reads.push_back({0, it.d, v + 2});
-            if ((v & 1) == 0) reads.push_back({0, it.d, v + 3});
+            rb[0] = block(0, it.d, v + 2, it.tile);
+            if ((v & 1) == 0) rb[1] = block(0, it.d, v + 3, it.tile);
           }
-          wblk = {1, it.d, v};
+          wb = block(1, it.d, v, it.tile);
           break;
         case LC_K_DOWN:
-          reads = {{1, it.d + 1, v >> 1}, {1, it.d, v}};
-          wblk = {1, it.d, v};
+          rb[0] = block(1, it.d + 1, v >> 1, it.tile);
+          rb[1] = block(1, it.d, v, it.tile);
+          wb = block(1, it.d, v, it.tile);
           break;
         default:
           return false;
       }
-      for (size_t i = 0; i < reads.size(); ++i) {
-        auto f = blocks.find({std::get<0>(reads[i]), std::get<1>(reads[i]), std::get<2>(reads[i]), it.tile});
-        if (f == blocks.end() || f->second.writers.empty()) return false;
-        t.rd[i] = f->second.slot;
-        t.need[i] = int32_t(f->second.writers.size());
-        pr[i] = f->second.writers.back();
-        f->second.readers.push_back({me, t.need[i]});
+      int32_t own_need = -1;  // the need of this item's read of the block it writes
+      for (int i = 0; i < 2; ++i) {
+        if (rb[i] == -2) continue;
+        if (rb[i] < 0 || nw[size_t(rb[i])] == 0) return false;  // no earlier writer
+        const size_t b = size_t(rb[i]);
+        t.rd[i] = slot[b];
+        t.need[i] = nw[b];
+        pr[i] = last[b];
+        reads_all.push_back({me, rb[i], nw[b]});
+        if (rb[i] == wb) own_need = nw[b];
       }
-      if (std::get<0>(wblk) >= 0) {
-        Block& b = blocks[{std::get<0>(wblk), std::get<1>(wblk), std::get<2>(wblk), it.tile}];
-        if (b.writers.empty()) b.slot = me;
-        b.writers.push_back(me);
-        t.wr = b.slot;
-      }
+      if (wb < 0) return false;
+      const size_t b = size_t(wb);
+      if (nw[b] == 0) slot[b] = me;
+      else if (own_need != nw[b]) return false;  // a rewrite must read the write before it
+      ++nw[b];
+      last[b] = me;
+      t.wr = slot[b];
       items.push_back(t);
       pred.push_back(pr);
+      wblk_of.push_back(wb);
     }
   }
-  for (const auto& kv : blocks) {
-    const Block& b = kv.second;
-    for (const auto& rd : b.readers)
-      if (rd.second < int32_t(b.writers.size()) && b.writers[rd.second] != rd.first) return false;
-    for (size_t j = 1; j < b.writers.size(); ++j) {  // each rewrite waits for the write before it
-      bool chained = false;
-      for (const auto& rd : b.readers) chained |= rd.first == b.writers[j] && rd.second == int32_t(j);
-      if (!chained) return false;
-    }
-  }
+  // a read that needs fewer writes than its block gets must be the next
+  // writer's own read-modify-write
+  for (const auto& r : reads_all)
+    if (r[2] < nw[size_t(r[1])] && wblk_of[size_t(r[0])] != r[1]) return false;
   const int32_t n = int32_t(items.size());
   if (size_t(n) >= (size_t(1) << 29)) return false;
-  // dependants, and the longest chain from each item (level order is topological)
-  std::vector<std::vector<int32_t>> succ(n);
-  std::vector<int32_t> indeg(n, 0), rank(n, 1);
+  // dependants (CSR), and the longest chain from each item (level order is topological)
+  std::vector<int32_t> indeg(size_t(n), 0), rank(size_t(n), 1), sfirst(size_t(n) + 1, 0);
+  auto for_preds = [&](int32_t i, auto&& f) {
+    const int32_t q0 = pred[size_t(i)][0], q1 = pred[size_t(i)][1];
+    if (q0 >= 0) f(q0);
+    if (q1 >= 0 && q1 != q0) f(q1);
+  };
+  for (int32_t i = 0; i < n; ++i) for_preds(i, [&](int32_t q) { ++sfirst[size_t(q) + 1]; });
+  for (int32_t i = 0; i < n; ++i) sfirst[size_t(i) + 1] += sfirst[size_t(i)];
+  const size_t nsucc = size_t(sfirst[size_t(n)]);
+  std::vector<int32_t> succ(nsucc);
+  std::vector<int32_t> fill(sfirst.begin(), sfirst.end() - 1);
   for (int32_t i = 0; i < n; ++i)
-    for (int k = 0; k < 2; ++k) {
-      const int32_t q = pred[i][k];
-      if (q < 0 || (k == 1 && q == pred[i][0])) continue;
-      succ[q].push_back(i);
-      ++indeg[i];
-    }
+    for_preds(i, [&](int32_t q) {
+      succ[size_t(fill[size_t(q)]++)] = i;
+      ++indeg[size_t(i)];
+    });
   for (int32_t i = n - 1; i >= 0; --i)
-    for (int32_t j : succ[i]) rank[i] = std::max(rank[i], rank[j] + 1);
-  // the list schedule: two tickets (parities) per item
+    for (int32_t k = sfirst[size_t(i)]; k < sfirst[size_t(i) + 1]; ++k)
+      rank[size_t(i)] = std::max(rank[size_t(i)], rank[size_t(succ[size_t(k)])] + 1);
+  // the list schedule: two tickets (parities) per item; ready items in
+  // buckets by chain length (first come, first served within a bucket)
   const size_t cap = size_t(std::max(1, workers / 2));
-  auto later = [&](int32_t a, int32_t b) { return rank[a] != rank[b] ? rank[a] < rank[b] : a > b; };
-  std::priority_queue<int32_t, std::vector<int32_t>, decltype(later)> ready(later);
+  int32_t maxrank = 0;
+  for (int32_t r : rank) maxrank = std::max(maxrank, r);
+  std::vector<std::vector<int32_t>> bucket(size_t(maxrank) + 1);
+  std::vector<size_t> head(size_t(maxrank) + 1, 0);
+  int32_t top = 0;  // highest bucket that may hold ready items
+  auto push = [&](int32_t i) {
+    bucket[size_t(rank[size_t(i)])].push_back(i);
+    top = std::max(top, rank[size_t(i)]);
+  };
   for (int32_t i = 0; i < n; ++i)
-    if (indeg[i] == 0) ready.push(i);
+    if (indeg[size_t(i)] == 0) push(i);
   std::vector<int32_t> round, next;
   out.reserve(size_t(n));
-  while (!ready.empty()) {
+  for (;;) {
     round.clear();
-    while (!ready.empty() && round.size() < cap) {
-      round.push_back(ready.top());
-      ready.pop();
+    while (round.size() < cap && top > 0) {
+      const size_t r = size_t(top);
+      if (head[r] < bucket[r].size()) round.push_back(bucket[r][head[r]++]);
+      else --top;
     }
+    if (round.empty()) break;
     for (int32_t i : round) {
-      out.push_back(items[i]);
-      for (int32_t j : succ[i])
-        if (--indeg[j] == 0) next.push_back(j);
+      out.push_back(items[size_t(i)]);
+      for (int32_t k = sfirst[size_t(i)]; k < sfirst[size_t(i) + 1]; ++k)
+        if (--indeg[size_t(succ[size_t(k)])] == 0) next.push_back(succ[size_t(k)]);
     }
-    for (int32_t j : next) ready.push(j);
+    for (int32_t j : next) push(j);
     next.clear();
   }
   return out.size() == size_t(n);
@@ -270,7 +299,16 @@ bool build_ptasks(bool adj, const std::vector<Work>& work, const std::vector<int
 // Build all host tables and the byte layout of the split region.
 // `workers`: CTAs of the persistent launch (its ticket order is scheduled
 // for them; the layout does not depend on it).
-void build_host(const lc_plan_s* p, SplitHost& h, int workers) {
+// Items of Steps 1-4 in a work list (the tasks of the persistent schedule).
+size_t stage_items(const std::vector<int64_t>& loff, const std::vector<int>& lkind) {
+  size_t c = 0;
+  for (size_t l = 0; l < lkind.size(); ++l)
+    if (lkind[l] != LC_K_FINAL) c += size_t(loff[l + 1] - loff[l]);
+  return c;
+}
+
+// schedule = false builds only what the byte layout needs (no task graph).
+void build_host(const lc_plan_s* p, SplitHost& h, int workers, bool schedule) {
   h.S = p->opt.slices;
   h.s = p->g.s;
   h.Lmax = p->g.L;
@@ -305,10 +343,12 @@ void build_host(const lc_plan_s* p, SplitHost& h, int workers) {
   };
   h.nstrips = (h.Nmax + 2 * h.s - 1) / (2 * h.s);
   h.cntN.assign(h.nstrips, 0);
-  for (int64_t t = 0; t < h.nstrips; ++t) {
-    int64_t c = 0;
-    while (c < h.count && h.len_sorted[c] > 2 * int64_t(h.s) * t) ++c;
-    h.cntN[t] = c;
+  {  // members longer than 2 s t: a prefix of the descending order, shrinking with t
+    int64_t c = h.count;
+    for (int64_t t = 0; t < h.nstrips; ++t) {
+      while (c > 0 && h.len_sorted[c - 1] <= 2 * int64_t(h.s) * t) --c;
+      h.cntN[t] = c;
+    }
   }
   // row bases: per d, per g < 2^(Lmax+1-d): 2 x cnt(d, g) rows (sigma-major)
   h.rowbase.clear();
@@ -379,8 +419,9 @@ void build_host(const lc_plan_s* p, SplitHost& h, int workers) {
   }
   for (int64_t t = 0; t < h.nstrips; ++t) aadd(0, t, h.cntN[t]);
   aclose(LC_K_FINAL);
-  h.persist = build_ptasks(false, h.work, h.launch_off, h.launch_kind, workers, h.ptask) &&
-              build_ptasks(true, h.awork, h.alaunch_off, h.alaunch_kind, workers, h.aptask);
+  h.persist = schedule && build_ptasks(false, h.Lmax, h.work, h.launch_off, h.launch_kind, workers, h.ptask) &&
+              build_ptasks(true, h.Lmax, h.awork, h.alaunch_off, h.alaunch_kind, workers, h.aptask);
+  const size_t nfwd = stage_items(h.launch_off, h.launch_kind), nadj = stage_items(h.alaunch_off, h.alaunch_kind);
 
   // Y tables
   const int s = h.s;
@@ -420,9 +461,9 @@ void build_host(const lc_plan_s* p, SplitHost& h, int workers) {
   h.off_rowbase = take(h.rowbase.size() * 8);
   h.off_work = take(h.work.size() * sizeof(Work));
   h.off_awork = take(h.awork.size() * sizeof(Work));
-  h.off_ptask = take(h.ptask.size() * sizeof(PTask));
-  h.off_aptask = take(h.aptask.size() * sizeof(PTask));
-  h.off_sched = take((4 + 2 * std::max(h.ptask.size(), h.aptask.size())) * sizeof(int));
+  h.off_ptask = take(nfwd * sizeof(PTask));
+  h.off_aptask = take(nadj * sizeof(PTask));
+  h.off_sched = take((4 + 2 * std::max(nfwd, nadj)) * sizeof(int));
   h.off_W = take(size_t(h.rows) * LC_M * 8);
   h.off_We = take(size_t(h.rows) * 4);
   h.off_C = take(size_t(h.rows) * LC_M * 8);
@@ -1438,7 +1479,7 @@ size_t persist_smem(const SplitHost& h) {
 
 size_t lc_split_bytes(const lc_plan_s* p) {
   SplitHost h;
-  build_host(p, h, 2);
+  build_host(p, h, 2, false);
   return h.total;
 }
 
@@ -1449,7 +1490,7 @@ lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st)
   LC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   SplitHost* h = new (std::nothrow) SplitHost;
   if (!h) return LC_ERR_HOST_ALLOC;
-  build_host(p, *h, 2 * sms);
+  build_host(p, *h, 2 * sms, true);
   if (h->total > bytes) {
     delete h;
     return LC_ERR_WORKSPACE_TOO_SMALL;
@@ -1517,7 +1558,8 @@ void lc_split_release(lc_plan p) {
 int lc_exec_split_launches(const lc_plan_s* p) {
   const SplitHost* h = static_cast<const SplitHost*>(p->ragged_dev);
   if (!h) return 0;
-  return lc_split_persistent(p) ? 2 : int(h->launch_kind.size());
+  if (!lc_split_persistent(p)) return int(h->launch_kind.size());
+  return (h->ptask.empty() ? 0 : 1) + 1;  // the persistent launch (if there are levels) and the final one
 }
 
 bool lc_split_persistent(const lc_plan_s* p) {
