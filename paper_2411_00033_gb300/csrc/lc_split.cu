@@ -665,15 +665,14 @@ struct Dev {
   int64_t inner, iob, oob;  // two-level batches (lc_layout)
 };
 
+// Lcount in shared memory, loaded by every stage kernel at its start
+// (ctx_begin): the member counts every task looks up first.
+constexpr int kMaxLcount = 64;
+__shared__ int64_t s_lcount[kMaxLcount];
 __device__ __forceinline__ int64_t dcnt(const Dev& D, int d, int64_t g) {
-  int lg = 0;
-  int64_t gg = g;
-  while (gg >= 2) {
-    gg >>= 1;
-    ++lg;
-  }
+  const int lg = g >= 2 ? 63 - __clzll(g) : 0;  // floor(log2 g)
   const int th = d + (lg > 1 ? lg : 1);
-  return th <= D.Lmax + 1 ? D.Lcount[th] : 0;
+  return th <= D.Lmax + 1 ? s_lcount[th] : 0;
 }
 __device__ __forceinline__ int64_t drow(const Dev& D, int d, int64_t g, int sigma, int64_t r) {
   const int64_t db = (int64_t(4) << D.Lmax) - (int64_t(4) << (D.Lmax - d));  // sum_{d'<d} 2^(Lmax+1-d')
@@ -863,7 +862,8 @@ struct Ctx {
   TcState tc;
   uint32_t ycount;
 };
-__device__ __forceinline__ Ctx ctx_begin(CtaShared& sh) {
+__device__ __forceinline__ Ctx ctx_begin(const Dev& D, CtaShared& sh) {
+  for (int i = threadIdx.x; i <= D.Lmax + 1; i += blockDim.x) s_lcount[i] = D.Lcount[i];
   if (threadIdx.x == 0) {
     lc_mbar_init(lc_smem_u32(&sh.mbar_y));
     lc_mbar_init(lc_smem_u32(&sh.mbar_mma));
@@ -1255,7 +1255,7 @@ template <int KIND>
 __device__ __forceinline__ void level_task(const Dev& D, int64_t w0) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   __shared__ __align__(16) CtaShared sh;
-  Ctx c = ctx_begin(sh);
+  Ctx c = ctx_begin(D, sh);
   const Work it = D.work[w0 + (blockIdx.x >> 1)];
   const int sigma = int(blockIdx.x & 1);
   const bool ok = KIND == LC_K_FINAL ? s_final(D, it, sigma, sm_raw, c)
@@ -1266,14 +1266,16 @@ __device__ __forceinline__ void level_task(const Dev& D, int64_t w0) {
 __global__ void __launch_bounds__(kThreads) k_s_leaf(Dev D, int64_t w0) { level_task<LC_K_LEAF>(D, w0); }
 __global__ void __launch_bounds__(kThreads) k_s_up(Dev D, int64_t w0) { level_task<LC_K_UP>(D, w0); }
 __global__ void __launch_bounds__(kThreads) k_s_couple(Dev D, int64_t w0) { level_task<LC_K_COUPLE>(D, w0); }
-__global__ void __launch_bounds__(kThreads) k_s_down(Dev D, int64_t w0) { level_task<LC_K_DOWN>(D, w0); }
+// (three CTAs of the down stage fit an SM by shared memory: keep their registers to a third)
+__global__ void __launch_bounds__(kThreads, 3) k_s_down(Dev D, int64_t w0) { level_task<LC_K_DOWN>(D, w0); }
 __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) { level_task<LC_K_FINAL>(D, w0); }
 
 // Steps 1-4 of an execution in one persistent launch.  Each CTA takes TMEM
 // once, before its first task, then draws tickets (task = ticket / 2,
 // parity = ticket % 2) from a global counter until they run out, always one
 // ticket ahead (the next one is drawn while the current task runs, so the
-// atomic's latency is hidden).  A task waits only for blocks written by
+// atomic's and the task load's latency are hidden, by a thread other than
+// the one that issues the copies and MMAs).  A task waits only for blocks written by
 // tasks of smaller tickets; the smallest unfinished ticket is always the
 // current task of the CTA holding it, and its inputs are complete, so the
 // launch finishes whatever the number of resident CTAs.  After the task's
@@ -1289,14 +1291,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_s_persist(Dev D, const PTask* _
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   __shared__ __align__(16) CtaShared sh;
   __shared__ int tk[2];
-  if (threadIdx.x == 0) tk[0] = draw(D, ntickets);
-  Ctx c = ctx_begin(sh);
+  __shared__ PTask ptk[2];
+  if (threadIdx.x == 0) {
+    tk[0] = draw(D, ntickets);
+    if (tk[0] < ntickets) ptk[0] = tasks[tk[0] >> 1];
+  }
+  Ctx c = ctx_begin(D, sh);
   tc_acquire(c.tc);
   for (int it = 0;; ++it) {
     const int t = tk[it & 1];
     if (t >= ntickets) break;
-    if (threadIdx.x == 0) tk[(it + 1) & 1] = draw(D, ntickets);  // read after the barrier below
-    const PTask pt = tasks[t >> 1];
+    if (threadIdx.x == 64) {  // the next ticket and its task, off thread 0's path; read after the barrier below
+      const int tn = draw(D, ntickets);
+      tk[(it + 1) & 1] = tn;
+      if (tn < ntickets) ptk[(it + 1) & 1] = tasks[tn >> 1];
+    }
+    const PTask pt = ptk[it & 1];
     const bool ok = s_stage(D, pt.kind, Work{pt.d, pt.seg, pt.tile}, t & 1, sm_raw, c, &pt);
     __syncthreads();  // the task's stores are issued; the next ticket is visible
     if (threadIdx.x == 32) {
@@ -1485,6 +1495,7 @@ size_t lc_split_bytes(const lc_plan_s* p) {
 
 lc_status lc_split_prepare(lc_plan p, char* base, size_t bytes, cudaStream_t st) {
   if (p->g.s > 32) return LC_ERR_UNSUPPORTED;  // K tiles sized for s <= 32
+  if (p->g.L + 2 > kMaxLcount) return LC_ERR_UNSUPPORTED;
   int dev = 0, sms = 0;
   LC_CUDA_TRY(cudaGetDevice(&dev));
   LC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
