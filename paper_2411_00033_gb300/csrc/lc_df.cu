@@ -143,6 +143,7 @@ lc_status lc_exec_df(lc_plan p, const void* in, void* out, const lc_layout& lay,
   a.batch = p->batch; a.dir = int(p->dir);
   a.two_alpha = p->geg.two_alpha;
   a.nodal = 0;
+  a.trigger = 0;
   a.t = lc_tables<lc_df>{static_cast<const lc_df*>(p->df_lam), static_cast<const lc_df*>(p->df_lam2),
                          static_cast<const lc_df*>(p->df_T), static_cast<const lc_df*>(p->df_B),
                          static_cast<const lc_df*>(p->df_Ahat), static_cast<lc_df*>(p->df_W),

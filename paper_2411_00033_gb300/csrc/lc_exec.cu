@@ -23,6 +23,7 @@ lc_status lc_exec_cuda_cores(lc_plan p, const void* in, void* out, const lc_layo
     a.inner = lay.inner; a.iob = lay.iob; a.oob = lay.oob;
     a.n = p->g.n; a.N = p->g.N; a.L = p->g.L; a.s = p->g.s; a.nseg = p->g.nseg;
     a.batch = p->batch; a.dir = int(p->dir); a.two_alpha = p->geg.two_alpha; a.nodal = p->opt.nodal;
+    a.trigger = 0;
     a.t = lc_tables<double>{p->lam, p->lam2, p->T, p->B, p->Ahat, p->W, p->Cc, p->err, p->opt.debug_flags};
     a.xe = a.xe_part = nullptr;
     a.xe_cnt = nullptr;
@@ -35,6 +36,7 @@ lc_status lc_exec_cuda_cores(lc_plan p, const void* in, void* out, const lc_layo
     a.inner = lay.inner; a.iob = lay.iob; a.oob = lay.oob;
     a.n = p->g.n; a.N = p->g.N; a.L = p->g.L; a.s = p->g.s; a.nseg = p->g.nseg;
     a.batch = p->batch; a.dir = int(p->dir); a.two_alpha = p->geg.two_alpha; a.nodal = p->opt.nodal;
+    a.trigger = 0;
     a.t = lc_tables<float>{p->lamf, p->lam2f, p->Tf, p->Bf, p->Ahatf, p->Wf, p->Ccf, p->err, p->opt.debug_flags};
     a.xe = a.xe_part = nullptr;
     a.xe_cnt = nullptr;

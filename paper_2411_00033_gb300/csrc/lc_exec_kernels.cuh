@@ -70,7 +70,20 @@ struct Args {
   // Nodal variant (eq:AijLag): t.B holds the dense level maps P(0), P(1)
   // ([2][M][M]) instead of the triangular B(0).
   int nodal;
+  // 1: let the next kernel of the stream start early (programmatic
+  // dependent launch; set for the small grids of the coarse chain).
+  int trigger;
 };
+
+// Programmatic dependent launch.  A kernel launched with the attribute may
+// be scheduled while its predecessor in the stream is still running;
+// lc_grid_wait() returns once the predecessor has completed and its memory
+// is visible, so every kernel calls it before it reads or writes data other
+// kernels share (plan tables only before).  lc_grid_trigger() lets the
+// successor be scheduled once every CTA of this grid has called it or
+// exited.  Both are no-ops without the attribute.
+__device__ __forceinline__ void lc_grid_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void lc_grid_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
 template <typename R>
 __device__ __forceinline__ R cinv(int64_t i) {
@@ -241,12 +254,14 @@ __global__ void __launch_bounds__(kThreads) k_up_chunk(Args<R> a, int rho, int d
   const int gb = rho + depth;
   const int nb = 1 << depth;
   const int nB = a.nodal ? 2 : 1;
+  if (a.trigger) lc_grid_trigger();
   for (int i = threadIdx.x; i < nB * LC_M * LC_M; i += blockDim.x) {
     const int r = i % (LC_M * LC_M);
     (i < LC_M * LC_M ? Bt : Bt1)[(r % LC_M) * LC_M + r / LC_M] = a.t.B[i];
   }
   if (leaf)
     for (int i = threadIdx.x; i < 2 * s * LC_M; i += blockDim.x) Ts[i] = a.t.T[i];
+  lc_grid_wait();  // (the plan tables above are constant)
   for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
     R* Wb = a.t.W + b * a.nseg * kSeg;
     __syncthreads();
@@ -443,7 +458,9 @@ __global__ void __launch_bounds__(kThreads) k_couple_blocks(Args<R> a, int adj, 
   const int64_t nblk = (int64_t(2) << gamma) - 1;  // b_gamma
   const int64_t b0 = first * kCBlocks;
   const int nb = int(nblk - b0 < kCBlocks ? nblk - b0 : kCBlocks);
+  if (a.trigger) lc_grid_trigger();
   if (nb <= 0) return;
+  lc_grid_wait();
   const int64_t m0 = lc_ahat_offset(gamma) + 3 * b0;
   const uint32_t bytesA = uint32_t(3 * nb * mat);
   const uint32_t bytesW = uint32_t(2 * nb * kSeg * sizeof(R));
@@ -914,12 +931,14 @@ __global__ void __launch_bounds__(kThreads, fuse ? 5 : 6) k_down_chunk(Args<R> a
   // B(1): B(0) with odd diagonals negated; nodal: the second level map P(1)
   __shared__ R Bs1[LC_M * LC_M];
   constexpr int U = fuse ? 1 : 4;
+  if (a.trigger) lc_grid_trigger();
   stage<U>(LC_M * LC_M, [&](int i) { return a.t.B[i]; }, [&](int i, R v) {
     Bs[i] = v;
     if (!a.nodal) Bs1[i] = ((i / LC_M - i % LC_M) & 1) ? negate(v) : v;
   });
   if (a.nodal) stage<U>(LC_M * LC_M, [&](int i) { return a.t.B[LC_M * LC_M + i]; }, [&](int i, R v) { Bs1[i] = v; });
   if (fin) stage<U>(2 * s * LC_M, [&](int i) { return a.t.T[i]; }, [&](int i, R v) { Ts[i] = v; });
+  lc_grid_wait();  // (the plan tables above are constant)
   for (int64_t b = blockIdx.y; b < a.batch; b += gridDim.y) {
     R* Cb = a.t.Cc + b * a.nseg * kSeg;
     {
@@ -1194,6 +1213,8 @@ __global__ void __launch_bounds__(256) k_vec_exponent(const IO* __restrict__ in,
                                                       int* __restrict__ xe, int* part, unsigned* cnt) {
   __shared__ int red[8];
   __shared__ int last;
+  lc_grid_trigger();  // the leaf restriction may be scheduled meanwhile (it waits for this grid)
+  lc_grid_wait();
   const int64_t j0 = int64_t(blockIdx.x) * kExpChunk;
   for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
     const IO* f = in + lc_boff(b, ib, inner, iob);
@@ -1344,6 +1365,24 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
   cudaStream_t sf = overlap ? p->fine : st;    // far-field chain
   cudaStream_t sn = overlap ? p->nearst : st;  // band
   cudaStream_t sk = coarse_side ? p->side : st;  // coarse chain
+  // Consecutive kernels of one stream with programmatic dependent launch
+  // (never in per-kernel timing mode, whose events sit between kernels).
+  auto launch = [&](bool pdl, cudaStream_t stm, dim3 grid, size_t sm, auto kern, auto... args) -> lc_status {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = stm;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = (pdl && streams) ? 1 : 0;
+    LC_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, args...));
+    return LC_OK;
+  };
+  Args<R> ac = a;  // the coarse chain's kernels let their successors start early
+  ac.trigger = 1;
   if (overlap) {
     LC_CUDA_TRY(cudaEventRecord(p->ev_start, st));
     LC_CUDA_TRY(cudaStreamWaitEvent(sf, p->ev_start, 0));
@@ -1375,8 +1414,9 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
     lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_up_chunk<R>), sm);
     if (e != LC_OK) return e;
     lc_timer_mark(p, st, LC_K_LEAF);
-    k_up_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sf>>>(a, rho, depth, 1, adjoint);
-    LC_LAUNCH_CHECK();
+    e = launch(a.xe != nullptr, sf, dim3(unsigned(int64_t(4) << rho), gy), sm, k_up_chunk<R>, a, rho, depth, 1,
+               adjoint);  // after the exponent pre-pass on the same stream
+    if (e != LC_OK) return e;
   }
   if (!fused) {
     if (band_late) {  // the band starts once the first up chunk is done
@@ -1398,12 +1438,13 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
       lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_up_chunk<R>), sm);
       if (e != LC_OK) return e;
       lc_timer_mark(p, st, LC_K_UP);
-      k_up_chunk<R><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sk>>>(a, rho, depth, 0, adjoint);
-      LC_LAUNCH_CHECK();
+      e = launch(c > 1, sk, dim3(unsigned(int64_t(4) << rho), gy), sm, k_up_chunk<R>, ac, rho, depth, 0, adjoint);
+      if (e != LC_OK) return e;
     }
     lc_timer_mark(p, st, LC_K_COUPLE);  // coupling of the coarse levels
-    k_couple_blocks<R><<<dim3(unsigned(couple_ctas<R>(0, roots[0])), gy), kThreads, smc, sk>>>(a, adjoint, 0, roots[0]);
-    LC_LAUNCH_CHECK();
+    lc_status e = launch(nr > 1, sk, dim3(unsigned(couple_ctas<R>(0, roots[0])), gy), smc, k_couple_blocks<R>, ac,
+                         adjoint, 0, roots[0]);
+    if (e != LC_OK) return e;
     for (int c = nr - 1; c >= 1; --c) {  // coarse down chunks: levels [roots[c], roots[c-1] - 1]
       const int rho = roots[c];
       const int depth = roots[c - 1] - 1 - rho;
@@ -1411,8 +1452,9 @@ lc_status run(lc_plan_s* p, Args<R> a, cudaStream_t st, int adjoint) {
       lc_status e = set_smem<R>(reinterpret_cast<const void*>(k_down_chunk<R, false>), sm);
       if (e != LC_OK) return e;
       lc_timer_mark(p, st, LC_K_DOWN);
-      k_down_chunk<R, false><<<dim3(unsigned(int64_t(4) << rho), gy), kThreads, sm, sk>>>(a, rho, depth, 0, adjoint);
-      LC_LAUNCH_CHECK();
+      e = launch(true, sk, dim3(unsigned(int64_t(4) << rho), gy), sm, k_down_chunk<R, false>, ac, rho, depth, 0,
+                 adjoint);
+      if (e != LC_OK) return e;
     }
     if (coarse_side) LC_CUDA_TRY(cudaEventRecord(p->ev_join, sk));
   }
