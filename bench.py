@@ -692,6 +692,12 @@ def run_ours(args):
     _, _, stages = time_tier(pl, args.steps, 2, stage_timing=True)
     ms_per_step, value = replica_throughput(sum(ms) / len(ms), 2 * n, dev)
 
+    # one transform at a time on the plan's own streams (the latency a caller
+    # with a single vector sees), cold L2, median
+    one_ms = {}
+    for d, p1, z1 in (("l2c", pl[0], outs[0]), ("c2l", pl[1], outs[1])):
+        one_ms[d] = time_fn(lambda: p1(x, out=z1), flush, max(10, min(50, args.steps)), 3)
+
     # per-tier numbers (median of a shorter run each)
     tier_vals = {}
     for t, p2 in tiers.items():
@@ -951,6 +957,7 @@ def run_ours(args):
         "plan_ms": plan_ms,
         "stage_ms_per_step": {KIND_NAMES[k]: v / args.steps for k, v in sorted(totals.items())},
         "ms_per_step_warm_l2": sum(ms_warm) / len(ms_warm),
+        "one_transform_ms": one_ms,
         "coefficients_per_s_warm_l2": 2 * n / (sum(ms_warm) / len(ms_warm) / 1e3),
         "hbm_step": hbm_step,
         "roofline": roofline,
