@@ -75,15 +75,6 @@ struct Args {
   int trigger;
 };
 
-// Programmatic dependent launch.  A kernel launched with the attribute may
-// be scheduled while its predecessor in the stream is still running;
-// lc_grid_wait() returns once the predecessor has completed and its memory
-// is visible, so every kernel calls it before it reads or writes data other
-// kernels share (plan tables only before).  lc_grid_trigger() lets the
-// successor be scheduled once every CTA of this grid has called it or
-// exited.  Both are no-ops without the attribute.
-__device__ __forceinline__ void lc_grid_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-__device__ __forceinline__ void lc_grid_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
 template <typename R>
 __device__ __forceinline__ R cinv(int64_t i) {

@@ -219,6 +219,17 @@ inline void lc_timer_end(lc_plan_s* p, cudaStream_t st) {
   ++m;
 }
 
+// ---- programmatic dependent launch -------------------------------------------
+// A kernel launched with cudaLaunchAttributeProgrammaticStreamSerialization
+// may be scheduled while its predecessor in the stream is still running;
+// lc_grid_wait() returns once the predecessor has completed and its memory
+// is visible, so such a kernel calls it before it reads or writes data other
+// kernels share (plan tables and the caller's input only before).
+// lc_grid_trigger() lets the successor be scheduled once every CTA of this
+// grid has called it or exited.  Both are no-ops without the attribute.
+__device__ __forceinline__ void lc_grid_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void lc_grid_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // ---- error helpers ---------------------------------------------------------
 #define LC_CUDA_TRY(expr)                        \
   do {                                           \
