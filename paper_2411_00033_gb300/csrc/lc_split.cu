@@ -1273,12 +1273,12 @@ __global__ void __launch_bounds__(kThreads) k_s_final(Dev D, int64_t w0) { level
 // Steps 1-4 of an execution in one persistent launch.  Each CTA takes TMEM
 // once, before its first task, then draws tickets (task = ticket / 2,
 // parity = ticket % 2) from a global counter until they run out, always one
-// ticket ahead (the next one is drawn while the current task runs, so the
-// atomic's and the task load's latency are hidden, by a thread other than
-// the one that issues the copies and MMAs).  A task waits only for blocks written by
-// tasks of smaller tickets; the smallest unfinished ticket is always the
-// current task of the CTA holding it, and its inputs are complete, so the
-// launch finishes whatever the number of resident CTAs.  After the task's
+// ticket ahead: thread 64 draws the next ticket and loads its task while the
+// current task runs, off the path of thread 0, which issues the copies and
+// MMAs.  A task waits only for blocks written by tasks of smaller tickets;
+// the smallest unfinished ticket is always the current task of the CTA
+// holding it, and its inputs are complete, so the launch finishes whatever
+// the number of resident CTAs.  After the task's
 // stores, thread 32 publishes its block (a release increment of its counter)
 // while thread 0 starts the next task's copies.  A failed wait sets the abort
 // word: every CTA then stops drawing tickets and every waiter gives up, and
