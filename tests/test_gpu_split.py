@@ -295,3 +295,21 @@ def test_split_schedule_other_tiers_unsupported(lc):
     plan = lc.Plan(1000, "l2c", 2, "f64_df", dev)
     with pytest.raises(lc.LegChebError):
         plan.set_split_schedule(True)
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_persistent_repeated_executions_see_only_their_own_data(lc, adjoint):
+    # the intermediate rows of an execution are rewritten in place by the next
+    # one: a second execution on new data must match a fresh plan bit for bit
+    lengths = [64, 300, 1025, 5000, 9000] + list(workloads.ragged_lengths(200, 64, 20000, seed=41))
+    dev = torch.device("cuda", 0)
+    xa = torch.as_tensor(workloads.ragged_batch(lengths, seed=42), device=dev)
+    xb = torch.as_tensor(workloads.ragged_batch(lengths, seed=43), device=dev)
+    used = lc.Plan(direction="c2l", dtype="f64_split", device=dev, lengths=lengths)
+    used.execute(xa, adjoint=adjoint)
+    zb = used.execute(xb, adjoint=adjoint).cpu().numpy()
+    fresh = lc.Plan(direction="c2l", dtype="f64_split", device=dev, lengths=lengths)
+    zf = fresh.execute(xb, adjoint=adjoint).cpu().numpy()
+    used.check()
+    fresh.check()
+    assert np.array_equal(zb, zf)
